@@ -1,0 +1,373 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: a dense
+textbook computation (numpy/LAPACK), a closed form, an invariant, or a
+hand-derived special case.  Citations are to the paper's sections/algorithms.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    d = synth.generate(synth.tiny())
+    dense = oracle.dense_system(d)
+    return d, dense
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def test_default_options_follow_paper():
+    """delta^a = 1e-50 and m = m_A = m_S = n_max = 200 (Sec. 3.1, last paragraphs)."""
+    with open(os.path.join(GOLDEN, "paper_solver_settings.json")) as f:
+        g = json.load(f)
+    o = oracle.default_options()
+    assert o.atol == g["delta_a"]
+    assert o.m == o.m_A == o.m_S == g["m"]
+    assert o.nmax == o.nmax_A == o.nmax_S == g["n_max"]
+
+
+def test_apply_blocks_match_dense(tiny):
+    """A = A_sp + sum_k r_k a^k a^kT (Sec. 2.5, K term) and the full block product."""
+    d, (A, B, C, D, F) = tiny
+    o = oracle.Oracle(d)
+    rng = np.random.default_rng(1)
+    x = rng.standard_normal(4 * d["n_nodes"])
+    nv = 3 * d["n_nodes"]
+    assert _rel(o.apply_A(x[:nv]), A @ x[:nv]) < 1e-14
+    assert _rel(o.apply_B(x[nv:]), B @ x[nv:]) < 1e-14
+    assert _rel(o.apply_C(x[:nv]), C @ x[:nv]) < 1e-14
+    assert _rel(o.apply_D(x[nv:]), D @ x[nv:]) < 1e-14
+    assert _rel(o.apply_full(x), F @ x) < 1e-14
+
+
+def test_diag_A_includes_rank_one_terms(tiny):
+    d, (A, B, C, D, F) = tiny
+    o = oracle.Oracle(d)
+    assert np.allclose(o.diag_A(), np.diag(A), rtol=1e-15, atol=0)
+
+
+def test_nested_solve_matches_dense_lu(tiny):
+    """x = A^{-1} b: FGMRES + P_SCR (Sec. 3, Algorithm 3) against LAPACK LU."""
+    d, (A, B, C, D, F) = tiny
+    o = oracle.Oracle(d)
+    o.setup()
+    x, info, rc = o.solve(d["b"])
+    assert rc == 0
+    x_lu = np.linalg.solve(F, d["b"])
+    assert np.linalg.norm(d["b"] - F @ x) / np.linalg.norm(d["b"]) <= 1e-8
+    assert info.rel_res_true <= 1e-8
+    assert _rel(x, x_lu) <= 1e-6
+    assert 1 <= info.outer_iters <= 20
+    # tighter outer tolerance drives the error further down
+    o.set_options(rtol=1e-12)
+    x2, info2, rc2 = o.solve(d["b"])
+    assert rc2 == 0 and _rel(x2, x_lu) <= 1e-9
+
+
+def test_exact_inner_solves_give_one_outer_iteration(tiny):
+    """With exact A^{-1} and S^{-1}, Algorithm 3 is the exact inverse of the
+    block LDU factorisation (Sec. 3.1), so FGMRES stops after one iteration."""
+    d, _ = tiny
+    o = oracle.Oracle(d, rtol_A=1e-13, rtol_S=1e-13, rtol_I=1e-13)
+    o.setup()
+    x, info, rc = o.solve(d["b"])
+    assert rc == 0 and info.outer_iters == 1
+
+
+def test_block_triangular_preconditioner_gives_two_iterations(tiny):
+    """P = [[A, B], [0, S]] gives A P^{-1} = [[I, 0], [C A^{-1}, I]] (from the
+    block LDU factorisation, Sec. 3.1): (A P^{-1} - I)^2 = 0, so GMRES needs
+    exactly two iterations with exact inner solves."""
+    d, (A, B, C, D, F) = tiny
+    o = oracle.Oracle(d, rtol_A=1e-13, rtol_S=1e-13, rtol_I=1e-13, variant=1)
+    o.setup()
+    x, info, rc = o.solve(d["b"])
+    assert rc == 0 and info.outer_iters == 2
+    # the closed form itself, densely
+    S = D - C @ np.linalg.solve(A, B)
+    N = d["n_nodes"]
+    P = np.block([[A, B], [np.zeros((N, 3 * N)), S]])
+    E = F @ np.linalg.inv(P) - np.eye(4 * N)
+    assert np.abs(E @ E).max() <= 1e-9 * max(1.0, np.abs(E).max())
+
+
+def test_matrix_free_schur_matches_dense(tiny):
+    """Algorithm 2 with an exact inner solve equals (D - C A^{-1} B) x."""
+    d, (A, B, C, D, F) = tiny
+    o = oracle.Oracle(d, rtol_I=1e-14)
+    o.setup()
+    S = D - C @ np.linalg.solve(A, B)
+    rng = np.random.default_rng(2)
+    for _ in range(3):
+        xp = rng.standard_normal(d["n_nodes"])
+        assert _rel(o.apply_S(xp), S @ xp) <= 1e-10
+
+
+def test_pscr_with_exact_solves_is_inverse(tiny):
+    """Algorithm 3 with exact intermediate/inner solves returns A^{-1} s."""
+    d, (A, B, C, D, F) = tiny
+    o = oracle.Oracle(d, rtol_A=1e-14, rtol_S=1e-14, rtol_I=1e-14)
+    o.setup()
+    s = np.random.default_rng(3).standard_normal(4 * d["n_nodes"])
+    y = o.apply_pscr(s)
+    assert _rel(F @ y, s) <= 1e-9
+
+
+def test_shat_matches_dense_formula(tiny):
+    """S_hat = D - C diag(A)^{-1} B with the scalar diagonal of A (Sec. 3.1)."""
+    d, (A, B, C, D, F) = tiny
+    o = oracle.Oracle(d)
+    o.setup()
+    rp, ci, v = o.shat()
+    N = d["n_nodes"]
+    Sh = oracle.dense_block(rp, ci, v, 1, 1, N, N)
+    ref = D - C @ np.diag(1.0 / np.diag(A)) @ B
+    assert np.abs(Sh - ref).max() <= 1e-13 * np.abs(ref).max()
+    # pattern: sorted rows, distance-2 graph of the node pattern
+    for i in range(N):
+        assert np.all(np.diff(ci[rp[i]:rp[i + 1]]) > 0)
+
+
+def _path(n, w=1.0):
+    rp, ci, v = [0], [], []
+    for i in range(n):
+        for j in (i - 1, i, i + 1):
+            if 0 <= j < n:
+                ci.append(j)
+                v.append(2.0 if i == j else -w)
+        rp.append(len(ci))
+    return np.array(rp, np.int32), np.array(ci, np.int32), np.array(v)
+
+
+def test_aggregation_path_graph_closed_form():
+    """Handshake matching on a uniform path: pass 1 pairs (0,1),(2,3),...
+    (ties go to the smaller index), three passes give blocks of 8 consecutive
+    nodes (golden fixture written by hand from the matching rule)."""
+    with open(os.path.join(GOLDEN, "aggregation_path16.json")) as f:
+        g = json.load(f)
+    rp, ci, v = _path(16)
+    nc, agg = oracle.aggregate(rp, ci, v, 1, 0.0064)
+    assert nc == g["n_aggregates"]
+    assert agg.tolist() == g["agg"]
+
+
+def test_aggregation_isolated_and_weak():
+    # diagonal matrix: every node isolated -> no aggregate
+    n = 10
+    rp = np.arange(n + 1, dtype=np.int32)
+    ci = np.arange(n, dtype=np.int32)
+    nc, agg = oracle.aggregate(rp, ci, np.ones(n), 1, 0.0064)
+    assert nc == 0 and np.all(agg == -1)
+    # weak couplings: sigma = w^2 / (2*2) = 0.0025 < theta -> isolated
+    rp, ci, v = _path(8, w=0.1)
+    nc, agg = oracle.aggregate(rp, ci, v, 1, 0.0064)
+    assert nc == 0
+    # strong couplings, then one decoupled node in the middle
+    rp, ci, v = _path(8)
+    v = v.copy()
+    for i in (3, 4):
+        for e in range(rp[i], rp[i + 1]):
+            if (i == 3 and ci[e] == 4) or (i == 4 and ci[e] == 3):
+                v[e] = 0.0
+    nc, agg = oracle.aggregate(rp, ci, v, 1, 0.0064)
+    assert set(agg[:4]) == {0} and set(agg[4:]) == {1}
+
+
+def test_aggregation_invariants_on_tangent(tiny):
+    d, _ = tiny
+    o = oracle.Oracle(d)
+    o.setup()
+    for which in (0, 1):
+        levels = o.amg_levels(which)
+        for l in levels[:-1]:
+            agg = l["agg"]
+            nc = len(levels[levels.index(l) + 1]["rowptr"]) - 1
+            used = agg[agg >= 0]
+            sizes = np.bincount(used, minlength=nc)
+            assert sizes.min() >= 1 and sizes.max() <= 8
+            # numbering by smallest member
+            first = np.array([np.min(np.nonzero(agg == I)[0]) for I in range(nc)])
+            assert np.all(np.diff(first) > 0)
+
+
+def test_galerkin_matches_dense_triple_product(tiny):
+    d, _ = tiny
+    o = oracle.Oracle(d)
+    o.setup()
+    for which, bs in ((0, 3), (1, 1)):
+        L = o.amg_levels(which)
+        n0 = len(L[0]["rowptr"]) - 1
+        n1 = len(L[1]["rowptr"]) - 1
+        A0 = oracle.dense_block(L[0]["rowptr"], L[0]["col"], L[0]["val"], bs, bs, n0, n0)
+        A1 = oracle.dense_block(L[1]["rowptr"], L[1]["col"], L[1]["val"], bs, bs, n1, n1)
+        P = np.zeros((n0 * bs, n1 * bs))
+        for i, I in enumerate(L[0]["agg"]):
+            if I >= 0:
+                P[i * bs:(i + 1) * bs, I * bs:(I + 1) * bs] = np.eye(bs)
+        assert np.abs(P.T @ A0 @ P - A1).max() <= 1e-14 * np.abs(A1).max()
+
+
+def _cheb_closed_form(Ad, Dinv, rho, k, b):
+    """x = (I - q(D^{-1}A)) A^{-1} b, q(t) = T_k((theta - t)/delta) / T_k(theta/delta)."""
+    lmax, lmin = rho, rho / 10.0
+    th, de = 0.5 * (lmax + lmin), 0.5 * (lmax - lmin)
+    n = Ad.shape[0]
+    X = (th * np.eye(n) - Dinv @ Ad) / de
+    T0, T1 = np.eye(n), X
+    for _ in range(k - 1):
+        T0, T1 = T1, 2 * X @ T1 - T0
+    s = th / de
+    t0, t1 = 1.0, s
+    for _ in range(k - 1):
+        t0, t1 = t1, 2 * s * t1 - t0
+    Q = (T1 if k >= 1 else T0) / (t1 if k >= 1 else t0)
+    if b is None:                                       # the smoother as a matrix
+        return (np.eye(n) - Q) @ np.linalg.inv(Ad)
+    return (np.eye(n) - Q) @ np.linalg.solve(Ad, b)
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_chebyshev_matches_closed_form(tiny, k):
+    """Chebyshev smoother (Saad, Alg. 12.1) vs its residual polynomial."""
+    d, _ = tiny
+    o = oracle.Oracle(d)
+    o.setup()
+    L = o.amg_levels(0)
+    n = len(L[0]["rowptr"]) - 1
+    Ad = oracle.dense_block(L[0]["rowptr"], L[0]["col"], L[0]["val"], 3, 3, n, n)
+    Db = np.zeros_like(Ad)
+    for i in range(n):
+        Db[3 * i:3 * i + 3, 3 * i:3 * i + 3] = Ad[3 * i:3 * i + 3, 3 * i:3 * i + 3]
+    Dinv = np.linalg.inv(Db)
+    rho = np.abs(Dinv @ Ad).sum(axis=1).max()          # Gershgorin bound of D^{-1}A
+    assert np.isclose(rho, L[0]["rho"], rtol=1e-13)
+    b = np.random.default_rng(4).standard_normal(3 * n)
+    x = oracle.chebyshev(L[0]["rowptr"], L[0]["col"], L[0]["val"], 3, L[0]["rho"], k, b)
+    assert _rel(x, _cheb_closed_form(Ad, Dinv, L[0]["rho"], k, b)) <= 1e-10
+
+
+def test_two_level_cycle_is_coarse_projection(tiny):
+    """With no smoothing and an exact coarse solve, the cycle is P (P^T A P)^{-1} P^T."""
+    d, _ = tiny
+    o = oracle.Oracle(d, amg_max_levels=2, cheb_degree=0, amg_coarse_max=10)
+    o.setup()
+    L = o.amg_levels(0)
+    assert len(L) == 2
+    n0, n1 = len(L[0]["rowptr"]) - 1, len(L[1]["rowptr"]) - 1
+    A0 = oracle.dense_block(L[0]["rowptr"], L[0]["col"], L[0]["val"], 3, 3, n0, n0)
+    P = np.zeros((3 * n0, 3 * n1))
+    for i, I in enumerate(L[0]["agg"]):
+        if I >= 0:
+            P[3 * i:3 * i + 3, 3 * I:3 * I + 3] = np.eye(3)
+    b = np.random.default_rng(5).standard_normal(3 * n0)
+    ref = P @ np.linalg.solve(P.T @ A0 @ P, P.T @ b)
+    assert _rel(o.vcycle(0, b), ref) <= 1e-12
+
+
+def test_vcycle_error_propagation(tiny):
+    """Two-level V(1,1): E = (I - S A)(I - P A_c^{-1} P^T A)(I - S A), M^{-1} = (I - E) A^{-1}."""
+    d, _ = tiny
+    o = oracle.Oracle(d, amg_max_levels=2, amg_coarse_max=10)
+    o.setup()
+    L = o.amg_levels(0)
+    n0, n1 = len(L[0]["rowptr"]) - 1, len(L[1]["rowptr"]) - 1
+    A0 = oracle.dense_block(L[0]["rowptr"], L[0]["col"], L[0]["val"], 3, 3, n0, n0)
+    Db = np.zeros_like(A0)
+    for i in range(n0):
+        Db[3 * i:3 * i + 3, 3 * i:3 * i + 3] = A0[3 * i:3 * i + 3, 3 * i:3 * i + 3]
+    Dinv = np.linalg.inv(Db)
+    n = 3 * n0
+    # smoother as a matrix: x = S b from x0 = 0
+    Sm = _cheb_closed_form(A0, Dinv, L[0]["rho"], 2, None)
+    P = np.zeros((n, 3 * n1))
+    for i, I in enumerate(L[0]["agg"]):
+        if I >= 0:
+            P[3 * i:3 * i + 3, 3 * I:3 * I + 3] = np.eye(3)
+    CC = np.eye(n) - P @ np.linalg.solve(P.T @ A0 @ P, P.T @ A0)
+    E = (np.eye(n) - Sm @ A0) @ CC @ (np.eye(n) - Sm @ A0)
+    b = np.random.default_rng(6).standard_normal(n)
+    ref = (np.eye(n) - E) @ np.linalg.solve(A0, b)
+    assert _rel(o.vcycle(0, b), ref) <= 1e-9
+    # and it contracts: the preconditioner is useful
+    assert np.abs(np.linalg.eigvals(E)).max() < 0.9
+
+
+def test_gmres_iterate_is_krylov_minimiser(tiny):
+    """GMRES (Saad & Schultz) iterate k minimises ||b - A x|| over K_k(A, b):
+    brute force by dense least squares on an orthonormalised Krylov basis."""
+    d, (A, B, C, D, F) = tiny
+    o = oracle.Oracle(d)
+    b = np.random.default_rng(7).standard_normal(3 * d["n_nodes"])
+    for k in (1, 3, 6):
+        x, its, rel, rc = o.gmres_A(b, 1e-30, 200, k, 0)
+        assert its == k
+        K = np.empty((len(b), k))
+        v = b / np.linalg.norm(b)
+        for j in range(k):
+            K[:, j] = v
+            v = A @ v
+            for i in range(j + 1):          # re-orthonormalise for stability
+                v -= (K[:, i] @ v) * K[:, i]
+            v /= np.linalg.norm(v)
+        Q, _ = np.linalg.qr(K)
+        y, *_ = np.linalg.lstsq(A @ Q, b, rcond=None)
+        x_ref = Q @ y
+        assert _rel(x, x_ref) <= 1e-8
+        # Givens residual estimate equals the true residual
+        assert abs(rel - np.linalg.norm(b - A @ x) / np.linalg.norm(b)) <= 1e-10
+
+
+@pytest.fixture(scope="module")
+def tiny4():
+    spec = synth.MeshSpec(8, 8, 8, Re=100.0, seed=0, R=(1e2, 1e3, 3e3, 1e4), name="cube8_re100_q4")
+    d = synth.generate(spec)
+    return d, oracle.dense_system(d)
+
+
+def test_adjoint_matches_dense_and_finite_differences(tiny4):
+    """lambda = A^{-T} g, dL/dr_k = -(lambda_v . a^k)(a^k . x_v) because
+    dA/dr_k = [[a^k a^kT, 0], [0, 0]] (Sec. 2.5, K term); L = sum_k (a^k.u - q_k)^2.
+    Four outlets: with one outlet and a prescribed inflow the outlet flux is
+    fixed by continuity and dL/dr vanishes."""
+    d, (A, B, C, D, F) = tiny4
+    N = d["n_nodes"]
+    nv = 3 * N
+    n_out = len(d["out_ptr"]) - 1
+    av = []
+    for k in range(n_out):
+        v = np.zeros(nv)
+        v[d["out_idx"][d["out_ptr"][k]:d["out_ptr"][k + 1]]] = d["out_val"][d["out_ptr"][k]:d["out_ptr"][k + 1]]
+        av.append(v)
+    x = np.linalg.solve(F, d["b"])
+    flux = np.array([a @ x[:nv] for a in av])
+    q = (2 * synth.uniforms(44, n_out) - 1) * np.abs(flux).max()
+
+    def loss(rv):
+        dd = dict(d)
+        dd["r"] = np.asarray(rv)
+        *_, Fr = oracle.dense_system(dd)
+        xr = np.linalg.solve(Fr, d["b"])
+        return sum((av[k] @ xr[:nv] - q[k]) ** 2 for k in range(n_out))
+
+    g = np.zeros(4 * N)
+    for k in range(n_out):
+        g[:nv] += 2 * (av[k] @ x[:nv] - q[k]) * av[k]
+    lam, dLdr, info = oracle.adjoint(d, g, x, rtol=1e-12)
+    lam_ref = np.linalg.solve(F.T, g)
+    assert _rel(lam, lam_ref) <= 1e-6
+    for k in range(n_out):
+        e = np.zeros(n_out)
+        e[k] = 1e-6 * d["r"][k]
+        fd = (loss(d["r"] + e) - loss(d["r"] - e)) / (2 * e[k])
+        assert abs(dLdr[k] - fd) <= 1e-5 * abs(fd)
