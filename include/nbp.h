@@ -1,0 +1,201 @@
+/*
+ * nbp.h -- C ABI of the GB300 nested block preconditioned solver.
+ *
+ * Solves A x = b for the block tangent
+ *
+ *        A = [[A_sp + sum_k r_k a^k a^kT , B],
+ *             [C                          , D]]
+ *
+ * of the P1-P1 VMS / generalized-alpha Navier-Stokes discretisation (paper
+ * Sec. 2.5: definitions of A, B, C, D and of the resistance term
+ * K = alpha_f gamma dt sum_k m^k a^k a^kT; Sec. 3: the block system) with an
+ * outer flexible GMRES preconditioned by the Schur complement reduction
+ * P_SCR (Sec. 3.1, Algorithm 3), whose Schur complement S = D - C A^{-1} B is
+ * applied matrix-free (Algorithm 2) and preconditioned by AMG on
+ * S_hat = D - C diag(A)^{-1} B (Sec. 3.1).
+ *
+ * Conventions for every entry point:
+ *   - Unknowns are ordered x = [x_v (3N, node-interleaved u,v,w); x_p (N)].
+ *   - Unless stated otherwise, vector arguments are DEVICE pointers owned by
+ *     the caller, and all work is ordered on the stream given to nbp_create.
+ *     Entry points return after the stream has been synchronised, except where
+ *     stated.
+ *   - Every entry point returns an nbp_status; on error nbp_last_error()
+ *     gives a one-line message.  No entry point aborts the process.
+ *   - The library owns the context and all device memory it allocates (with
+ *     cudaMallocAsync on the context stream); nbp_destroy releases it.
+ */
+#ifndef NBP_H
+#define NBP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct nbp_ctx nbp_ctx;   /* opaque, library-owned */
+
+typedef enum {
+    NBP_OK = 0,
+    NBP_ERR_INVALID = 1,      /* bad argument, malformed sparse structure, NaN input */
+    NBP_ERR_CUDA = 2,         /* a CUDA runtime call failed (message has the call) */
+    NBP_ERR_OOM = 3,          /* device allocation failed */
+    NBP_NOT_CONVERGED = 4,    /* solve ended at n_max; x and info are still filled */
+    NBP_ERR_BREAKDOWN = 5,    /* zero Givens denominator with a nonzero residual */
+    NBP_ERR_NAN = 6,          /* NaN/Inf met in the iteration */
+    NBP_ERR_TIMEOUT = 7,      /* a bounded device wait ran out */
+    NBP_ERR_STATE = 8         /* call order violated (e.g. solve before setup) */
+} nbp_status;
+
+/* Inputs of nbp_create.  All arrays are DEVICE pointers owned by the caller;
+ * they are read (copied) during nbp_create only.
+ *   A: block CSR with 3x3 row-major blocks, N block rows (velocity nodes).
+ *   B: block CSR with 3x1 blocks (velocity row dofs x pressure column), N block rows.
+ *   C: block CSR with 1x3 blocks (pressure row x velocity column dofs), N rows.
+ *   D: CSR, N x N.
+ *   Column indices must be sorted and unique within each row; rowptr[0] = 0.
+ *   Outlet k (0 <= k < n_out) is the sparse vector a^k over velocity dofs
+ *   0..3N-1 with entries out_idx/out_val[out_ptr[k] .. out_ptr[k+1]-1]
+ *   (indices unique within one outlet).  r[k] (host or device, see flag) is
+ *   the coefficient r_k multiplying a^k a^kT in A, i.e. the paper's
+ *   alpha_f gamma dt m^k (Sec. 2.5); out_ptr is a DEVICE array. */
+typedef struct {
+    int32_t n_nodes;
+    const int32_t *a_rowptr, *a_col; const double *a_val;
+    const int32_t *b_rowptr, *b_col; const double *b_val;
+    const int32_t *c_rowptr, *c_col; const double *c_val;
+    const int32_t *d_rowptr, *d_col; const double *d_val;
+    int32_t n_out;
+    const int32_t *out_ptr, *out_idx; const double *out_val;
+    const double *r;          /* HOST array of n_out weights */
+} nbp_system;
+
+/* Solver settings (paper Sec. 3.1: delta^r, delta^r_A, delta^r_S, delta^r_I,
+ * delta^a, m, m_A, m_S, n_max).  Defaults from nbp_default_options():
+ * rtol 1e-8, rtol_A 1e-3, rtol_S 1e-2, rtol_I 1e-2, atol 1e-50,
+ * m = m_A = m_S = nmax = nmax_A = nmax_S = 200. */
+typedef struct {
+    double rtol, rtol_A, rtol_S, rtol_I, atol;
+    int32_t m, m_A, m_S, nmax, nmax_A, nmax_S;
+    int32_t precision;      /* 0 FP64 everywhere; 1 FP32 inner (values, vectors, basis);
+                               2 BF16 inner matrix values with FP32 vectors/accumulation.
+                               The outer FGMRES, Givens update, true residual and the
+                               rank-one term stay FP64 in every mode. */
+    int32_t pc_A;           /* 0 AMG V-cycle, 1 point Jacobi diag(A)^{-1} */
+    int32_t pc_S;           /* 0 AMG on S_hat, 1 none */
+    int32_t variant;        /* 0 P_SCR (Algorithm 3); 1 upper block-triangular [[A,B],[0,S]] */
+    int32_t amg_max_levels; /* default 5 */
+    int32_t amg_coarse_max; /* default 300 block rows */
+    int32_t cheb_degree;    /* default 2 */
+    double theta;           /* aggregation strength threshold, default 0.0064 */
+} nbp_options;
+
+typedef struct {
+    int32_t outer_iters;
+    int64_t A_iters, S_iters, I_iters;          /* intermediate A, S, inner A iterations */
+    int64_t n_A_solves, n_I_solves, n_S_solves;
+    double rel_res_est, rel_res_true;           /* outer estimate and FP64 true residual */
+    double setup_s, solve_s;                    /* wall seconds of the last setup / solve */
+    int32_t status;
+} nbp_info;
+
+void nbp_default_options(nbp_options *opt);
+
+/* Copies the system to device memory owned by the context; validates the
+ * sparse structure on the device (monotone row pointers, column indices in
+ * range and sorted, finite values).  `stream` is a cudaStream_t (NULL for the
+ * legacy default stream).  The current CUDA device at this call is used for
+ * the life of the context.  Errors: NBP_ERR_INVALID, NBP_ERR_CUDA, NBP_ERR_OOM. */
+nbp_status nbp_create(nbp_ctx **ctx, const nbp_system *sys, const nbp_options *opt, void *stream);
+
+/* Builds, on the device: the aggregation AMG hierarchy of A_sp, S_hat =
+ * D - C diag(A)^{-1} B (diag(A) includes the rank-one terms), the AMG
+ * hierarchy of S_hat, and the FP32/BF16 value copies the precision mode
+ * needs.  Time is reported in info.setup_s of the next solve. */
+nbp_status nbp_setup(nbp_ctx *ctx);
+
+/* Replaces the n_out weights r_k (HOST array).  S_hat depends on them through
+ * diag(A); call nbp_setup again before solving if P_S should track them. */
+nbp_status nbp_set_resistances(nbp_ctx *ctx, const double *r);
+
+/* Nested solve (paper Sec. 3): outer FGMRES(m) preconditioned by P_SCR
+ * (Algorithm 3) to ||b - A x|| <= max(rtol ||b||, atol), x_0 = 0.  b, x:
+ * DEVICE arrays of 4N doubles.  `opt` may be NULL (context options).  The
+ * true residual is recomputed in FP64 before returning.  Returns NBP_OK,
+ * NBP_NOT_CONVERGED (x filled), or an error. */
+nbp_status nbp_solve(nbp_ctx *ctx, const double *b, double *x, const nbp_options *opt, nbp_info *info);
+
+/* Same as nbp_solve with HOST b and x (copied in and out on the context
+ * stream inside the call). */
+nbp_status nbp_solve_host(nbp_ctx *ctx, const double *b_host, double *x_host, const nbp_options *opt,
+                          nbp_info *info);
+
+/* Adjoint of the nested solve: lambda = A^{-T} g by the same nested method on
+ * the transposed tangent [[A^T, C^T], [B^T, D^T]] (whose Schur complement is
+ * S^T, so Algorithms 2 and 3 apply unchanged), then dL/db = lambda and
+ * dL/dr_k = -(lambda_v . a^k)(a^k . x_v) because dA/dr_k = a^k a^kT (Sec. 2.5).
+ * g, x, lambda: DEVICE arrays of 4N doubles; dL_dr: HOST array of n_out.
+ * The transposed hierarchy is built on the first call (and after setup). */
+nbp_status nbp_adjoint(nbp_ctx *ctx, const double *g, const double *x, double *lambda, double *dL_dr,
+                       nbp_info *info);
+
+nbp_status nbp_destroy(nbp_ctx *ctx);
+const char *nbp_last_error(const nbp_ctx *ctx);
+
+/* ---- steps of the method, exposed for parity tests and benchmarks ---- */
+
+/* y = A x = A_sp x + sum_k r_k a^k (a^kT x) (Sec. 2.5).  x, y: DEVICE, 3N
+ * doubles.  precision 0 uses FP64 values; 1/2 use the FP32/BF16 value copies
+ * made by nbp_setup with FP32 vectors (x, y are then float*). */
+nbp_status nbp_apply_A(nbp_ctx *ctx, const void *x, void *y, int32_t precision);
+
+/* y = [[A, B], [C, D]] x in FP64 (the outer operator of Sec. 3). */
+nbp_status nbp_apply_full(nbp_ctx *ctx, const double *x, double *y);
+
+/* Algorithm 2: y = D x_p - C A^{-1} B x_p with the inner GMRES(m_A) + P_A to
+ * rtol_I.  x_p, y: DEVICE, N doubles.  Needs nbp_setup. */
+nbp_status nbp_apply_S(nbp_ctx *ctx, const double *xp, double *y);
+
+/* Algorithm 3: y = P_SCR^{-1} s.  s, y: DEVICE, 4N doubles.  Needs nbp_setup. */
+nbp_status nbp_apply_pscr(nbp_ctx *ctx, const double *s, double *y);
+
+/* GMRES(m_A) + P_A on A y = s to relative tolerance rtol (Sec. 3.1).
+ * s, y: DEVICE, 3N doubles.  *iters receives the iteration count. */
+nbp_status nbp_solve_A(nbp_ctx *ctx, const double *s, double *y, double rtol, int32_t *iters);
+
+/* One AMG V(1,1)-cycle, x = M^{-1} b, on the hierarchy of A_sp (which = 0,
+ * 3N doubles) or of S_hat (which = 1, N doubles).  DEVICE arrays. */
+nbp_status nbp_vcycle(nbp_ctx *ctx, int32_t which, const double *b, double *x);
+
+/* Hierarchy introspection (after nbp_setup).  nbp_amg_level_sizes returns the
+ * number of levels; rows/nnz (HOST arrays of length >= levels) get the block
+ * rows and stored blocks of each level.  nbp_amg_level_get copies level l to
+ * HOST arrays: rowptr (rows+1), col (nnz), val (nnz*bs*bs doubles) and the
+ * aggregate map to level l+1 (rows; -1 = left out), any of which may be NULL. */
+int32_t nbp_amg_level_sizes(nbp_ctx *ctx, int32_t which, int32_t *rows, int64_t *nnz, int32_t max_levels);
+nbp_status nbp_amg_level_get(nbp_ctx *ctx, int32_t which, int32_t l, int32_t *rowptr, int32_t *col, double *val,
+                             int32_t *agg, double *rho);
+
+/* S_hat after nbp_setup: nnz, then its CSR copied to HOST arrays. */
+int64_t nbp_shat_nnz(nbp_ctx *ctx);
+nbp_status nbp_shat_get(nbp_ctx *ctx, int32_t *rowptr, int32_t *col, double *val);
+
+/* Per-kernel device-time accounting of the last solve: total milliseconds and
+ * algorithmic bytes of the SpMV family and of the Arnoldi (CGS2) kernels,
+ * measured with CUDA events on the context stream when `enable` was set by
+ * nbp_profile(ctx, 1) before the solve. */
+typedef struct {
+    double spmv_ms, spmv_bytes, arnoldi_ms, arnoldi_bytes;
+    double a0_ms, a0_bytes;     /* the fine-level A product (A_sp + rank-one) alone */
+    double vcycle_ms;
+    int64_t spmv_launches, arnoldi_launches, a0_launches;
+    int64_t kernel_launches;    /* every kernel this library launched in the last call */
+} nbp_profile_info;
+nbp_status nbp_profile(nbp_ctx *ctx, int32_t enable);
+nbp_status nbp_profile_get(nbp_ctx *ctx, nbp_profile_info *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NBP_H */

@@ -1,0 +1,290 @@
+// kernels.cuh -- hand-written sm_103a kernels of the nested block solver:
+// block-sparse products with fused epilogues, deterministic multi-dot /
+// multi-axpy for CGS2 Arnoldi, the device Givens least-squares update and the
+// AMG transfer operators.  Internal header (templates), included by the
+// translation units that launch them.
+#pragma once
+
+#include "nbp_common.cuh"
+
+namespace nbp {
+
+// ===================================================== block-sparse products
+// y = epilogue(M x) for a block CSR matrix with BR x BC blocks.  A group of G
+// lanes walks one block row's values as one flat, contiguous array (perfectly
+// coalesced loads whatever the block shape), keeps BR partial sums, and
+// reduces them with xor shuffles inside the group.  Epilogues:
+//   EPI_SET  y = Mx (+ rank-one term, LR)      EPI_ADD  y += Mx
+//   EPI_SUB  y -= Mx                           EPI_RES  y = b - Mx
+//   EPI_CHEB r = b - Mx; d = c1 d + c2 Dinv r; xout = x + d   (Chebyshev step)
+enum Epi { EPI_SET = 0, EPI_ADD = 1, EPI_SUB = 2, EPI_RES = 3, EPI_CHEB = 4 };
+
+struct SpmvArgs {
+    int nbr;
+    const int *rp, *ci;
+    const void *val;
+    const void *x;
+    void *y;
+    const void *b;          // EPI_RES / EPI_CHEB
+    const void *dinv;       // EPI_CHEB: BR x BR per row (same type as vectors)
+    void *d;                // EPI_CHEB: Chebyshev direction (in/out)
+    void *xout;             // EPI_CHEB: x + d
+    double c1, c2;          // EPI_CHEB coefficients
+    const int *lr_rp, *lr_k, *lr_c;   // rank-one epilogue (EPI_SET only)
+    const double *lr_val, *lr_f;
+};
+
+template <int BR, int BC, int G, typename VT, typename XT, int EPI, bool LR>
+__global__ void __launch_bounds__(256) k_bspmv(SpmvArgs a) {
+    using AT = XT;   // accumulate in the vector type (FP64 or FP32)
+    constexpr int BB = BR * BC;
+    const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int row = (int)(gid / G);
+    const int lane = (int)(gid % G);
+    if (row >= a.nbr) return;   // whole groups leave together (G divides 32)
+    const unsigned wl = threadIdx.x & 31u;
+    const unsigned mask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (wl & ~(unsigned)(G - 1)));
+    const int e0 = __ldg(a.rp + row);
+    const int cnt = (__ldg(a.rp + row + 1) - e0) * BB;
+    const VT *__restrict__ val = (const VT *)a.val + (long long)e0 * BB;
+    const int *__restrict__ ci = a.ci + e0;
+    const XT *__restrict__ x = (const XT *)a.x;
+    AT acc0 = 0, acc1 = 0, acc2 = 0;
+#pragma unroll 4
+    for (int v = lane; v < cnt; v += G) {
+        const int e = v / BB;
+        const int rc = v - e * BB;
+        const int r = rc / BC;
+        const int c = rc - r * BC;
+        const AT p = cvt<AT>(__ldg(val + v)) * __ldg(x + (long long)__ldg(ci + e) * BC + c);
+        if (BR == 1) acc0 += p;
+        else {
+            acc0 += (r == 0) ? p : AT(0);
+            acc1 += (r == 1) ? p : AT(0);
+            acc2 += (r == 2) ? p : AT(0);
+        }
+    }
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) {
+        acc0 += __shfl_xor_sync(mask, acc0, o);
+        if (BR > 1) {
+            acc1 += __shfl_xor_sync(mask, acc1, o);
+            acc2 += __shfl_xor_sync(mask, acc2, o);
+        }
+    }
+    if (lane >= BR) return;
+    AT s = (lane == 0) ? acc0 : (lane == 1 ? acc1 : acc2);
+    const long long idx = (long long)row * BR + lane;
+    XT *y = (XT *)a.y;
+    if (EPI == EPI_SET) {
+        if (LR) {
+            double t = 0.0;
+            for (int q = a.lr_rp[row]; q < a.lr_rp[row + 1]; ++q)
+                if (a.lr_c[q] == lane) t += a.lr_f[a.lr_k[q]] * a.lr_val[q];
+            s = (AT)((double)s + t);
+        }
+        y[idx] = s;
+    } else if (EPI == EPI_ADD) {
+        y[idx] += s;
+    } else if (EPI == EPI_SUB) {
+        y[idx] -= s;
+    } else if (EPI == EPI_RES) {
+        y[idx] = ((const XT *)a.b)[idx] - s;
+    } else {   // EPI_CHEB, BR == BC
+        const XT *b = (const XT *)a.b;
+        const XT *dinv = (const XT *)a.dinv + (long long)row * BR * BR + lane * BR;
+        AT t;
+        if (BR == 1) {
+            t = dinv[0] * (b[idx] - s);
+        } else {
+            const AT r0 = b[(long long)row * 3 + 0] - acc0;
+            const AT r1 = b[(long long)row * 3 + 1] - acc1;
+            const AT r2 = b[(long long)row * 3 + 2] - acc2;
+            t = dinv[0] * r0 + dinv[1] * r1 + dinv[2] * r2;
+        }
+        XT *d = (XT *)a.d;
+        const AT dn = (AT)a.c1 * d[idx] + (AT)a.c2 * t;
+        d[idx] = dn;
+        ((XT *)a.xout)[idx] = x[idx] + dn;
+    }
+}
+
+// ============================================ deterministic reductions
+// Partial dot products of columns 0..ncols-1 of V (column j at V + j*ldv)
+// with w over a fixed grid of kReduceBlocks blocks; block b covers a fixed
+// contiguous chunk.  partial layout: [col][block].
+template <typename T, int CB>
+__global__ void __launch_bounds__(256) k_mdot(const T *__restrict__ V, long long ldv, int ncols, const T *__restrict__ w,
+                                              long long n, double *__restrict__ partial) {
+    __shared__ double red[CB][8];
+    const long long chunk = (n + gridDim.x - 1) / gridDim.x;
+    const long long lo = (long long)blockIdx.x * chunk;
+    const long long hi = min(n, lo + chunk);
+    const int warp = threadIdx.x >> 5, ln = threadIdx.x & 31;
+    for (int c0 = 0; c0 < ncols; c0 += CB) {
+        using AT = T;
+        AT acc[CB];
+#pragma unroll
+        for (int q = 0; q < CB; ++q) acc[q] = 0;
+        for (long long t = lo + threadIdx.x; t < hi; t += blockDim.x) {
+            const AT wt = w[t];
+#pragma unroll
+            for (int q = 0; q < CB; ++q)
+                if (c0 + q < ncols) acc[q] += V[(long long)(c0 + q) * ldv + t] * wt;
+        }
+#pragma unroll
+        for (int q = 0; q < CB; ++q) {
+            double v = warp_sum((double)acc[q]);
+            if (ln == 0) red[q][warp] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x < CB && c0 + (int)threadIdx.x < ncols) {
+            double s = 0.0;
+            for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += red[threadIdx.x][k];
+            partial[(long long)(c0 + threadIdx.x) * gridDim.x + blockIdx.x] = s;
+        }
+        __syncthreads();
+    }
+}
+
+// out[j] (+)= sum_b partial[j][b] in a fixed order (one warp per column).
+__global__ void k_reduce_partials(const double *__restrict__ partial, int nblocks, int ncols, double *__restrict__ out,
+                                  int accumulate);
+
+// w[t] += alpha * sum_j coef[j] V[j][t]  (coef on the device, FP64)
+template <typename T>
+__global__ void __launch_bounds__(256) k_maxpy(const T *__restrict__ V, long long ldv, int ncols, const double *__restrict__ coef,
+                                               double alpha, T *__restrict__ w, long long n) {
+    __shared__ double cs[256];
+    for (int c0 = 0; c0 < ncols; c0 += 256) {
+        const int cn = min(256, ncols - c0);
+        __syncthreads();
+        if ((int)threadIdx.x < cn) cs[threadIdx.x] = alpha * coef[c0 + threadIdx.x];
+        __syncthreads();
+        for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+            T acc = 0;
+            int j = 0;
+            for (; j + 4 <= cn; j += 4) {
+                acc += (T)cs[j] * V[(long long)(c0 + j) * ldv + t];
+                acc += (T)cs[j + 1] * V[(long long)(c0 + j + 1) * ldv + t];
+                acc += (T)cs[j + 2] * V[(long long)(c0 + j + 2) * ldv + t];
+                acc += (T)cs[j + 3] * V[(long long)(c0 + j + 3) * ldv + t];
+            }
+            for (; j < cn; ++j) acc += (T)cs[j] * V[(long long)(c0 + j) * ldv + t];
+            w[t] += acc;
+        }
+    }
+}
+
+// ============================================================== vectors
+template <typename T> __global__ void k_fill(T *x, T v, long long n) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) x[i] = v;
+}
+template <typename D, typename S> __global__ void k_convert(D *dst, const S *src, long long n) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        dst[i] = (D)src[i];
+}
+// y = a*x + b*y
+template <typename T> __global__ void k_axpby(T *y, const T *x, double a, double b, long long n) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        y[i] = (T)a * x[i] + (T)b * y[i];
+}
+// z = x - y
+template <typename T> __global__ void k_sub(T *z, const T *x, const T *y, long long n) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        z[i] = x[i] - y[i];
+}
+// v = w / s[0] (skips when s[0] == 0)
+template <typename T> __global__ void k_scale_inv(T *v, const T *w, const double *s, long long n) {
+    const double d = *s;
+    if (d == 0.0) return;
+    const T inv = (T)(1.0 / d);
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        v[i] = w[i] * inv;
+}
+
+// ================================================ Givens / least squares
+struct GmState {
+    double res;      // |g_{j+1}|
+    double beta;     // h_{j+1,j}
+    int nan;         // NaN/Inf met
+    int pad;
+};
+// Column j of the Hessenberg matrix from h1 + h2 (CGS2) and ||w||^2, previous
+// rotations applied, new rotation formed, g updated (Saad 1993).  One thread.
+__global__ void k_givens(double *H, int ldh, int j, const double *h1, const double *h2, const double *nrm2, double *cs,
+                         double *sn, double *g, GmState *st);
+// y = H(0:k,0:k)^{-1} g(0:k), upper triangular.  One thread.
+__global__ void k_trisolve(const double *H, int ldh, const double *g, double *y, int k);
+// g = [beta, 0, ...]; st->res = beta
+__global__ void k_gm_init(double *g, int m1, const double *beta2, double *beta, GmState *st);
+
+__global__ void k_recip(long long n, const double *a, double *b);
+
+// ================================================================= AMG
+// coarse r_c[I] = sum_{i in I} r[i] (members ascending), bs components
+template <typename T>
+__global__ void k_restrict(const int *__restrict__ mptr, const int *__restrict__ mem, int nc, int bs, const T *__restrict__ r,
+                           T *__restrict__ rc) {
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    if (I >= nc) return;
+    for (int a = 0; a < bs; ++a) {
+        T s = 0;
+        for (int q = mptr[I]; q < mptr[I + 1]; ++q) s += r[(long long)mem[q] * bs + a];
+        rc[(long long)I * bs + a] = s;
+    }
+}
+// x[i] += e_c[agg[i]]
+template <typename T>
+__global__ void k_prolong(const int *__restrict__ agg, int n, int bs, const T *__restrict__ ec, T *__restrict__ x) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long long)n * bs) return;
+    const int i = (int)(t / bs), a = (int)(t - (long long)i * bs);
+    const int I = agg[i];
+    if (I >= 0) x[t] += ec[(long long)I * bs + a];
+}
+// Chebyshev first step from x = 0: d = c2 Dinv b; x = d
+template <typename T>
+__global__ void k_cheb_first(int nbr, int bs, const T *__restrict__ dinv, const T *__restrict__ b, double c2, T *__restrict__ d,
+                             T *__restrict__ x) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long long)nbr * bs) return;
+    const int i = (int)(t / bs), a = (int)(t - (long long)i * bs);
+    T s = 0;
+    for (int c = 0; c < bs; ++c) s += dinv[(long long)i * bs * bs + a * bs + c] * b[(long long)i * bs + c];
+    const T dn = (T)c2 * s;
+    d[t] = dn;
+    x[t] = dn;
+}
+// x = Cinv b, dense (coarsest level); one warp per row
+template <typename T>
+__global__ void k_dense_gemv(const double *__restrict__ Cinv, int n, const T *__restrict__ b, T *__restrict__ x) {
+    const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int ln = threadIdx.x & 31;
+    if (row >= n) return;
+    double s = 0.0;
+    for (int c = ln; c < n; c += 32) s += Cinv[(long long)row * n + c] * (double)b[c];
+    s = warp_sum(s);
+    if (ln == 0) x[row] = (T)s;
+}
+
+// =============================================================== rank one
+// f[k] = r_k * (a^k . x), one block per outlet (fixed-order tree reduction)
+template <typename T>
+__global__ void k_lowrank_dots(const int *__restrict__ optr, const int *__restrict__ oidx, const double *__restrict__ oval,
+                               const double *__restrict__ r, const T *__restrict__ x, double *__restrict__ f) {
+    __shared__ double red[8];
+    const int k = blockIdx.x;
+    double s = 0.0;
+    for (int q = optr[k] + threadIdx.x; q < optr[k + 1]; q += blockDim.x) s += oval[q] * (double)x[oidx[q]];
+    s = warp_sum(s);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        f[k] = r[k] * t;
+    }
+}
+
+}  // namespace nbp

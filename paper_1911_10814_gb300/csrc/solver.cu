@@ -1,0 +1,1092 @@
+// solver.cu -- the nested block preconditioned solve on one GB300 and its C ABI.
+//
+//   outer   FGMRES(m), FP64, right preconditioned by P_SCR      (paper Sec. 3)
+//   P_SCR   Algorithm 3: A-solve, C product, S-solve, B product, A-solve
+//   S x     Algorithm 2: D x - C A^{-1} B x with an inner A-solve (delta_I)
+//   A-solve GMRES(m_A) with P_A = aggregation AMG V(1,1) (or Jacobi)
+//   S-solve GMRES(m_S) with P_S = AMG(S_hat), S_hat = D - C diag(A)^{-1} B
+//
+// Every level runs the flexible form of GMRES (the preconditioned directions
+// Z are stored), which equals right-preconditioned GMRES for a fixed linear
+// preconditioner and saves the final preconditioner application.  Arnoldi is
+// classical Gram-Schmidt with one re-orthogonalisation (CGS2) on fused
+// multi-dot / multi-axpy kernels with fixed-order reductions, so a run is
+// bitwise repeatable.  The Givens update runs on the device; the host reads a
+// 24-byte status per iteration to decide convergence.
+//
+// Precision modes: 0 = FP64 throughout; 1 = the intermediate/inner solves
+// (Algorithms 2-3 and below) in FP32 values, vectors and Krylov basis; 2 = as
+// 1 with BF16 matrix values.  The outer FGMRES, its Givens update, the true
+// residual and the rank-one resistance term stay FP64; the flexible outer
+// iteration absorbs the inexact preconditioner (Sec. 3: the preconditioner
+// may vary between iterations).
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <memory>
+
+#include "kernels.cuh"
+#include "spmv.cuh"
+
+namespace nbp {
+
+// ------------------------------------------------------------ profiling
+struct Prof {
+    bool on = false;
+    std::vector<cudaEvent_t> pool;
+    size_t used = 0;
+    struct Rec { int cat; size_t e0; double bytes; };
+    std::vector<Rec> recs;
+    long long launches = 0;
+    cudaEvent_t get() {
+        if (used == pool.size()) {
+            cudaEvent_t e;
+            NBP_CUDA(cudaEventCreate(&e));
+            pool.push_back(e);
+        }
+        return pool[used++];
+    }
+    ~Prof() {
+        for (auto e : pool) cudaEventDestroy(e);
+    }
+};
+enum { CAT_SPMV = 0, CAT_SPMV_A0 = 1, CAT_ARNOLDI = 2, CAT_VCYCLE = 3 };
+
+// ------------------------------------------------------------ Krylov space
+template <typename T> struct Krylov {
+    long long n = 0;
+    int m = 0;
+    T *V = nullptr, *Z = nullptr, *w = nullptr, *r = nullptr;
+    double *H = nullptr, *cs = nullptr, *sn = nullptr, *g = nullptr, *y = nullptr;
+    double *h1 = nullptr, *h2 = nullptr, *nrm = nullptr, *beta = nullptr, *partial = nullptr;
+    GmState *st = nullptr;
+    void ensure(long long n_, int m_, cudaStream_t s) {
+        if (n_ == n && m_ <= m) return;
+        release(s);
+        n = n_; m = m_;
+        V = dmalloc<T>((size_t)n * (m + 1), s);
+        Z = dmalloc<T>((size_t)n * m, s);
+        w = dmalloc<T>(n, s);
+        r = dmalloc<T>(n, s);
+        H = dmalloc<double>((size_t)(m + 1) * m, s);
+        cs = dmalloc<double>(m, s); sn = dmalloc<double>(m, s);
+        g = dmalloc<double>(m + 1, s); y = dmalloc<double>(m, s);
+        h1 = dmalloc<double>(m + 1, s); h2 = dmalloc<double>(m + 1, s);
+        nrm = dmalloc<double>(1, s); beta = dmalloc<double>(1, s);
+        partial = dmalloc<double>((size_t)kReduceBlocks * (m + 1), s);
+        st = dmalloc<GmState>(1, s);
+    }
+    void release(cudaStream_t s) {
+        dfree(V, s); dfree(Z, s); dfree(w, s); dfree(r, s); dfree(H, s); dfree(cs, s); dfree(sn, s); dfree(g, s);
+        dfree(y, s); dfree(h1, s); dfree(h2, s); dfree(nrm, s); dfree(beta, s); dfree(partial, s); dfree(st, s);
+        *this = Krylov();
+    }
+};
+
+template <typename T> struct Bufs {   // vectors of Algorithms 2-3 in the inner type
+    long long N = 0;
+    T *sv = nullptr, *sp = nullptr, *yvh = nullptr, *sp2 = nullptr, *yp = nullptr, *sv2 = nullptr, *yv = nullptr;
+    T *xbar = nullptr, *xtil = nullptr, *dinvA = nullptr;
+    void ensure(long long N_, cudaStream_t s) {
+        if (N_ == N) return;
+        release(s);
+        N = N_;
+        sv = dmalloc<T>(3 * N, s); sp = dmalloc<T>(N, s); yvh = dmalloc<T>(3 * N, s); sp2 = dmalloc<T>(N, s);
+        yp = dmalloc<T>(N, s); sv2 = dmalloc<T>(3 * N, s); yv = dmalloc<T>(3 * N, s);
+        xbar = dmalloc<T>(3 * N, s); xtil = dmalloc<T>(3 * N, s); dinvA = dmalloc<T>(3 * N, s);
+    }
+    void release(cudaStream_t s) {
+        dfree(sv, s); dfree(sp, s); dfree(yvh, s); dfree(sp2, s); dfree(yp, s); dfree(sv2, s); dfree(yv, s);
+        dfree(xbar, s); dfree(xtil, s); dfree(dinvA, s);
+        *this = Bufs();
+    }
+};
+
+}  // namespace nbp
+
+// ------------------------------------------------------------------ context
+struct nbp_ctx {
+    int dev = 0;
+    cudaStream_t s = nullptr;
+    int N = 0;
+    nbp::DMat A, B, C, D, Shat;
+    nbp::LowRank lr;
+    nbp_options opt{};
+    nbp::Hier HA, HS;
+    double *diagA = nullptr;      // scalar diagonal of A incl. rank-one terms (3N)
+    bool setup_done = false;
+    int setup_precision = -1;
+    double setup_s = 0.0;
+    nbp::Krylov<double> Kout, KA64, KS64;
+    nbp::Krylov<float> KA32, KS32;
+    nbp::Bufs<double> B64;
+    nbp::Bufs<float> B32;
+    double *full_w = nullptr;     // 4N scratch of the outer operator
+    nbp::GmState *hst = nullptr;  // pinned host status
+    nbp_info info{};
+    nbp::Prof prof;
+    nbp_profile_info pinfo{};
+    std::string err;
+    nbp_ctx *tctx = nullptr;      // transposed system (adjoint), built lazily
+    bool is_transposed = false;
+};
+
+namespace nbp {
+
+// ------------------------------------------------------------ small helpers
+static inline int vsel_of(int precision) { return precision == 2 ? 2 : (precision == 1 ? 1 : 0); }
+
+template <typename T> static void fill(T *x, T v, long long n, cudaStream_t s) {
+    k_fill<T><<<grid_for(n), 256, 0, s>>>(x, v, n);
+    NBP_LAUNCHED();
+}
+template <typename D_, typename S_> static void convert(D_ *d, const S_ *src, long long n, cudaStream_t s) {
+    k_convert<D_, S_><<<grid_for(n), 256, 0, s>>>(d, src, n);
+    NBP_LAUNCHED();
+}
+template <typename T> static void copy(T *d, const T *src, long long n, cudaStream_t s) {
+    NBP_CUDA(cudaMemcpyAsync(d, src, sizeof(T) * n, cudaMemcpyDeviceToDevice, s));
+}
+
+static void prof_begin(nbp_ctx *c, cudaEvent_t &e) {
+    c->prof.launches++;
+    if (!c->prof.on) return;
+    e = c->prof.get();
+    NBP_CUDA(cudaEventRecord(e, c->s));
+}
+static void prof_end(nbp_ctx *c, int cat, double bytes) {
+    if (!c->prof.on) return;
+    cudaEvent_t e1 = c->prof.get();
+    NBP_CUDA(cudaEventRecord(e1, c->s));
+    c->prof.recs.push_back({cat, c->prof.used - 2, bytes});
+}
+
+// algorithmic bytes of one block-sparse product
+template <typename XT> static double spmv_bytes(const DMat &M, int vsel, int epi) {
+    const double vb = vsel == 0 ? 8.0 : (vsel == 1 ? 4.0 : 2.0);
+    double b = (double)M.nnz * M.bb() * vb + (double)M.nnz * 4.0 + (double)(M.nbr + 1) * 4.0;
+    const double xs = sizeof(XT);
+    const double nx = (double)M.nbc * M.bc, ny = (double)M.nbr * M.br;
+    b += nx * xs;
+    if (epi == EPI_SET) b += ny * xs;
+    else if (epi == EPI_ADD || epi == EPI_SUB || epi == EPI_RES) b += 2.0 * ny * xs;
+    else b += 5.0 * ny * xs + (double)M.nbr * M.br * M.br * xs;   // Chebyshev: b, d in/out, xout, dinv
+    return b;
+}
+
+template <typename XT>
+static void do_spmv(nbp_ctx *c, const DMat &M, int vsel, SpmvArgs a, int epi, bool lr, bool fineA = false) {
+    cudaEvent_t e0;
+    prof_begin(c, e0);
+    spmv<XT>(M, vsel, a, epi, lr, c->s);
+    prof_end(c, fineA ? CAT_SPMV_A0 : CAT_SPMV, spmv_bytes<XT>(M, vsel, epi));
+}
+
+static SpmvArgs sargs(const void *x, void *y) {
+    SpmvArgs a{};
+    a.x = x;
+    a.y = y;
+    return a;
+}
+
+// y = A x (+ sum_k r_k a^k (a^k . x)); the rank-one factors f_k are FP64
+template <typename T> static void apply_A(nbp_ctx *c, int vsel, const T *x, T *y) {
+    LowRank &lr = c->lr;
+    SpmvArgs a = sargs(x, y);
+    if (lr.n_out > 0) {
+        c->prof.launches++;
+        k_lowrank_dots<T><<<lr.n_out, 256, 0, c->s>>>(lr.optr, lr.oidx, lr.oval, lr.r, x, lr.f);
+        NBP_LAUNCHED();
+        a.lr_rp = lr.lr_rp; a.lr_k = lr.lr_k; a.lr_c = lr.lr_c; a.lr_val = lr.lr_val; a.lr_f = lr.f;
+    }
+    do_spmv<T>(c, c->A, vsel, a, EPI_SET, lr.n_out > 0, true);
+}
+
+// ------------------------------------------------------------ CGS2 Arnoldi
+template <typename T> static void mdot(nbp_ctx *c, Krylov<T> &K, const T *V, long long ldv, int ncols, const T *w, double *out) {
+    cudaEvent_t e0;
+    prof_begin(c, e0);
+    k_mdot<T, 8><<<kReduceBlocks, 256, 0, c->s>>>(V, ldv, ncols, w, K.n, K.partial);
+    NBP_LAUNCHED();
+    prof_end(c, CAT_ARNOLDI, (double)(ncols + 1) * K.n * sizeof(T));
+    c->prof.launches++;
+    k_reduce_partials<<<grid_exact((long long)ncols * 32), 256, 0, c->s>>>(K.partial, kReduceBlocks, ncols, out, 0);
+    NBP_LAUNCHED();
+}
+template <typename T> static void maxpy(nbp_ctx *c, long long n, const T *V, long long ldv, int ncols, const double *coef,
+                                        double alpha, T *w) {
+    cudaEvent_t e0;
+    prof_begin(c, e0);
+    k_maxpy<T><<<grid_for(n, 256, 8LL * kSMs * 4), 256, 0, c->s>>>(V, ldv, ncols, coef, alpha, w, n);
+    NBP_LAUNCHED();
+    prof_end(c, CAT_ARNOLDI, (double)(ncols + 2) * n * sizeof(T));
+}
+
+// ----------------------------------------------------------------- GMRES
+struct GmResult { int its = 0; double rel = 0.0, rel_true = -1.0; int conv = 0; };
+
+static void read_state(nbp_ctx *c, const GmState *st) {
+    NBP_CUDA(cudaMemcpyAsync(c->hst, st, sizeof(GmState), cudaMemcpyDeviceToHost, c->s));
+    NBP_CUDA(cudaStreamSynchronize(c->s));
+}
+
+// Restarted flexible GMRES, x_0 = 0; stops when the residual estimate
+// |g_{j+1}| <= max(rtol ||b||, atol) (confirmed on the true residual when
+// check_true) or after nmax iterations.
+template <typename T, typename Op, typename Pc>
+static GmResult gmres(nbp_ctx *c, Krylov<T> &K, long long n, Op op, Pc pc, const T *b, T *x, double rtol, double atol,
+                      int m, int nmax, bool check_true) {
+    cudaStream_t s = c->s;
+    GmResult R;
+    m = std::max(1, std::min(m, std::max(nmax, 1)));
+    K.ensure(n, m, s);
+    fill<T>(x, T(0), n, s);
+    mdot<T>(c, K, b, n, 1, b, K.nrm);
+    c->prof.launches++;
+    k_gm_init<<<1, 256, 0, s>>>(K.g, m + 1, K.nrm, K.beta, K.st);
+    NBP_LAUNCHED();
+    read_state(c, K.st);
+    const double bnorm = c->hst->res;
+    require(std::isfinite(bnorm), NBP_ERR_NAN, "gmres: right-hand side is not finite");
+    const double tol = std::max(rtol * bnorm, atol);
+    double res = bnorm;
+    R.rel_true = bnorm > 0 ? 1.0 : 0.0;
+    if (bnorm <= tol) { R.conv = 1; R.rel = bnorm > 0 ? res / bnorm : 0.0; return R; }
+    const T *r0 = b;   // first cycle: r = b (x_0 = 0)
+    while (R.its < nmax) {
+        c->prof.launches++;
+        k_scale_inv<T><<<grid_for(n), 256, 0, s>>>(K.V, r0, K.beta, n);
+        NBP_LAUNCHED();
+        int jend = 0;
+        for (int j = 0; j < m && R.its < nmax; ++j) {
+            T *vj = K.V + (size_t)j * n, *zj = K.Z + (size_t)j * n;
+            pc(vj, zj);
+            op(zj, K.w);
+            // CGS2: two Gram-Schmidt passes against V(:, 0..j)
+            mdot<T>(c, K, K.V, n, j + 1, K.w, K.h1);
+            maxpy<T>(c, n, K.V, n, j + 1, K.h1, -1.0, K.w);
+            mdot<T>(c, K, K.V, n, j + 1, K.w, K.h2);
+            maxpy<T>(c, n, K.V, n, j + 1, K.h2, -1.0, K.w);
+            mdot<T>(c, K, K.w, n, 1, K.w, K.nrm);
+            c->prof.launches += 2;
+            k_givens<<<1, 1, 0, s>>>(K.H, m, j, K.h1, K.h2, K.nrm, K.cs, K.sn, K.g, K.st);
+            k_scale_inv<T><<<grid_for(n), 256, 0, s>>>(K.V + (size_t)(j + 1) * n, K.w, &K.st->beta, n);
+            NBP_LAUNCHED();
+            read_state(c, K.st);
+            require(!c->hst->nan, NBP_ERR_NAN, "gmres: NaN/Inf in the Arnoldi process");
+            res = c->hst->res;
+            ++R.its;
+            jend = j + 1;
+            if (res <= tol || c->hst->beta == 0.0) break;
+        }
+        c->prof.launches += 1;
+        k_trisolve<<<1, 1, 0, s>>>(K.H, m, K.g, K.y, jend);
+        NBP_LAUNCHED();
+        maxpy<T>(c, n, K.Z, n, jend, K.y, 1.0, x);
+        const bool est_conv = res <= tol;
+        if (est_conv && !check_true) { R.conv = 1; break; }
+        // true residual: confirmation, or the next restart vector
+        op(x, K.w);
+        c->prof.launches++;
+        k_sub<T><<<grid_for(n), 256, 0, s>>>(K.r, b, K.w, n);
+        NBP_LAUNCHED();
+        mdot<T>(c, K, K.r, n, 1, K.r, K.nrm);
+        c->prof.launches++;
+        k_gm_init<<<1, 256, 0, s>>>(K.g, m + 1, K.nrm, K.beta, K.st);
+        NBP_LAUNCHED();
+        read_state(c, K.st);
+        res = c->hst->res;
+        R.rel_true = bnorm > 0 ? res / bnorm : 0.0;
+        if (res <= tol) { R.conv = 1; break; }
+        if (res == 0.0) break;
+        r0 = K.r;
+    }
+    R.rel = bnorm > 0 ? res / bnorm : 0.0;
+    return R;
+}
+
+// ----------------------------------------------------------- AMG V-cycle
+template <typename T> static T *wvec(Level &L, int q);
+template <> double *wvec<double>(Level &L, int q) { return L.w64[q]; }
+template <> float *wvec<float>(Level &L, int q) { return L.w32[q]; }
+template <typename T> static const T *dinv_of(const Level &L);
+template <> const double *dinv_of<double>(const Level &L) { return L.dinv; }
+template <> const float *dinv_of<float>(const Level &L) { return L.dinv32; }
+
+struct Cheb { double theta, delta, sigma; };
+static Cheb cheb_of(double rho) {
+    const double lmax = rho, lmin = rho / 10.0;
+    Cheb ch;
+    ch.theta = 0.5 * (lmax + lmin);
+    ch.delta = 0.5 * (lmax - lmin);
+    ch.sigma = ch.theta / ch.delta;
+    return ch;
+}
+
+// One Chebyshev step on level L: r = b - A x; d = c1 d + c2 Dinv r; xout = x + d
+template <typename T>
+static void cheb_step(nbp_ctx *c, Level &L, int vsel, const T *b, const T *x, T *xout, T *d, double c1, double c2) {
+    SpmvArgs a = sargs(x, nullptr);
+    a.b = b; a.dinv = dinv_of<T>(L); a.d = d; a.xout = xout; a.c1 = c1; a.c2 = c2;
+    do_spmv<T>(c, L.M, vsel, a, EPI_CHEB, false);
+}
+
+// Chebyshev smoothing of degree k on level L; from x = 0 when zero_start.
+// Returns the buffer holding the result (x or alt).
+template <typename T>
+static T *chebyshev(nbp_ctx *c, Level &L, int vsel, int k, const T *b, T *x, T *alt, bool zero_start) {
+    const int bs = L.M.br;
+    const Cheb ch = cheb_of(L.rho);
+    T *d = wvec<T>(L, 4);
+    double rho_old = 1.0 / ch.sigma;
+    T *cur = x, *nxt = alt;
+    if (k <= 0) return cur;
+    if (zero_start) {
+        c->prof.launches++;
+        k_cheb_first<T><<<grid_exact((long long)L.M.nbr * bs), 256, 0, c->s>>>(L.M.nbr, bs, dinv_of<T>(L), b, 1.0 / ch.theta,
+                                                                               d, cur);
+        NBP_LAUNCHED();
+    } else {
+        cheb_step<T>(c, L, vsel, b, cur, nxt, d, 0.0, 1.0 / ch.theta);
+        std::swap(cur, nxt);
+    }
+    for (int it = 1; it < k; ++it) {
+        const double rho_new = 1.0 / (2.0 * ch.sigma - rho_old);
+        cheb_step<T>(c, L, vsel, b, cur, nxt, d, rho_new * rho_old, 2.0 * rho_new / ch.delta);
+        std::swap(cur, nxt);
+        rho_old = rho_new;
+    }
+    return cur;
+}
+
+// V(1,1)-cycle from level l with right-hand side b; result written to out.
+template <typename T>
+static void vcycle_level(nbp_ctx *c, Hier &H, int l, int vsel, const T *b, T *out) {
+    Level &L = H.L[l];
+    const int bs = H.bs;
+    const long long n = (long long)L.M.nbr * bs;
+    const int k = c->opt.cheb_degree;
+    if (l == H.nlev - 1) {
+        if (H.cinv) {
+            c->prof.launches++;
+            k_dense_gemv<T><<<grid_exact((long long)H.nc * 32), 256, 0, c->s>>>(H.cinv, H.nc, b, out);
+            NBP_LAUNCHED();
+        } else {
+            T *res = chebyshev<T>(c, L, vsel, std::max(k, 1), b, out, wvec<T>(L, 2), true);
+            if (res != out) copy<T>(out, res, n, c->s);
+        }
+        return;
+    }
+    // pre-smoothing from zero; start so that the odd number of ping-pong
+    // swaps (2k - 1) leaves the final result in `out`
+    T *alt = wvec<T>(L, 2);
+    T *x = (k > 0) ? alt : out;
+    T *other = (k > 0) ? out : alt;
+    if (k <= 0) fill<T>(x, T(0), n, c->s);
+    T *cur = chebyshev<T>(c, L, vsel, k, b, x, other, true);
+    T *oth = (cur == out) ? alt : out;
+    // residual and restriction
+    T *r = wvec<T>(L, 3);
+    do_spmv<T>(c, L.M, vsel, [&] { SpmvArgs a = sargs(cur, r); a.b = b; return a; }(), EPI_RES, false);
+    Level &Lc = H.L[l + 1];
+    T *bc = wvec<T>(Lc, 0), *xc = wvec<T>(Lc, 1);
+    c->prof.launches++;
+    k_restrict<T><<<grid_exact(Lc.M.nbr), 256, 0, c->s>>>(L.mptr, L.mem, Lc.M.nbr, bs, r, bc);
+    NBP_LAUNCHED();
+    vcycle_level<T>(c, H, l + 1, vsel, bc, xc);
+    c->prof.launches++;
+    k_prolong<T><<<grid_exact(n), 256, 0, c->s>>>(L.agg, L.M.nbr, bs, xc, cur);
+    NBP_LAUNCHED();
+    T *fin = chebyshev<T>(c, L, vsel, k, b, cur, oth, false);
+    if (fin != out) copy<T>(out, fin, n, c->s);
+}
+
+template <typename T> static void vcycle(nbp_ctx *c, Hier &H, int vsel, const T *b, T *x) {
+    cudaEvent_t e0;
+    const bool on = c->prof.on;
+    if (on) { e0 = c->prof.get(); NBP_CUDA(cudaEventRecord(e0, c->s)); }
+    vcycle_level<T>(c, H, 0, vsel, b, x);
+    if (on) {
+        cudaEvent_t e1 = c->prof.get();
+        NBP_CUDA(cudaEventRecord(e1, c->s));
+        c->prof.recs.push_back({CAT_VCYCLE, c->prof.used - 2, 0.0});
+    }
+}
+
+// ------------------------------------------------- nested method pieces
+template <typename T> static Krylov<T> &KA(nbp_ctx *c);
+template <> Krylov<double> &KA<double>(nbp_ctx *c) { return c->KA64; }
+template <> Krylov<float> &KA<float>(nbp_ctx *c) { return c->KA32; }
+template <typename T> static Krylov<T> &KS(nbp_ctx *c);
+template <> Krylov<double> &KS<double>(nbp_ctx *c) { return c->KS64; }
+template <> Krylov<float> &KS<float>(nbp_ctx *c) { return c->KS32; }
+template <typename T> static Bufs<T> &BUF(nbp_ctx *c);
+template <> Bufs<double> &BUF<double>(nbp_ctx *c) { return c->B64; }
+template <> Bufs<float> &BUF<float>(nbp_ctx *c) { return c->B32; }
+
+template <typename T> __global__ void k_mul(T *y, const T *x, const T *d, long long n) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) y[i] = x[i] * d[i];
+}
+
+// GMRES(m_A) + P_A on A y = s to rtol (Sec. 3.1)
+template <typename T> static GmResult solve_A(nbp_ctx *c, int vsel, const T *s, T *y, double rtol) {
+    const long long n = 3LL * c->N;
+    auto op = [&](const T *x, T *out) { apply_A<T>(c, vsel, x, out); };
+    if (c->opt.pc_A == 1) {
+        const T *dinv = BUF<T>(c).dinvA;
+        auto pc = [&](const T *x, T *out) {
+            c->prof.launches++;
+            k_mul<T><<<grid_for(n), 256, 0, c->s>>>(out, x, dinv, n);
+            NBP_LAUNCHED();
+        };
+        return gmres<T>(c, KA<T>(c), n, op, pc, s, y, rtol, c->opt.atol, c->opt.m_A, c->opt.nmax_A, false);
+    }
+    auto pc = [&](const T *x, T *out) { vcycle<T>(c, c->HA, vsel, x, out); };
+    return gmres<T>(c, KA<T>(c), n, op, pc, s, y, rtol, c->opt.atol, c->opt.m_A, c->opt.nmax_A, false);
+}
+
+// Algorithm 2: y = D x_p - C A^{-1} B x_p, inner solve to delta_I
+template <typename T> static void apply_S(nbp_ctx *c, int vsel, const T *xp, T *y) {
+    Bufs<T> &Bf = BUF<T>(c);
+    do_spmv<T>(c, c->D, vsel, sargs(xp, y), EPI_SET, false);          // line 1: x_hat = D x_p (into y)
+    do_spmv<T>(c, c->B, vsel, sargs(xp, Bf.xbar), EPI_SET, false);    // line 2: x_bar = B x_p
+    GmResult R = solve_A<T>(c, vsel, Bf.xbar, Bf.xtil, c->opt.rtol_I);  // line 3
+    c->info.I_iters += R.its;
+    c->info.n_I_solves++;
+    do_spmv<T>(c, c->C, vsel, sargs(Bf.xtil, y), EPI_SUB, false);     // lines 4-5: y = x_hat - C x_tilde
+}
+
+// Algorithm 3: y = P_SCR^{-1} s (FP64 in/out; inner type T)
+template <typename T> static void apply_pscr(nbp_ctx *c, const double *s, double *y) {
+    const int vsel = vsel_of(c->opt.precision);
+    const long long N = c->N, nv = 3 * N;
+    Bufs<T> &Bf = BUF<T>(c);
+    convert<T, double>(Bf.sv, s, nv, c->s);
+    convert<T, double>(Bf.sp, s + nv, N, c->s);
+    if (c->opt.variant == 0) {
+        GmResult R1 = solve_A<T>(c, vsel, Bf.sv, Bf.yvh, c->opt.rtol_A);             // step 1
+        c->info.A_iters += R1.its;
+        c->info.n_A_solves++;
+        do_spmv<T>(c, c->C, vsel, sargs(Bf.yvh, Bf.sp), EPI_SUB, false);            // step 2: s_p -= C y_hat
+    }
+    auto opS = [&](const T *x, T *out) { apply_S<T>(c, vsel, x, out); };
+    GmResult R3;
+    if (c->opt.pc_S == 0) {
+        auto pcS = [&](const T *x, T *out) { vcycle<T>(c, c->HS, vsel, x, out); };
+        R3 = gmres<T>(c, KS<T>(c), N, opS, pcS, Bf.sp, Bf.yp, c->opt.rtol_S, c->opt.atol, c->opt.m_S, c->opt.nmax_S, false);
+    } else {
+        auto pcI = [&](const T *x, T *out) { copy<T>(out, x, N, c->s); };
+        R3 = gmres<T>(c, KS<T>(c), N, opS, pcI, Bf.sp, Bf.yp, c->opt.rtol_S, c->opt.atol, c->opt.m_S, c->opt.nmax_S, false);
+    }
+    c->info.S_iters += R3.its;                                                         // step 3
+    c->info.n_S_solves++;
+    do_spmv<T>(c, c->B, vsel, sargs(Bf.yp, Bf.sv), EPI_SUB, false);                   // step 4: s_v -= B y_p
+    GmResult R5 = solve_A<T>(c, vsel, Bf.sv, Bf.yv, c->opt.rtol_A);                   // step 5
+    c->info.A_iters += R5.its;
+    c->info.n_A_solves++;
+    convert<double, T>(y, Bf.yv, nv, c->s);
+    convert<double, T>(y + nv, Bf.yp, N, c->s);
+}
+
+// y = [[A, B], [C, D]] x in FP64
+static void apply_full(nbp_ctx *c, const double *x, double *y) {
+    const long long nv = 3LL * c->N;
+    apply_A<double>(c, 0, x, y);
+    do_spmv<double>(c, c->B, 0, sargs(x + nv, y), EPI_ADD, false);
+    do_spmv<double>(c, c->C, 0, sargs(x, y + nv), EPI_SET, false);
+    do_spmv<double>(c, c->D, 0, sargs(x + nv, y + nv), EPI_ADD, false);
+}
+
+static void prepare_inner(nbp_ctx *c) {
+    require(c->setup_done, NBP_ERR_STATE, "nbp: call nbp_setup before solving");
+    require(c->opt.precision <= c->setup_precision || c->opt.precision == 0, NBP_ERR_STATE,
+            "nbp: precision mode needs nbp_setup with that mode");
+    const long long N = c->N;
+    if (c->opt.precision == 0) {
+        c->B64.ensure(N, c->s);
+        c->prof.launches++;
+        k_recip<<<grid_exact(3 * N), 256, 0, c->s>>>(3 * N, c->diagA, c->B64.dinvA);
+        NBP_LAUNCHED();
+    } else {
+        c->B32.ensure(N, c->s);
+        c->B64.ensure(N, c->s);
+        c->prof.launches += 2;
+        k_recip<<<grid_exact(3 * N), 256, 0, c->s>>>(3 * N, c->diagA, c->B64.dinvA);
+        k_convert<float, double><<<grid_for(3 * N), 256, 0, c->s>>>(c->B32.dinvA, c->B64.dinvA, 3 * N);
+        NBP_LAUNCHED();
+    }
+}
+
+static void pscr(nbp_ctx *c, const double *s, double *y) {
+    if (c->opt.precision == 0) apply_pscr<double>(c, s, y);
+    else apply_pscr<float>(c, s, y);
+}
+
+// Outer FGMRES(m) + P_SCR (Sec. 3)
+static nbp_status nested_solve(nbp_ctx *c, const double *b, double *x) {
+    prepare_inner(c);
+    const long long n = 4LL * c->N;
+    if (!c->full_w) c->full_w = dmalloc<double>(n, c->s);
+    auto op = [&](const double *xx, double *yy) { apply_full(c, xx, yy); };
+    auto pc = [&](const double *ss, double *yy) { pscr(c, ss, yy); };
+    GmResult R = gmres<double>(c, c->Kout, n, op, pc, b, x, c->opt.rtol, c->opt.atol, c->opt.m, c->opt.nmax, true);
+    c->info.outer_iters = R.its;
+    c->info.rel_res_est = R.rel;
+    c->info.rel_res_true = R.rel_true;
+    c->info.status = R.conv ? NBP_OK : NBP_NOT_CONVERGED;
+    return R.conv ? NBP_OK : NBP_NOT_CONVERGED;
+}
+
+// ---------------------------------------------------------- create / setup
+__global__ void k_validate(int nbr, int nbc, const int *rp, const int *ci, long long nnz, int *bad) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i > nbr) return;
+    if (i == 0 && rp[0] != 0) atomicOr(bad, 1);
+    if (i == nbr) { if ((long long)rp[nbr] != nnz) atomicOr(bad, 2); return; }
+    const int a = rp[i], b = rp[i + 1];
+    if (b < a) { atomicOr(bad, 4); return; }
+    for (int e = a; e < b; ++e) {
+        const int j = ci[e];
+        if (j < 0 || j >= nbc) atomicOr(bad, 8);
+        if (e > a && ci[e - 1] >= j) atomicOr(bad, 16);
+    }
+}
+__global__ void k_finite(const double *v, long long n, int *bad) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        if (!isfinite(v[i])) atomicOr(bad, 32);
+}
+
+static void load_mat(nbp_ctx *c, DMat &M, const char *name, int nbr, int nbc, int br, int bc, const int32_t *rp,
+                     const int32_t *ci, const double *v) {
+    require(rp && ci && v, NBP_ERR_INVALID, std::string("nbp_create: null array in ") + name);
+    cudaStream_t s = c->s;
+    int nnz = 0;
+    NBP_CUDA(cudaMemcpyAsync(&nnz, rp + nbr, sizeof(int), cudaMemcpyDeviceToHost, s));
+    NBP_CUDA(cudaStreamSynchronize(s));
+    require(nnz >= 0, NBP_ERR_INVALID, std::string("nbp_create: negative nnz in ") + name);
+    M.nbr = nbr; M.nbc = nbc; M.br = br; M.bc = bc; M.nnz = nnz;
+    M.rp = dmalloc<int>(nbr + 1, s);
+    M.ci = dmalloc<int>(nnz, s);
+    M.v = dmalloc<double>((long long)nnz * br * bc, s);
+    NBP_CUDA(cudaMemcpyAsync(M.rp, rp, sizeof(int) * (nbr + 1), cudaMemcpyDeviceToDevice, s));
+    NBP_CUDA(cudaMemcpyAsync(M.ci, ci, sizeof(int) * (size_t)nnz, cudaMemcpyDeviceToDevice, s));
+    NBP_CUDA(cudaMemcpyAsync(M.v, v, sizeof(double) * (size_t)nnz * br * bc, cudaMemcpyDeviceToDevice, s));
+    int *bad = dmalloc<int>(1, s);
+    NBP_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
+    k_validate<<<grid_exact(nbr + 1), 256, 0, s>>>(nbr, nbc, M.rp, M.ci, nnz, bad);
+    k_finite<<<grid_for((long long)nnz * br * bc), 256, 0, s>>>(M.v, (long long)nnz * br * bc, bad);
+    NBP_LAUNCHED();
+    const int b = readback(bad, s);
+    dfree(bad, s);
+    require(b == 0, NBP_ERR_INVALID, std::string("nbp_create: malformed ") + name + " (code " + std::to_string(b) + ")");
+}
+
+// rank-one data per velocity block row (host-side reorganisation of the small outlet arrays)
+static void load_lowrank(nbp_ctx *c, const nbp_system *sys) {
+    LowRank &lr = c->lr;
+    cudaStream_t s = c->s;
+    lr.n_out = sys->n_out;
+    const int N = c->N;
+    lr.lr_rp = dmalloc<int>(N + 1, s);
+    if (lr.n_out <= 0) {
+        lr.n_out = 0;
+        NBP_CUDA(cudaMemsetAsync(lr.lr_rp, 0, sizeof(int) * (N + 1), s));
+        return;
+    }
+    require(sys->out_ptr && sys->r, NBP_ERR_INVALID, "nbp_create: outlet arrays missing");
+    std::vector<int> optr(lr.n_out + 1);
+    NBP_CUDA(cudaMemcpyAsync(optr.data(), sys->out_ptr, sizeof(int) * (lr.n_out + 1), cudaMemcpyDeviceToHost, s));
+    NBP_CUDA(cudaStreamSynchronize(s));
+    const int no = optr[lr.n_out];
+    require(optr[0] == 0 && no >= 0, NBP_ERR_INVALID, "nbp_create: bad out_ptr");
+    std::vector<int> oidx(no);
+    std::vector<double> oval(no);
+    if (no > 0) {
+        require(sys->out_idx && sys->out_val, NBP_ERR_INVALID, "nbp_create: outlet arrays missing");
+        NBP_CUDA(cudaMemcpyAsync(oidx.data(), sys->out_idx, sizeof(int) * no, cudaMemcpyDeviceToHost, s));
+        NBP_CUDA(cudaMemcpyAsync(oval.data(), sys->out_val, sizeof(double) * no, cudaMemcpyDeviceToHost, s));
+        NBP_CUDA(cudaStreamSynchronize(s));
+    }
+    lr.r_host.assign(sys->r, sys->r + lr.n_out);
+    for (int k = 0; k < lr.n_out; ++k) {
+        require(optr[k + 1] >= optr[k], NBP_ERR_INVALID, "nbp_create: out_ptr not monotone");
+        require(std::isfinite(lr.r_host[k]), NBP_ERR_INVALID, "nbp_create: non-finite resistance weight");
+    }
+    std::vector<int> cnt(N + 1, 0);
+    for (int q = 0; q < no; ++q) {
+        require(oidx[q] >= 0 && oidx[q] < 3 * N, NBP_ERR_INVALID, "nbp_create: outlet index out of range");
+        require(std::isfinite(oval[q]), NBP_ERR_INVALID, "nbp_create: non-finite outlet value");
+        cnt[oidx[q] / 3 + 1]++;
+    }
+    for (int i = 0; i < N; ++i) cnt[i + 1] += cnt[i];
+    std::vector<int> lk(no), lc(no), fillp(cnt.begin(), cnt.end() - 1);
+    std::vector<double> lv(no);
+    for (int k = 0; k < lr.n_out; ++k)      // k ascending inside each row
+        for (int q = optr[k]; q < optr[k + 1]; ++q) {
+            const int p = fillp[oidx[q] / 3]++;
+            lk[p] = k; lc[p] = oidx[q] % 3; lv[p] = oval[q];
+        }
+    lr.optr = dmalloc<int>(lr.n_out + 1, s);
+    lr.oidx = dmalloc<int>(no, s);
+    lr.oval = dmalloc<double>(no, s);
+    lr.r = dmalloc<double>(lr.n_out, s);
+    lr.f = dmalloc<double>(lr.n_out, s);
+    lr.lr_k = dmalloc<int>(no, s); lr.lr_c = dmalloc<int>(no, s); lr.lr_val = dmalloc<double>(no, s);
+    NBP_CUDA(cudaMemcpyAsync(lr.optr, optr.data(), sizeof(int) * (lr.n_out + 1), cudaMemcpyHostToDevice, s));
+    NBP_CUDA(cudaMemcpyAsync(lr.oidx, oidx.data(), sizeof(int) * no, cudaMemcpyHostToDevice, s));
+    NBP_CUDA(cudaMemcpyAsync(lr.oval, oval.data(), sizeof(double) * no, cudaMemcpyHostToDevice, s));
+    NBP_CUDA(cudaMemcpyAsync(lr.r, lr.r_host.data(), sizeof(double) * lr.n_out, cudaMemcpyHostToDevice, s));
+    NBP_CUDA(cudaMemcpyAsync(lr.lr_rp, cnt.data(), sizeof(int) * (N + 1), cudaMemcpyHostToDevice, s));
+    NBP_CUDA(cudaMemcpyAsync(lr.lr_k, lk.data(), sizeof(int) * no, cudaMemcpyHostToDevice, s));
+    NBP_CUDA(cudaMemcpyAsync(lr.lr_c, lc.data(), sizeof(int) * no, cudaMemcpyHostToDevice, s));
+    NBP_CUDA(cudaMemcpyAsync(lr.lr_val, lv.data(), sizeof(double) * no, cudaMemcpyHostToDevice, s));
+    NBP_CUDA(cudaStreamSynchronize(s));
+}
+
+static void free_lowrank(LowRank &lr, cudaStream_t s) {
+    dfree(lr.optr, s); dfree(lr.oidx, s); dfree(lr.oval, s); dfree(lr.r, s); dfree(lr.f, s);
+    dfree(lr.lr_rp, s); dfree(lr.lr_k, s); dfree(lr.lr_c, s); dfree(lr.lr_val, s);
+    lr = LowRank();
+}
+
+static void do_setup(nbp_ctx *c) {
+    auto t0 = std::chrono::steady_clock::now();
+    cudaStream_t s = c->s;
+    const int prec = c->opt.precision;
+    if (!c->diagA) c->diagA = dmalloc<double>(3LL * c->N, s);
+    amg_build(c->HA, c->A, c->opt, prec, s);
+    build_shat(c->A, c->B, c->C, c->D, c->lr, c->N, c->Shat, c->diagA, s);
+    amg_build(c->HS, c->Shat, c->opt, prec, s);
+    if (prec >= 1) {
+        make_lowcopies(c->A, prec, s);
+        make_lowcopies(c->B, prec, s);
+        make_lowcopies(c->C, prec, s);
+        make_lowcopies(c->D, prec, s);
+    }
+    NBP_CUDA(cudaStreamSynchronize(s));
+    c->setup_done = true;
+    c->setup_precision = prec;
+    c->setup_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (c->tctx) { c->tctx->setup_done = false; }
+}
+
+static void destroy_ctx(nbp_ctx *c) {
+    if (!c) return;
+    cudaSetDevice(c->dev);
+    cudaStream_t s = c->s;
+    if (c->tctx) destroy_ctx(c->tctx);
+    dmat_free(c->A, s); dmat_free(c->B, s); dmat_free(c->C, s); dmat_free(c->D, s); dmat_free(c->Shat, s);
+    free_lowrank(c->lr, s);
+    hier_free(c->HA, s); hier_free(c->HS, s);
+    dfree(c->diagA, s); dfree(c->full_w, s);
+    c->Kout.release(s); c->KA64.release(s); c->KS64.release(s); c->KA32.release(s); c->KS32.release(s);
+    c->B64.release(s); c->B32.release(s);
+    cudaStreamSynchronize(s);
+    if (c->hst && !c->is_transposed) cudaFreeHost(c->hst);
+    delete c;
+}
+
+// transposed tangent [[A^T, C^T], [B^T, D^T]] sharing the stream and outlets
+static nbp_ctx *make_transposed(nbp_ctx *c) {
+    nbp_ctx *t = new nbp_ctx();
+    t->dev = c->dev; t->s = c->s; t->N = c->N; t->opt = c->opt; t->hst = c->hst; t->is_transposed = true;
+    try {
+        transpose_dmat(c->A, t->A, c->s);
+        transpose_dmat(c->C, t->B, c->s);   // C^T has 3x1 blocks: plays B
+        transpose_dmat(c->B, t->C, c->s);   // B^T has 1x3 blocks: plays C
+        transpose_dmat(c->D, t->D, c->s);
+        // same outlets and weights (the rank-one term is symmetric)
+        LowRank &a = c->lr, &b = t->lr;
+        b.n_out = a.n_out;
+        b.r_host = a.r_host;
+        const int N = c->N;
+        b.lr_rp = dmalloc<int>(N + 1, c->s);
+        NBP_CUDA(cudaMemcpyAsync(b.lr_rp, a.lr_rp, sizeof(int) * (N + 1), cudaMemcpyDeviceToDevice, c->s));
+        if (a.n_out > 0) {
+            int no = 0;
+            NBP_CUDA(cudaMemcpyAsync(&no, a.optr + a.n_out, sizeof(int), cudaMemcpyDeviceToHost, c->s));
+            NBP_CUDA(cudaStreamSynchronize(c->s));
+            b.optr = dmalloc<int>(a.n_out + 1, c->s);
+            b.oidx = dmalloc<int>(no, c->s); b.oval = dmalloc<double>(no, c->s);
+            b.r = dmalloc<double>(a.n_out, c->s); b.f = dmalloc<double>(a.n_out, c->s);
+            b.lr_k = dmalloc<int>(no, c->s); b.lr_c = dmalloc<int>(no, c->s); b.lr_val = dmalloc<double>(no, c->s);
+            NBP_CUDA(cudaMemcpyAsync(b.optr, a.optr, sizeof(int) * (a.n_out + 1), cudaMemcpyDeviceToDevice, c->s));
+            NBP_CUDA(cudaMemcpyAsync(b.oidx, a.oidx, sizeof(int) * no, cudaMemcpyDeviceToDevice, c->s));
+            NBP_CUDA(cudaMemcpyAsync(b.oval, a.oval, sizeof(double) * no, cudaMemcpyDeviceToDevice, c->s));
+            NBP_CUDA(cudaMemcpyAsync(b.r, a.r, sizeof(double) * a.n_out, cudaMemcpyDeviceToDevice, c->s));
+            NBP_CUDA(cudaMemcpyAsync(b.lr_k, a.lr_k, sizeof(int) * no, cudaMemcpyDeviceToDevice, c->s));
+            NBP_CUDA(cudaMemcpyAsync(b.lr_c, a.lr_c, sizeof(int) * no, cudaMemcpyDeviceToDevice, c->s));
+            NBP_CUDA(cudaMemcpyAsync(b.lr_val, a.lr_val, sizeof(double) * no, cudaMemcpyDeviceToDevice, c->s));
+        }
+    } catch (...) {
+        destroy_ctx(t);
+        throw;
+    }
+    return t;
+}
+
+// dL/dr_k = -(lambda_v . a^k)(a^k . x_v): both inner products on the device
+__global__ void k_adj_grad(const int *optr, const int *oidx, const double *oval, const double *lam, const double *x,
+                           double *out) {
+    __shared__ double r1[8], r2[8];
+    const int k = blockIdx.x;
+    double s1 = 0.0, s2 = 0.0;
+    for (int q = optr[k] + threadIdx.x; q < optr[k + 1]; q += blockDim.x) {
+        s1 += oval[q] * lam[oidx[q]];
+        s2 += oval[q] * x[oidx[q]];
+    }
+    s1 = warp_sum(s1); s2 = warp_sum(s2);
+    if ((threadIdx.x & 31) == 0) { r1[threadIdx.x >> 5] = s1; r2[threadIdx.x >> 5] = s2; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { a += r1[w]; b += r2[w]; }
+        out[k] = -a * b;
+    }
+}
+
+static void finish_profile(nbp_ctx *c) {
+    nbp_profile_info &p = c->pinfo;
+    p = nbp_profile_info{};
+    p.kernel_launches = c->prof.launches;
+    if (!c->prof.on) return;
+    NBP_CUDA(cudaStreamSynchronize(c->s));
+    for (auto &r : c->prof.recs) {
+        float ms = 0.f;
+        NBP_CUDA(cudaEventElapsedTime(&ms, c->prof.pool[r.e0], c->prof.pool[r.e0 + 1]));
+        if (r.cat == CAT_SPMV || r.cat == CAT_SPMV_A0) { p.spmv_ms += ms; p.spmv_bytes += r.bytes; p.spmv_launches++; }
+        if (r.cat == CAT_SPMV_A0) { p.a0_ms += ms; p.a0_bytes += r.bytes; p.a0_launches++; }
+        if (r.cat == CAT_ARNOLDI) { p.arnoldi_ms += ms; p.arnoldi_bytes += r.bytes; p.arnoldi_launches++; }
+        if (r.cat == CAT_VCYCLE) p.vcycle_ms += ms;
+    }
+}
+
+static void begin_call(nbp_ctx *c) {
+    NBP_CUDA(cudaSetDevice(c->dev));
+    c->prof.used = 0;
+    c->prof.recs.clear();
+    c->prof.launches = 0;
+}
+
+}  // namespace nbp
+
+// =================================================================== C ABI
+using namespace nbp;
+
+#define NBP_API_BEGIN(ctx) \
+    if (!(ctx)) return NBP_ERR_INVALID; \
+    try {
+#define NBP_API_END(ctx)                                  \
+    }                                                     \
+    catch (const nbp::Error &e) {                         \
+        (ctx)->err = e.msg;                               \
+        return e.st;                                      \
+    }                                                     \
+    catch (const std::exception &e) {                     \
+        (ctx)->err = e.what();                            \
+        return NBP_ERR_CUDA;                              \
+    }
+
+extern "C" {
+
+void nbp_default_options(nbp_options *o) {
+    if (!o) return;
+    o->rtol = 1e-8; o->rtol_A = 1e-3; o->rtol_S = 1e-2; o->rtol_I = 1e-2; o->atol = 1e-50;
+    o->m = 200; o->m_A = 200; o->m_S = 200; o->nmax = 200; o->nmax_A = 200; o->nmax_S = 200;
+    o->precision = 0; o->pc_A = 0; o->pc_S = 0; o->variant = 0;
+    o->amg_max_levels = 5; o->amg_coarse_max = 300; o->cheb_degree = 2; o->theta = 0.0064;
+}
+
+static nbp_status check_options(const nbp_options *o, std::string &msg) {
+    if (!(o->rtol >= 0 && o->rtol_A >= 0 && o->rtol_S >= 0 && o->rtol_I >= 0 && o->atol >= 0)) { msg = "negative tolerance"; return NBP_ERR_INVALID; }
+    if (o->m < 1 || o->m_A < 1 || o->m_S < 1 || o->nmax < 1 || o->nmax_A < 1 || o->nmax_S < 1) { msg = "restart/n_max < 1"; return NBP_ERR_INVALID; }
+    if (o->precision < 0 || o->precision > 2 || o->pc_A < 0 || o->pc_A > 1 || o->pc_S < 0 || o->pc_S > 1 || o->variant < 0 || o->variant > 1) { msg = "bad mode switch"; return NBP_ERR_INVALID; }
+    if (o->cheb_degree < 0 || o->cheb_degree > 8 || o->amg_max_levels < 1) { msg = "bad AMG option"; return NBP_ERR_INVALID; }
+    return NBP_OK;
+}
+
+nbp_status nbp_create(nbp_ctx **out, const nbp_system *sys, const nbp_options *opt, void *stream) {
+    if (!out || !sys) return NBP_ERR_INVALID;
+    *out = nullptr;
+    nbp_ctx *c = new nbp_ctx();
+    try {
+        NBP_CUDA(cudaGetDevice(&c->dev));
+        c->s = (cudaStream_t)stream;
+        nbp_default_options(&c->opt);
+        if (opt) c->opt = *opt;
+        std::string m;
+        nbp_status st = check_options(&c->opt, m);
+        require(st == NBP_OK, st, "nbp_create: " + m);
+        require(sys->n_nodes > 0, NBP_ERR_INVALID, "nbp_create: n_nodes must be positive");
+        c->N = sys->n_nodes;
+        NBP_CUDA(cudaMallocHost(&c->hst, sizeof(GmState)));
+        load_mat(c, c->A, "A", c->N, c->N, 3, 3, sys->a_rowptr, sys->a_col, sys->a_val);
+        load_mat(c, c->B, "B", c->N, c->N, 3, 1, sys->b_rowptr, sys->b_col, sys->b_val);
+        load_mat(c, c->C, "C", c->N, c->N, 1, 3, sys->c_rowptr, sys->c_col, sys->c_val);
+        load_mat(c, c->D, "D", c->N, c->N, 1, 1, sys->d_rowptr, sys->d_col, sys->d_val);
+        load_lowrank(c, sys);
+    } catch (const nbp::Error &e) {
+        fprintf(stderr, "nbp_create: %s\n", e.msg.c_str());
+        destroy_ctx(c);
+        return e.st;
+    } catch (const std::exception &e) {
+        fprintf(stderr, "nbp_create: %s\n", e.what());
+        destroy_ctx(c);
+        return NBP_ERR_INVALID;
+    }
+    *out = c;
+    return NBP_OK;
+}
+
+nbp_status nbp_setup(nbp_ctx *c) {
+    NBP_API_BEGIN(c)
+    begin_call(c);
+    do_setup(c);
+    return NBP_OK;
+    NBP_API_END(c)
+}
+
+nbp_status nbp_set_resistances(nbp_ctx *c, const double *r) {
+    NBP_API_BEGIN(c)
+    begin_call(c);
+    if (c->lr.n_out == 0) return NBP_OK;
+    require(r != nullptr, NBP_ERR_INVALID, "nbp_set_resistances: null r");
+    for (int k = 0; k < c->lr.n_out; ++k) require(std::isfinite(r[k]), NBP_ERR_INVALID, "nbp_set_resistances: non-finite r");
+    c->lr.r_host.assign(r, r + c->lr.n_out);
+    NBP_CUDA(cudaMemcpyAsync(c->lr.r, c->lr.r_host.data(), sizeof(double) * c->lr.n_out, cudaMemcpyHostToDevice, c->s));
+    NBP_CUDA(cudaStreamSynchronize(c->s));
+    if (c->tctx) {
+        c->tctx->lr.r_host = c->lr.r_host;
+        NBP_CUDA(cudaMemcpyAsync(c->tctx->lr.r, c->lr.r, sizeof(double) * c->lr.n_out, cudaMemcpyDeviceToDevice, c->s));
+        c->tctx->setup_done = false;
+    }
+    return NBP_OK;
+    NBP_API_END(c)
+}
+
+static nbp_status solve_common(nbp_ctx *c, const double *b, double *x, const nbp_options *opt, nbp_info *info) {
+    nbp_options saved = c->opt;
+    if (opt) {
+        std::string m;
+        nbp_status st = check_options(opt, m);
+        require(st == NBP_OK, st, "nbp_solve: " + m);
+        c->opt = *opt;
+    }
+    memset(&c->info, 0, sizeof(c->info));
+    auto t0 = std::chrono::steady_clock::now();
+    nbp_status st;
+    try {
+        st = nested_solve(c, b, x);
+    } catch (...) {
+        c->opt = saved;
+        throw;
+    }
+    NBP_CUDA(cudaStreamSynchronize(c->s));
+    c->info.solve_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    c->info.setup_s = c->setup_s;
+    c->opt = saved;
+    finish_profile(c);
+    if (info) *info = c->info;
+    return st;
+}
+
+nbp_status nbp_solve(nbp_ctx *c, const double *b, double *x, const nbp_options *opt, nbp_info *info) {
+    NBP_API_BEGIN(c)
+    require(b && x, NBP_ERR_INVALID, "nbp_solve: null vector");
+    begin_call(c);
+    return solve_common(c, b, x, opt, info);
+    NBP_API_END(c)
+}
+
+nbp_status nbp_solve_host(nbp_ctx *c, const double *bh, double *xh, const nbp_options *opt, nbp_info *info) {
+    NBP_API_BEGIN(c)
+    require(bh && xh, NBP_ERR_INVALID, "nbp_solve_host: null vector");
+    begin_call(c);
+    const long long n = 4LL * c->N;
+    double *b = dmalloc<double>(n, c->s), *x = dmalloc<double>(n, c->s);
+    nbp_status st;
+    try {
+        NBP_CUDA(cudaMemcpyAsync(b, bh, sizeof(double) * n, cudaMemcpyHostToDevice, c->s));
+        st = solve_common(c, b, x, opt, info);
+        NBP_CUDA(cudaMemcpyAsync(xh, x, sizeof(double) * n, cudaMemcpyDeviceToHost, c->s));
+        NBP_CUDA(cudaStreamSynchronize(c->s));
+    } catch (...) {
+        dfree(b, c->s); dfree(x, c->s);
+        throw;
+    }
+    dfree(b, c->s); dfree(x, c->s);
+    return st;
+    NBP_API_END(c)
+}
+
+nbp_status nbp_adjoint(nbp_ctx *c, const double *g, const double *x, double *lambda, double *dL_dr, nbp_info *info) {
+    NBP_API_BEGIN(c)
+    require(g && x && lambda, NBP_ERR_INVALID, "nbp_adjoint: null vector");
+    begin_call(c);
+    require(c->setup_done, NBP_ERR_STATE, "nbp_adjoint: call nbp_setup first");
+    if (!c->tctx) c->tctx = make_transposed(c);
+    nbp_ctx *t = c->tctx;
+    t->opt = c->opt;
+    if (!t->setup_done) do_setup(t);
+    t->prof.on = c->prof.on;
+    begin_call(t);
+    nbp_status st;
+    try {
+        st = solve_common(t, g, lambda, nullptr, info);
+    } catch (const nbp::Error &e) {
+        c->err = e.msg;
+        return e.st;
+    }
+    if (dL_dr && c->lr.n_out > 0) {
+        double *d = dmalloc<double>(c->lr.n_out, c->s);
+        k_adj_grad<<<c->lr.n_out, 256, 0, c->s>>>(c->lr.optr, c->lr.oidx, c->lr.oval, lambda, x, d);
+        NBP_LAUNCHED();
+        NBP_CUDA(cudaMemcpyAsync(dL_dr, d, sizeof(double) * c->lr.n_out, cudaMemcpyDeviceToHost, c->s));
+        NBP_CUDA(cudaStreamSynchronize(c->s));
+        dfree(d, c->s);
+    }
+    c->pinfo = t->pinfo;
+    return st;
+    NBP_API_END(c)
+}
+
+nbp_status nbp_destroy(nbp_ctx *c) {
+    if (!c) return NBP_ERR_INVALID;
+    destroy_ctx(c);
+    return NBP_OK;
+}
+
+const char *nbp_last_error(const nbp_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+nbp_status nbp_apply_A(nbp_ctx *c, const void *x, void *y, int32_t precision) {
+    NBP_API_BEGIN(c)
+    require(x && y, NBP_ERR_INVALID, "nbp_apply_A: null vector");
+    begin_call(c);
+    if (precision == 0) apply_A<double>(c, 0, (const double *)x, (double *)y);
+    else {
+        require(c->setup_done && c->setup_precision >= precision, NBP_ERR_STATE, "nbp_apply_A: setup with that precision first");
+        apply_A<float>(c, vsel_of(precision), (const float *)x, (float *)y);
+    }
+    NBP_CUDA(cudaStreamSynchronize(c->s));
+    finish_profile(c);
+    return NBP_OK;
+    NBP_API_END(c)
+}
+
+nbp_status nbp_apply_full(nbp_ctx *c, const double *x, double *y) {
+    NBP_API_BEGIN(c)
+    require(x && y, NBP_ERR_INVALID, "nbp_apply_full: null vector");
+    begin_call(c);
+    apply_full(c, x, y);
+    NBP_CUDA(cudaStreamSynchronize(c->s));
+    return NBP_OK;
+    NBP_API_END(c)
+}
+
+nbp_status nbp_apply_S(nbp_ctx *c, const double *xp, double *y) {
+    NBP_API_BEGIN(c)
+    require(xp && y, NBP_ERR_INVALID, "nbp_apply_S: null vector");
+    begin_call(c);
+    nbp_options saved = c->opt;
+    c->opt.precision = 0;
+    try { prepare_inner(c); apply_S<double>(c, 0, xp, y); } catch (...) { c->opt = saved; throw; }
+    c->opt = saved;
+    NBP_CUDA(cudaStreamSynchronize(c->s));
+    return NBP_OK;
+    NBP_API_END(c)
+}
+
+nbp_status nbp_apply_pscr(nbp_ctx *c, const double *sv, double *y) {
+    NBP_API_BEGIN(c)
+    require(sv && y, NBP_ERR_INVALID, "nbp_apply_pscr: null vector");
+    begin_call(c);
+    memset(&c->info, 0, sizeof(c->info));
+    prepare_inner(c);
+    pscr(c, sv, y);
+    NBP_CUDA(cudaStreamSynchronize(c->s));
+    return NBP_OK;
+    NBP_API_END(c)
+}
+
+nbp_status nbp_solve_A(nbp_ctx *c, const double *sv, double *y, double rtol, int32_t *iters) {
+    NBP_API_BEGIN(c)
+    require(sv && y, NBP_ERR_INVALID, "nbp_solve_A: null vector");
+    begin_call(c);
+    nbp_options saved = c->opt;
+    c->opt.precision = 0;
+    GmResult R;
+    try { prepare_inner(c); R = solve_A<double>(c, 0, sv, y, rtol); } catch (...) { c->opt = saved; throw; }
+    c->opt = saved;
+    if (iters) *iters = R.its;
+    NBP_CUDA(cudaStreamSynchronize(c->s));
+    return R.conv ? NBP_OK : NBP_NOT_CONVERGED;
+    NBP_API_END(c)
+}
+
+nbp_status nbp_vcycle(nbp_ctx *c, int32_t which, const double *b, double *x) {
+    NBP_API_BEGIN(c)
+    require(b && x, NBP_ERR_INVALID, "nbp_vcycle: null vector");
+    require(c->setup_done, NBP_ERR_STATE, "nbp_vcycle: call nbp_setup first");
+    begin_call(c);
+    vcycle<double>(c, which ? c->HS : c->HA, 0, b, x);
+    NBP_CUDA(cudaStreamSynchronize(c->s));
+    return NBP_OK;
+    NBP_API_END(c)
+}
+
+int32_t nbp_amg_level_sizes(nbp_ctx *c, int32_t which, int32_t *rows, int64_t *nnz, int32_t max_levels) {
+    if (!c || !c->setup_done) return 0;
+    Hier &H = which ? c->HS : c->HA;
+    for (int l = 0; l < H.nlev && l < max_levels; ++l) {
+        if (rows) rows[l] = H.L[l].M.nbr;
+        if (nnz) nnz[l] = H.L[l].M.nnz;
+    }
+    return H.nlev;
+}
+
+nbp_status nbp_amg_level_get(nbp_ctx *c, int32_t which, int32_t l, int32_t *rowptr, int32_t *col, double *val, int32_t *agg,
+                             double *rho) {
+    NBP_API_BEGIN(c)
+    require(c->setup_done, NBP_ERR_STATE, "nbp_amg_level_get: call nbp_setup first");
+    Hier &H = which ? c->HS : c->HA;
+    require(l >= 0 && l < H.nlev, NBP_ERR_INVALID, "nbp_amg_level_get: level out of range");
+    Level &L = H.L[l];
+    cudaStream_t s = c->s;
+    if (rowptr) NBP_CUDA(cudaMemcpyAsync(rowptr, L.M.rp, sizeof(int) * (L.M.nbr + 1), cudaMemcpyDeviceToHost, s));
+    if (col) NBP_CUDA(cudaMemcpyAsync(col, L.M.ci, sizeof(int) * L.M.nnz, cudaMemcpyDeviceToHost, s));
+    if (val) NBP_CUDA(cudaMemcpyAsync(val, L.M.v, sizeof(double) * L.M.nnz * L.M.bb(), cudaMemcpyDeviceToHost, s));
+    if (agg && L.agg) NBP_CUDA(cudaMemcpyAsync(agg, L.agg, sizeof(int) * L.M.nbr, cudaMemcpyDeviceToHost, s));
+    if (rho) *rho = L.rho;
+    NBP_CUDA(cudaStreamSynchronize(s));
+    return NBP_OK;
+    NBP_API_END(c)
+}
+
+int64_t nbp_shat_nnz(nbp_ctx *c) { return (c && c->setup_done) ? c->Shat.nnz : -1; }
+
+nbp_status nbp_shat_get(nbp_ctx *c, int32_t *rowptr, int32_t *col, double *val) {
+    NBP_API_BEGIN(c)
+    require(c->setup_done, NBP_ERR_STATE, "nbp_shat_get: call nbp_setup first");
+    cudaStream_t s = c->s;
+    if (rowptr) NBP_CUDA(cudaMemcpyAsync(rowptr, c->Shat.rp, sizeof(int) * (c->N + 1), cudaMemcpyDeviceToHost, s));
+    if (col) NBP_CUDA(cudaMemcpyAsync(col, c->Shat.ci, sizeof(int) * c->Shat.nnz, cudaMemcpyDeviceToHost, s));
+    if (val) NBP_CUDA(cudaMemcpyAsync(val, c->Shat.v, sizeof(double) * c->Shat.nnz, cudaMemcpyDeviceToHost, s));
+    NBP_CUDA(cudaStreamSynchronize(s));
+    return NBP_OK;
+    NBP_API_END(c)
+}
+
+nbp_status nbp_profile(nbp_ctx *c, int32_t enable) {
+    if (!c) return NBP_ERR_INVALID;
+    c->prof.on = enable != 0;
+    if (c->tctx) c->tctx->prof.on = c->prof.on;
+    return NBP_OK;
+}
+
+nbp_status nbp_profile_get(nbp_ctx *c, nbp_profile_info *out) {
+    if (!c || !out) return NBP_ERR_INVALID;
+    *out = c->pinfo;
+    return NBP_OK;
+}
+
+}  // extern "C"

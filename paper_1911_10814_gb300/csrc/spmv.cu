@@ -1,0 +1,91 @@
+// spmv.cu -- instantiation and dispatch of the block-sparse product kernels
+// (A: 3x3, B: 3x1, C: 1x3, D / S_hat: 1x1 blocks) for FP64, FP32 and BF16
+// values, FP64 or FP32 vectors, and the fused epilogues.
+#include "kernels.cuh"
+#include "spmv.cuh"
+
+namespace nbp {
+
+template <int BR, int BC, int G, typename VT, typename XT>
+static void launch_epi(const SpmvArgs &a, int epi, bool lr, cudaStream_t s) {
+    const long long threads = (long long)a.nbr * G;
+    const unsigned grid = grid_exact(threads);
+    switch (epi) {
+    case EPI_SET:
+        if constexpr (BR == 3 && BC == 3) {
+            if (lr) { k_bspmv<BR, BC, G, VT, XT, EPI_SET, true><<<grid, 256, 0, s>>>(a); break; }
+        }
+        k_bspmv<BR, BC, G, VT, XT, EPI_SET, false><<<grid, 256, 0, s>>>(a);
+        break;
+    case EPI_ADD: k_bspmv<BR, BC, G, VT, XT, EPI_ADD, false><<<grid, 256, 0, s>>>(a); break;
+    case EPI_SUB: k_bspmv<BR, BC, G, VT, XT, EPI_SUB, false><<<grid, 256, 0, s>>>(a); break;
+    case EPI_RES:
+        if constexpr (BR == BC) { k_bspmv<BR, BC, G, VT, XT, EPI_RES, false><<<grid, 256, 0, s>>>(a); break; }
+        throw Error{NBP_ERR_INVALID, "spmv: residual epilogue needs square blocks"};
+    case EPI_CHEB:
+        if constexpr (BR == BC) { k_bspmv<BR, BC, G, VT, XT, EPI_CHEB, false><<<grid, 256, 0, s>>>(a); break; }
+        throw Error{NBP_ERR_INVALID, "spmv: Chebyshev epilogue needs square blocks"};
+    default: throw Error{NBP_ERR_INVALID, "spmv: unknown epilogue"};
+    }
+    NBP_LAUNCHED();
+}
+
+template <int BR, int BC, typename VT, typename XT>
+static void launch_g(const SpmvArgs &a, int G, int epi, bool lr, cudaStream_t s) {
+    if constexpr (BR == BC) {
+        switch (G) {
+        case 4: launch_epi<BR, BC, 4, VT, XT>(a, epi, lr, s); return;
+        case 8: launch_epi<BR, BC, 8, VT, XT>(a, epi, lr, s); return;
+        case 16: launch_epi<BR, BC, 16, VT, XT>(a, epi, lr, s); return;
+        default: launch_epi<BR, BC, 32, VT, XT>(a, epi, lr, s); return;
+        }
+    } else {
+        launch_epi<BR, BC, 8, VT, XT>(a, epi, lr, s);
+    }
+}
+
+template <int BR, int BC, typename XT>
+static void launch_vt(const DMat &M, int vsel, SpmvArgs a, int G, int epi, bool lr, cudaStream_t s) {
+    if constexpr (sizeof(XT) == 8) {
+        require(vsel == 0, NBP_ERR_INVALID, "spmv: FP64 vectors need FP64 values");
+        a.val = M.v;
+        launch_g<BR, BC, double, double>(a, G, epi, lr, s);
+    } else {
+        if (vsel == 2) {
+            require(M.v16 != nullptr, NBP_ERR_STATE, "spmv: BF16 values not built (run setup with precision 2)");
+            a.val = M.v16;
+            launch_g<BR, BC, __nv_bfloat16, float>(a, G, epi, lr, s);
+        } else {
+            require(M.v32 != nullptr, NBP_ERR_STATE, "spmv: FP32 values not built (run setup with precision >= 1)");
+            a.val = M.v32;
+            launch_g<BR, BC, float, float>(a, G, epi, lr, s);
+        }
+    }
+}
+
+int choose_group(const DMat &M) {
+    const double per_row = M.nbr ? (double)M.nnz * M.bb() / M.nbr : 0.0;
+    if (per_row <= 10) return 4;
+    if (per_row <= 40) return 8;
+    if (per_row <= 160) return 16;
+    return 32;
+}
+
+template <typename XT>
+void spmv(const DMat &M, int vsel, SpmvArgs a, int epi, bool lr, cudaStream_t s, int G) {
+    a.nbr = M.nbr;
+    a.rp = M.rp;
+    a.ci = M.ci;
+    if (a.nbr == 0) return;
+    if (G <= 0) G = choose_group(M);
+    if (M.br == 3 && M.bc == 3) launch_vt<3, 3, XT>(M, vsel, a, G, epi, lr, s);
+    else if (M.br == 3 && M.bc == 1) launch_vt<3, 1, XT>(M, vsel, a, G, epi, lr, s);
+    else if (M.br == 1 && M.bc == 3) launch_vt<1, 3, XT>(M, vsel, a, G, epi, lr, s);
+    else if (M.br == 1 && M.bc == 1) launch_vt<1, 1, XT>(M, vsel, a, G, epi, lr, s);
+    else throw Error{NBP_ERR_INVALID, "spmv: unsupported block shape"};
+}
+
+template void spmv<double>(const DMat &, int, SpmvArgs, int, bool, cudaStream_t, int);
+template void spmv<float>(const DMat &, int, SpmvArgs, int, bool, cudaStream_t, int);
+
+}  // namespace nbp

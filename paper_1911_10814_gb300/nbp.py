@@ -1,0 +1,316 @@
+"""ctypes binding of libnbp (include/nbp.h): argument marshalling only.
+
+Every function of the C ABI is exposed under its own name; ``Solver`` wraps
+one context for a tangent given as numpy arrays (the format of the ``synth``
+package: shared or per-block patterns, outlet vectors, weights r_k) and moves
+them to device memory with PyTorch.  All arithmetic of the method runs in the
+library's CUDA kernels; there is no fallback: without the built library or a
+CUDA device every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+
+class nbp_system(ctypes.Structure):
+    _fields_ = [("n_nodes", ctypes.c_int32)] + [
+        (f"{b}_{f}", t) for b in "abcd" for f, t in (("rowptr", ctypes.c_void_p), ("col", ctypes.c_void_p),
+                                                     ("val", ctypes.c_void_p))
+    ] + [("n_out", ctypes.c_int32), ("out_ptr", ctypes.c_void_p), ("out_idx", ctypes.c_void_p),
+         ("out_val", ctypes.c_void_p), ("r", ctypes.c_void_p)]
+
+
+class nbp_options(ctypes.Structure):
+    _fields_ = [
+        ("rtol", ctypes.c_double), ("rtol_A", ctypes.c_double), ("rtol_S", ctypes.c_double),
+        ("rtol_I", ctypes.c_double), ("atol", ctypes.c_double),
+        ("m", ctypes.c_int32), ("m_A", ctypes.c_int32), ("m_S", ctypes.c_int32),
+        ("nmax", ctypes.c_int32), ("nmax_A", ctypes.c_int32), ("nmax_S", ctypes.c_int32),
+        ("precision", ctypes.c_int32), ("pc_A", ctypes.c_int32), ("pc_S", ctypes.c_int32),
+        ("variant", ctypes.c_int32), ("amg_max_levels", ctypes.c_int32), ("amg_coarse_max", ctypes.c_int32),
+        ("cheb_degree", ctypes.c_int32), ("theta", ctypes.c_double),
+    ]
+
+
+class nbp_info(ctypes.Structure):
+    _fields_ = [
+        ("outer_iters", ctypes.c_int32),
+        ("A_iters", ctypes.c_int64), ("S_iters", ctypes.c_int64), ("I_iters", ctypes.c_int64),
+        ("n_A_solves", ctypes.c_int64), ("n_I_solves", ctypes.c_int64), ("n_S_solves", ctypes.c_int64),
+        ("rel_res_est", ctypes.c_double), ("rel_res_true", ctypes.c_double),
+        ("setup_s", ctypes.c_double), ("solve_s", ctypes.c_double), ("status", ctypes.c_int32),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class nbp_profile_info(ctypes.Structure):
+    _fields_ = [
+        ("spmv_ms", ctypes.c_double), ("spmv_bytes", ctypes.c_double),
+        ("arnoldi_ms", ctypes.c_double), ("arnoldi_bytes", ctypes.c_double),
+        ("a0_ms", ctypes.c_double), ("a0_bytes", ctypes.c_double),
+        ("vcycle_ms", ctypes.c_double),
+        ("spmv_launches", ctypes.c_int64), ("arnoldi_launches", ctypes.c_int64), ("a0_launches", ctypes.c_int64),
+        ("kernel_launches", ctypes.c_int64),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+STATUS = {0: "NBP_OK", 1: "NBP_ERR_INVALID", 2: "NBP_ERR_CUDA", 3: "NBP_ERR_OOM", 4: "NBP_NOT_CONVERGED",
+          5: "NBP_ERR_BREAKDOWN", 6: "NBP_ERR_NAN", 7: "NBP_ERR_TIMEOUT", 8: "NBP_ERR_STATE"}
+
+# name -> (restype, argtypes)
+_vp, _i32, _i64, _d = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+SIGNATURES = {
+    "nbp_default_options": (None, [ctypes.POINTER(nbp_options)]),
+    "nbp_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.POINTER(nbp_system), ctypes.POINTER(nbp_options), _vp]),
+    "nbp_setup": (ctypes.c_int, [_vp]),
+    "nbp_set_resistances": (ctypes.c_int, [_vp, ctypes.POINTER(_d)]),
+    "nbp_solve": (ctypes.c_int, [_vp, _vp, _vp, ctypes.POINTER(nbp_options), ctypes.POINTER(nbp_info)]),
+    "nbp_solve_host": (ctypes.c_int, [_vp, _vp, _vp, ctypes.POINTER(nbp_options), ctypes.POINTER(nbp_info)]),
+    "nbp_adjoint": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.POINTER(_d), ctypes.POINTER(nbp_info)]),
+    "nbp_destroy": (ctypes.c_int, [_vp]),
+    "nbp_last_error": (ctypes.c_char_p, [_vp]),
+    "nbp_apply_A": (ctypes.c_int, [_vp, _vp, _vp, _i32]),
+    "nbp_apply_full": (ctypes.c_int, [_vp, _vp, _vp]),
+    "nbp_apply_S": (ctypes.c_int, [_vp, _vp, _vp]),
+    "nbp_apply_pscr": (ctypes.c_int, [_vp, _vp, _vp]),
+    "nbp_solve_A": (ctypes.c_int, [_vp, _vp, _vp, _d, ctypes.POINTER(_i32)]),
+    "nbp_vcycle": (ctypes.c_int, [_vp, _i32, _vp, _vp]),
+    "nbp_amg_level_sizes": (_i32, [_vp, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_i64), _i32]),
+    "nbp_amg_level_get": (ctypes.c_int, [_vp, _i32, _i32, _vp, _vp, _vp, _vp, ctypes.POINTER(_d)]),
+    "nbp_shat_nnz": (_i64, [_vp]),
+    "nbp_shat_get": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "nbp_profile": (ctypes.c_int, [_vp, _i32]),
+    "nbp_profile_get": (ctypes.c_int, [_vp, ctypes.POINTER(nbp_profile_info)]),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libnbp.so (building it in-tree when missing or stale)."""
+    global _lib
+    if _lib is None:
+        if build_if_missing:
+            _build.build()
+        if not os.path.exists(_build.LIB):
+            raise RuntimeError("libnbp.so is not built; run __graft_entry__.build()")
+        lib = ctypes.CDLL(_build.LIB)
+        for name, (rt, args) in SIGNATURES.items():
+            f = getattr(lib, name)
+            f.restype = rt
+            f.argtypes = args
+        _lib = lib
+    return _lib
+
+
+class NbpError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def default_options(**kw) -> nbp_options:
+    o = nbp_options()
+    load().nbp_default_options(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Solver:
+    """One library context for a tangent (numpy arrays in the synth format)."""
+
+    def __init__(self, sysd: dict, device: int = 0, stream=None, **opts):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("nbp.Solver needs a CUDA device (no CPU fallback)")
+        self.torch = torch
+        self.lib = load()
+        self.dev = torch.device("cuda", device)
+        torch.cuda.set_device(self.dev)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.dev)
+        self.N = int(sysd["n_nodes"])
+        self.n_out = len(sysd["out_ptr"]) - 1
+        rp, col = sysd["rowptr"], sysd["col"]
+        keep = []
+
+        def dev(a, dt):
+            t = torch.as_tensor(np.ascontiguousarray(a), dtype=dt).to(self.dev)
+            keep.append(t)
+            return t
+
+        s = nbp_system()
+        s.n_nodes = self.N
+        for key in "ABCD":
+            k = key.lower()
+            r_ = dev(sysd.get(key + "_rowptr", rp), torch.int32)
+            c_ = dev(sysd.get(key + "_col", col), torch.int32)
+            v_ = dev(np.asarray(sysd[key]).reshape(-1), torch.float64)
+            setattr(s, f"{k}_rowptr", r_.data_ptr())
+            setattr(s, f"{k}_col", c_.data_ptr())
+            setattr(s, f"{k}_val", v_.data_ptr())
+        s.n_out = self.n_out
+        s.out_ptr = dev(sysd["out_ptr"], torch.int32).data_ptr()
+        s.out_idx = dev(sysd["out_idx"], torch.int32).data_ptr() if len(sysd["out_idx"]) else None
+        s.out_val = dev(sysd["out_val"], torch.float64).data_ptr() if len(sysd["out_val"]) else None
+        self._r = np.ascontiguousarray(sysd["r"], dtype=np.float64)
+        s.r = self._r.ctypes.data if self.n_out else None
+        self.opts = default_options(**opts)
+        ctx = ctypes.c_void_p()
+        st = self.lib.nbp_create(ctypes.byref(ctx), ctypes.byref(s), ctypes.byref(self.opts),
+                                 ctypes.c_void_p(self.stream.cuda_stream))
+        if st != 0:
+            raise NbpError(st, "nbp_create failed (see stderr)")
+        self.ctx = ctx
+        torch.cuda.synchronize(self.dev)
+        del keep   # the library copied everything during nbp_create
+
+    # ---------------------------------------------------------------- api
+    def _check(self, st, ok=(0,)):
+        if st not in ok:
+            raise NbpError(st, self.lib.nbp_last_error(self.ctx).decode())
+        return st
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.nbp_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def setup(self):
+        self._check(self.lib.nbp_setup(self.ctx))
+
+    def set_resistances(self, r):
+        r = np.ascontiguousarray(r, dtype=np.float64)
+        self._check(self.lib.nbp_set_resistances(self.ctx, r.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+
+    def options(self, **kw) -> nbp_options:
+        o = nbp_options()
+        ctypes.memmove(ctypes.byref(o), ctypes.byref(self.opts), ctypes.sizeof(o))
+        for k, v in kw.items():
+            setattr(o, k, v)
+        return o
+
+    def zeros(self, n, dtype=None):
+        return self.torch.zeros(n, dtype=dtype or self.torch.float64, device=self.dev)
+
+    def solve(self, b, x=None, allow_not_converged=False, **kw):
+        """b: CUDA float64 tensor (4N). Returns (x, info dict)."""
+        x = self.zeros(4 * self.N) if x is None else x
+        info = nbp_info()
+        o = self.options(**kw)
+        st = self.lib.nbp_solve(self.ctx, _ptr(b), _ptr(x), ctypes.byref(o), ctypes.byref(info))
+        self._check(st, (0, 4) if allow_not_converged else (0,))
+        return x, info.as_dict()
+
+    def solve_host(self, b_host: np.ndarray, x_host: np.ndarray = None, **kw):
+        """b_host: pinned or pageable float64 numpy/tensor on the host; copies inside the call."""
+        if x_host is None:
+            x_host = np.zeros(4 * self.N)
+        info = nbp_info()
+        o = self.options(**kw)
+        bp = b_host.data_ptr() if hasattr(b_host, "data_ptr") else b_host.ctypes.data
+        xp = x_host.data_ptr() if hasattr(x_host, "data_ptr") else x_host.ctypes.data
+        st = self.lib.nbp_solve_host(self.ctx, ctypes.c_void_p(bp), ctypes.c_void_p(xp), ctypes.byref(o),
+                                     ctypes.byref(info))
+        self._check(st)
+        return x_host, info.as_dict()
+
+    def adjoint(self, g, x):
+        lam = self.zeros(4 * self.N)
+        dldr = np.zeros(max(self.n_out, 1))
+        info = nbp_info()
+        st = self.lib.nbp_adjoint(self.ctx, _ptr(g), _ptr(x), _ptr(lam),
+                                  dldr.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(info))
+        self._check(st)
+        return lam, dldr[:self.n_out], info.as_dict()
+
+    def apply_A(self, x, precision=0):
+        y = self.torch.empty_like(x)
+        self._check(self.lib.nbp_apply_A(self.ctx, _ptr(x), _ptr(y), precision))
+        return y
+
+    def apply_full(self, x):
+        y = self.torch.empty_like(x)
+        self._check(self.lib.nbp_apply_full(self.ctx, _ptr(x), _ptr(y)))
+        return y
+
+    def apply_S(self, xp):
+        y = self.torch.empty_like(xp)
+        self._check(self.lib.nbp_apply_S(self.ctx, _ptr(xp), _ptr(y)))
+        return y
+
+    def apply_pscr(self, s):
+        y = self.torch.empty_like(s)
+        self._check(self.lib.nbp_apply_pscr(self.ctx, _ptr(s), _ptr(y)))
+        return y
+
+    def solve_A(self, s, rtol):
+        y = self.torch.empty_like(s)
+        its = ctypes.c_int32(0)
+        st = self.lib.nbp_solve_A(self.ctx, _ptr(s), _ptr(y), rtol, ctypes.byref(its))
+        self._check(st, (0, 4))
+        return y, its.value
+
+    def vcycle(self, which, b):
+        x = self.torch.empty_like(b)
+        self._check(self.lib.nbp_vcycle(self.ctx, which, _ptr(b), _ptr(x)))
+        return x
+
+    def amg_levels(self, which=0):
+        rows = (ctypes.c_int32 * 16)()
+        nnz = (ctypes.c_int64 * 16)()
+        nl = self.lib.nbp_amg_level_sizes(self.ctx, which, rows, nnz, 16)
+        bs = 3 if which == 0 else 1
+        out = []
+        for l in range(nl):
+            n, z = rows[l], nnz[l]
+            rp = np.zeros(n + 1, np.int32)
+            ci = np.zeros(max(z, 1), np.int32)
+            v = np.zeros(max(z, 1) * bs * bs)
+            agg = np.full(n, -1, np.int32)
+            rho = ctypes.c_double(0)
+            self._check(self.lib.nbp_amg_level_get(self.ctx, which, l, rp.ctypes.data, ci.ctypes.data, v.ctypes.data,
+                                                   agg.ctypes.data, ctypes.byref(rho)))
+            out.append(dict(rowptr=rp, col=ci[:z], val=(v[:z * bs * bs].reshape(z, bs, bs) if bs > 1 else v[:z]),
+                            agg=agg if l + 1 < nl else None, rho=rho.value))
+        return out
+
+    def shat(self):
+        z = self.lib.nbp_shat_nnz(self.ctx)
+        rp = np.zeros(self.N + 1, np.int32)
+        ci = np.zeros(max(z, 1), np.int32)
+        v = np.zeros(max(z, 1))
+        self._check(self.lib.nbp_shat_get(self.ctx, rp.ctypes.data, ci.ctypes.data, v.ctypes.data))
+        return rp, ci[:z], v[:z]
+
+    def profile(self, enable=True):
+        self._check(self.lib.nbp_profile(self.ctx, int(enable)))
+
+    def profile_info(self):
+        p = nbp_profile_info()
+        self._check(self.lib.nbp_profile_get(self.ctx, ctypes.byref(p)))
+        return p.as_dict()
