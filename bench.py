@@ -1,0 +1,345 @@
+"""Benchmark of the nested block preconditioned solve on one GB300 (per rank).
+
+Workload: the 4.34M-unknown box tangent (64x64x256 hexes -> 6.29M tets,
+1,085,825 nodes) at Re 2000 with 4 quadrant outlets (R_k log-uniform in
+[1e2, 1e5], seed 2), outer FGMRES tolerance 1e-8.  One step = one nested solve
+(setup excluded, reported separately) with FP32 inner solves and FP64 outer
+iteration; the FP64-everywhere solve of the same tangent is reported beside
+it.  Inputs stay resident in HBM; the matrices (> 1.2 GB) exceed L2, so no
+flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line (rank 0).  Under torchrun each rank solves its own
+replica (the method has no data-parallel split on one tangent: replicas only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import glob
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "nested solve s at 4.4M DOF, mixed vs FP64 @ rel.res 1e-8; SpMV/Arnoldi HBM GB/s"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def _args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="nbp", choices=["nbp", "reference"])
+    p.add_argument("--scale", type=int, default=64, help="hexes across the box width (64 = the 4.34M-unknown tangent)")
+    p.add_argument("--precision", type=int, default=1, help="inner precision of the headline solve (1 FP32, 2 BF16)")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--skip-fp64", action="store_true", help="skip the FP64 comparison solve (profiling runs)")
+    return p.parse_args()
+
+
+def _spec(scale):
+    import synth
+    return synth.large_mixed(scale)
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            with open(path) as f:
+                d = json.load(f)
+            for k in ("hbm_gbs", "hbm_GBs", "hbm"):
+                if k in d:
+                    return float(d[k]), "measured"
+        except Exception:
+            pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def _source_hash():
+    h = hashlib.sha256()
+    for p in sorted(glob.glob(os.path.join(ROOT, "paper_1911_10814_gb300", "csrc", "*"))):
+        with open(p, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic_record():
+    """DRAM bytes per launch of the dominant kernel from a committed ncu
+    summary, valid only while the kernel sources are unchanged."""
+    path = os.path.join(ROOT, "profiles", "roofline_traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        if d.get("source_hash") != _source_hash():
+            return None
+        return d
+    except Exception:
+        return None
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev):
+        self.dev = dev
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.dev)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 8:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[4 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_oracle_sample(d, counts, budget_s=20.0):
+    """Time the oracle on a bounded sample of the same workload: inner
+    GMRES(m_A) iterations with the AMG V-cycle on the full-size A (the unit
+    that dominates a nested solve), then scale to one solve with the
+    iteration counts of the measured solve.  Oracle setup is not timed."""
+    import oracle
+    o = oracle.Oracle(d)
+    t0 = time.perf_counter()
+    o.setup()
+    t_setup = time.perf_counter() - t0
+    nv = 3 * d["n_nodes"]
+    b = np.random.default_rng(0).standard_normal(nv)
+    its_s = 3
+    t0 = time.perf_counter()
+    _, its, _, _ = o.gmres_A(b, 1e-30, its_s, its_s, 1)
+    t_it = (time.perf_counter() - t0) / max(its, 1)
+    # S-level and outer iterations each add one operator application of the
+    # same order as an A-iteration (B, C, D products + V-cycle on S_hat, or the
+    # full tangent product): counted as one A-iteration equivalent each.
+    units = counts["A_iters"] + counts["I_iters"] + counts["S_iters"] + counts["outer_iters"]
+    return {"value": t_it * units, "unit": "s", "cores": 1, "kind": "oracle",
+            "sample": f"{its} oracle GMRES(m_A)+AMG iterations on the full 4.34M-unknown tangent "
+                      f"({t_it:.3f} s/iteration), scaled by {units} iteration equivalents of one nested solve; "
+                      f"oracle setup {t_setup:.1f} s untimed"}
+
+
+def run_reference(a):
+    """Reference arm: the FP64 CPU oracle on the same workload (rank 0 only)."""
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    import synth
+    import oracle
+    d = synth.generate(_spec(a.scale))
+    counts_path = os.path.join(ROOT, "profiles", "nested_solve_counts.json")
+    with open(counts_path) as f:
+        counts = json.load(f)["fp64"]
+    o = oracle.Oracle(d)
+    o.setup()
+    nv = 3 * d["n_nodes"]
+    b = np.random.default_rng(0).standard_normal(nv)
+    units = counts["A_iters"] + counts["I_iters"] + counts["S_iters"] + counts["outer_iters"]
+    its_s = 2
+    for _ in range(a.warmup):
+        o.gmres_A(b, 1e-30, its_s, its_s, 1)
+    ts = []
+    for _ in range(a.steps):
+        t0 = time.perf_counter()
+        _, its, _, _ = o.gmres_A(b, 1e-30, its_s, its_s, 1)
+        ts.append((time.perf_counter() - t0) / its * units)
+    v = float(np.mean(ts))
+    line = {"metric": METRIC, "value": v, "unit": "s", "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": synth.large_mixed(a.scale).name, "unknowns": 4 * d["n_nodes"],
+                       "tolerance": 1e-8, "l2": "inputs larger than L2"},
+            "cpu_baseline": {"value": v, "unit": "s", "cores": 1, "kind": "oracle",
+                             "sample": f"per step {its_s} oracle GMRES(m_A)+AMG iterations on the full tangent, "
+                                       f"scaled by {units} iteration equivalents of one nested solve "
+                                       f"(counts from profiles/nested_solve_counts.json)"},
+            "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    a = _args()
+    if a.impl == "reference":
+        run_reference(a)
+        return
+    import torch
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    dev = local if torch.cuda.is_available() else 0
+    torch.cuda.set_device(dev)
+    import synth
+    from paper_1911_10814_gb300 import Solver
+
+    spec = _spec(a.scale)
+    t0 = time.perf_counter()
+    d = synth.generate(spec)
+    t_gen = time.perf_counter() - t0
+    s = Solver(d, device=dev, precision=a.precision)
+    s.setup()
+    b = torch.as_tensor(d["b"], device=f"cuda:{dev}")
+    n = 4 * d["n_nodes"]
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    # FP64 solve of the same tangent (outside the timed region)
+    if a.skip_fp64:
+        x64, info64 = None, None
+    else:
+        x64, info64 = s.solve(b, precision=0)
+    for _ in range(a.warmup):
+        x, info = s.solve(b)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    clocks = Clocks(dev)
+    prof = {"a0_ms": 0.0, "a0_bytes": 0.0, "a0_launches": 0, "spmv_ms": 0.0, "spmv_bytes": 0.0, "arnoldi_ms": 0.0,
+            "arnoldi_bytes": 0.0, "kernel_launches": 0}
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    infos = []
+    launches = 0
+    for _ in range(a.steps):
+        x, info = s.solve(b)
+        infos.append(info)
+        launches += s.profile_info()["kernel_launches"]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ck = clocks.stop()
+    ms = e0.elapsed_time(e1) / a.steps
+    # per-kernel CUDA-event timing of the same solves, in a separate pass so the
+    # event records do not perturb the headline time
+    s.profile(True)
+    for _ in range(a.steps):
+        s.solve(b)
+        p = s.profile_info()
+        for k in prof:
+            prof[k] += p[k]
+    s.profile(False)
+    prof["kernel_launches"] = launches
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device=f"cuda:{dev}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = ms / 1e3 / ws   # seconds per solve over the whole job (each rank solves one replica per step)
+    err_vs_fp64 = float(torch.linalg.norm(x - x64) / torch.linalg.norm(x64)) if x64 is not None else None
+
+    # end to end through the public C ABI with host buffers (copies inside the call)
+    e2e = None
+    if not a.no_e2e:
+        bh = torch.as_tensor(d["b"]).pin_memory()
+        xh = torch.empty(n, dtype=torch.float64).pin_memory()
+        s.solve_host(bh, xh)
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(a.steps):
+            s.solve_host(bh, xh)
+        torch.cuda.synchronize()
+        barrier()
+        e2e_s = (time.perf_counter() - t0) / a.steps / ws
+        e2e = {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": n * 8, "d2h_bytes_per_step": n * 8}
+
+    peak, peak_kind = _peaks()
+    a0_avg_ms = prof["a0_ms"] / max(prof["a0_launches"], 1)
+    a0_bytes = prof["a0_bytes"] / max(prof["a0_launches"], 1)
+    achieved = a0_bytes / (a0_avg_ms * 1e-3) / 1e9 if a0_avg_ms > 0 else None
+    tr = _traffic_record()
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": (achieved / peak) if achieved else None,
+                "traffic": tr["dram_bytes_per_launch"] if tr else None,
+                "kernel": "k_bspmv<3,3> fine-level A product (FP32 values, rank-one epilogue)",
+                "peak_kind": peak_kind,
+                "spmv_family_GBs": prof["spmv_bytes"] / (prof["spmv_ms"] * 1e-3) / 1e9 if prof["spmv_ms"] else None,
+                "arnoldi_GBs": prof["arnoldi_bytes"] / (prof["arnoldi_ms"] * 1e-3) / 1e9 if prof["arnoldi_ms"] else None}
+    counts = {k: infos[-1][k] for k in ("outer_iters", "A_iters", "S_iters", "I_iters")}
+    counts64 = {k: info64[k] for k in ("outer_iters", "A_iters", "S_iters", "I_iters")} if info64 else counts
+    line = {
+        "metric": METRIC, "value": value, "unit": "s", "n_gpus": ws, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if a.precision == 1 else "bf16", "data": "synthetic",
+        "config": {"workload": spec.name, "unknowns": n, "tets": 6 * spec.nx * spec.ny * spec.nz,
+                   "outlets": spec.n_out, "tolerance": 1e-8, "inner_precision": a.precision,
+                   "parallelism": f"replicas{ws}", "l2": "inputs larger than L2 (no flush)"},
+        "fp64": ({"solve_s": info64["solve_s"], "rel_res_true": info64["rel_res_true"], **counts64} if info64 else None),
+        "mixed": {"solve_s": ms / 1e3, "rel_res_true": infos[-1]["rel_res_true"], "err_vs_fp64": err_vs_fp64,
+                  **counts},
+        "setup_s": info["setup_s"], "generate_s": t_gen,
+        "speedup_vs_fp64": (info64["solve_s"] / (ms / 1e3)) if info64 else None,
+        "roofline": roofline,
+        "clocks": ck,
+        "gpu_launches": int(prof["kernel_launches"]),
+        "e2e": e2e,
+    }
+    if rank == 0 and ws == 1 and not a.no_cpu_baseline:
+        try:
+            line["cpu_baseline"] = cpu_oracle_sample(d, counts64)
+        except Exception as ex:   # report, never hide
+            line["cpu_baseline"] = {"value": None, "error": repr(ex)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    s.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()
