@@ -31,7 +31,7 @@
  *       strength  sigma_ij = 0.5 (|A_ij|_F^2 + |A_ji|_F^2) / sqrt(|A_ii|_F^2 |A_jj|_F^2)
  *                 (squared Frobenius norms summed in row-major order, no
  *                 fused multiply-add), strong iff sigma_ij >= theta;
- *       matching  8 synchronous rounds: every unmatched node picks its
+ *       matching  64 synchronous rounds: every unmatched node picks its
  *                 strongest unmatched strong neighbour (ties: smaller index),
  *                 mutual picks are matched; leftovers are singletons;
  *       passes    3 matching passes, pass k+1 on the aggregate graph of pass
@@ -57,6 +57,9 @@
 #include <string.h>
 
 #define OR_MAXLEV 12
+/* handshake rounds per matching pass; a round that adds no pair leaves the
+ * state unchanged, so extra rounds after convergence are no-ops */
+#define MATCH_ROUNDS 64
 
 /* ----------------------------------------------------------------- types */
 typedef struct {
@@ -73,6 +76,7 @@ typedef struct {
     int variant;        /* 0 P_SCR (Algorithm 3), 1 upper block-triangular [[A,B],[0,S]] */
     int amg_max_levels, amg_coarse_max, cheb_degree;
     double theta;
+    int amg_cycle;      /* 0 V-cycle; 1 K-cycle: two GCR steps on every coarse level */
 } or_options;
 
 typedef struct {
@@ -92,7 +96,8 @@ typedef struct {
     double rho[OR_MAXLEV];
     double *lu; int *piv; int nc; /* coarsest dense LU, nc = rows */
     double *bl[OR_MAXLEV], *xl[OR_MAXLEV], *rl[OR_MAXLEV], *dl[OR_MAXLEV];
-    int cheb_degree;
+    double *kr[OR_MAXLEV], *kz1[OR_MAXLEV], *kw1[OR_MAXLEV], *kz2[OR_MAXLEV], *kw2[OR_MAXLEV]; /* K-cycle */
+    int cheb_degree, cycle;
 } amg;
 
 typedef struct {
@@ -287,13 +292,13 @@ static int find_entry(const bmat *M, int i, int j) {
 typedef struct { int n; int *p; int *j; double *w; } wgraph;
 static void wgraph_free(wgraph *g) { free(g->p); free(g->j); free(g->w); }
 
-/* One matching pass: 8 synchronous handshake rounds; returns number of
+/* One matching pass: MATCH_ROUNDS synchronous handshake rounds; returns number of
  * aggregates and writes map[u] (aggregates numbered by smallest member). */
 static int match_pass(const wgraph *G, double theta, int *map) {
     int n = G->n;
     int *mate = (int *)xmalloc(sizeof(int) * n), *pick = (int *)xmalloc(sizeof(int) * n);
     for (int u = 0; u < n; ++u) mate[u] = -1;
-    for (int round = 0; round < 8; ++round) {
+    for (int round = 0; round < MATCH_ROUNDS; ++round) {
         for (int u = 0; u < n; ++u) {
             pick[u] = -1;
             if (mate[u] >= 0) continue;
@@ -575,6 +580,7 @@ static void amg_build(amg *H, const bmat *fine, const or_options *o) {
     memset(H, 0, sizeof(*H));
     H->bs = fine->br;
     H->cheb_degree = o->cheb_degree;
+    H->cycle = o->amg_cycle;
     bmat_copy(&H->L[0], fine->nbr, fine->nbc, fine->br, fine->bc, fine->rp, fine->ci, fine->v);
     int l = 0;
     while (H->L[l].nbr > o->amg_coarse_max && l + 1 < o->amg_max_levels && l + 1 < OR_MAXLEV) {
@@ -590,6 +596,8 @@ static void amg_build(amg *H, const bmat *fine, const or_options *o) {
         int n = H->L[k].nbr, bs = H->bs;
         H->bl[k] = dvec((size_t)n * bs); H->xl[k] = dvec((size_t)n * bs);
         H->rl[k] = dvec((size_t)n * bs); H->dl[k] = dvec((size_t)n * bs);
+        H->kr[k] = dvec((size_t)n * bs); H->kz1[k] = dvec((size_t)n * bs); H->kw1[k] = dvec((size_t)n * bs);
+        H->kz2[k] = dvec((size_t)n * bs); H->kw2[k] = dvec((size_t)n * bs);
         if (k + 1 < H->nlev) {
             H->dinv[k] = dvec((size_t)n * bs * bs);
             block_diag_inv(&H->L[k], H->dinv[k]);
@@ -614,6 +622,7 @@ static void amg_free(amg *H) {
     for (int k = 0; k < H->nlev; ++k) {
         bmat_free(&H->L[k]);
         free(H->agg[k]); free(H->dinv[k]); free(H->bl[k]); free(H->xl[k]); free(H->rl[k]); free(H->dl[k]);
+        free(H->kr[k]); free(H->kz1[k]); free(H->kw1[k]); free(H->kz2[k]); free(H->kw2[k]);
     }
     free(H->lu); free(H->piv);
     memset(H, 0, sizeof(*H));
@@ -645,6 +654,37 @@ static void chebyshev(const bmat *M, const double *dinv, double rho, int k, cons
     free(t);
 }
 
+static void vcycle(amg *H, int l);
+
+/* K-cycle coarse solve on level c (Notay's Krylov-accelerated cycle): two
+ * steps of GCR on L_c e = b_c, each preconditioned by one cycle on level c;
+ * the result goes to x_c.  With w_1 = L_c z_1, a_1 = (w_1.b)/(w_1.w_1),
+ * r_1 = b - a_1 w_1; w_2 = L_c z_2 - beta w_1, z_2 -= beta z_1 with
+ * beta = (L_c z_2 . w_1)/(w_1.w_1); a_2 = (w_2.r_1)/(w_2.w_2);
+ * e = a_1 z_1 + a_2 z_2. */
+static void kcycle(amg *H, int c) {
+    bmat *M = &H->L[c];
+    int n = M->nbr * H->bs;
+    double *b = H->bl[c], *r = H->kr[c], *z1 = H->kz1[c], *w1 = H->kw1[c], *z2 = H->kz2[c], *w2 = H->kw2[c];
+    memcpy(r, b, sizeof(double) * n);
+    vcycle(H, c);                                   /* z1 = cycle(b) */
+    memcpy(z1, H->xl[c], sizeof(double) * n);
+    spmv(M, z1, w1);
+    double ww = dot(n, w1, w1);
+    double a1 = (ww > 0.0) ? dot(n, w1, r) / ww : 0.0;
+    for (int i = 0; i < n; ++i) r[i] = r[i] - a1 * w1[i];
+    memcpy(b, r, sizeof(double) * n);               /* z2 = cycle(r_1) */
+    vcycle(H, c);
+    memcpy(z2, H->xl[c], sizeof(double) * n);
+    spmv(M, z2, w2);
+    double beta = (ww > 0.0) ? dot(n, w2, w1) / ww : 0.0;
+    for (int i = 0; i < n; ++i) { w2[i] = w2[i] - beta * w1[i]; z2[i] = z2[i] - beta * z1[i]; }
+    double w22 = dot(n, w2, w2);
+    double a2 = (w22 > 0.0) ? dot(n, w2, r) / w22 : 0.0;
+    double *x = H->xl[c];
+    for (int i = 0; i < n; ++i) x[i] = a1 * z1[i] + a2 * z2[i];
+}
+
 /* V(1,1)-cycle on level l: x_l ~= L_l^{-1} b_l */
 static void vcycle(amg *H, int l) {
     bmat *M = &H->L[l];
@@ -662,7 +702,8 @@ static void vcycle(amg *H, int l) {
     for (int i = 0; i < M->nbr; ++i)              /* restriction P^T r, ascending i */
         if (H->agg[l][i] >= 0)
             for (int a = 0; a < bs; ++a) bc[(size_t)H->agg[l][i] * bs + a] += r[(size_t)i * bs + a];
-    vcycle(H, l + 1);
+    if (H->cycle == 1 && l + 1 < H->nlev - 1) kcycle(H, l + 1);
+    else vcycle(H, l + 1);
     const double *xc = H->xl[l + 1];
     for (int i = 0; i < M->nbr; ++i)              /* prolongation x += P e_c */
         if (H->agg[l][i] >= 0)
@@ -838,6 +879,7 @@ void or_default_options(or_options *o) {
     o->m = 200; o->m_A = 200; o->m_S = 200; o->nmax = 200; o->nmax_A = 200; o->nmax_S = 200;
     o->pc_A = 0; o->pc_S = 0; o->variant = 0;
     o->amg_max_levels = 5; o->amg_coarse_max = 300; o->cheb_degree = 2; o->theta = 0.0064;
+    o->amg_cycle = 0;
 }
 
 or_ctx *or_create(int N, const int *arp, const int *aci, const double *av, const int *brp, const int *bci,

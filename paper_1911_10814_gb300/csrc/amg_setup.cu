@@ -10,7 +10,7 @@
 // bit for bit because every decision is taken on values computed with the
 // same IEEE operations in the same order, with no fused multiply-add):
 //   sigma_ij = 0.5 (|A_ij|_F^2 + |A_ji|_F^2) / sqrt(|A_ii|_F^2 |A_jj|_F^2),
-//   strong iff sigma_ij >= theta; 3 passes of 8 synchronous handshake rounds
+//   strong iff sigma_ij >= theta; 3 passes of 64 synchronous handshake rounds
 //   (strongest unmatched strong neighbour, ties to the smaller index), pass
 //   k+1 on the aggregate graph with max-reduced weights; aggregates numbered
 //   by smallest fine index; nodes without any strong connection left out.
@@ -24,6 +24,8 @@
 #include "kernels.cuh"
 
 namespace nbp {
+
+constexpr int kMatchRounds = 64;   // rounds per matching pass (extra rounds after convergence are no-ops)
 
 // ------------------------------------------------------------- utilities
 void dmat_free(DMat &m, cudaStream_t s) {
@@ -483,7 +485,7 @@ static int match_pass(const Graph &G, double theta, int *map, cudaStream_t s) {
     int *mate = dmalloc<int>(n, s), *pick = dmalloc<int>(n, s);
     k_fill<int><<<grid_for(n), 256, 0, s>>>(mate, -1, n);
     NBP_LAUNCHED();
-    for (int round = 0; round < 8; ++round) {   // a round without a new pair changes nothing after it
+    for (int round = 0; round < kMatchRounds; ++round) {   // a round without a new pair changes nothing after it
         k_pick<<<grid_exact(n), 256, 0, s>>>(n, G.rp, G.ci, G.w, theta, mate, pick);
         k_match<<<grid_exact(n), 256, 0, s>>>(n, pick, mate);
         NBP_LAUNCHED();
