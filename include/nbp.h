@@ -195,6 +195,30 @@ typedef struct {
 nbp_status nbp_profile(nbp_ctx *ctx, int32_t enable);
 nbp_status nbp_profile_get(nbp_ctx *ctx, nbp_profile_info *out);
 
+/* ---- allocation-free variant (no counterpart in the paper) ----
+ * y = A x = A_sp x + sum_k r_k a^k (a^kT x) like nbp_apply_A (precision 0),
+ * but without a context and without allocating any memory, for callers that
+ * cannot call cudaMalloc: code running after a framework has frozen its
+ * memory pool, real-time or embedded callers that forbid allocation once they
+ * are running, and callers that hold no library context.  The per-outlet inner
+ * products live in a fixed device array inside the library (8 KiB on every
+ * GPU that loads it, held until the process exits), so n_out is limited to
+ * 1024; larger n_out, negative sizes or null pointers return NBP_ERR_INVALID
+ * before anything is launched.  The call allocates nothing and frees nothing.
+ * Arrays (all DEVICE, caller-owned): A in block CSR with 3x3 row-major blocks
+ * (N = n_nodes block rows, sorted in-range columns: they are not validated
+ * here), outlet k as out_idx/out_val[out_ptr[k] .. out_ptr[k+1]-1] over
+ * velocity dofs with indices unique within one outlet, r (n_out weights), x
+ * and y (3N doubles).  Work is queued on `stream` and the call returns
+ * without synchronising; NBP_ERR_CUDA reports a failed launch.  The first
+ * call on a device looks up the device address of the fixed array, so make
+ * that first call before any stream capture.  Every call shares the array:
+ * each call overwrites the entries it uses before reading them, and calls
+ * that overlap on the GPU (on unordered streams) race on it. */
+nbp_status nbp_apply_A_noalloc(int32_t n_nodes, const int32_t *a_rowptr, const int32_t *a_col, const double *a_val,
+                               int32_t n_out, const int32_t *out_ptr, const int32_t *out_idx, const double *out_val,
+                               const double *r, const double *x, double *y, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -93,6 +93,7 @@ SIGNATURES = {
     "nbp_shat_get": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "nbp_profile": (ctypes.c_int, [_vp, _i32]),
     "nbp_profile_get": (ctypes.c_int, [_vp, ctypes.POINTER(nbp_profile_info)]),
+    "nbp_apply_A_noalloc": (ctypes.c_int, [_i32, _vp, _vp, _vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
 }
 
 
