@@ -32,6 +32,9 @@ struct SpmvArgs {
     double c1, c2;          // EPI_CHEB coefficients
     const int *lr_rp, *lr_k, *lr_c;   // rank-one epilogue (EPI_SET only)
     const double *lr_val, *lr_f;
+    int nslice;                       // sliced-ELL layout (k_sell)
+    const long long *sl_ptr;
+    const int *sl_ci;
 };
 
 template <int BR, int BC, int G, typename VT, typename XT, int EPI, bool LR>
@@ -106,6 +109,81 @@ __global__ void __launch_bounds__(256) k_bspmv(SpmvArgs a) {
         const AT dn = (AT)a.c1 * d[idx] + (AT)a.c2 * t;
         d[idx] = dn;
         ((XT *)a.xout)[idx] = x[idx] + dn;
+    }
+}
+
+// Sliced-ELL product for square BS x BS blocks: one thread per block row;
+// every load of values and columns is one 32-wide contiguous segment per
+// warp.  Same epilogues as k_bspmv (a.rp unused; a.sl_* describe the slices).
+template <int BS, typename VT, typename XT, int EPI, bool LR>
+__global__ void __launch_bounds__(256) k_sell(SpmvArgs a) {
+    using AT = XT;
+    constexpr int BB = BS * BS;
+    const int row = blockIdx.x * blockDim.x + threadIdx.x;
+    const int sl = row >> 5, t = row & 31;
+    if (sl >= a.nslice) return;
+    const long long base = a.sl_ptr[sl];
+    const int w = (int)((a.sl_ptr[sl + 1] - base) >> 5);
+    const VT *__restrict__ val = (const VT *)a.val;
+    const int *__restrict__ ci = a.sl_ci;
+    const XT *__restrict__ x = (const XT *)a.x;
+    AT acc0 = 0, acc1 = 0, acc2 = 0;
+#pragma unroll 2
+    for (int k = 0; k < w; ++k) {
+        const long long g = base + 32LL * k;
+        const int c = __ldg(ci + g + t);
+        const VT *v = val + g * BB + t;
+        if (BS == 1) {
+            acc0 += cvt<AT>(__ldg(v)) * __ldg(x + c);
+        } else {
+            const AT x0 = __ldg(x + 3LL * c), x1 = __ldg(x + 3LL * c + 1), x2 = __ldg(x + 3LL * c + 2);
+            acc0 += cvt<AT>(__ldg(v)) * x0 + cvt<AT>(__ldg(v + 32)) * x1 + cvt<AT>(__ldg(v + 64)) * x2;
+            acc1 += cvt<AT>(__ldg(v + 96)) * x0 + cvt<AT>(__ldg(v + 128)) * x1 + cvt<AT>(__ldg(v + 160)) * x2;
+            acc2 += cvt<AT>(__ldg(v + 192)) * x0 + cvt<AT>(__ldg(v + 224)) * x1 + cvt<AT>(__ldg(v + 256)) * x2;
+        }
+    }
+    if (row >= a.nbr) return;
+    AT accs[3] = {acc0, acc1, acc2};
+    XT *y = (XT *)a.y;
+    if (EPI == EPI_CHEB) {
+        const XT *b = (const XT *)a.b;
+        const XT *dinv = (const XT *)a.dinv + (long long)row * BB;
+        XT *d = (XT *)a.d;
+        XT *xo = (XT *)a.xout;
+        AT r[3];
+#pragma unroll
+        for (int q = 0; q < BS; ++q) r[q] = b[(long long)row * BS + q] - accs[q];
+#pragma unroll
+        for (int q = 0; q < BS; ++q) {
+            AT tq = 0;
+#pragma unroll
+            for (int c = 0; c < BS; ++c) tq += dinv[q * BS + c] * r[c];
+            const long long idx = (long long)row * BS + q;
+            const AT dn = (AT)a.c1 * d[idx] + (AT)a.c2 * tq;
+            d[idx] = dn;
+            xo[idx] = x[idx] + dn;
+        }
+        return;
+    }
+#pragma unroll
+    for (int q = 0; q < BS; ++q) {
+        const long long idx = (long long)row * BS + q;
+        AT s = accs[q];
+        if (EPI == EPI_SET) {
+            if (LR) {
+                double tt = 0.0;
+                for (int e = a.lr_rp[row]; e < a.lr_rp[row + 1]; ++e)
+                    if (a.lr_c[e] == q) tt += a.lr_f[a.lr_k[e]] * a.lr_val[e];
+                s = (AT)((double)s + tt);
+            }
+            y[idx] = s;
+        } else if (EPI == EPI_ADD) {
+            y[idx] += s;
+        } else if (EPI == EPI_SUB) {
+            y[idx] -= s;
+        } else {
+            y[idx] = ((const XT *)a.b)[idx] - s;
+        }
     }
 }
 

@@ -78,6 +78,15 @@ struct DMat {
     double *v = nullptr;             // FP64 values (always present)
     float *v32 = nullptr;            // FP32 copy (mixed precision)
     __nv_bfloat16 *v16 = nullptr;    // BF16 copy (mixed precision)
+    // Sliced-ELL copy for square blocks (32-row slices; slot k of row t of
+    // slice s at sl_ptr[s] + 32 k + t; its bs*bs values component-major:
+    // value q of the 32 slots of one k at (sl_ptr[s] + 32 k) * bb + 32 q + t).
+    int nslice = 0;
+    long long *sl_ptr = nullptr;
+    int *sl_ci = nullptr;
+    double *sl_v = nullptr;
+    float *sl_v32 = nullptr;
+    __nv_bfloat16 *sl_v16 = nullptr;
     int bb() const { return br * bc; }
 };
 
@@ -153,6 +162,7 @@ void amg_build(Hier &H, const DMat &fine, const nbp_options &o, int precision, c
 void build_shat(const DMat &A, const DMat &B, const DMat &C, const DMat &D, const LowRank &lr, int N, DMat &Shat,
                 double *diagA_out, cudaStream_t s);
 void make_lowcopies(DMat &m, int precision, cudaStream_t s);
+void make_sell(DMat &m, int precision, cudaStream_t s);
 void transpose_dmat(const DMat &in, DMat &out, cudaStream_t s);
 
 }  // namespace nbp

@@ -129,6 +129,11 @@ struct nbp_ctx {
     std::string err;
     nbp_ctx *tctx = nullptr;      // transposed system (adjoint), built lazily
     bool is_transposed = false;
+    // CUDA graphs of the AMG cycles, keyed by (hierarchy, value precision)
+    struct CycleGraph { cudaGraphExec_t exec = nullptr; int cheb = -1; long long kernels = 0; };
+    CycleGraph graphs[2][3];
+    cudaStream_t cap = nullptr;   // private stream used only while capturing
+    bool use_graphs = true;
 };
 
 namespace nbp {
@@ -401,11 +406,62 @@ static void vcycle_level(nbp_ctx *c, Hier &H, int l, int vsel, const T *b, T *ou
     if (fin != out) copy<T>(out, fin, n, c->s);
 }
 
+static void drop_graphs(nbp_ctx *c) {
+    for (auto &row : c->graphs)
+        for (auto &g : row) {
+            if (g.exec) cudaGraphExecDestroy(g.exec);
+            g = nbp_ctx::CycleGraph();
+        }
+}
+
+// One AMG cycle x = M^{-1} b.  Outside profiling the whole cycle (every level,
+// every smoothing step, the coarsest solve) is replayed from a CUDA graph
+// captured once per hierarchy and precision on fixed level-0 buffers; b and x
+// are copied in and out around the replay.
 template <typename T> static void vcycle(nbp_ctx *c, Hier &H, int vsel, const T *b, T *x) {
     cudaEvent_t e0;
     const bool on = c->prof.on;
     if (on) { e0 = c->prof.get(); NBP_CUDA(cudaEventRecord(e0, c->s)); }
-    vcycle_level<T>(c, H, 0, vsel, b, x);
+    if (on || !c->use_graphs) {
+        vcycle_level<T>(c, H, 0, vsel, b, x);
+    } else {
+        Level &L0 = H.L[0];
+        T *gb = wvec<T>(L0, 0), *gx = wvec<T>(L0, 1);
+        const long long n = (long long)L0.M.nbr * H.bs;
+        nbp_ctx::CycleGraph &G = c->graphs[&H == &c->HS ? 1 : 0][vsel];
+        if (G.exec && G.cheb != c->opt.cheb_degree) {
+            cudaGraphExecDestroy(G.exec);
+            G.exec = nullptr;
+        }
+        if (!G.exec) {
+            if (!c->cap) NBP_CUDA(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
+            NBP_CUDA(cudaStreamSynchronize(c->s));
+            cudaStream_t saved = c->s;
+            const long long k0 = c->prof.launches;
+            c->s = c->cap;
+            cudaGraph_t g = nullptr;
+            NBP_CUDA(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
+            try {
+                vcycle_level<T>(c, H, 0, vsel, gb, gx);
+            } catch (...) {
+                cudaStreamEndCapture(c->cap, &g);
+                if (g) cudaGraphDestroy(g);
+                c->s = saved;
+                throw;
+            }
+            NBP_CUDA(cudaStreamEndCapture(c->cap, &g));
+            c->s = saved;
+            NBP_CUDA(cudaGraphInstantiate(&G.exec, g, 0));
+            NBP_CUDA(cudaGraphDestroy(g));
+            G.cheb = c->opt.cheb_degree;
+            G.kernels = c->prof.launches - k0;
+            c->prof.launches = k0;
+        }
+        copy<T>(gb, b, n, c->s);
+        NBP_CUDA(cudaGraphLaunch(G.exec, c->s));
+        copy<T>(x, gx, n, c->s);
+        c->prof.launches += G.kernels;
+    }
     if (on) {
         cudaEvent_t e1 = c->prof.get();
         NBP_CUDA(cudaEventRecord(e1, c->s));
@@ -652,11 +708,13 @@ static void free_lowrank(LowRank &lr, cudaStream_t s) {
 static void do_setup(nbp_ctx *c) {
     auto t0 = std::chrono::steady_clock::now();
     cudaStream_t s = c->s;
+    drop_graphs(c);
     const int prec = c->opt.precision;
     if (!c->diagA) c->diagA = dmalloc<double>(3LL * c->N, s);
     amg_build(c->HA, c->A, c->opt, prec, s);
     build_shat(c->A, c->B, c->C, c->D, c->lr, c->N, c->Shat, c->diagA, s);
     amg_build(c->HS, c->Shat, c->opt, prec, s);
+    make_sell(c->A, prec, s);
     if (prec >= 1) {
         make_lowcopies(c->A, prec, s);
         make_lowcopies(c->B, prec, s);
@@ -675,6 +733,8 @@ static void destroy_ctx(nbp_ctx *c) {
     cudaSetDevice(c->dev);
     cudaStream_t s = c->s;
     if (c->tctx) destroy_ctx(c->tctx);
+    drop_graphs(c);
+    if (c->cap) cudaStreamDestroy(c->cap);
     dmat_free(c->A, s); dmat_free(c->B, s); dmat_free(c->C, s); dmat_free(c->D, s); dmat_free(c->Shat, s);
     free_lowrank(c->lr, s);
     hier_free(c->HA, s); hier_free(c->HS, s);

@@ -71,12 +71,56 @@ int choose_group(const DMat &M) {
     return 32;
 }
 
+template <int BS, typename VT, typename XT>
+static void launch_sell_epi(const SpmvArgs &a, int epi, bool lr, cudaStream_t s) {
+    const unsigned grid = grid_exact((long long)a.nslice * 32);
+    switch (epi) {
+    case EPI_SET:
+        if constexpr (BS == 3) {
+            if (lr) { k_sell<BS, VT, XT, EPI_SET, true><<<grid, 256, 0, s>>>(a); break; }
+        }
+        k_sell<BS, VT, XT, EPI_SET, false><<<grid, 256, 0, s>>>(a);
+        break;
+    case EPI_ADD: k_sell<BS, VT, XT, EPI_ADD, false><<<grid, 256, 0, s>>>(a); break;
+    case EPI_SUB: k_sell<BS, VT, XT, EPI_SUB, false><<<grid, 256, 0, s>>>(a); break;
+    case EPI_RES: k_sell<BS, VT, XT, EPI_RES, false><<<grid, 256, 0, s>>>(a); break;
+    case EPI_CHEB: k_sell<BS, VT, XT, EPI_CHEB, false><<<grid, 256, 0, s>>>(a); break;
+    default: throw Error{NBP_ERR_INVALID, "spmv: unknown epilogue"};
+    }
+    NBP_LAUNCHED();
+}
+
+template <int BS, typename XT>
+static void launch_sell(const DMat &M, int vsel, SpmvArgs a, int epi, bool lr, cudaStream_t s) {
+    a.nslice = M.nslice;
+    a.sl_ptr = M.sl_ptr;
+    a.sl_ci = M.sl_ci;
+    if constexpr (sizeof(XT) == 8) {
+        a.val = M.sl_v;
+        launch_sell_epi<BS, double, double>(a, epi, lr, s);
+    } else if (vsel == 2) {
+        require(M.sl_v16 != nullptr, NBP_ERR_STATE, "spmv: BF16 sliced values not built");
+        a.val = M.sl_v16;
+        launch_sell_epi<BS, __nv_bfloat16, float>(a, epi, lr, s);
+    } else {
+        require(M.sl_v32 != nullptr, NBP_ERR_STATE, "spmv: FP32 sliced values not built");
+        a.val = M.sl_v32;
+        launch_sell_epi<BS, float, float>(a, epi, lr, s);
+    }
+}
+
 template <typename XT>
 void spmv(const DMat &M, int vsel, SpmvArgs a, int epi, bool lr, cudaStream_t s, int G) {
     a.nbr = M.nbr;
     a.rp = M.rp;
     a.ci = M.ci;
     if (a.nbr == 0) return;
+    const bool sell_ok = M.sl_ci && M.br == M.bc && (sizeof(XT) == 8 ? M.sl_v != nullptr : true);
+    if (sell_ok && G == 0) {
+        if (M.br == 3) launch_sell<3, XT>(M, vsel, a, epi, lr, s);
+        else launch_sell<1, XT>(M, vsel, a, epi, lr, s);
+        return;
+    }
     if (G <= 0) G = choose_group(M);
     if (M.br == 3 && M.bc == 3) launch_vt<3, 3, XT>(M, vsel, a, G, epi, lr, s);
     else if (M.br == 3 && M.bc == 1) launch_vt<3, 1, XT>(M, vsel, a, G, epi, lr, s);
