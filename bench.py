@@ -45,6 +45,7 @@ def _args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--skip-fp64", action="store_true", help="skip the FP64 comparison solve (profiling runs)")
+    p.add_argument("--pc-A", type=int, default=0, help="P_A: 0 AMG V-cycle (default), 1 Jacobi")
     return p.parse_args()
 
 
@@ -224,7 +225,7 @@ def main():
     t0 = time.perf_counter()
     d = synth.generate(spec)
     t_gen = time.perf_counter() - t0
-    s = Solver(d, device=dev, precision=a.precision)
+    s = Solver(d, device=dev, precision=a.precision, pc_A=a.pc_A)
     s.setup()
     b = torch.as_tensor(d["b"], device=f"cuda:{dev}")
     n = 4 * d["n_nodes"]
@@ -317,6 +318,7 @@ def main():
         "dtype": "f32" if a.precision == 1 else "bf16", "data": "synthetic",
         "config": {"workload": spec.name, "unknowns": n, "tets": 6 * spec.nx * spec.ny * spec.nz,
                    "outlets": spec.n_out, "tolerance": 1e-8, "inner_precision": a.precision,
+                   "P_A": "AMG" if a.pc_A == 0 else "Jacobi",
                    "parallelism": f"replicas{ws}", "l2": "inputs larger than L2 (no flush)"},
         "fp64": ({"solve_s": info64["solve_s"], "rel_res_true": info64["rel_res_true"], **counts64} if info64 else None),
         "mixed": {"solve_s": ms / 1e3, "rel_res_true": infos[-1]["rel_res_true"], "err_vs_fp64": err_vs_fp64,
