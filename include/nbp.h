@@ -74,7 +74,8 @@ typedef struct {
 /* Solver settings (paper Sec. 3.1: delta^r, delta^r_A, delta^r_S, delta^r_I,
  * delta^a, m, m_A, m_S, n_max).  Defaults from nbp_default_options():
  * rtol 1e-8, rtol_A 1e-3, rtol_S 1e-2, rtol_I 1e-2, atol 1e-50,
- * m = m_A = m_S = nmax = nmax_A = nmax_S = 200. */
+ * m = m_A = m_S = nmax = nmax_A = nmax_S = 200, AMG P_A and P_S with a
+ * K-cycle on the S_hat hierarchy. */
 typedef struct {
     double rtol, rtol_A, rtol_S, rtol_I, atol;
     int32_t m, m_A, m_S, nmax, nmax_A, nmax_S;
@@ -89,6 +90,9 @@ typedef struct {
     int32_t amg_coarse_max; /* default 300 block rows */
     int32_t cheb_degree;    /* default 2 */
     double theta;           /* aggregation strength threshold, default 0.0064 */
+    int32_t amg_cycle;      /* 0 V-cycle on both hierarchies; 1 (default) K-cycle on the
+                               coarse levels of AMG(S_hat); 2 K-cycle on both.  Takes
+                               effect at nbp_setup. */
 } nbp_options;
 
 typedef struct {

@@ -76,7 +76,8 @@ typedef struct {
     int variant;        /* 0 P_SCR (Algorithm 3), 1 upper block-triangular [[A,B],[0,S]] */
     int amg_max_levels, amg_coarse_max, cheb_degree;
     double theta;
-    int amg_cycle;      /* 0 V-cycle; 1 K-cycle: two GCR steps on every coarse level */
+    int amg_cycle;      /* 0 V-cycles; 1 K-cycle (two GCR steps on every coarse level) on
+                           AMG(S_hat); 2 K-cycle on both hierarchies */
 } or_options;
 
 typedef struct {
@@ -576,11 +577,11 @@ static double gershgorin_rho(const bmat *M, const double *dinv) {
     return rho;
 }
 
-static void amg_build(amg *H, const bmat *fine, const or_options *o) {
+static void amg_build(amg *H, const bmat *fine, const or_options *o, int kcycle) {
     memset(H, 0, sizeof(*H));
     H->bs = fine->br;
     H->cheb_degree = o->cheb_degree;
-    H->cycle = o->amg_cycle;
+    H->cycle = kcycle;
     bmat_copy(&H->L[0], fine->nbr, fine->nbc, fine->br, fine->bc, fine->rp, fine->ci, fine->v);
     int l = 0;
     while (H->L[l].nbr > o->amg_coarse_max && l + 1 < o->amg_max_levels && l + 1 < OR_MAXLEV) {
@@ -879,7 +880,7 @@ void or_default_options(or_options *o) {
     o->m = 200; o->m_A = 200; o->m_S = 200; o->nmax = 200; o->nmax_A = 200; o->nmax_S = 200;
     o->pc_A = 0; o->pc_S = 0; o->variant = 0;
     o->amg_max_levels = 5; o->amg_coarse_max = 300; o->cheb_degree = 2; o->theta = 0.0064;
-    o->amg_cycle = 0;
+    o->amg_cycle = 1;
 }
 
 or_ctx *or_create(int N, const int *arp, const int *aci, const double *av, const int *brp, const int *bci,
@@ -922,10 +923,10 @@ void or_set_resistances(or_ctx *c, const double *r) {
 int or_setup(or_ctx *c) {
     if (c->have_amgA) amg_free(&c->amgA);
     if (c->have_amgS) amg_free(&c->amgS);
-    amg_build(&c->amgA, &c->A, &c->opt);
+    amg_build(&c->amgA, &c->A, &c->opt, c->opt.amg_cycle == 2);
     c->have_amgA = 1;
     build_shat(c);
-    amg_build(&c->amgS, &c->Shat, &c->opt);
+    amg_build(&c->amgS, &c->Shat, &c->opt, c->opt.amg_cycle >= 1);
     c->have_amgS = 1;
     return 0;
 }

@@ -39,7 +39,8 @@ void hier_free(Hier &H, cudaStream_t s) {
         Level &L = H.L[l];
         dmat_free(L.M, s);
         dfree(L.agg, s); dfree(L.mptr, s); dfree(L.mem, s); dfree(L.dinv, s); dfree(L.dinv32, s);
-        for (int q = 0; q < 5; ++q) { dfree(L.w64[q], s); dfree(L.w32[q], s); }
+        for (int q = 0; q < Level::kWork; ++q) { dfree(L.w64[q], s); dfree(L.w32[q], s); }
+        dfree(L.kdots, s);
         L = Level();
     }
     dfree(H.cinv, s);
@@ -722,10 +723,11 @@ void amg_build(Hier &H, const DMat &fine, const nbp_options &o, int precision, c
         Level &L = H.L[k];
         const int n = L.M.nbr, bs = H.bs;
         const long long nv = (long long)n * bs;
-        for (int q = 0; q < 5; ++q) {
+        for (int q = 0; q < Level::kWork; ++q) {
             L.w64[q] = dmalloc<double>(nv, s);
             L.w32[q] = dmalloc<float>(nv, s);
         }
+        L.kdots = dmalloc<double>(8, s);
         {   // every level, the coarsest included (it is smoothed when too large for a dense solve)
             L.dinv = dmalloc<double>(nv * bs, s);
             k_block_dinv<<<grid_exact(n), 256, 0, s>>>(n, bs, L.M.rp, L.M.ci, L.M.v, L.dinv, singular);

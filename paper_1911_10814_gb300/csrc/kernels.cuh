@@ -254,6 +254,58 @@ __global__ void __launch_bounds__(256) k_maxpy(const T *__restrict__ V, long lon
     }
 }
 
+// Fused CGS pass for up to MAXC columns: w_new = w - sum_j coef[j] V[j], then
+// partial dots of the same columns with w_new (norm_only = 0) or the partial
+// squared norm of w_new (norm_only = 1), V read once.  Same fixed grid and
+// chunking as k_mdot, so the partials reduce in a fixed order.
+template <typename T, int MAXC>
+__global__ void __launch_bounds__(256) k_maxpy_dot(const T *__restrict__ V, long long ldv, int ncols,
+                                                   const double *__restrict__ coef, T *__restrict__ w, long long n,
+                                                   int norm_only, double *__restrict__ partial) {
+    __shared__ double red[MAXC][8];
+    __shared__ double cs[MAXC];
+    if ((int)threadIdx.x < ncols) cs[threadIdx.x] = coef[threadIdx.x];
+    __syncthreads();
+    const long long chunk = (n + gridDim.x - 1) / gridDim.x;
+    const long long lo = (long long)blockIdx.x * chunk;
+    const long long hi = min(n, lo + chunk);
+    const int warp = threadIdx.x >> 5, ln = threadIdx.x & 31;
+    T acc[MAXC];
+#pragma unroll
+    for (int q = 0; q < MAXC; ++q) acc[q] = 0;
+    for (long long t = lo + threadIdx.x; t < hi; t += blockDim.x) {
+        T v[MAXC];
+        T s = w[t];
+#pragma unroll
+        for (int q = 0; q < MAXC; ++q)
+            if (q < ncols) {
+                v[q] = V[(long long)q * ldv + t];
+                s -= (T)cs[q] * v[q];
+            }
+        w[t] = s;
+        if (norm_only) acc[0] += s * s;
+        else {
+#pragma unroll
+            for (int q = 0; q < MAXC; ++q)
+                if (q < ncols) acc[q] += v[q] * s;
+        }
+    }
+    const int nout = norm_only ? 1 : ncols;
+#pragma unroll
+    for (int q = 0; q < MAXC; ++q) {
+        if (q < nout) {
+            double r = warp_sum((double)acc[q]);
+            if (ln == 0) red[q][warp] = r;
+        }
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < nout) {
+        double u = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) u += red[threadIdx.x][k];
+        partial[(long long)threadIdx.x * gridDim.x + blockIdx.x] = u;
+    }
+}
+
 // ============================================================== vectors
 template <typename T> __global__ void k_fill(T *x, T v, long long n) {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) x[i] = v;
@@ -344,6 +396,51 @@ __global__ void k_dense_gemv(const double *__restrict__ Cinv, int n, const T *__
     for (int c = ln; c < n; c += 32) s += Cinv[(long long)row * n + c] * (double)b[c];
     s = warp_sum(s);
     if (ln == 0) x[row] = (T)s;
+}
+
+// ============================================================== K-cycle
+// One block (fixed order): kd[o0] = a.b and, when c != nullptr, kd[o1] = c.d
+template <typename T>
+__global__ void __launch_bounds__(1024) k_kdots(const T *__restrict__ a, const T *__restrict__ b, const T *__restrict__ c,
+                                                const T *__restrict__ d, long long n, double *kd, int o0, int o1) {
+    __shared__ double s0[32], s1[32];
+    double t0 = 0.0, t1 = 0.0;
+    for (long long i = threadIdx.x; i < n; i += blockDim.x) {
+        t0 += (double)a[i] * (double)b[i];
+        if (c) t1 += (double)c[i] * (double)d[i];
+    }
+    t0 = warp_sum(t0);
+    t1 = warp_sum(t1);
+    if ((threadIdx.x & 31) == 0) { s0[threadIdx.x >> 5] = t0; s1[threadIdx.x >> 5] = t1; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double u0 = 0.0, u1 = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { u0 += s0[w]; u1 += s1[w]; }
+        kd[o0] = u0;
+        if (c) kd[o1] = u1;
+    }
+}
+// r -= a1 w1 with a1 = (w1.r)/(w1.w1) = kd[1]/kd[0]; a1 saved in kd[2]
+template <typename T> __global__ void k_kupd1(T *r, const T *w1, double *kd, long long n) {
+    const double a1 = kd[0] > 0.0 ? kd[1] / kd[0] : 0.0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) kd[2] = a1;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        r[i] = r[i] - (T)a1 * w1[i];
+}
+// beta = (w2.w1)/(w1.w1) = kd[3]/kd[0]; w2 -= beta w1; z2 -= beta z1
+template <typename T> __global__ void k_kupd2(T *w2, T *z2, const T *w1, const T *z1, const double *kd, long long n) {
+    const double beta = kd[0] > 0.0 ? kd[3] / kd[0] : 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        w2[i] = w2[i] - (T)beta * w1[i];
+        z2[i] = z2[i] - (T)beta * z1[i];
+    }
+}
+// x = a1 z1 + a2 z2 with a2 = (w2.r)/(w2.w2) = kd[5]/kd[4]
+template <typename T> __global__ void k_kupd3(T *x, const T *z1, const T *z2, const double *kd, long long n) {
+    const double a1 = kd[2];
+    const double a2 = kd[4] > 0.0 ? kd[5] / kd[4] : 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        x[i] = (T)a1 * z1[i] + (T)a2 * z2[i];
 }
 
 // =============================================================== rank one

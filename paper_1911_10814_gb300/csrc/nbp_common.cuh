@@ -111,13 +111,17 @@ struct Level {
     double *dinv = nullptr;                  // bs*bs per row
     float *dinv32 = nullptr;
     double rho = 0.0;
-    // work vectors: [0] b, [1] x, [2] x (ping-pong), [3] r, [4] d; FP64 and FP32 sets
-    double *w64[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
-    float *w32[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    // work vectors: [0] b, [1] x, [2] x (ping-pong), [3] r, [4] d, and for the
+    // K-cycle [5] r, [6] z1, [7] w1, [8] z2, [9] w2; FP64 and FP32 sets
+    static constexpr int kWork = 10;
+    double *w64[kWork] = {};
+    float *w32[kWork] = {};
+    double *kdots = nullptr;                 // K-cycle inner products (device)
 };
 
 struct Hier {
     int nlev = 0, bs = 1;
+    bool kcycle = false;                     // Krylov-accelerated cycle on the coarse levels
     Level L[kMaxLevels];
     double *cinv = nullptr;                  // coarsest dense inverse (nc x nc, row-major) or null
     int nc = 0;

@@ -227,6 +227,23 @@ template <typename T> static void maxpy(nbp_ctx *c, long long n, const T *V, lon
     prof_end(c, CAT_ARNOLDI, (double)(ncols + 2) * n * sizeof(T));
 }
 
+constexpr int kFusedCols = 16;
+
+// w -= V coef (ncols <= kFusedCols columns), then out = V^T w (or ||w||^2
+// when norm_only), in one pass over V
+template <typename T> static void maxpy_dot(nbp_ctx *c, Krylov<T> &K, const T *V, long long ldv, int ncols,
+                                            const double *coef, T *w, int norm_only, double *out) {
+    cudaEvent_t e0;
+    prof_begin(c, e0);
+    k_maxpy_dot<T, kFusedCols><<<kReduceBlocks, 256, 0, c->s>>>(V, ldv, ncols, coef, w, K.n, norm_only, K.partial);
+    NBP_LAUNCHED();
+    prof_end(c, CAT_ARNOLDI, (double)(ncols + 2) * K.n * sizeof(T));
+    c->prof.launches++;
+    const int nout = norm_only ? 1 : ncols;
+    k_reduce_partials<<<grid_exact((long long)nout * 32), 256, 0, c->s>>>(K.partial, kReduceBlocks, nout, out, 0);
+    NBP_LAUNCHED();
+}
+
 // ----------------------------------------------------------------- GMRES
 struct GmResult { int its = 0; double rel = 0.0, rel_true = -1.0; int conv = 0; };
 
@@ -267,12 +284,18 @@ static GmResult gmres(nbp_ctx *c, Krylov<T> &K, long long n, Op op, Pc pc, const
             T *vj = K.V + (size_t)j * n, *zj = K.Z + (size_t)j * n;
             pc(vj, zj);
             op(zj, K.w);
-            // CGS2: two Gram-Schmidt passes against V(:, 0..j)
+            // CGS2: two Gram-Schmidt passes against V(:, 0..j); for short
+            // bases each subtraction is fused with the next inner products
             mdot<T>(c, K, K.V, n, j + 1, K.w, K.h1);
-            maxpy<T>(c, n, K.V, n, j + 1, K.h1, -1.0, K.w);
-            mdot<T>(c, K, K.V, n, j + 1, K.w, K.h2);
-            maxpy<T>(c, n, K.V, n, j + 1, K.h2, -1.0, K.w);
-            mdot<T>(c, K, K.w, n, 1, K.w, K.nrm);
+            if (j + 1 <= kFusedCols) {
+                maxpy_dot<T>(c, K, K.V, n, j + 1, K.h1, K.w, 0, K.h2);
+                maxpy_dot<T>(c, K, K.V, n, j + 1, K.h2, K.w, 1, K.nrm);
+            } else {
+                maxpy<T>(c, n, K.V, n, j + 1, K.h1, -1.0, K.w);
+                mdot<T>(c, K, K.V, n, j + 1, K.w, K.h2);
+                maxpy<T>(c, n, K.V, n, j + 1, K.h2, -1.0, K.w);
+                mdot<T>(c, K, K.w, n, 1, K.w, K.nrm);
+            }
             c->prof.launches += 2;
             k_givens<<<1, 1, 0, s>>>(K.H, m, j, K.h1, K.h2, K.nrm, K.cs, K.sn, K.g, K.st);
             k_scale_inv<T><<<grid_for(n), 256, 0, s>>>(K.V + (size_t)(j + 1) * n, K.w, &K.st->beta, n);
@@ -364,6 +387,37 @@ static T *chebyshev(nbp_ctx *c, Level &L, int vsel, int k, const T *b, T *x, T *
     return cur;
 }
 
+template <typename T>
+static void vcycle_level(nbp_ctx *c, Hier &H, int l, int vsel, const T *b, T *out);
+
+// K-cycle on coarse level cl (Notay's Krylov-accelerated multigrid): two GCR
+// steps on L_cl e = b, each preconditioned by one cycle on level cl; every
+// coefficient stays on the device, so the whole cycle can be replayed from a
+// CUDA graph.  x = a1 z1 + a2 z2 with a1 = (w1.b)/(w1.w1), r = b - a1 w1,
+// beta = (w2.w1)/(w1.w1), w2 -= beta w1, z2 -= beta z1, a2 = (w2.r)/(w2.w2).
+template <typename T>
+static void kcycle_level(nbp_ctx *c, Hier &H, int cl, int vsel, const T *b, T *x) {
+    Level &L = H.L[cl];
+    const long long n = (long long)L.M.nbr * H.bs;
+    T *r = wvec<T>(L, 5), *z1 = wvec<T>(L, 6), *w1 = wvec<T>(L, 7), *z2 = wvec<T>(L, 8), *w2 = wvec<T>(L, 9);
+    const unsigned g = grid_for(n);
+    copy<T>(r, b, n, c->s);
+    vcycle_level<T>(c, H, cl, vsel, b, z1);
+    do_spmv<T>(c, L.M, vsel, sargs(z1, w1), EPI_SET, false);
+    c->prof.launches += 2;
+    k_kdots<T><<<1, 1024, 0, c->s>>>(w1, w1, w1, r, n, L.kdots, 0, 1);
+    k_kupd1<T><<<g, 256, 0, c->s>>>(r, w1, L.kdots, n);
+    NBP_LAUNCHED();
+    vcycle_level<T>(c, H, cl, vsel, r, z2);
+    do_spmv<T>(c, L.M, vsel, sargs(z2, w2), EPI_SET, false);
+    c->prof.launches += 4;
+    k_kdots<T><<<1, 1024, 0, c->s>>>(w2, w1, (const T *)nullptr, (const T *)nullptr, n, L.kdots, 3, 3);
+    k_kupd2<T><<<g, 256, 0, c->s>>>(w2, z2, w1, z1, L.kdots, n);
+    k_kdots<T><<<1, 1024, 0, c->s>>>(w2, w2, w2, r, n, L.kdots, 4, 5);
+    k_kupd3<T><<<g, 256, 0, c->s>>>(x, z1, z2, L.kdots, n);
+    NBP_LAUNCHED();
+}
+
 // V(1,1)-cycle from level l with right-hand side b; result written to out.
 template <typename T>
 static void vcycle_level(nbp_ctx *c, Hier &H, int l, int vsel, const T *b, T *out) {
@@ -398,7 +452,8 @@ static void vcycle_level(nbp_ctx *c, Hier &H, int l, int vsel, const T *b, T *ou
     c->prof.launches++;
     k_restrict<T><<<grid_exact(Lc.M.nbr), 256, 0, c->s>>>(L.mptr, L.mem, Lc.M.nbr, bs, r, bc);
     NBP_LAUNCHED();
-    vcycle_level<T>(c, H, l + 1, vsel, bc, xc);
+    if (H.kcycle && l + 1 < H.nlev - 1) kcycle_level<T>(c, H, l + 1, vsel, bc, xc);
+    else vcycle_level<T>(c, H, l + 1, vsel, bc, xc);
     c->prof.launches++;
     k_prolong<T><<<grid_exact(n), 256, 0, c->s>>>(L.agg, L.M.nbr, bs, xc, cur);
     NBP_LAUNCHED();
@@ -714,6 +769,8 @@ static void do_setup(nbp_ctx *c) {
     amg_build(c->HA, c->A, c->opt, prec, s);
     build_shat(c->A, c->B, c->C, c->D, c->lr, c->N, c->Shat, c->diagA, s);
     amg_build(c->HS, c->Shat, c->opt, prec, s);
+    c->HA.kcycle = c->opt.amg_cycle == 2;
+    c->HS.kcycle = c->opt.amg_cycle >= 1;
     make_sell(c->A, prec, s);
     if (prec >= 1) {
         make_lowcopies(c->A, prec, s);
@@ -855,13 +912,14 @@ void nbp_default_options(nbp_options *o) {
     o->m = 200; o->m_A = 200; o->m_S = 200; o->nmax = 200; o->nmax_A = 200; o->nmax_S = 200;
     o->precision = 0; o->pc_A = 0; o->pc_S = 0; o->variant = 0;
     o->amg_max_levels = 5; o->amg_coarse_max = 300; o->cheb_degree = 2; o->theta = 0.0064;
+    o->amg_cycle = 1;
 }
 
 static nbp_status check_options(const nbp_options *o, std::string &msg) {
     if (!(o->rtol >= 0 && o->rtol_A >= 0 && o->rtol_S >= 0 && o->rtol_I >= 0 && o->atol >= 0)) { msg = "negative tolerance"; return NBP_ERR_INVALID; }
     if (o->m < 1 || o->m_A < 1 || o->m_S < 1 || o->nmax < 1 || o->nmax_A < 1 || o->nmax_S < 1) { msg = "restart/n_max < 1"; return NBP_ERR_INVALID; }
     if (o->precision < 0 || o->precision > 2 || o->pc_A < 0 || o->pc_A > 1 || o->pc_S < 0 || o->pc_S > 1 || o->variant < 0 || o->variant > 1) { msg = "bad mode switch"; return NBP_ERR_INVALID; }
-    if (o->cheb_degree < 0 || o->cheb_degree > 8 || o->amg_max_levels < 1) { msg = "bad AMG option"; return NBP_ERR_INVALID; }
+    if (o->cheb_degree < 0 || o->cheb_degree > 8 || o->amg_max_levels < 1 || o->amg_cycle < 0 || o->amg_cycle > 2) { msg = "bad AMG option"; return NBP_ERR_INVALID; }
     return NBP_OK;
 }
 

@@ -35,7 +35,7 @@ class nbp_options(ctypes.Structure):
         ("nmax", ctypes.c_int32), ("nmax_A", ctypes.c_int32), ("nmax_S", ctypes.c_int32),
         ("precision", ctypes.c_int32), ("pc_A", ctypes.c_int32), ("pc_S", ctypes.c_int32),
         ("variant", ctypes.c_int32), ("amg_max_levels", ctypes.c_int32), ("amg_coarse_max", ctypes.c_int32),
-        ("cheb_degree", ctypes.c_int32), ("theta", ctypes.c_double),
+        ("cheb_degree", ctypes.c_int32), ("theta", ctypes.c_double), ("amg_cycle", ctypes.c_int32),
     ]
 
 

@@ -218,3 +218,23 @@ def test_invalid_input_rejected():
     from paper_1911_10814_gb300.nbp import NbpError
     with pytest.raises(NbpError):
         Solver(bad)
+
+
+@pytest.mark.parametrize("cycle", [1, 2])
+def test_kcycle_vcycle_vs_oracle(cycle):
+    """K-cycle on the coarse levels (device coefficients, graph replay) vs the oracle."""
+    d = synth.generate(CASES["box9x11x23_q4"])
+    s = Solver(d, amg_coarse_max=10, amg_cycle=cycle)
+    s.setup()
+    o = oracle.Oracle(d, amg_coarse_max=10, amg_cycle=cycle)
+    o.setup()
+    rng = np.random.default_rng(8)
+    for which, n in ((0, 3 * d["n_nodes"]), (1, d["n_nodes"])):
+        assert len(s.amg_levels(which)) >= 3
+        b = rng.standard_normal(n)
+        for _ in range(2):   # second call replays the captured graph
+            x = s.vcycle(which, _t(b)).cpu().numpy()
+            assert _rel(x, o.vcycle(which, b)) <= 1e-10
+    x, info = s.solve(_t(d["b"]))
+    assert np.linalg.norm(d["b"] - o.apply_full(x.cpu().numpy())) / np.linalg.norm(d["b"]) <= 1e-8
+    s.close()

@@ -371,3 +371,57 @@ def test_adjoint_matches_dense_and_finite_differences(tiny4):
         e[k] = 1e-6 * d["r"][k]
         fd = (loss(d["r"] + e) - loss(d["r"] - e)) / (2 * e[k])
         assert abs(dLdr[k] - fd) <= 1e-5 * abs(fd)
+
+
+def test_kcycle_is_two_step_minimal_residual(tiny):
+    """K-cycle on AMG(S_hat): on level 1 the coarse correction is the element of
+    span{z1, z2} with the least residual (two GCR steps), z1 = T b and
+    z2 = T r1, T the two-grid cycle of level 1 and r1 the residual after the
+    best multiple of z1.  Checked by dense least squares on a 3-level
+    hierarchy, composed with the level-0 smoothing and transfers."""
+    import scipy.linalg as sla
+    d, _ = tiny
+    o = oracle.Oracle(d, amg_max_levels=3, amg_coarse_max=10, amg_cycle=1)
+    o.setup()
+    L = o.amg_levels(1)
+    assert len(L) == 3
+    mats, Ps = [], []
+    for l in range(3):
+        n = len(L[l]["rowptr"]) - 1
+        mats.append(oracle.dense_block(L[l]["rowptr"], L[l]["col"], L[l]["val"], 1, 1, n, n))
+    for l in range(2):
+        n, nc = mats[l].shape[0], mats[l + 1].shape[0]
+        P = np.zeros((n, nc))
+        for i, I in enumerate(L[l]["agg"]):
+            if I >= 0:
+                P[i, I] = 1.0
+        Ps.append(P)
+
+    def smoother(l):
+        A = mats[l]
+        Dinv = np.diag(1.0 / np.diag(A))
+        return _cheb_closed_form(A, Dinv, L[l]["rho"], 2, None)
+
+    def two_grid(l, b):
+        A, P, S = mats[l], Ps[l], smoother(l)
+        n = A.shape[0]
+        CC = np.eye(n) - P @ np.linalg.solve(P.T @ A @ P, P.T @ A)
+        E = (np.eye(n) - S @ A) @ CC @ (np.eye(n) - S @ A)
+        return (np.eye(n) - E) @ np.linalg.solve(A, b)
+
+    def kcycle(b):
+        A1 = mats[1]
+        z1 = two_grid(1, b)
+        w1 = A1 @ z1
+        a1 = sla.lstsq(w1[:, None], b)[0][0]
+        z2 = two_grid(1, b - a1 * w1)
+        Z = np.column_stack([z1, z2])
+        y = sla.lstsq(A1 @ Z, b)[0]
+        return Z @ y
+
+    A0, P0, S0 = mats[0], Ps[0], smoother(0)
+    b = np.random.default_rng(9).standard_normal(A0.shape[0])
+    x = S0 @ b
+    x = x + P0 @ kcycle(P0.T @ (b - A0 @ x))
+    x = x + S0 @ (b - A0 @ x)
+    assert _rel(o.vcycle(1, b), x) <= 1e-9
