@@ -199,6 +199,24 @@ typedef struct {
 nbp_status nbp_profile(nbp_ctx *ctx, int32_t enable);
 nbp_status nbp_profile_get(nbp_ctx *ctx, nbp_profile_info *out);
 
+/* ---- batched solves (many independent tangents of uneven size) ----
+ * One context and one CUDA stream per instance; nbp_batch_setup and
+ * nbp_batch_solve drive the instances from a pool of host threads so that
+ * their kernels overlap on the GPU.  systems: HOST array of `count` nbp_system
+ * (each with its own DEVICE arrays, copied during the call).  b, x: HOST arrays
+ * of `count` DEVICE pointers (4 N_i doubles each); infos: HOST array of
+ * `count` (may be NULL).  Returns NBP_OK when every instance converged, else
+ * the first error (nbp_batch_last_error names the instance) or
+ * NBP_NOT_CONVERGED.  Each solve is the nested method of nbp_solve. */
+typedef struct nbp_batch nbp_batch;
+nbp_status nbp_batch_create(nbp_batch **batch, int32_t count, const nbp_system *systems, const nbp_options *opt);
+nbp_status nbp_batch_setup(nbp_batch *batch);
+nbp_status nbp_batch_solve(nbp_batch *batch, const double *const *b, double *const *x, const nbp_options *opt,
+                           nbp_info *infos);
+int32_t nbp_batch_size(const nbp_batch *batch);
+nbp_status nbp_batch_destroy(nbp_batch *batch);
+const char *nbp_batch_last_error(const nbp_batch *batch);
+
 /* ---- allocation-free variant (no counterpart in the paper) ----
  * y = A x = A_sp x + sum_k r_k a^k (a^kT x) like nbp_apply_A (precision 0),
  * but without a context and without allocating any memory, for callers that

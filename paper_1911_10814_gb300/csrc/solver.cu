@@ -1208,3 +1208,85 @@ nbp_status nbp_profile_get(nbp_ctx *c, nbp_profile_info *out) {
 }
 
 }  // extern "C"
+
+// ============================================================ batched solves
+// Many independent tangents solved concurrently: one context and one CUDA
+// stream per instance, a pool of host threads driving the instances' nested
+// solves so that their kernels (and graph replays) overlap on the GPU.
+#include <atomic>
+#include <thread>
+
+struct nbp_batch {
+    std::vector<nbp_ctx *> ctx;
+    std::vector<cudaStream_t> streams;
+    int dev = 0;
+    std::string err;
+};
+
+namespace nbp {
+template <typename F> static nbp_status batch_run(nbp_batch *B, F f) {
+    const int n = (int)B->ctx.size();
+    const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
+    const int nt = std::max(1, std::min(n, hw));
+    std::atomic<int> next(0);
+    std::vector<nbp_status> st(n, NBP_OK);
+    std::vector<std::thread> pool;
+    for (int t = 0; t < nt; ++t)
+        pool.emplace_back([&]() {
+            cudaSetDevice(B->dev);
+            for (int i = next++; i < n; i = next++) st[i] = f(i);
+        });
+    for (auto &th : pool) th.join();
+    nbp_status worst = NBP_OK;
+    for (int i = 0; i < n; ++i)
+        if (st[i] != NBP_OK && (worst == NBP_OK || worst == NBP_NOT_CONVERGED)) {
+            worst = st[i];
+            if (st[i] != NBP_NOT_CONVERGED) B->err = "instance " + std::to_string(i) + ": " + B->ctx[i]->err;
+        }
+    return worst;
+}
+}  // namespace nbp
+
+extern "C" {
+
+nbp_status nbp_batch_create(nbp_batch **out, int32_t count, const nbp_system *systems, const nbp_options *opt) {
+    if (!out || !systems || count <= 0) return NBP_ERR_INVALID;
+    *out = nullptr;
+    nbp_batch *B = new nbp_batch();
+    cudaGetDevice(&B->dev);
+    for (int i = 0; i < count; ++i) {
+        cudaStream_t s = nullptr;
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) { nbp_batch_destroy(B); return NBP_ERR_CUDA; }
+        B->streams.push_back(s);
+        nbp_ctx *c = nullptr;
+        nbp_status st = nbp_create(&c, &systems[i], opt, (void *)s);
+        if (st != NBP_OK) { nbp_batch_destroy(B); return st; }
+        B->ctx.push_back(c);
+    }
+    *out = B;
+    return NBP_OK;
+}
+
+nbp_status nbp_batch_setup(nbp_batch *B) {
+    if (!B) return NBP_ERR_INVALID;
+    return nbp::batch_run(B, [&](int i) { return nbp_setup(B->ctx[i]); });
+}
+
+nbp_status nbp_batch_solve(nbp_batch *B, const double *const *b, double *const *x, const nbp_options *opt, nbp_info *infos) {
+    if (!B || !b || !x) return NBP_ERR_INVALID;
+    return nbp::batch_run(B, [&](int i) { return nbp_solve(B->ctx[i], b[i], x[i], opt, infos ? &infos[i] : nullptr); });
+}
+
+int32_t nbp_batch_size(const nbp_batch *B) { return B ? (int32_t)B->ctx.size() : 0; }
+
+nbp_status nbp_batch_destroy(nbp_batch *B) {
+    if (!B) return NBP_ERR_INVALID;
+    for (auto *c : B->ctx) nbp_destroy(c);
+    for (auto s : B->streams) cudaStreamDestroy(s);
+    delete B;
+    return NBP_OK;
+}
+
+const char *nbp_batch_last_error(const nbp_batch *B) { return B ? B->err.c_str() : "null batch"; }
+
+}  // extern "C"

@@ -93,6 +93,13 @@ SIGNATURES = {
     "nbp_shat_get": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "nbp_profile": (ctypes.c_int, [_vp, _i32]),
     "nbp_profile_get": (ctypes.c_int, [_vp, ctypes.POINTER(nbp_profile_info)]),
+    "nbp_batch_create": (ctypes.c_int, [ctypes.POINTER(_vp), _i32, ctypes.POINTER(nbp_system), ctypes.POINTER(nbp_options)]),
+    "nbp_batch_setup": (ctypes.c_int, [_vp]),
+    "nbp_batch_solve": (ctypes.c_int, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(nbp_options),
+                                       ctypes.POINTER(nbp_info)]),
+    "nbp_batch_size": (_i32, [_vp]),
+    "nbp_batch_destroy": (ctypes.c_int, [_vp]),
+    "nbp_batch_last_error": (ctypes.c_char_p, [_vp]),
     "nbp_apply_A_noalloc": (ctypes.c_int, [_i32, _vp, _vp, _vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
 }
 
@@ -134,6 +141,92 @@ def default_options(**kw) -> nbp_options:
 
 def _ptr(t):
     return ctypes.c_void_p(t.data_ptr())
+
+
+def _system(sysd, dev, keep):
+    """nbp_system for a tangent in the synth format; device copies appended to keep."""
+    import torch
+
+    def put(a, dt):
+        t = torch.as_tensor(np.ascontiguousarray(a), dtype=dt).to(dev)
+        keep.append(t)
+        return t
+
+    rp, col = sysd["rowptr"], sysd["col"]
+    s = nbp_system()
+    s.n_nodes = int(sysd["n_nodes"])
+    for key in "ABCD":
+        k = key.lower()
+        setattr(s, f"{k}_rowptr", put(sysd.get(key + "_rowptr", rp), torch.int32).data_ptr())
+        setattr(s, f"{k}_col", put(sysd.get(key + "_col", col), torch.int32).data_ptr())
+        setattr(s, f"{k}_val", put(np.asarray(sysd[key]).reshape(-1), torch.float64).data_ptr())
+    n_out = len(sysd["out_ptr"]) - 1
+    s.n_out = n_out
+    s.out_ptr = put(sysd["out_ptr"], torch.int32).data_ptr()
+    s.out_idx = put(sysd["out_idx"], torch.int32).data_ptr() if len(sysd["out_idx"]) else None
+    s.out_val = put(sysd["out_val"], torch.float64).data_ptr() if len(sysd["out_val"]) else None
+    r = np.ascontiguousarray(sysd["r"], dtype=np.float64)
+    keep.append(r)
+    s.r = r.ctypes.data if n_out else None
+    return s
+
+
+class BatchSolver:
+    """Many independent tangents solved concurrently (nbp_batch_*)."""
+
+    def __init__(self, systems, device: int = 0, **opts):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("nbp.BatchSolver needs a CUDA device (no CPU fallback)")
+        self.torch = torch
+        self.lib = load()
+        self.dev = torch.device("cuda", device)
+        torch.cuda.set_device(self.dev)
+        keep = []
+        arr = (nbp_system * len(systems))(*[_system(d, self.dev, keep) for d in systems])
+        self.sizes = [4 * int(d["n_nodes"]) for d in systems]
+        self.opts = default_options(**opts)
+        h = ctypes.c_void_p()
+        torch.cuda.synchronize(self.dev)
+        st = self.lib.nbp_batch_create(ctypes.byref(h), len(systems), arr, ctypes.byref(self.opts))
+        if st != 0:
+            raise NbpError(st, "nbp_batch_create failed (see stderr)")
+        self.h = h
+        del keep
+
+    def _check(self, st, ok=(0,)):
+        if st not in ok:
+            raise NbpError(st, self.lib.nbp_batch_last_error(self.h).decode())
+        return st
+
+    def setup(self):
+        self._check(self.lib.nbp_batch_setup(self.h))
+
+    def solve(self, bs, xs=None, **kw):
+        """bs: list of CUDA float64 tensors; returns (xs, list of info dicts)."""
+        n = len(bs)
+        if xs is None:
+            xs = [self.torch.zeros(m, dtype=self.torch.float64, device=self.dev) for m in self.sizes]
+        bp = (ctypes.c_void_p * n)(*[b.data_ptr() for b in bs])
+        xp = (ctypes.c_void_p * n)(*[x.data_ptr() for x in xs])
+        infos = (nbp_info * n)()
+        o = default_options()
+        ctypes.memmove(ctypes.byref(o), ctypes.byref(self.opts), ctypes.sizeof(o))
+        for k, v in kw.items():
+            setattr(o, k, v)
+        self._check(self.lib.nbp_batch_solve(self.h, bp, xp, ctypes.byref(o), infos))
+        return xs, [i.as_dict() for i in infos]
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.nbp_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Solver:
