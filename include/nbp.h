@@ -192,8 +192,9 @@ nbp_status nbp_shat_get(nbp_ctx *ctx, int32_t *rowptr, int32_t *col, double *val
 typedef struct {
     double spmv_ms, spmv_bytes, arnoldi_ms, arnoldi_bytes;
     double a0_ms, a0_bytes;     /* the fine-level A product (A_sp + rank-one) alone */
+    double cheb0_ms, cheb0_bytes; /* fine-level Chebyshev steps of the AMG(A) cycle */
     double vcycle_ms;
-    int64_t spmv_launches, arnoldi_launches, a0_launches;
+    int64_t spmv_launches, arnoldi_launches, a0_launches, cheb0_launches;
     int64_t kernel_launches;    /* every kernel this library launched in the last call */
 } nbp_profile_info;
 nbp_status nbp_profile(nbp_ctx *ctx, int32_t enable);

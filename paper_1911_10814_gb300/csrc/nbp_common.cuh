@@ -87,6 +87,7 @@ struct DMat {
     double *sl_v = nullptr;
     float *sl_v32 = nullptr;
     __nv_bfloat16 *sl_v16 = nullptr;
+    int tuned = -1;                  // autotuned kernel: -1 untuned, 0 sliced ELL, >0 flat with that many lanes per row
     int bb() const { return br * bc; }
 };
 

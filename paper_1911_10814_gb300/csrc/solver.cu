@@ -50,7 +50,7 @@ struct Prof {
         for (auto e : pool) cudaEventDestroy(e);
     }
 };
-enum { CAT_SPMV = 0, CAT_SPMV_A0 = 1, CAT_ARNOLDI = 2, CAT_VCYCLE = 3 };
+enum { CAT_SPMV = 0, CAT_SPMV_A0 = 1, CAT_ARNOLDI = 2, CAT_VCYCLE = 3, CAT_CHEB_A0 = 4 };
 
 // ------------------------------------------------------------ Krylov space
 template <typename T> struct Krylov {
@@ -180,11 +180,11 @@ template <typename XT> static double spmv_bytes(const DMat &M, int vsel, int epi
 }
 
 template <typename XT>
-static void do_spmv(nbp_ctx *c, const DMat &M, int vsel, SpmvArgs a, int epi, bool lr, bool fineA = false) {
+static void do_spmv(nbp_ctx *c, const DMat &M, int vsel, SpmvArgs a, int epi, bool lr, int cat = CAT_SPMV) {
     cudaEvent_t e0;
     prof_begin(c, e0);
     spmv<XT>(M, vsel, a, epi, lr, c->s);
-    prof_end(c, fineA ? CAT_SPMV_A0 : CAT_SPMV, spmv_bytes<XT>(M, vsel, epi));
+    prof_end(c, cat, spmv_bytes<XT>(M, vsel, epi));
 }
 
 static SpmvArgs sargs(const void *x, void *y) {
@@ -204,7 +204,7 @@ template <typename T> static void apply_A(nbp_ctx *c, int vsel, const T *x, T *y
         NBP_LAUNCHED();
         a.lr_rp = lr.lr_rp; a.lr_k = lr.lr_k; a.lr_c = lr.lr_c; a.lr_val = lr.lr_val; a.lr_f = lr.f;
     }
-    do_spmv<T>(c, c->A, vsel, a, EPI_SET, lr.n_out > 0, true);
+    do_spmv<T>(c, c->A, vsel, a, EPI_SET, lr.n_out > 0, CAT_SPMV_A0);
 }
 
 // ------------------------------------------------------------ CGS2 Arnoldi
@@ -356,7 +356,7 @@ template <typename T>
 static void cheb_step(nbp_ctx *c, Level &L, int vsel, const T *b, const T *x, T *xout, T *d, double c1, double c2) {
     SpmvArgs a = sargs(x, nullptr);
     a.b = b; a.dinv = dinv_of<T>(L); a.d = d; a.xout = xout; a.c1 = c1; a.c2 = c2;
-    do_spmv<T>(c, L.M, vsel, a, EPI_CHEB, false);
+    do_spmv<T>(c, L.M, vsel, a, EPI_CHEB, false, (&L == &c->HA.L[0]) ? CAT_CHEB_A0 : CAT_SPMV);
 }
 
 // Chebyshev smoothing of degree k on level L; from x = 0 when zero_start.
@@ -778,6 +778,10 @@ static void do_setup(nbp_ctx *c) {
         make_lowcopies(c->C, prec, s);
         make_lowcopies(c->D, prec, s);
     }
+    // kernel choice per matrix, timed once per setup
+    autotune_spmv(c->A, prec, s);
+    for (Hier *H : {&c->HA, &c->HS})
+        for (int l = 0; l < H->nlev; ++l) autotune_spmv(H->L[l].M, prec, s);
     NBP_CUDA(cudaStreamSynchronize(s));
     c->setup_done = true;
     c->setup_precision = prec;
@@ -871,8 +875,11 @@ static void finish_profile(nbp_ctx *c) {
     for (auto &r : c->prof.recs) {
         float ms = 0.f;
         NBP_CUDA(cudaEventElapsedTime(&ms, c->prof.pool[r.e0], c->prof.pool[r.e0 + 1]));
-        if (r.cat == CAT_SPMV || r.cat == CAT_SPMV_A0) { p.spmv_ms += ms; p.spmv_bytes += r.bytes; p.spmv_launches++; }
+        if (r.cat == CAT_SPMV || r.cat == CAT_SPMV_A0 || r.cat == CAT_CHEB_A0) {
+            p.spmv_ms += ms; p.spmv_bytes += r.bytes; p.spmv_launches++;
+        }
         if (r.cat == CAT_SPMV_A0) { p.a0_ms += ms; p.a0_bytes += r.bytes; p.a0_launches++; }
+        if (r.cat == CAT_CHEB_A0) { p.cheb0_ms += ms; p.cheb0_bytes += r.bytes; p.cheb0_launches++; }
         if (r.cat == CAT_ARNOLDI) { p.arnoldi_ms += ms; p.arnoldi_bytes += r.bytes; p.arnoldi_launches++; }
         if (r.cat == CAT_VCYCLE) p.vcycle_ms += ms;
     }

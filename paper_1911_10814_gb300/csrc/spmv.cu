@@ -116,12 +116,13 @@ void spmv(const DMat &M, int vsel, SpmvArgs a, int epi, bool lr, cudaStream_t s,
     a.ci = M.ci;
     if (a.nbr == 0) return;
     const bool sell_ok = M.sl_ci && M.br == M.bc && (sizeof(XT) == 8 ? M.sl_v != nullptr : true);
+    if (G < 0) G = (M.tuned >= 0) ? M.tuned : (sell_ok ? 0 : choose_group(M));
+    if (G == 0 && !sell_ok) G = choose_group(M);
     if (sell_ok && G == 0) {
         if (M.br == 3) launch_sell<3, XT>(M, vsel, a, epi, lr, s);
         else launch_sell<1, XT>(M, vsel, a, epi, lr, s);
         return;
     }
-    if (G <= 0) G = choose_group(M);
     if (M.br == 3 && M.bc == 3) launch_vt<3, 3, XT>(M, vsel, a, G, epi, lr, s);
     else if (M.br == 3 && M.bc == 1) launch_vt<3, 1, XT>(M, vsel, a, G, epi, lr, s);
     else if (M.br == 1 && M.bc == 3) launch_vt<1, 3, XT>(M, vsel, a, G, epi, lr, s);
@@ -131,5 +132,58 @@ void spmv(const DMat &M, int vsel, SpmvArgs a, int epi, bool lr, cudaStream_t s,
 
 template void spmv<double>(const DMat &, int, SpmvArgs, int, bool, cudaStream_t, int);
 template void spmv<float>(const DMat &, int, SpmvArgs, int, bool, cudaStream_t, int);
+
+template <typename XT> static float time_choice(const DMat &M, int vsel, int G, XT *x, XT *y, cudaStream_t s,
+                                                cudaEvent_t e0, cudaEvent_t e1) {
+    SpmvArgs a{};
+    a.x = x;
+    a.y = y;
+    spmv<XT>(M, vsel, a, EPI_SET, false, s, G);   // warm
+    NBP_CUDA(cudaEventRecord(e0, s));
+    for (int r = 0; r < 3; ++r) spmv<XT>(M, vsel, a, EPI_SET, false, s, G);
+    NBP_CUDA(cudaEventRecord(e1, s));
+    NBP_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    NBP_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    return ms;
+}
+
+void autotune_spmv(DMat &M, int precision, cudaStream_t s) {
+    if (M.nbr == 0 || M.br != M.bc) return;
+    const int vsel = precision == 2 ? 2 : (precision == 1 ? 1 : 0);
+    const long long nx = (long long)M.nbc * M.bc, ny = (long long)M.nbr * M.br;
+    cudaEvent_t e0, e1;
+    NBP_CUDA(cudaEventCreate(&e0));
+    NBP_CUDA(cudaEventCreate(&e1));
+    const int g0 = choose_group(M);
+    std::vector<int> cands = {0, g0};
+    if (g0 > 4) cands.push_back(g0 / 2);
+    if (g0 < 32) cands.push_back(g0 * 2);
+    float best = 1e30f;
+    int arg = 0;
+    if (vsel == 0) {
+        double *x = dmalloc<double>(nx, s), *y = dmalloc<double>(ny, s);
+        NBP_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * nx, s));
+        for (int G : cands) {
+            if (G == 0 && !M.sl_v) continue;
+            const float t = time_choice<double>(M, vsel, G, x, y, s, e0, e1);
+            if (t < best) { best = t; arg = G; }
+        }
+        dfree(x, s); dfree(y, s);
+    } else {
+        float *x = dmalloc<float>(nx, s), *y = dmalloc<float>(ny, s);
+        NBP_CUDA(cudaMemsetAsync(x, 0, sizeof(float) * nx, s));
+        for (int G : cands) {
+            if (G == 0 && !(vsel == 2 ? M.sl_v16 : M.sl_v32)) continue;
+            if (G > 0 && !(vsel == 2 ? M.v16 : M.v32)) continue;
+            const float t = time_choice<float>(M, vsel, G, x, y, s, e0, e1);
+            if (t < best) { best = t; arg = G; }
+        }
+        dfree(x, s); dfree(y, s);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    M.tuned = arg;
+}
 
 }  // namespace nbp

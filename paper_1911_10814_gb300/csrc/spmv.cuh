@@ -6,10 +6,16 @@ namespace nbp {
 
 // Launch y = epilogue(M x) on stream s.  vsel selects the value copy
 // (0 FP64, 1 FP32, 2 BF16); XT is the vector type (double needs vsel 0).
-// G = lanes per block row (0: chosen from the average row length).
+// G: -1 = the autotuned choice (else sliced ELL when built); 0 = sliced ELL;
+// > 0 = flat kernel with G lanes per block row.
 template <typename XT>
-void spmv(const DMat &M, int vsel, SpmvArgs a, int epi, bool lr, cudaStream_t s, int G = 0);
+void spmv(const DMat &M, int vsel, SpmvArgs a, int epi, bool lr, cudaStream_t s, int G = -1);
 
 int choose_group(const DMat &M);
+
+// Times the sliced-ELL kernel and the flat kernel with several lane counts on
+// M (y = Mx, the setup precision's value and vector types) and stores the
+// fastest choice in M.tuned.
+void autotune_spmv(DMat &M, int precision, cudaStream_t s);
 
 }  // namespace nbp

@@ -57,8 +57,10 @@ class nbp_profile_info(ctypes.Structure):
         ("spmv_ms", ctypes.c_double), ("spmv_bytes", ctypes.c_double),
         ("arnoldi_ms", ctypes.c_double), ("arnoldi_bytes", ctypes.c_double),
         ("a0_ms", ctypes.c_double), ("a0_bytes", ctypes.c_double),
+        ("cheb0_ms", ctypes.c_double), ("cheb0_bytes", ctypes.c_double),
         ("vcycle_ms", ctypes.c_double),
         ("spmv_launches", ctypes.c_int64), ("arnoldi_launches", ctypes.c_int64), ("a0_launches", ctypes.c_int64),
+        ("cheb0_launches", ctypes.c_int64),
         ("kernel_launches", ctypes.c_int64),
     ]
 
