@@ -174,8 +174,8 @@ void autotune_spmv(DMat &M, int precision, cudaStream_t s) {
         float *x = dmalloc<float>(nx, s), *y = dmalloc<float>(ny, s);
         NBP_CUDA(cudaMemsetAsync(x, 0, sizeof(float) * nx, s));
         for (int G : cands) {
-            if (G == 0 && !(vsel == 2 ? M.sl_v16 : M.sl_v32)) continue;
-            if (G > 0 && !(vsel == 2 ? M.v16 : M.v32)) continue;
+            if (G == 0 && !(vsel == 2 ? (const void *)M.sl_v16 : (const void *)M.sl_v32)) continue;
+            if (G > 0 && !(vsel == 2 ? (const void *)M.v16 : (const void *)M.v32)) continue;
             const float t = time_choice<float>(M, vsel, G, x, y, s, e0, e1);
             if (t < best) { best = t; arg = G; }
         }
