@@ -17,7 +17,6 @@ from __future__ import annotations
 
 import argparse
 import hashlib
-import glob
 import json
 import os
 import subprocess
@@ -71,11 +70,12 @@ def _peaks():
 
 
 def _source_hash():
-    h = hashlib.sha256()
-    for p in sorted(glob.glob(os.path.join(ROOT, "paper_1911_10814_gb300", "csrc", "*"))):
-        with open(p, "rb") as f:
-            h.update(f.read())
-    return h.hexdigest()[:16]
+    """Hash of the source text of the dominant kernel (k_sell in kernels.cuh)."""
+    with open(os.path.join(ROOT, "paper_1911_10814_gb300", "csrc", "kernels.cuh")) as f:
+        src = f.read()
+    a = src.index("template <int BS, typename VT, typename XT, int EPI, bool LR>\n__global__ void __launch_bounds__(256) k_sell")
+    b = src.index("// ====", a)
+    return hashlib.sha256(src[a:b].encode()).hexdigest()[:16]
 
 
 def _traffic_record():

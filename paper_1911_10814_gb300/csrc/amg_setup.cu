@@ -727,7 +727,8 @@ void amg_build(Hier &H, const DMat &fine, const nbp_options &o, int precision, c
             L.w64[q] = dmalloc<double>(nv, s);
             L.w32[q] = dmalloc<float>(nv, s);
         }
-        L.kdots = dmalloc<double>(8, s);
+        L.kdots = dmalloc<double>(8 + 2 * kKdotBlocks, s);
+        NBP_CUDA(cudaMemsetAsync(L.kdots, 0, sizeof(double) * (8 + 2 * kKdotBlocks), s));
         {   // every level, the coarsest included (it is smoothed when too large for a dense solve)
             L.dinv = dmalloc<double>(nv * bs, s);
             k_block_dinv<<<grid_exact(n), 256, 0, s>>>(n, bs, L.M.rp, L.M.ci, L.M.v, L.dinv, singular);

@@ -399,13 +399,20 @@ __global__ void k_dense_gemv(const double *__restrict__ Cinv, int n, const T *__
 }
 
 // ============================================================== K-cycle
-// One block (fixed order): kd[o0] = a.b and, when c != nullptr, kd[o1] = c.d
+// kd[o0] = a.b and, when c != nullptr, kd[o1] = c.d.  Each block reduces a
+// fixed contiguous chunk into kd[8 + 2 blk], and the last block to finish
+// (ticket in kd[7]) sums the block partials in index order: one launch,
+// same result whatever order the blocks run in.
+constexpr int kKdotBlocks = 96;
 template <typename T>
-__global__ void __launch_bounds__(1024) k_kdots(const T *__restrict__ a, const T *__restrict__ b, const T *__restrict__ c,
-                                                const T *__restrict__ d, long long n, double *kd, int o0, int o1) {
-    __shared__ double s0[32], s1[32];
+__global__ void __launch_bounds__(256) k_kdots(const T *__restrict__ a, const T *__restrict__ b, const T *__restrict__ c,
+                                               const T *__restrict__ d, long long n, double *kd, int o0, int o1) {
+    __shared__ double s0[8], s1[8];
+    __shared__ bool last;
+    const long long chunk = (n + gridDim.x - 1) / gridDim.x;
+    const long long lo = (long long)blockIdx.x * chunk, hi = min(n, lo + chunk);
     double t0 = 0.0, t1 = 0.0;
-    for (long long i = threadIdx.x; i < n; i += blockDim.x) {
+    for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
         t0 += (double)a[i] * (double)b[i];
         if (c) t1 += (double)c[i] * (double)d[i];
     }
@@ -416,8 +423,23 @@ __global__ void __launch_bounds__(1024) k_kdots(const T *__restrict__ a, const T
     if (threadIdx.x == 0) {
         double u0 = 0.0, u1 = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { u0 += s0[w]; u1 += s1[w]; }
+        kd[8 + 2 * blockIdx.x] = u0;
+        kd[9 + 2 * blockIdx.x] = u1;
+        __threadfence();
+        unsigned int *ticket = (unsigned int *)(kd + 7);
+        last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        __threadfence();
+        double u0 = 0.0, u1 = 0.0;
+        for (unsigned q = 0; q < gridDim.x; ++q) {
+            u0 += ((volatile double *)kd)[8 + 2 * q];
+            u1 += ((volatile double *)kd)[9 + 2 * q];
+        }
         kd[o0] = u0;
         if (c) kd[o1] = u1;
+        *(unsigned int *)(kd + 7) = 0u;   // ready for the next call
     }
 }
 // r -= a1 w1 with a1 = (w1.r)/(w1.w1) = kd[1]/kd[0]; a1 saved in kd[2]

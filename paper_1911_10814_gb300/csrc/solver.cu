@@ -405,15 +405,15 @@ static void kcycle_level(nbp_ctx *c, Hier &H, int cl, int vsel, const T *b, T *x
     vcycle_level<T>(c, H, cl, vsel, b, z1);
     do_spmv<T>(c, L.M, vsel, sargs(z1, w1), EPI_SET, false);
     c->prof.launches += 2;
-    k_kdots<T><<<1, 1024, 0, c->s>>>(w1, w1, w1, r, n, L.kdots, 0, 1);
+    k_kdots<T><<<kKdotBlocks, 256, 0, c->s>>>(w1, w1, w1, r, n, L.kdots, 0, 1);
     k_kupd1<T><<<g, 256, 0, c->s>>>(r, w1, L.kdots, n);
     NBP_LAUNCHED();
     vcycle_level<T>(c, H, cl, vsel, r, z2);
     do_spmv<T>(c, L.M, vsel, sargs(z2, w2), EPI_SET, false);
     c->prof.launches += 4;
-    k_kdots<T><<<1, 1024, 0, c->s>>>(w2, w1, (const T *)nullptr, (const T *)nullptr, n, L.kdots, 3, 3);
+    k_kdots<T><<<kKdotBlocks, 256, 0, c->s>>>(w2, w1, (const T *)nullptr, (const T *)nullptr, n, L.kdots, 3, 3);
     k_kupd2<T><<<g, 256, 0, c->s>>>(w2, z2, w1, z1, L.kdots, n);
-    k_kdots<T><<<1, 1024, 0, c->s>>>(w2, w2, w2, r, n, L.kdots, 4, 5);
+    k_kdots<T><<<kKdotBlocks, 256, 0, c->s>>>(w2, w2, w2, r, n, L.kdots, 4, 5);
     k_kupd3<T><<<g, 256, 0, c->s>>>(x, z1, z2, L.kdots, n);
     NBP_LAUNCHED();
 }

@@ -4,6 +4,10 @@
 #include "kernels.cuh"
 #include "spmv.cuh"
 
+#include <map>
+#include <mutex>
+#include <tuple>
+
 namespace nbp {
 
 template <int BR, int BC, int G, typename VT, typename XT>
@@ -148,8 +152,20 @@ template <typename XT> static float time_choice(const DMat &M, int vsel, int G, 
     return ms;
 }
 
+// Decisions are cached per (rows, stored blocks, block size, precision) for
+// the life of the process, so every context that meets a matrix of the same
+// shape uses the same kernel (and therefore the same rounding).
+static std::mutex g_tune_mutex;
+static std::map<std::tuple<int, long long, int, int>, int> g_tune_cache;
+
 void autotune_spmv(DMat &M, int precision, cudaStream_t s) {
     if (M.nbr == 0 || M.br != M.bc) return;
+    const auto key = std::make_tuple(M.nbr, (long long)M.nnz, M.br, precision);
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) { M.tuned = it->second; return; }
+    }
     const int vsel = precision == 2 ? 2 : (precision == 1 ? 1 : 0);
     const long long nx = (long long)M.nbc * M.bc, ny = (long long)M.nbr * M.br;
     cudaEvent_t e0, e1;
@@ -183,6 +199,10 @@ void autotune_spmv(DMat &M, int precision, cudaStream_t s) {
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) arg = it->second;   // another context decided first
+    else g_tune_cache[key] = arg;
     M.tuned = arg;
 }
 
