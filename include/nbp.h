@@ -85,7 +85,9 @@ typedef struct {
                                rank-one term stay FP64 in every mode. */
     int32_t pc_A;           /* 0 AMG V-cycle, 1 point Jacobi diag(A)^{-1} */
     int32_t pc_S;           /* 0 AMG on S_hat, 1 none */
-    int32_t variant;        /* 0 P_SCR (Algorithm 3); 1 upper block-triangular [[A,B],[0,S]] */
+    int32_t variant;        /* 0 P_SCR (Algorithm 3); 1 upper block-triangular [[A,B],[0,S]];
+                               2 SIMPLE (Sec. 3.2: S replaced by S_hat, diag(A)^{-1} B in the
+                               upper factor, no inner solver) */
     int32_t amg_max_levels; /* default 5 */
     int32_t amg_coarse_max; /* default 300 block rows */
     int32_t cheb_degree;    /* default 2 */

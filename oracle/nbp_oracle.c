@@ -73,7 +73,7 @@ typedef struct {
     int m, m_A, m_S, nmax, nmax_A, nmax_S;
     int pc_A;           /* 0 AMG, 1 point Jacobi diag(A)^{-1} */
     int pc_S;           /* 0 AMG(S_hat), 1 none */
-    int variant;        /* 0 P_SCR (Algorithm 3), 1 upper block-triangular [[A,B],[0,S]] */
+    int variant;        /* 0 P_SCR (Algorithm 3), 1 upper block-triangular [[A,B],[0,S]], 2 SIMPLE */
     int amg_max_levels, amg_coarse_max, cheb_degree;
     double theta;
     int amg_cycle;      /* 0 V-cycles; 1 K-cycle (two GCR steps on every coarse level) on
@@ -831,8 +831,31 @@ void or_apply_S(or_ctx *c, const double *xp, double *y) {
 }
 static void op_S(void *ctx, const double *x, double *y) { or_apply_S((or_ctx *)ctx, x, y); }
 
-/* Algorithm 3: y = P_SCR^{-1} s (variant 1: upper block-triangular [[A,B],[0,S]]) */
+static void op_Shat(void *ctx, const double *x, double *y) { spmv(&((or_ctx *)ctx)->Shat, x, y); }
+
+/* SIMPLE (Sec. 3.2): P = [[I,0],[C A^{-1},I]] [[A,0],[0,S_hat]] [[I, diag(A)^{-1} B],[0,I]];
+ * its inverse is Algorithm 3 with steps 3-4 replaced by a GMRES(m_S) solve with
+ * S_hat (P_S = AMG(S_hat)) and y_v = y_hat_v - diag(A)^{-1} B y_p, no step 5. */
+static void apply_simple(or_ctx *c, const double *s, double *y) {
+    int N = c->N, nv = 3 * N, its;
+    double rel;
+    double *sp2 = dvec(N), *t = dvec(nv), *ct = dvec(N);
+    or_solve_A(c, s, y, c->opt.rtol_A, &its);                                /* step 1 */
+    c->info.A_iters += its; c->info.n_A_solves++;
+    spmv(&c->C, y, ct);                                                       /* step 2 */
+    for (int i = 0; i < N; ++i) sp2[i] = s[nv + i] - ct[i];
+    fgmres(N, op_Shat, c, pc_S, c, sp2, y + nv, c->opt.rtol_S, c->opt.atol, c->opt.m_S, c->opt.nmax_S, 0, &its, &rel,
+           NULL);                                                             /* step 3' */
+    c->info.S_iters += its; c->info.n_S_solves++;
+    spmv(&c->B, y + nv, t);                                                   /* step 4' */
+    for (int i = 0; i < nv; ++i) y[i] = y[i] - t[i] / c->diagA[i];
+    free(sp2); free(t); free(ct);
+}
+
+/* Algorithm 3: y = P_SCR^{-1} s (variant 1: upper block-triangular [[A,B],[0,S]];
+ * variant 2: SIMPLE) */
 void or_apply_pscr(or_ctx *c, const double *s, double *y) {
+    if (c->opt.variant == 2) { apply_simple(c, s, y); return; }
     int N = c->N, nv = 3 * N, its;
     double rel;
     const double *sv = s, *sp = s + nv;

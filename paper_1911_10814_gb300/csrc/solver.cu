@@ -567,6 +567,32 @@ template <typename T> static void apply_S(nbp_ctx *c, int vsel, const T *xp, T *
     do_spmv<T>(c, c->C, vsel, sargs(Bf.xtil, y), EPI_SUB, false);     // lines 4-5: y = x_hat - C x_tilde
 }
 
+template <typename T> __global__ void k_simple_update(T *yv, const T *yh, const T *dinv, const T *t, long long n) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        yv[i] = yh[i] - dinv[i] * t[i];
+}
+
+// SIMPLE (Sec. 3.2): Algorithm 3 with steps 3-4 replaced by a GMRES(m_S)
+// solve with S_hat (P_S = AMG(S_hat)) and y_v = y_hat_v - diag(A)^{-1} B y_p.
+template <typename T> static void apply_simple(nbp_ctx *c, int vsel, Bufs<T> &Bf) {
+    const long long N = c->N, nv = 3 * N;
+    GmResult R1 = solve_A<T>(c, vsel, Bf.sv, Bf.yvh, c->opt.rtol_A);                 // step 1
+    c->info.A_iters += R1.its;
+    c->info.n_A_solves++;
+    do_spmv<T>(c, c->C, vsel, sargs(Bf.yvh, Bf.sp), EPI_SUB, false);                // step 2
+    const DMat &Sh = c->HS.L[0].M;
+    auto opH = [&](const T *x, T *out) { do_spmv<T>(c, Sh, vsel, sargs(x, out), EPI_SET, false); };
+    auto pcS = [&](const T *x, T *out) { vcycle<T>(c, c->HS, vsel, x, out); };
+    GmResult R3 = gmres<T>(c, KS<T>(c), N, opH, pcS, Bf.sp, Bf.yp, c->opt.rtol_S, c->opt.atol, c->opt.m_S, c->opt.nmax_S,
+                           false);                                                   // step 3'
+    c->info.S_iters += R3.its;
+    c->info.n_S_solves++;
+    do_spmv<T>(c, c->B, vsel, sargs(Bf.yp, Bf.xbar), EPI_SET, false);               // step 4'
+    c->prof.launches++;
+    k_simple_update<T><<<grid_for(nv), 256, 0, c->s>>>(Bf.yv, Bf.yvh, Bf.dinvA, Bf.xbar, nv);
+    NBP_LAUNCHED();
+}
+
 // Algorithm 3: y = P_SCR^{-1} s (FP64 in/out; inner type T)
 template <typename T> static void apply_pscr(nbp_ctx *c, const double *s, double *y) {
     const int vsel = vsel_of(c->opt.precision);
@@ -574,6 +600,12 @@ template <typename T> static void apply_pscr(nbp_ctx *c, const double *s, double
     Bufs<T> &Bf = BUF<T>(c);
     convert<T, double>(Bf.sv, s, nv, c->s);
     convert<T, double>(Bf.sp, s + nv, N, c->s);
+    if (c->opt.variant == 2) {
+        apply_simple<T>(c, vsel, Bf);
+        convert<double, T>(y, Bf.yv, nv, c->s);
+        convert<double, T>(y + nv, Bf.yp, N, c->s);
+        return;
+    }
     if (c->opt.variant == 0) {
         GmResult R1 = solve_A<T>(c, vsel, Bf.sv, Bf.yvh, c->opt.rtol_A);             // step 1
         c->info.A_iters += R1.its;
@@ -925,7 +957,7 @@ void nbp_default_options(nbp_options *o) {
 static nbp_status check_options(const nbp_options *o, std::string &msg) {
     if (!(o->rtol >= 0 && o->rtol_A >= 0 && o->rtol_S >= 0 && o->rtol_I >= 0 && o->atol >= 0)) { msg = "negative tolerance"; return NBP_ERR_INVALID; }
     if (o->m < 1 || o->m_A < 1 || o->m_S < 1 || o->nmax < 1 || o->nmax_A < 1 || o->nmax_S < 1) { msg = "restart/n_max < 1"; return NBP_ERR_INVALID; }
-    if (o->precision < 0 || o->precision > 2 || o->pc_A < 0 || o->pc_A > 1 || o->pc_S < 0 || o->pc_S > 1 || o->variant < 0 || o->variant > 1) { msg = "bad mode switch"; return NBP_ERR_INVALID; }
+    if (o->precision < 0 || o->precision > 2 || o->pc_A < 0 || o->pc_A > 1 || o->pc_S < 0 || o->pc_S > 1 || o->variant < 0 || o->variant > 2) { msg = "bad mode switch"; return NBP_ERR_INVALID; }
     if (o->cheb_degree < 0 || o->cheb_degree > 8 || o->amg_max_levels < 1 || o->amg_cycle < 0 || o->amg_cycle > 2) { msg = "bad AMG option"; return NBP_ERR_INVALID; }
     return NBP_OK;
 }

@@ -238,3 +238,22 @@ def test_kcycle_vcycle_vs_oracle(cycle):
     x, info = s.solve(_t(d["b"]))
     assert np.linalg.norm(d["b"] - o.apply_full(x.cpu().numpy())) / np.linalg.norm(d["b"]) <= 1e-8
     s.close()
+
+
+def test_simple_variant_solves_and_matches_oracle():
+    d = synth.generate(CASES["box9x11x23_q4"])
+    s = Solver(d, variant=2)
+    s.setup()
+    o = oracle.Oracle(d, variant=2)
+    o.setup()
+    x, info = s.solve(_t(d["b"]))
+    xh = x.cpu().numpy()
+    assert np.linalg.norm(d["b"] - o.apply_full(xh)) / np.linalg.norm(d["b"]) <= 1e-8
+    sv = np.random.default_rng(13).standard_normal(4 * d["n_nodes"])
+    o2 = oracle.Oracle(d, variant=2, rtol_A=1e-12, rtol_S=1e-12)
+    o2.setup()
+    s2 = Solver(d, variant=2, rtol_A=1e-12, rtol_S=1e-12)
+    s2.setup()
+    assert _rel(s2.apply_pscr(_t(sv)).cpu().numpy(), o2.apply_pscr(sv)) <= 1e-7
+    s.close()
+    s2.close()

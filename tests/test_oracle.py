@@ -425,3 +425,19 @@ def test_kcycle_is_two_step_minimal_residual(tiny):
     x = x + P0 @ kcycle(P0.T @ (b - A0 @ x))
     x = x + S0 @ (b - A0 @ x)
     assert _rel(o.vcycle(1, b), x) <= 1e-9
+
+
+def test_simple_preconditioner_identity(tiny):
+    """SIMPLE (Sec. 3.2): with exact solves its inverse is the inverse of
+    [[A, A diag(A)^{-1} B], [C, D]] (the product of its three factors)."""
+    d, (A, B, C, D, F) = tiny
+    o = oracle.Oracle(d, variant=2, rtol_A=1e-14, rtol_S=1e-14)
+    o.setup()
+    N = d["n_nodes"]
+    P = np.block([[A, A @ np.diag(1.0 / np.diag(A)) @ B], [C, D]])
+    y = np.random.default_rng(12).standard_normal(4 * N)
+    assert _rel(o.apply_pscr(P @ y), y) <= 1e-8
+    # and the nested FGMRES with it still solves the system
+    o.set_options(rtol_A=1e-3, rtol_S=1e-2)
+    x, info, rc = o.solve(d["b"])
+    assert rc == 0 and np.linalg.norm(d["b"] - F @ x) <= 1e-8 * np.linalg.norm(d["b"])
