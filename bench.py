@@ -73,7 +73,8 @@ def _source_hash():
     """Hash of the source text of the dominant kernel (k_sell in kernels.cuh)."""
     with open(os.path.join(ROOT, "paper_1911_10814_gb300", "csrc", "kernels.cuh")) as f:
         src = f.read()
-    a = src.index("template <int BS, typename VT, typename XT, int EPI, bool LR>\n__global__ void __launch_bounds__(256) k_sell")
+    k = src.index("__global__ void __launch_bounds__(256) k_sell(")
+    a = src.rindex("template <", 0, k)
     b = src.index("// ====", a)
     return hashlib.sha256(src[a:b].encode()).hexdigest()[:16]
 

@@ -198,6 +198,8 @@ typedef struct {
     double vcycle_ms;
     int64_t spmv_launches, arnoldi_launches, a0_launches, cheb0_launches;
     int64_t kernel_launches;    /* every kernel this library launched in the last call */
+    double host_wait_s;         /* host time blocked in per-iteration status reads */
+    int64_t host_syncs;         /* number of those reads */
 } nbp_profile_info;
 nbp_status nbp_profile(nbp_ctx *ctx, int32_t enable);
 nbp_status nbp_profile_get(nbp_ctx *ctx, nbp_profile_info *out);

@@ -402,32 +402,32 @@ __global__ void k_to_bf16(const double *a, __nv_bfloat16 *b, long long n) {
 }
 
 // ------------------------------------------------------------ sliced ELL
-__global__ void k_sell_width(int nbr, int nslice, const int *rp, long long *slots) {
+__global__ void k_sell_width(int nbr, int nslice, int C, const int *rp, long long *slots) {
     const int sl = blockIdx.x * blockDim.x + threadIdx.x;
     if (sl >= nslice) return;
     int w = 0;
-    for (int t = 0; t < 32; ++t) {
-        const int i = sl * 32 + t;
+    for (int t = 0; t < C; ++t) {
+        const int i = sl * C + t;
         if (i < nbr) w = max(w, rp[i + 1] - rp[i]);
     }
-    slots[sl] = 32LL * w;
+    slots[sl] = (long long)C * w;
 }
-__global__ void k_sell_fill(int nbr, int nslice, int bb, const int *rp, const int *ci, const double *v, const long long *sp,
-                            int *sci, double *sv, float *sv32, __nv_bfloat16 *sv16) {
+__global__ void k_sell_fill(int nbr, int nslice, int C, int bb, const int *rp, const int *ci, const double *v,
+                            const long long *sp, int *sci, double *sv, float *sv32, __nv_bfloat16 *sv16) {
     const int row = blockIdx.x * blockDim.x + threadIdx.x;
-    const int sl = row >> 5, t = row & 31;
+    const int sl = row / C, t = row % C;
     if (sl >= nslice) return;
     const long long base = sp[sl];
-    const int w = (int)((sp[sl + 1] - base) >> 5);
+    const int w = (int)((sp[sl + 1] - base) / C);
     const int len = (row < nbr) ? rp[row + 1] - rp[row] : 0;
     const int e0 = (row < nbr) ? rp[row] : 0;
     for (int k = 0; k < w; ++k) {
-        const long long g = base + 32LL * k;
+        const long long g = base + (long long)C * k;
         const bool real = k < len;
         sci[g + t] = real ? ci[e0 + k] : 0;
         for (int q = 0; q < bb; ++q) {
             const double val = real ? v[(long long)(e0 + k) * bb + q] : 0.0;
-            const long long o = g * bb + 32LL * q + t;
+            const long long o = g * bb + (long long)C * q + t;
             sv[o] = val;
             if (sv32) sv32[o] = (float)val;
             if (sv16) sv16[o] = __float2bfloat16_rn((float)val);
@@ -435,27 +435,41 @@ __global__ void k_sell_fill(int nbr, int nslice, int bb, const int *rp, const in
     }
 }
 
+// slice pointers for slice height C; returns the padded slot count
+static long long sell_layout(const DMat &m, int C, long long *&sp, cudaStream_t s) {
+    const int ns = (m.nbr + C - 1) / C;
+    long long *slots = dmalloc<long long>(ns + 1, s);
+    k_sell_width<<<grid_exact(ns), 256, 0, s>>>(m.nbr, ns, C, m.rp, slots);
+    NBP_LAUNCHED();
+    NBP_CUDA(cudaMemsetAsync(slots + ns, 0, sizeof(long long), s));
+    sp = dmalloc<long long>(ns + 1, s);
+    exclusive_scan(slots, sp, ns + 1, s);
+    dfree(slots, s);
+    return readback(sp + ns, s);
+}
+
 void make_sell(DMat &m, int precision, cudaStream_t s) {
     if (m.br != m.bc || m.nbr == 0) return;
     if (m.sl_ci && (precision < 1 || m.sl_v32) && (precision < 2 || m.sl_v16)) return;
     dfree(m.sl_ptr, s); dfree(m.sl_ci, s); dfree(m.sl_v, s); dfree(m.sl_v32, s); dfree(m.sl_v16, s);
     m.sl_ptr = nullptr; m.sl_ci = nullptr; m.sl_v = nullptr; m.sl_v32 = nullptr; m.sl_v16 = nullptr;
-    m.nslice = (m.nbr + 31) / 32;
-    long long *slots = dmalloc<long long>(m.nslice + 1, s);
-    k_sell_width<<<grid_exact(m.nslice), 256, 0, s>>>(m.nbr, m.nslice, m.rp, slots);
-    NBP_LAUNCHED();
-    NBP_CUDA(cudaMemsetAsync(slots + m.nslice, 0, sizeof(long long), s));
-    m.sl_ptr = dmalloc<long long>(m.nslice + 1, s);
-    exclusive_scan(slots, m.sl_ptr, m.nslice + 1, s);
-    dfree(slots, s);
-    const long long total = readback(m.sl_ptr + m.nslice, s);
+    // 32-row slices unless their padding exceeds 10% of the stored blocks
+    int C = 32;
+    long long total = sell_layout(m, 32, m.sl_ptr, s);
+    if (total > m.nnz + m.nnz / 10) {
+        dfree(m.sl_ptr, s);
+        C = 8;
+        total = sell_layout(m, 8, m.sl_ptr, s);
+    }
+    m.sl_c = C;
+    m.nslice = (m.nbr + C - 1) / C;
     const int bb = m.bb();
     m.sl_ci = dmalloc<int>(total, s);
     m.sl_v = dmalloc<double>(total * bb, s);
     if (precision >= 1) m.sl_v32 = dmalloc<float>(total * bb, s);
     if (precision == 2) m.sl_v16 = dmalloc<__nv_bfloat16>(total * bb, s);
-    k_sell_fill<<<grid_exact((long long)m.nslice * 32), 256, 0, s>>>(m.nbr, m.nslice, bb, m.rp, m.ci, m.v, m.sl_ptr, m.sl_ci,
-                                                                     m.sl_v, m.sl_v32, m.sl_v16);
+    k_sell_fill<<<grid_exact((long long)m.nslice * C), 256, 0, s>>>(m.nbr, m.nslice, C, bb, m.rp, m.ci, m.v, m.sl_ptr,
+                                                                    m.sl_ci, m.sl_v, m.sl_v32, m.sl_v16);
     NBP_LAUNCHED();
 }
 

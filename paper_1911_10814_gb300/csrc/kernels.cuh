@@ -32,7 +32,7 @@ struct SpmvArgs {
     double c1, c2;          // EPI_CHEB coefficients
     const int *lr_rp, *lr_k, *lr_c;   // rank-one epilogue (EPI_SET only)
     const double *lr_val, *lr_f;
-    int nslice;                       // sliced-ELL layout (k_sell)
+    int nslice;                       // sliced-ELL layout (k_sell): slices of C rows
     const long long *sl_ptr;
     const int *sl_ci;
 };
@@ -112,34 +112,36 @@ __global__ void __launch_bounds__(256) k_bspmv(SpmvArgs a) {
     }
 }
 
-// Sliced-ELL product for square BS x BS blocks: one thread per block row;
-// every load of values and columns is one 32-wide contiguous segment per
-// warp.  Same epilogues as k_bspmv (a.rp unused; a.sl_* describe the slices).
-template <int BS, typename VT, typename XT, int EPI, bool LR>
+// Sliced-ELL product for square BS x BS blocks: one thread per block row, C
+// rows per slice (C = 32: a warp per slice; C = 8 for matrices whose row
+// lengths vary, to cut padding).  Every load of values and columns by the C
+// threads of a slice is one contiguous segment (C x value bytes).  Same
+// epilogues as k_bspmv (a.rp unused; a.sl_* describe the slices).
+template <int BS, typename VT, typename XT, int EPI, bool LR, int C>
 __global__ void __launch_bounds__(256) k_sell(SpmvArgs a) {
     using AT = XT;
     constexpr int BB = BS * BS;
     const int row = blockIdx.x * blockDim.x + threadIdx.x;
-    const int sl = row >> 5, t = row & 31;
+    const int sl = row / C, t = row % C;
     if (sl >= a.nslice) return;
     const long long base = a.sl_ptr[sl];
-    const int w = (int)((a.sl_ptr[sl + 1] - base) >> 5);
+    const int w = (int)((a.sl_ptr[sl + 1] - base) / C);
     const VT *__restrict__ val = (const VT *)a.val;
     const int *__restrict__ ci = a.sl_ci;
     const XT *__restrict__ x = (const XT *)a.x;
     AT acc0 = 0, acc1 = 0, acc2 = 0;
 #pragma unroll 2
     for (int k = 0; k < w; ++k) {
-        const long long g = base + 32LL * k;
+        const long long g = base + (long long)C * k;
         const int c = __ldg(ci + g + t);
         const VT *v = val + g * BB + t;
         if (BS == 1) {
             acc0 += cvt<AT>(__ldg(v)) * __ldg(x + c);
         } else {
             const AT x0 = __ldg(x + 3LL * c), x1 = __ldg(x + 3LL * c + 1), x2 = __ldg(x + 3LL * c + 2);
-            acc0 += cvt<AT>(__ldg(v)) * x0 + cvt<AT>(__ldg(v + 32)) * x1 + cvt<AT>(__ldg(v + 64)) * x2;
-            acc1 += cvt<AT>(__ldg(v + 96)) * x0 + cvt<AT>(__ldg(v + 128)) * x1 + cvt<AT>(__ldg(v + 160)) * x2;
-            acc2 += cvt<AT>(__ldg(v + 192)) * x0 + cvt<AT>(__ldg(v + 224)) * x1 + cvt<AT>(__ldg(v + 256)) * x2;
+            acc0 += cvt<AT>(__ldg(v)) * x0 + cvt<AT>(__ldg(v + C)) * x1 + cvt<AT>(__ldg(v + 2 * C)) * x2;
+            acc1 += cvt<AT>(__ldg(v + 3 * C)) * x0 + cvt<AT>(__ldg(v + 4 * C)) * x1 + cvt<AT>(__ldg(v + 5 * C)) * x2;
+            acc2 += cvt<AT>(__ldg(v + 6 * C)) * x0 + cvt<AT>(__ldg(v + 7 * C)) * x1 + cvt<AT>(__ldg(v + 8 * C)) * x2;
         }
     }
     if (row >= a.nbr) return;
@@ -194,21 +196,30 @@ __global__ void __launch_bounds__(256) k_sell(SpmvArgs a) {
 template <typename T, int CB>
 __global__ void __launch_bounds__(256) k_mdot(const T *__restrict__ V, long long ldv, int ncols, const T *__restrict__ w,
                                               long long n, double *__restrict__ partial) {
+    constexpr int U = 4;   // elements in flight per thread and column
     __shared__ double red[CB][8];
     const long long chunk = (n + gridDim.x - 1) / gridDim.x;
     const long long lo = (long long)blockIdx.x * chunk;
     const long long hi = min(n, lo + chunk);
     const int warp = threadIdx.x >> 5, ln = threadIdx.x & 31;
+    const long long step = (long long)blockDim.x;
     for (int c0 = 0; c0 < ncols; c0 += CB) {
         using AT = T;
         AT acc[CB];
 #pragma unroll
         for (int q = 0; q < CB; ++q) acc[q] = 0;
-        for (long long t = lo + threadIdx.x; t < hi; t += blockDim.x) {
-            const AT wt = w[t];
+        for (long long t0 = lo + threadIdx.x; t0 < hi; t0 += U * step) {
+            AT wt[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) wt[u] = (t0 + u * step < hi) ? w[t0 + u * step] : AT(0);
 #pragma unroll
             for (int q = 0; q < CB; ++q)
-                if (c0 + q < ncols) acc[q] += V[(long long)(c0 + q) * ldv + t] * wt;
+                if (c0 + q < ncols) {
+                    const T *Vq = V + (long long)(c0 + q) * ldv;
+#pragma unroll
+                    for (int u = 0; u < U; ++u)
+                        if (t0 + u * step < hi) acc[q] += Vq[t0 + u * step] * wt[u];
+                }
         }
 #pragma unroll
         for (int q = 0; q < CB; ++q) {
@@ -273,21 +284,32 @@ __global__ void __launch_bounds__(256) k_maxpy_dot(const T *__restrict__ V, long
     T acc[MAXC];
 #pragma unroll
     for (int q = 0; q < MAXC; ++q) acc[q] = 0;
-    for (long long t = lo + threadIdx.x; t < hi; t += blockDim.x) {
-        T v[MAXC];
-        T s = w[t];
+    constexpr int U = 2;   // elements in flight per thread and column
+    const long long step = (long long)blockDim.x;
+    for (long long t0 = lo + threadIdx.x; t0 < hi; t0 += U * step) {
+        T v[U][MAXC];
+        T s[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) s[u] = (t0 + u * step < hi) ? w[t0 + u * step] : T(0);
 #pragma unroll
         for (int q = 0; q < MAXC; ++q)
             if (q < ncols) {
-                v[q] = V[(long long)q * ldv + t];
-                s -= (T)cs[q] * v[q];
-            }
-        w[t] = s;
-        if (norm_only) acc[0] += s * s;
-        else {
+                const T *Vq = V + (long long)q * ldv;
 #pragma unroll
-            for (int q = 0; q < MAXC; ++q)
-                if (q < ncols) acc[q] += v[q] * s;
+                for (int u = 0; u < U; ++u) {
+                    v[u][q] = (t0 + u * step < hi) ? Vq[t0 + u * step] : T(0);
+                    s[u] -= (T)cs[q] * v[u][q];
+                }
+            }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (t0 + u * step < hi) w[t0 + u * step] = s[u];
+            if (norm_only) acc[0] += s[u] * s[u];
+            else {
+#pragma unroll
+                for (int q = 0; q < MAXC; ++q)
+                    if (q < ncols) acc[q] += v[u][q] * s[u];
+            }
         }
     }
     const int nout = norm_only ? 1 : ncols;

@@ -15,7 +15,7 @@ namespace nbp {
 
 constexpr int kMaxLevels = 12;
 constexpr int kSMs = 152;                 // GB300: 2 dies x 76 SMs
-constexpr int kReduceBlocks = 4 * kSMs;   // fixed grid for deterministic reductions
+constexpr int kReduceBlocks = 8 * kSMs;   // fixed grid for deterministic reductions
 constexpr int kCoarseDenseMax = 4096;     // largest coarsest level (scalar rows) solved densely
 
 // ------------------------------------------------------------------ errors
@@ -78,10 +78,10 @@ struct DMat {
     double *v = nullptr;             // FP64 values (always present)
     float *v32 = nullptr;            // FP32 copy (mixed precision)
     __nv_bfloat16 *v16 = nullptr;    // BF16 copy (mixed precision)
-    // Sliced-ELL copy for square blocks (32-row slices; slot k of row t of
-    // slice s at sl_ptr[s] + 32 k + t; its bs*bs values component-major:
-    // value q of the 32 slots of one k at (sl_ptr[s] + 32 k) * bb + 32 q + t).
-    int nslice = 0;
+    // Sliced-ELL copy for square blocks (C-row slices, C = sl_c; slot k of row
+    // t of slice s at sl_ptr[s] + C k + t; its bs*bs values component-major:
+    // value q of the C slots of one k at (sl_ptr[s] + C k) * bb + C q + t).
+    int nslice = 0, sl_c = 32;       // number of slices, rows per slice (8 or 32)
     long long *sl_ptr = nullptr;
     int *sl_ci = nullptr;
     double *sl_v = nullptr;

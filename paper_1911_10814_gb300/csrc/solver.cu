@@ -249,7 +249,10 @@ struct GmResult { int its = 0; double rel = 0.0, rel_true = -1.0; int conv = 0; 
 
 static void read_state(nbp_ctx *c, const GmState *st) {
     NBP_CUDA(cudaMemcpyAsync(c->hst, st, sizeof(GmState), cudaMemcpyDeviceToHost, c->s));
+    const auto t0 = std::chrono::steady_clock::now();
     NBP_CUDA(cudaStreamSynchronize(c->s));
+    c->pinfo.host_wait_s += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    c->pinfo.host_syncs++;
 }
 
 // Restarted flexible GMRES, x_0 = 0; stops when the residual estimate
@@ -900,7 +903,11 @@ __global__ void k_adj_grad(const int *optr, const int *oidx, const double *oval,
 
 static void finish_profile(nbp_ctx *c) {
     nbp_profile_info &p = c->pinfo;
+    const double wait = p.host_wait_s;
+    const long long syncs = p.host_syncs;
     p = nbp_profile_info{};
+    p.host_wait_s = wait;
+    p.host_syncs = syncs;
     p.kernel_launches = c->prof.launches;
     if (!c->prof.on) return;
     NBP_CUDA(cudaStreamSynchronize(c->s));
@@ -922,6 +929,8 @@ static void begin_call(nbp_ctx *c) {
     c->prof.used = 0;
     c->prof.recs.clear();
     c->prof.launches = 0;
+    c->pinfo.host_wait_s = 0.0;
+    c->pinfo.host_syncs = 0;
 }
 
 }  // namespace nbp

@@ -75,23 +75,29 @@ int choose_group(const DMat &M) {
     return 32;
 }
 
-template <int BS, typename VT, typename XT>
+template <int BS, typename VT, typename XT, int C>
 static void launch_sell_epi(const SpmvArgs &a, int epi, bool lr, cudaStream_t s) {
-    const unsigned grid = grid_exact((long long)a.nslice * 32);
+    const unsigned grid = grid_exact((long long)a.nslice * C);
     switch (epi) {
     case EPI_SET:
         if constexpr (BS == 3) {
-            if (lr) { k_sell<BS, VT, XT, EPI_SET, true><<<grid, 256, 0, s>>>(a); break; }
+            if (lr) { k_sell<BS, VT, XT, EPI_SET, true, C><<<grid, 256, 0, s>>>(a); break; }
         }
-        k_sell<BS, VT, XT, EPI_SET, false><<<grid, 256, 0, s>>>(a);
+        k_sell<BS, VT, XT, EPI_SET, false, C><<<grid, 256, 0, s>>>(a);
         break;
-    case EPI_ADD: k_sell<BS, VT, XT, EPI_ADD, false><<<grid, 256, 0, s>>>(a); break;
-    case EPI_SUB: k_sell<BS, VT, XT, EPI_SUB, false><<<grid, 256, 0, s>>>(a); break;
-    case EPI_RES: k_sell<BS, VT, XT, EPI_RES, false><<<grid, 256, 0, s>>>(a); break;
-    case EPI_CHEB: k_sell<BS, VT, XT, EPI_CHEB, false><<<grid, 256, 0, s>>>(a); break;
+    case EPI_ADD: k_sell<BS, VT, XT, EPI_ADD, false, C><<<grid, 256, 0, s>>>(a); break;
+    case EPI_SUB: k_sell<BS, VT, XT, EPI_SUB, false, C><<<grid, 256, 0, s>>>(a); break;
+    case EPI_RES: k_sell<BS, VT, XT, EPI_RES, false, C><<<grid, 256, 0, s>>>(a); break;
+    case EPI_CHEB: k_sell<BS, VT, XT, EPI_CHEB, false, C><<<grid, 256, 0, s>>>(a); break;
     default: throw Error{NBP_ERR_INVALID, "spmv: unknown epilogue"};
     }
     NBP_LAUNCHED();
+}
+
+template <int BS, typename VT, typename XT>
+static void launch_sell_c(const DMat &M, const SpmvArgs &a, int epi, bool lr, cudaStream_t s) {
+    if (M.sl_c == 8) launch_sell_epi<BS, VT, XT, 8>(a, epi, lr, s);
+    else launch_sell_epi<BS, VT, XT, 32>(a, epi, lr, s);
 }
 
 template <int BS, typename XT>
@@ -101,15 +107,15 @@ static void launch_sell(const DMat &M, int vsel, SpmvArgs a, int epi, bool lr, c
     a.sl_ci = M.sl_ci;
     if constexpr (sizeof(XT) == 8) {
         a.val = M.sl_v;
-        launch_sell_epi<BS, double, double>(a, epi, lr, s);
+        launch_sell_c<BS, double, double>(M, a, epi, lr, s);
     } else if (vsel == 2) {
         require(M.sl_v16 != nullptr, NBP_ERR_STATE, "spmv: BF16 sliced values not built");
         a.val = M.sl_v16;
-        launch_sell_epi<BS, __nv_bfloat16, float>(a, epi, lr, s);
+        launch_sell_c<BS, __nv_bfloat16, float>(M, a, epi, lr, s);
     } else {
         require(M.sl_v32 != nullptr, NBP_ERR_STATE, "spmv: FP32 sliced values not built");
         a.val = M.sl_v32;
-        launch_sell_epi<BS, float, float>(a, epi, lr, s);
+        launch_sell_c<BS, float, float>(M, a, epi, lr, s);
     }
 }
 

@@ -62,6 +62,7 @@ class nbp_profile_info(ctypes.Structure):
         ("spmv_launches", ctypes.c_int64), ("arnoldi_launches", ctypes.c_int64), ("a0_launches", ctypes.c_int64),
         ("cheb0_launches", ctypes.c_int64),
         ("kernel_launches", ctypes.c_int64),
+        ("host_wait_s", ctypes.c_double), ("host_syncs", ctypes.c_int64),
     ]
 
     def as_dict(self):
