@@ -306,11 +306,17 @@ def main():
     # per-kernel CUDA-event timing of the same solves, in a separate pass so the
     # event records do not perturb the headline time
     s.profile(True)
+    breakdown = {}
     for _ in range(a.steps):
         s.solve(b)
         p = s.profile_info()
         for k in prof:
             prof[k] += p[k]
+        for tag, (cnt, ms_, by) in s.profile_report().items():
+            e = breakdown.setdefault(tag, [0, 0.0, 0.0])
+            e[0] += cnt
+            e[1] += ms_
+            e[2] += by
     s.profile(False)
     prof["kernel_launches"] = launches
     if ws > 1:
@@ -371,6 +377,8 @@ def main():
         "setup_s": info["setup_s"], "generate_s": t_gen,
         "speedup_vs_fp64": (info64["solve_s"] / (ms / 1e3)) if info64 else None,
         "roofline": roofline,
+        "kernel_breakdown_ms_per_solve": {k: [round(v[1] / a.steps, 2), round(v[2] / max(v[1], 1e-9) / 1e6, 1)]
+                                          for k, v in sorted(breakdown.items(), key=lambda kv: -kv[1][1])[:16]},
         "clocks": ck,
         "gpu_launches": int(prof["kernel_launches"]),
         "e2e": e2e,

@@ -203,6 +203,11 @@ typedef struct {
 } nbp_profile_info;
 nbp_status nbp_profile(nbp_ctx *ctx, int32_t enable);
 nbp_status nbp_profile_get(nbp_ctx *ctx, nbp_profile_info *out);
+/* Per-kernel breakdown of the last profiled call as a JSON object
+ * {"tag": [launches, total ms, algorithmic bytes]}; tags name the matrix
+ * (A, B, C, D, HA<level>, HS<level>), the epilogue and the kernel chosen.  The
+ * string is owned by the context and valid until its next profiled call. */
+const char *nbp_profile_report(const nbp_ctx *ctx);
 
 /* ---- batched solves (many independent tangents of uneven size) ----
  * One context and one CUDA stream per instance; nbp_batch_setup and

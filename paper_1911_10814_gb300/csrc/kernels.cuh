@@ -196,30 +196,21 @@ __global__ void __launch_bounds__(256) k_sell(SpmvArgs a) {
 template <typename T, int CB>
 __global__ void __launch_bounds__(256) k_mdot(const T *__restrict__ V, long long ldv, int ncols, const T *__restrict__ w,
                                               long long n, double *__restrict__ partial) {
-    constexpr int U = 4;   // elements in flight per thread and column
     __shared__ double red[CB][8];
     const long long chunk = (n + gridDim.x - 1) / gridDim.x;
     const long long lo = (long long)blockIdx.x * chunk;
     const long long hi = min(n, lo + chunk);
     const int warp = threadIdx.x >> 5, ln = threadIdx.x & 31;
-    const long long step = (long long)blockDim.x;
     for (int c0 = 0; c0 < ncols; c0 += CB) {
         using AT = T;
         AT acc[CB];
 #pragma unroll
         for (int q = 0; q < CB; ++q) acc[q] = 0;
-        for (long long t0 = lo + threadIdx.x; t0 < hi; t0 += U * step) {
-            AT wt[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u) wt[u] = (t0 + u * step < hi) ? w[t0 + u * step] : AT(0);
+        for (long long t = lo + threadIdx.x; t < hi; t += blockDim.x) {
+            const AT wt = w[t];
 #pragma unroll
             for (int q = 0; q < CB; ++q)
-                if (c0 + q < ncols) {
-                    const T *Vq = V + (long long)(c0 + q) * ldv;
-#pragma unroll
-                    for (int u = 0; u < U; ++u)
-                        if (t0 + u * step < hi) acc[q] += Vq[t0 + u * step] * wt[u];
-                }
+                if (c0 + q < ncols) acc[q] += V[(long long)(c0 + q) * ldv + t] * wt;
         }
 #pragma unroll
         for (int q = 0; q < CB; ++q) {
@@ -284,32 +275,21 @@ __global__ void __launch_bounds__(256) k_maxpy_dot(const T *__restrict__ V, long
     T acc[MAXC];
 #pragma unroll
     for (int q = 0; q < MAXC; ++q) acc[q] = 0;
-    constexpr int U = 2;   // elements in flight per thread and column
-    const long long step = (long long)blockDim.x;
-    for (long long t0 = lo + threadIdx.x; t0 < hi; t0 += U * step) {
-        T v[U][MAXC];
-        T s[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) s[u] = (t0 + u * step < hi) ? w[t0 + u * step] : T(0);
+    for (long long t = lo + threadIdx.x; t < hi; t += blockDim.x) {
+        T v[MAXC];
+        T s = w[t];
 #pragma unroll
         for (int q = 0; q < MAXC; ++q)
             if (q < ncols) {
-                const T *Vq = V + (long long)q * ldv;
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    v[u][q] = (t0 + u * step < hi) ? Vq[t0 + u * step] : T(0);
-                    s[u] -= (T)cs[q] * v[u][q];
-                }
+                v[q] = V[(long long)q * ldv + t];
+                s -= (T)cs[q] * v[q];
             }
+        w[t] = s;
+        if (norm_only) acc[0] += s * s;
+        else {
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            if (t0 + u * step < hi) w[t0 + u * step] = s[u];
-            if (norm_only) acc[0] += s[u] * s[u];
-            else {
-#pragma unroll
-                for (int q = 0; q < MAXC; ++q)
-                    if (q < ncols) acc[q] += v[u][q] * s[u];
-            }
+            for (int q = 0; q < MAXC; ++q)
+                if (q < ncols) acc[q] += v[q] * s;
         }
     }
     const int nout = norm_only ? 1 : ncols;

@@ -15,7 +15,7 @@ namespace nbp {
 
 constexpr int kMaxLevels = 12;
 constexpr int kSMs = 152;                 // GB300: 2 dies x 76 SMs
-constexpr int kReduceBlocks = 8 * kSMs;   // fixed grid for deterministic reductions
+constexpr int kReduceBlocks = 4 * kSMs;   // fixed grid for deterministic reductions
 constexpr int kCoarseDenseMax = 4096;     // largest coarsest level (scalar rows) solved densely
 
 // ------------------------------------------------------------------ errors

@@ -23,7 +23,9 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <memory>
+#include <tuple>
 
 #include "kernels.cuh"
 #include "spmv.cuh"
@@ -35,7 +37,7 @@ struct Prof {
     bool on = false;
     std::vector<cudaEvent_t> pool;
     size_t used = 0;
-    struct Rec { int cat; size_t e0; double bytes; };
+    struct Rec { int cat; size_t e0; double bytes; std::string tag; };
     std::vector<Rec> recs;
     long long launches = 0;
     cudaEvent_t get() {
@@ -50,7 +52,7 @@ struct Prof {
         for (auto e : pool) cudaEventDestroy(e);
     }
 };
-enum { CAT_SPMV = 0, CAT_SPMV_A0 = 1, CAT_ARNOLDI = 2, CAT_VCYCLE = 3, CAT_CHEB_A0 = 4 };
+enum { CAT_SPMV = 0, CAT_SPMV_A0 = 1, CAT_ARNOLDI = 2, CAT_VCYCLE = 3, CAT_CHEB_A0 = 4, CAT_OTHER = 5 };
 
 // ------------------------------------------------------------ Krylov space
 template <typename T> struct Krylov {
@@ -127,6 +129,7 @@ struct nbp_ctx {
     nbp::Prof prof;
     nbp_profile_info pinfo{};
     std::string err;
+    std::string report;
     nbp_ctx *tctx = nullptr;      // transposed system (adjoint), built lazily
     bool is_transposed = false;
     // CUDA graphs of the AMG cycles, keyed by (hierarchy, value precision)
@@ -159,11 +162,20 @@ static void prof_begin(nbp_ctx *c, cudaEvent_t &e) {
     e = c->prof.get();
     NBP_CUDA(cudaEventRecord(e, c->s));
 }
-static void prof_end(nbp_ctx *c, int cat, double bytes) {
+static void prof_end(nbp_ctx *c, int cat, double bytes, const std::string &tag = std::string()) {
     if (!c->prof.on) return;
     cudaEvent_t e1 = c->prof.get();
     NBP_CUDA(cudaEventRecord(e1, c->s));
-    c->prof.recs.push_back({cat, c->prof.used - 2, bytes});
+    c->prof.recs.push_back({cat, c->prof.used - 2, bytes, tag});
+}
+
+// launch f() with event timing under `tag` when profiling (small kernels)
+template <class F> static void timed(nbp_ctx *c, const char *tag, double bytes, F f) {
+    cudaEvent_t e0;
+    prof_begin(c, e0);
+    f();
+    NBP_LAUNCHED();
+    prof_end(c, CAT_OTHER, bytes, tag);
 }
 
 // algorithmic bytes of one block-sparse product
@@ -179,12 +191,30 @@ template <typename XT> static double spmv_bytes(const DMat &M, int vsel, int epi
     return b;
 }
 
+static std::string mat_tag(nbp_ctx *c, const DMat &M, int epi) {
+    static const char *en[] = {"set", "add", "sub", "res", "cheb"};
+    std::string t;
+    if (&M == &c->A) t = "A";
+    else if (&M == &c->B) t = "B";
+    else if (&M == &c->C) t = "C";
+    else if (&M == &c->D) t = "D";
+    else {
+        for (int l = 0; l < c->HA.nlev && t.empty(); ++l)
+            if (&M == &c->HA.L[l].M) t = "HA" + std::to_string(l);
+        for (int l = 0; l < c->HS.nlev && t.empty(); ++l)
+            if (&M == &c->HS.L[l].M) t = "HS" + std::to_string(l);
+        if (t.empty()) t = "M";
+    }
+    const int kind = M.tuned >= 0 ? M.tuned : (M.sl_ci ? 0 : -1);
+    return t + "/" + en[epi] + (kind == 0 ? "/sell" + std::to_string(M.sl_c) : "/flat" + std::to_string(kind));
+}
+
 template <typename XT>
 static void do_spmv(nbp_ctx *c, const DMat &M, int vsel, SpmvArgs a, int epi, bool lr, int cat = CAT_SPMV) {
     cudaEvent_t e0;
     prof_begin(c, e0);
     spmv<XT>(M, vsel, a, epi, lr, c->s);
-    prof_end(c, cat, spmv_bytes<XT>(M, vsel, epi));
+    prof_end(c, cat, spmv_bytes<XT>(M, vsel, epi), c->prof.on ? mat_tag(c, M, epi) : std::string());
 }
 
 static SpmvArgs sargs(const void *x, void *y) {
@@ -213,10 +243,10 @@ template <typename T> static void mdot(nbp_ctx *c, Krylov<T> &K, const T *V, lon
     prof_begin(c, e0);
     k_mdot<T, 8><<<kReduceBlocks, 256, 0, c->s>>>(V, ldv, ncols, w, K.n, K.partial);
     NBP_LAUNCHED();
-    prof_end(c, CAT_ARNOLDI, (double)(ncols + 1) * K.n * sizeof(T));
-    c->prof.launches++;
-    k_reduce_partials<<<grid_exact((long long)ncols * 32), 256, 0, c->s>>>(K.partial, kReduceBlocks, ncols, out, 0);
-    NBP_LAUNCHED();
+    prof_end(c, CAT_ARNOLDI, (double)(ncols + 1) * K.n * sizeof(T), "arnoldi/mdot");
+    timed(c, "arnoldi/reduce", 0.0, [&] {
+        k_reduce_partials<<<grid_exact((long long)ncols * 32), 256, 0, c->s>>>(K.partial, kReduceBlocks, ncols, out, 0);
+    });
 }
 template <typename T> static void maxpy(nbp_ctx *c, long long n, const T *V, long long ldv, int ncols, const double *coef,
                                         double alpha, T *w) {
@@ -224,7 +254,7 @@ template <typename T> static void maxpy(nbp_ctx *c, long long n, const T *V, lon
     prof_begin(c, e0);
     k_maxpy<T><<<grid_for(n, 256, 8LL * kSMs * 4), 256, 0, c->s>>>(V, ldv, ncols, coef, alpha, w, n);
     NBP_LAUNCHED();
-    prof_end(c, CAT_ARNOLDI, (double)(ncols + 2) * n * sizeof(T));
+    prof_end(c, CAT_ARNOLDI, (double)(ncols + 2) * n * sizeof(T), "arnoldi/maxpy");
 }
 
 constexpr int kFusedCols = 16;
@@ -237,11 +267,11 @@ template <typename T> static void maxpy_dot(nbp_ctx *c, Krylov<T> &K, const T *V
     prof_begin(c, e0);
     k_maxpy_dot<T, kFusedCols><<<kReduceBlocks, 256, 0, c->s>>>(V, ldv, ncols, coef, w, K.n, norm_only, K.partial);
     NBP_LAUNCHED();
-    prof_end(c, CAT_ARNOLDI, (double)(ncols + 2) * K.n * sizeof(T));
-    c->prof.launches++;
+    prof_end(c, CAT_ARNOLDI, (double)(ncols + 2) * K.n * sizeof(T), "arnoldi/maxpy_dot");
     const int nout = norm_only ? 1 : ncols;
-    k_reduce_partials<<<grid_exact((long long)nout * 32), 256, 0, c->s>>>(K.partial, kReduceBlocks, nout, out, 0);
-    NBP_LAUNCHED();
+    timed(c, "arnoldi/reduce", 0.0, [&] {
+        k_reduce_partials<<<grid_exact((long long)nout * 32), 256, 0, c->s>>>(K.partial, kReduceBlocks, nout, out, 0);
+    });
 }
 
 // ----------------------------------------------------------------- GMRES
@@ -299,10 +329,9 @@ static GmResult gmres(nbp_ctx *c, Krylov<T> &K, long long n, Op op, Pc pc, const
                 maxpy<T>(c, n, K.V, n, j + 1, K.h2, -1.0, K.w);
                 mdot<T>(c, K, K.w, n, 1, K.w, K.nrm);
             }
-            c->prof.launches += 2;
-            k_givens<<<1, 1, 0, s>>>(K.H, m, j, K.h1, K.h2, K.nrm, K.cs, K.sn, K.g, K.st);
-            k_scale_inv<T><<<grid_for(n), 256, 0, s>>>(K.V + (size_t)(j + 1) * n, K.w, &K.st->beta, n);
-            NBP_LAUNCHED();
+            timed(c, "arnoldi/givens", 0.0, [&] { k_givens<<<1, 1, 0, s>>>(K.H, m, j, K.h1, K.h2, K.nrm, K.cs, K.sn, K.g, K.st); });
+            timed(c, "arnoldi/scale", 2.0 * n * sizeof(T),
+                  [&] { k_scale_inv<T><<<grid_for(n), 256, 0, s>>>(K.V + (size_t)(j + 1) * n, K.w, &K.st->beta, n); });
             read_state(c, K.st);
             require(!c->hst->nan, NBP_ERR_NAN, "gmres: NaN/Inf in the Arnoldi process");
             res = c->hst->res;
@@ -373,10 +402,10 @@ static T *chebyshev(nbp_ctx *c, Level &L, int vsel, int k, const T *b, T *x, T *
     T *cur = x, *nxt = alt;
     if (k <= 0) return cur;
     if (zero_start) {
-        c->prof.launches++;
-        k_cheb_first<T><<<grid_exact((long long)L.M.nbr * bs), 256, 0, c->s>>>(L.M.nbr, bs, dinv_of<T>(L), b, 1.0 / ch.theta,
-                                                                               d, cur);
-        NBP_LAUNCHED();
+        timed(c, "amg/cheb_first", (double)L.M.nbr * bs * (bs + 3) * sizeof(T), [&] {
+            k_cheb_first<T><<<grid_exact((long long)L.M.nbr * bs), 256, 0, c->s>>>(L.M.nbr, bs, dinv_of<T>(L), b,
+                                                                                   1.0 / ch.theta, d, cur);
+        });
     } else {
         cheb_step<T>(c, L, vsel, b, cur, nxt, d, 0.0, 1.0 / ch.theta);
         std::swap(cur, nxt);
@@ -407,18 +436,16 @@ static void kcycle_level(nbp_ctx *c, Hier &H, int cl, int vsel, const T *b, T *x
     copy<T>(r, b, n, c->s);
     vcycle_level<T>(c, H, cl, vsel, b, z1);
     do_spmv<T>(c, L.M, vsel, sargs(z1, w1), EPI_SET, false);
-    c->prof.launches += 2;
-    k_kdots<T><<<kKdotBlocks, 256, 0, c->s>>>(w1, w1, w1, r, n, L.kdots, 0, 1);
-    k_kupd1<T><<<g, 256, 0, c->s>>>(r, w1, L.kdots, n);
-    NBP_LAUNCHED();
+    timed(c, "kcycle/dots", 0.0, [&] { k_kdots<T><<<kKdotBlocks, 256, 0, c->s>>>(w1, w1, w1, r, n, L.kdots, 0, 1); });
+    timed(c, "kcycle/update", 0.0, [&] { k_kupd1<T><<<g, 256, 0, c->s>>>(r, w1, L.kdots, n); });
     vcycle_level<T>(c, H, cl, vsel, r, z2);
     do_spmv<T>(c, L.M, vsel, sargs(z2, w2), EPI_SET, false);
-    c->prof.launches += 4;
-    k_kdots<T><<<kKdotBlocks, 256, 0, c->s>>>(w2, w1, (const T *)nullptr, (const T *)nullptr, n, L.kdots, 3, 3);
-    k_kupd2<T><<<g, 256, 0, c->s>>>(w2, z2, w1, z1, L.kdots, n);
-    k_kdots<T><<<kKdotBlocks, 256, 0, c->s>>>(w2, w2, w2, r, n, L.kdots, 4, 5);
-    k_kupd3<T><<<g, 256, 0, c->s>>>(x, z1, z2, L.kdots, n);
-    NBP_LAUNCHED();
+    timed(c, "kcycle/dots", 0.0, [&] {
+        k_kdots<T><<<kKdotBlocks, 256, 0, c->s>>>(w2, w1, (const T *)nullptr, (const T *)nullptr, n, L.kdots, 3, 3);
+    });
+    timed(c, "kcycle/update", 0.0, [&] { k_kupd2<T><<<g, 256, 0, c->s>>>(w2, z2, w1, z1, L.kdots, n); });
+    timed(c, "kcycle/dots", 0.0, [&] { k_kdots<T><<<kKdotBlocks, 256, 0, c->s>>>(w2, w2, w2, r, n, L.kdots, 4, 5); });
+    timed(c, "kcycle/update", 0.0, [&] { k_kupd3<T><<<g, 256, 0, c->s>>>(x, z1, z2, L.kdots, n); });
 }
 
 // V(1,1)-cycle from level l with right-hand side b; result written to out.
@@ -430,9 +457,8 @@ static void vcycle_level(nbp_ctx *c, Hier &H, int l, int vsel, const T *b, T *ou
     const int k = c->opt.cheb_degree;
     if (l == H.nlev - 1) {
         if (H.cinv) {
-            c->prof.launches++;
-            k_dense_gemv<T><<<grid_exact((long long)H.nc * 32), 256, 0, c->s>>>(H.cinv, H.nc, b, out);
-            NBP_LAUNCHED();
+            timed(c, "amg/coarsest_gemv", (double)H.nc * H.nc * 8.0,
+                  [&] { k_dense_gemv<T><<<grid_exact((long long)H.nc * 32), 256, 0, c->s>>>(H.cinv, H.nc, b, out); });
         } else {
             T *res = chebyshev<T>(c, L, vsel, std::max(k, 1), b, out, wvec<T>(L, 2), true);
             if (res != out) copy<T>(out, res, n, c->s);
@@ -452,14 +478,11 @@ static void vcycle_level(nbp_ctx *c, Hier &H, int l, int vsel, const T *b, T *ou
     do_spmv<T>(c, L.M, vsel, [&] { SpmvArgs a = sargs(cur, r); a.b = b; return a; }(), EPI_RES, false);
     Level &Lc = H.L[l + 1];
     T *bc = wvec<T>(Lc, 0), *xc = wvec<T>(Lc, 1);
-    c->prof.launches++;
-    k_restrict<T><<<grid_exact(Lc.M.nbr), 256, 0, c->s>>>(L.mptr, L.mem, Lc.M.nbr, bs, r, bc);
-    NBP_LAUNCHED();
+    timed(c, "amg/restrict", 0.0,
+          [&] { k_restrict<T><<<grid_exact(Lc.M.nbr), 256, 0, c->s>>>(L.mptr, L.mem, Lc.M.nbr, bs, r, bc); });
     if (H.kcycle && l + 1 < H.nlev - 1) kcycle_level<T>(c, H, l + 1, vsel, bc, xc);
     else vcycle_level<T>(c, H, l + 1, vsel, bc, xc);
-    c->prof.launches++;
-    k_prolong<T><<<grid_exact(n), 256, 0, c->s>>>(L.agg, L.M.nbr, bs, xc, cur);
-    NBP_LAUNCHED();
+    timed(c, "amg/prolong", 0.0, [&] { k_prolong<T><<<grid_exact(n), 256, 0, c->s>>>(L.agg, L.M.nbr, bs, xc, cur); });
     T *fin = chebyshev<T>(c, L, vsel, k, b, cur, oth, false);
     if (fin != out) copy<T>(out, fin, n, c->s);
 }
@@ -901,6 +924,8 @@ __global__ void k_adj_grad(const int *optr, const int *oidx, const double *oval,
     }
 }
 
+static std::string profile_report(nbp_ctx *c);
+
 static void finish_profile(nbp_ctx *c) {
     nbp_profile_info &p = c->pinfo;
     const double wait = p.host_wait_s;
@@ -911,6 +936,7 @@ static void finish_profile(nbp_ctx *c) {
     p.kernel_launches = c->prof.launches;
     if (!c->prof.on) return;
     NBP_CUDA(cudaStreamSynchronize(c->s));
+    c->report = profile_report(c);
     for (auto &r : c->prof.recs) {
         float ms = 0.f;
         NBP_CUDA(cudaEventElapsedTime(&ms, c->prof.pool[r.e0], c->prof.pool[r.e0 + 1]));
@@ -922,6 +948,29 @@ static void finish_profile(nbp_ctx *c) {
         if (r.cat == CAT_ARNOLDI) { p.arnoldi_ms += ms; p.arnoldi_bytes += r.bytes; p.arnoldi_launches++; }
         if (r.cat == CAT_VCYCLE) p.vcycle_ms += ms;
     }
+}
+
+// per-tag totals of the last profiled call, as a JSON object {tag: [launches, ms, bytes]}
+static std::string profile_report(nbp_ctx *c) {
+    if (!c->prof.on) return "{}";
+    std::map<std::string, std::tuple<long long, double, double>> m;
+    for (auto &r : c->prof.recs) {
+        if (r.tag.empty()) continue;
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, c->prof.pool[r.e0], c->prof.pool[r.e0 + 1]) != cudaSuccess) continue;
+        auto &e = m[r.tag];
+        std::get<0>(e) += 1;
+        std::get<1>(e) += ms;
+        std::get<2>(e) += r.bytes;
+    }
+    std::string out = "{";
+    char buf[256];
+    for (auto &kv : m) {
+        snprintf(buf, sizeof(buf), "%s\"%s\": [%lld, %.6f, %.0f]", out.size() > 1 ? ", " : "", kv.first.c_str(),
+                 std::get<0>(kv.second), std::get<1>(kv.second), std::get<2>(kv.second));
+        out += buf;
+    }
+    return out + "}";
 }
 
 static void begin_call(nbp_ctx *c) {
@@ -1254,6 +1303,8 @@ nbp_status nbp_profile_get(nbp_ctx *c, nbp_profile_info *out) {
     *out = c->pinfo;
     return NBP_OK;
 }
+
+const char *nbp_profile_report(const nbp_ctx *c) { return c ? c->report.c_str() : "{}"; }
 
 }  // extern "C"
 

@@ -4,6 +4,7 @@
 #include "kernels.cuh"
 #include "spmv.cuh"
 
+#include <algorithm>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -143,19 +144,26 @@ void spmv(const DMat &M, int vsel, SpmvArgs a, int epi, bool lr, cudaStream_t s,
 template void spmv<double>(const DMat &, int, SpmvArgs, int, bool, cudaStream_t, int);
 template void spmv<float>(const DMat &, int, SpmvArgs, int, bool, cudaStream_t, int);
 
-template <typename XT> static float time_choice(const DMat &M, int vsel, int G, XT *x, XT *y, cudaStream_t s,
-                                                cudaEvent_t e0, cudaEvent_t e1) {
+// Time of one launch with a cold L2 (a 256 MB buffer is written before each
+// timed launch, as the other levels' traffic does inside an AMG cycle); the
+// median of three.
+template <typename XT> static float time_choice(const DMat &M, int vsel, int G, XT *x, XT *y, char *flush,
+                                                size_t flush_bytes, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1) {
     SpmvArgs a{};
     a.x = x;
     a.y = y;
-    spmv<XT>(M, vsel, a, EPI_SET, false, s, G);   // warm
-    NBP_CUDA(cudaEventRecord(e0, s));
-    for (int r = 0; r < 3; ++r) spmv<XT>(M, vsel, a, EPI_SET, false, s, G);
-    NBP_CUDA(cudaEventRecord(e1, s));
-    NBP_CUDA(cudaEventSynchronize(e1));
-    float ms = 0.f;
-    NBP_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-    return ms;
+    spmv<XT>(M, vsel, a, EPI_SET, false, s, G);   // warm up the code path
+    float t[3];
+    for (int r = 0; r < 3; ++r) {
+        NBP_CUDA(cudaMemsetAsync(flush, r, flush_bytes, s));
+        NBP_CUDA(cudaEventRecord(e0, s));
+        spmv<XT>(M, vsel, a, EPI_SET, false, s, G);
+        NBP_CUDA(cudaEventRecord(e1, s));
+        NBP_CUDA(cudaEventSynchronize(e1));
+        NBP_CUDA(cudaEventElapsedTime(&t[r], e0, e1));
+    }
+    std::sort(t, t + 3);
+    return t[1];
 }
 
 // Decisions are cached per (rows, stored blocks, block size, precision) for
@@ -183,12 +191,14 @@ void autotune_spmv(DMat &M, int precision, cudaStream_t s) {
     if (g0 < 32) cands.push_back(g0 * 2);
     float best = 1e30f;
     int arg = 0;
+    const size_t flush_bytes = 256ull << 20;   // twice the L2
+    char *flush = dmalloc<char>(flush_bytes, s);
     if (vsel == 0) {
         double *x = dmalloc<double>(nx, s), *y = dmalloc<double>(ny, s);
         NBP_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * nx, s));
         for (int G : cands) {
             if (G == 0 && !M.sl_v) continue;
-            const float t = time_choice<double>(M, vsel, G, x, y, s, e0, e1);
+            const float t = time_choice<double>(M, vsel, G, x, y, flush, flush_bytes, s, e0, e1);
             if (t < best) { best = t; arg = G; }
         }
         dfree(x, s); dfree(y, s);
@@ -198,11 +208,12 @@ void autotune_spmv(DMat &M, int precision, cudaStream_t s) {
         for (int G : cands) {
             if (G == 0 && !(vsel == 2 ? (const void *)M.sl_v16 : (const void *)M.sl_v32)) continue;
             if (G > 0 && !(vsel == 2 ? (const void *)M.v16 : (const void *)M.v32)) continue;
-            const float t = time_choice<float>(M, vsel, G, x, y, s, e0, e1);
+            const float t = time_choice<float>(M, vsel, G, x, y, flush, flush_bytes, s, e0, e1);
             if (t < best) { best = t; arg = G; }
         }
         dfree(x, s); dfree(y, s);
     }
+    dfree(flush, s);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     std::lock_guard<std::mutex> lock(g_tune_mutex);

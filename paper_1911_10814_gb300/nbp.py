@@ -96,6 +96,7 @@ SIGNATURES = {
     "nbp_shat_get": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "nbp_profile": (ctypes.c_int, [_vp, _i32]),
     "nbp_profile_get": (ctypes.c_int, [_vp, ctypes.POINTER(nbp_profile_info)]),
+    "nbp_profile_report": (ctypes.c_char_p, [_vp]),
     "nbp_batch_create": (ctypes.c_int, [ctypes.POINTER(_vp), _i32, ctypes.POINTER(nbp_system), ctypes.POINTER(nbp_options)]),
     "nbp_batch_setup": (ctypes.c_int, [_vp]),
     "nbp_batch_solve": (ctypes.c_int, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(nbp_options),
@@ -411,3 +412,7 @@ class Solver:
         p = nbp_profile_info()
         self._check(self.lib.nbp_profile_get(self.ctx, ctypes.byref(p)))
         return p.as_dict()
+
+    def profile_report(self):
+        import json
+        return json.loads(self.lib.nbp_profile_report(self.ctx).decode())
