@@ -44,6 +44,7 @@ void hier_free(Hier &H, cudaStream_t s) {
         L = Level();
     }
     dfree(H.cinv, s);
+    dfree(H.cinv32, s);
     H = Hier();
 }
 
@@ -765,8 +766,13 @@ void amg_build(Hier &H, const DMat &fine, const nbp_options &o, int precision, c
     dfree(singular, s);
     require(sing == 0, NBP_ERR_INVALID, "setup: singular diagonal block in an AMG level");
     const Level &C = H.L[H.nlev - 1];
-    if ((long long)C.M.nbr * H.bs <= kCoarseDenseMax) dense_inverse(C.M, H.cinv, H.nc, s);
-    else { H.cinv = nullptr; H.nc = 0; }
+    if ((long long)C.M.nbr * H.bs <= kCoarseDenseMax) {
+        dense_inverse(C.M, H.cinv, H.nc, s);
+        const long long nn = (long long)H.nc * H.nc;
+        H.cinv32 = dmalloc<float>(nn, s);
+        k_to_f32<<<grid_for(nn), 256, 0, s>>>(H.cinv, H.cinv32, nn);
+        NBP_LAUNCHED();
+    } else { H.cinv = nullptr; H.nc = 0; }
     H.built = true;
 }
 

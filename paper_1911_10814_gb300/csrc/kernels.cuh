@@ -29,7 +29,8 @@ struct SpmvArgs {
     const void *dinv;       // EPI_CHEB: BR x BR per row (same type as vectors)
     void *d;                // EPI_CHEB: Chebyshev direction (in/out)
     void *xout;             // EPI_CHEB: x + d
-    double c1, c2;          // EPI_CHEB coefficients
+    double c1, c2;          // EPI_CHEB coefficients (FP64 vectors)
+    float c1f, c2f;         // the same, pre-rounded for FP32 vectors (no FP64 work per element)
     const int *lr_rp, *lr_k, *lr_c;   // rank-one epilogue (EPI_SET only)
     const double *lr_val, *lr_f;
     int nslice;                       // sliced-ELL layout (k_sell): slices of C rows
@@ -106,7 +107,8 @@ __global__ void __launch_bounds__(256) k_bspmv(SpmvArgs a) {
             t = dinv[0] * r0 + dinv[1] * r1 + dinv[2] * r2;
         }
         XT *d = (XT *)a.d;
-        const AT dn = (AT)a.c1 * d[idx] + (AT)a.c2 * t;
+        const AT c1 = sizeof(AT) == 4 ? (AT)a.c1f : (AT)a.c1, c2 = sizeof(AT) == 4 ? (AT)a.c2f : (AT)a.c2;
+        const AT dn = c1 * d[idx] + c2 * t;
         d[idx] = dn;
         ((XT *)a.xout)[idx] = x[idx] + dn;
     }
@@ -152,6 +154,7 @@ __global__ void __launch_bounds__(256) k_sell(SpmvArgs a) {
         const XT *dinv = (const XT *)a.dinv + (long long)row * BB;
         XT *d = (XT *)a.d;
         XT *xo = (XT *)a.xout;
+        const AT c1 = sizeof(AT) == 4 ? (AT)a.c1f : (AT)a.c1, c2 = sizeof(AT) == 4 ? (AT)a.c2f : (AT)a.c2;
         AT r[3];
 #pragma unroll
         for (int q = 0; q < BS; ++q) r[q] = b[(long long)row * BS + q] - accs[q];
@@ -161,7 +164,7 @@ __global__ void __launch_bounds__(256) k_sell(SpmvArgs a) {
 #pragma unroll
             for (int c = 0; c < BS; ++c) tq += dinv[q * BS + c] * r[c];
             const long long idx = (long long)row * BS + q;
-            const AT dn = (AT)a.c1 * d[idx] + (AT)a.c2 * tq;
+            const AT dn = c1 * d[idx] + c2 * tq;
             d[idx] = dn;
             xo[idx] = x[idx] + dn;
         }
@@ -235,22 +238,22 @@ __global__ void k_reduce_partials(const double *__restrict__ partial, int nblock
 template <typename T>
 __global__ void __launch_bounds__(256) k_maxpy(const T *__restrict__ V, long long ldv, int ncols, const double *__restrict__ coef,
                                                double alpha, T *__restrict__ w, long long n) {
-    __shared__ double cs[256];
+    __shared__ T cs[256];
     for (int c0 = 0; c0 < ncols; c0 += 256) {
         const int cn = min(256, ncols - c0);
         __syncthreads();
-        if ((int)threadIdx.x < cn) cs[threadIdx.x] = alpha * coef[c0 + threadIdx.x];
+        if ((int)threadIdx.x < cn) cs[threadIdx.x] = (T)(alpha * coef[c0 + threadIdx.x]);
         __syncthreads();
         for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
             T acc = 0;
             int j = 0;
             for (; j + 4 <= cn; j += 4) {
-                acc += (T)cs[j] * V[(long long)(c0 + j) * ldv + t];
-                acc += (T)cs[j + 1] * V[(long long)(c0 + j + 1) * ldv + t];
-                acc += (T)cs[j + 2] * V[(long long)(c0 + j + 2) * ldv + t];
-                acc += (T)cs[j + 3] * V[(long long)(c0 + j + 3) * ldv + t];
+                acc += cs[j] * V[(long long)(c0 + j) * ldv + t];
+                acc += cs[j + 1] * V[(long long)(c0 + j + 1) * ldv + t];
+                acc += cs[j + 2] * V[(long long)(c0 + j + 2) * ldv + t];
+                acc += cs[j + 3] * V[(long long)(c0 + j + 3) * ldv + t];
             }
-            for (; j < cn; ++j) acc += (T)cs[j] * V[(long long)(c0 + j) * ldv + t];
+            for (; j < cn; ++j) acc += cs[j] * V[(long long)(c0 + j) * ldv + t];
             w[t] += acc;
         }
     }
@@ -265,8 +268,8 @@ __global__ void __launch_bounds__(256) k_maxpy_dot(const T *__restrict__ V, long
                                                    const double *__restrict__ coef, T *__restrict__ w, long long n,
                                                    int norm_only, double *__restrict__ partial) {
     __shared__ double red[MAXC][8];
-    __shared__ double cs[MAXC];
-    if ((int)threadIdx.x < ncols) cs[threadIdx.x] = coef[threadIdx.x];
+    __shared__ T cs[MAXC];
+    if ((int)threadIdx.x < ncols) cs[threadIdx.x] = (T)coef[threadIdx.x];
     __syncthreads();
     const long long chunk = (n + gridDim.x - 1) / gridDim.x;
     const long long lo = (long long)blockIdx.x * chunk;
@@ -282,7 +285,7 @@ __global__ void __launch_bounds__(256) k_maxpy_dot(const T *__restrict__ V, long
         for (int q = 0; q < MAXC; ++q)
             if (q < ncols) {
                 v[q] = V[(long long)q * ldv + t];
-                s -= (T)cs[q] * v[q];
+                s -= cs[q] * v[q];
             }
         w[t] = s;
         if (norm_only) acc[0] += s * s;
@@ -328,9 +331,16 @@ template <typename T> __global__ void k_sub(T *z, const T *x, const T *y, long l
 }
 // v = w / s[0] (skips when s[0] == 0)
 template <typename T> __global__ void k_scale_inv(T *v, const T *w, const double *s, long long n) {
-    const double d = *s;
-    if (d == 0.0) return;
-    const T inv = (T)(1.0 / d);
+    __shared__ T inv_s;
+    __shared__ int zero;
+    if (threadIdx.x == 0) {   // one FP64 division per block, not per element
+        const double d = *s;
+        zero = (d == 0.0);
+        inv_s = zero ? T(0) : (T)(1.0 / d);
+    }
+    __syncthreads();
+    if (zero) return;
+    const T inv = inv_s;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         v[i] = w[i] * inv;
 }
@@ -377,27 +387,28 @@ __global__ void k_prolong(const int *__restrict__ agg, int n, int bs, const T *_
 }
 // Chebyshev first step from x = 0: d = c2 Dinv b; x = d
 template <typename T>
-__global__ void k_cheb_first(int nbr, int bs, const T *__restrict__ dinv, const T *__restrict__ b, double c2, T *__restrict__ d,
+__global__ void k_cheb_first(int nbr, int bs, const T *__restrict__ dinv, const T *__restrict__ b, T c2, T *__restrict__ d,
                              T *__restrict__ x) {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (long long)nbr * bs) return;
     const int i = (int)(t / bs), a = (int)(t - (long long)i * bs);
     T s = 0;
     for (int c = 0; c < bs; ++c) s += dinv[(long long)i * bs * bs + a * bs + c] * b[(long long)i * bs + c];
-    const T dn = (T)c2 * s;
+    const T dn = c2 * s;
     d[t] = dn;
     x[t] = dn;
 }
-// x = Cinv b, dense (coarsest level); one warp per row
+// x = Cinv b, dense (coarsest level); one warp per row; the inverse is stored
+// in the vector type (FP64 or FP32)
 template <typename T>
-__global__ void k_dense_gemv(const double *__restrict__ Cinv, int n, const T *__restrict__ b, T *__restrict__ x) {
+__global__ void k_dense_gemv(const T *__restrict__ Cinv, int n, const T *__restrict__ b, T *__restrict__ x) {
     const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int ln = threadIdx.x & 31;
     if (row >= n) return;
-    double s = 0.0;
-    for (int c = ln; c < n; c += 32) s += Cinv[(long long)row * n + c] * (double)b[c];
+    T s = 0;
+    for (int c = ln; c < n; c += 32) s += Cinv[(long long)row * n + c] * b[c];
     s = warp_sum(s);
-    if (ln == 0) x[row] = (T)s;
+    if (ln == 0) x[row] = s;
 }
 
 // ============================================================== K-cycle
@@ -413,13 +424,13 @@ __global__ void __launch_bounds__(256) k_kdots(const T *__restrict__ a, const T 
     __shared__ bool last;
     const long long chunk = (n + gridDim.x - 1) / gridDim.x;
     const long long lo = (long long)blockIdx.x * chunk, hi = min(n, lo + chunk);
-    double t0 = 0.0, t1 = 0.0;
+    T p0 = 0, p1 = 0;   // per-thread sums in the vector type; FP64 from the warp level up
     for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-        t0 += (double)a[i] * (double)b[i];
-        if (c) t1 += (double)c[i] * (double)d[i];
+        p0 += a[i] * b[i];
+        if (c) p1 += c[i] * d[i];
     }
-    t0 = warp_sum(t0);
-    t1 = warp_sum(t1);
+    double t0 = warp_sum((double)p0);
+    double t1 = warp_sum((double)p1);
     if ((threadIdx.x & 31) == 0) { s0[threadIdx.x >> 5] = t0; s1[threadIdx.x >> 5] = t1; }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -446,25 +457,39 @@ __global__ void __launch_bounds__(256) k_kdots(const T *__restrict__ a, const T 
 }
 // r -= a1 w1 with a1 = (w1.r)/(w1.w1) = kd[1]/kd[0]; a1 saved in kd[2]
 template <typename T> __global__ void k_kupd1(T *r, const T *w1, double *kd, long long n) {
-    const double a1 = kd[0] > 0.0 ? kd[1] / kd[0] : 0.0;
-    if (blockIdx.x == 0 && threadIdx.x == 0) kd[2] = a1;
+    __shared__ T a1s;
+    if (threadIdx.x == 0) {
+        const double a1 = kd[0] > 0.0 ? kd[1] / kd[0] : 0.0;
+        a1s = (T)a1;
+        if (blockIdx.x == 0) kd[2] = a1;
+    }
+    __syncthreads();
+    const T a1 = a1s;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        r[i] = r[i] - (T)a1 * w1[i];
+        r[i] = r[i] - a1 * w1[i];
 }
 // beta = (w2.w1)/(w1.w1) = kd[3]/kd[0]; w2 -= beta w1; z2 -= beta z1
 template <typename T> __global__ void k_kupd2(T *w2, T *z2, const T *w1, const T *z1, const double *kd, long long n) {
-    const double beta = kd[0] > 0.0 ? kd[3] / kd[0] : 0.0;
+    __shared__ T bs_;
+    if (threadIdx.x == 0) bs_ = (T)(kd[0] > 0.0 ? kd[3] / kd[0] : 0.0);
+    __syncthreads();
+    const T beta = bs_;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        w2[i] = w2[i] - (T)beta * w1[i];
-        z2[i] = z2[i] - (T)beta * z1[i];
+        w2[i] = w2[i] - beta * w1[i];
+        z2[i] = z2[i] - beta * z1[i];
     }
 }
 // x = a1 z1 + a2 z2 with a2 = (w2.r)/(w2.w2) = kd[5]/kd[4]
 template <typename T> __global__ void k_kupd3(T *x, const T *z1, const T *z2, const double *kd, long long n) {
-    const double a1 = kd[2];
-    const double a2 = kd[4] > 0.0 ? kd[5] / kd[4] : 0.0;
+    __shared__ T a1s, a2s;
+    if (threadIdx.x == 0) {
+        a1s = (T)kd[2];
+        a2s = (T)(kd[4] > 0.0 ? kd[5] / kd[4] : 0.0);
+    }
+    __syncthreads();
+    const T a1 = a1s, a2 = a2s;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        x[i] = (T)a1 * z1[i] + (T)a2 * z2[i];
+        x[i] = a1 * z1[i] + a2 * z2[i];
 }
 
 // =============================================================== rank one

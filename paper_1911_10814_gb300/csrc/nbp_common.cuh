@@ -125,6 +125,7 @@ struct Hier {
     bool kcycle = false;                     // Krylov-accelerated cycle on the coarse levels
     Level L[kMaxLevels];
     double *cinv = nullptr;                  // coarsest dense inverse (nc x nc, row-major) or null
+    float *cinv32 = nullptr;                 // its FP32 copy (FP32 inner solves)
     int nc = 0;
     bool built = false;
 };

@@ -369,6 +369,9 @@ static GmResult gmres(nbp_ctx *c, Krylov<T> &K, long long n, Op op, Pc pc, const
 template <typename T> static T *wvec(Level &L, int q);
 template <> double *wvec<double>(Level &L, int q) { return L.w64[q]; }
 template <> float *wvec<float>(Level &L, int q) { return L.w32[q]; }
+template <typename T> static const T *cinv_of(const Hier &H);
+template <> const double *cinv_of<double>(const Hier &H) { return H.cinv; }
+template <> const float *cinv_of<float>(const Hier &H) { return H.cinv32; }
 template <typename T> static const T *dinv_of(const Level &L);
 template <> const double *dinv_of<double>(const Level &L) { return L.dinv; }
 template <> const float *dinv_of<float>(const Level &L) { return L.dinv32; }
@@ -388,6 +391,7 @@ template <typename T>
 static void cheb_step(nbp_ctx *c, Level &L, int vsel, const T *b, const T *x, T *xout, T *d, double c1, double c2) {
     SpmvArgs a = sargs(x, nullptr);
     a.b = b; a.dinv = dinv_of<T>(L); a.d = d; a.xout = xout; a.c1 = c1; a.c2 = c2;
+    a.c1f = (float)c1; a.c2f = (float)c2;
     do_spmv<T>(c, L.M, vsel, a, EPI_CHEB, false, (&L == &c->HA.L[0]) ? CAT_CHEB_A0 : CAT_SPMV);
 }
 
@@ -404,7 +408,7 @@ static T *chebyshev(nbp_ctx *c, Level &L, int vsel, int k, const T *b, T *x, T *
     if (zero_start) {
         timed(c, "amg/cheb_first", (double)L.M.nbr * bs * (bs + 3) * sizeof(T), [&] {
             k_cheb_first<T><<<grid_exact((long long)L.M.nbr * bs), 256, 0, c->s>>>(L.M.nbr, bs, dinv_of<T>(L), b,
-                                                                                   1.0 / ch.theta, d, cur);
+                                                                                   (T)(1.0 / ch.theta), d, cur);
         });
     } else {
         cheb_step<T>(c, L, vsel, b, cur, nxt, d, 0.0, 1.0 / ch.theta);
@@ -458,7 +462,7 @@ static void vcycle_level(nbp_ctx *c, Hier &H, int l, int vsel, const T *b, T *ou
     if (l == H.nlev - 1) {
         if (H.cinv) {
             timed(c, "amg/coarsest_gemv", (double)H.nc * H.nc * 8.0,
-                  [&] { k_dense_gemv<T><<<grid_exact((long long)H.nc * 32), 256, 0, c->s>>>(H.cinv, H.nc, b, out); });
+                  [&] { k_dense_gemv<T><<<grid_exact((long long)H.nc * 32), 256, 0, c->s>>>(cinv_of<T>(H), H.nc, b, out); });
         } else {
             T *res = chebyshev<T>(c, L, vsel, std::max(k, 1), b, out, wvec<T>(L, 2), true);
             if (res != out) copy<T>(out, res, n, c->s);
