@@ -138,6 +138,23 @@ class Clocks:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
+def max_over_ranks(ms: float, device: str = "cpu") -> float:
+    """The slowest rank's time (all ranks receive it); identity without a process group."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(ms)
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_seconds_per_solve(ms_per_step: float, world_size: int) -> float:
+    """Replicas: every rank solves one tangent per step, so the whole job
+    completes world_size solves in the slowest rank's step time."""
+    return ms_per_step / 1e3 / world_size
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -319,12 +336,8 @@ def main():
             e[2] += by
     s.profile(False)
     prof["kernel_launches"] = launches
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device=f"cuda:{dev}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = ms / 1e3 / ws   # seconds per solve over the whole job (each rank solves one replica per step)
+    ms = max_over_ranks(ms, f"cuda:{dev}")
+    value = job_seconds_per_solve(ms, ws)
     err_vs_fp64 = float(torch.linalg.norm(x - x64) / torch.linalg.norm(x64)) if x64 is not None else None
 
     # end to end through the public C ABI with host buffers (copies inside the call)
