@@ -33,6 +33,10 @@ struct SpmvArgs {
     float c1f, c2f;         // the same, pre-rounded for FP32 vectors (no FP64 work per element)
     const int *lr_rp, *lr_k, *lr_c;   // rank-one epilogue (EPI_SET only)
     const double *lr_val, *lr_f;
+    const void *dV;                   // fused inner products (k_sell, EPI_SET): columns of V ...
+    long long dldv;                   // ... with this stride,
+    int ndot;                         // ... this many (<= 16),
+    double *dpart;                    // ... per-block partials [col][block]
     int nslice;                       // sliced-ELL layout (k_sell): slices of C rows
     const long long *sl_ptr;
     const int *sl_ci;
@@ -119,15 +123,17 @@ __global__ void __launch_bounds__(256) k_bspmv(SpmvArgs a) {
 // lengths vary, to cut padding).  Every load of values and columns by the C
 // threads of a slice is one contiguous segment (C x value bytes).  Same
 // epilogues as k_bspmv (a.rp unused; a.sl_* describe the slices).
-template <int BS, typename VT, typename XT, int EPI, bool LR, int C>
+template <int BS, typename VT, typename XT, int EPI, bool LR, int C, bool DOT = false>
 __global__ void __launch_bounds__(256) k_sell(SpmvArgs a) {
     using AT = XT;
     constexpr int BB = BS * BS;
+    constexpr int MAXD = 16;
     const int row = blockIdx.x * blockDim.x + threadIdx.x;
     const int sl = row / C, t = row % C;
-    if (sl >= a.nslice) return;
-    const long long base = a.sl_ptr[sl];
-    const int w = (int)((a.sl_ptr[sl + 1] - base) / C);
+    if (!DOT && sl >= a.nslice) return;
+    const bool live = sl < a.nslice;
+    const long long base = live ? a.sl_ptr[sl] : 0;
+    const int w = live ? (int)((a.sl_ptr[sl + 1] - base) / C) : 0;
     const VT *__restrict__ val = (const VT *)a.val;
     const int *__restrict__ ci = a.sl_ci;
     const XT *__restrict__ x = (const XT *)a.x;
@@ -146,7 +152,8 @@ __global__ void __launch_bounds__(256) k_sell(SpmvArgs a) {
             acc2 += cvt<AT>(__ldg(v + 6 * C)) * x0 + cvt<AT>(__ldg(v + 7 * C)) * x1 + cvt<AT>(__ldg(v + 8 * C)) * x2;
         }
     }
-    if (row >= a.nbr) return;
+    if (!DOT && row >= a.nbr) return;
+    const bool own = row < a.nbr;
     AT accs[3] = {acc0, acc1, acc2};
     XT *y = (XT *)a.y;
     if (EPI == EPI_CHEB) {
@@ -170,24 +177,52 @@ __global__ void __launch_bounds__(256) k_sell(SpmvArgs a) {
         }
         return;
     }
+    if (own) {
 #pragma unroll
-    for (int q = 0; q < BS; ++q) {
-        const long long idx = (long long)row * BS + q;
-        AT s = accs[q];
-        if (EPI == EPI_SET) {
-            if (LR) {
-                double tt = 0.0;
-                for (int e = a.lr_rp[row]; e < a.lr_rp[row + 1]; ++e)
-                    if (a.lr_c[e] == q) tt += a.lr_f[a.lr_k[e]] * a.lr_val[e];
-                s = (AT)((double)s + tt);
+        for (int q = 0; q < BS; ++q) {
+            const long long idx = (long long)row * BS + q;
+            AT s = accs[q];
+            if (EPI == EPI_SET) {
+                if (LR) {
+                    double tt = 0.0;
+                    for (int e = a.lr_rp[row]; e < a.lr_rp[row + 1]; ++e)
+                        if (a.lr_c[e] == q) tt += a.lr_f[a.lr_k[e]] * a.lr_val[e];
+                    s = (AT)((double)s + tt);
+                }
+                y[idx] = s;
+            } else if (EPI == EPI_ADD) {
+                y[idx] += s;
+            } else if (EPI == EPI_SUB) {
+                y[idx] -= s;
+            } else {
+                y[idx] = ((const XT *)a.b)[idx] - s;
             }
-            y[idx] = s;
-        } else if (EPI == EPI_ADD) {
-            y[idx] += s;
-        } else if (EPI == EPI_SUB) {
-            y[idx] -= s;
-        } else {
-            y[idx] = ((const XT *)a.b)[idx] - s;
+            accs[q] = s;
+        }
+    }
+    if constexpr (DOT) {
+        // partial inner products of y with columns 0..ndot-1 of V (the first
+        // Gram-Schmidt pass of the Arnoldi step that follows this product)
+        __shared__ double red[MAXD][8];
+        const XT *V = (const XT *)a.dV;
+        const int warp = threadIdx.x >> 5, ln = threadIdx.x & 31;
+#pragma unroll
+        for (int cidx = 0; cidx < MAXD; ++cidx) {
+            if (cidx < a.ndot) {
+                AT p = 0;
+                if (own) {
+#pragma unroll
+                    for (int q = 0; q < BS; ++q) p += accs[q] * V[(long long)cidx * a.dldv + (long long)row * BS + q];
+                }
+                const double r = warp_sum((double)p);
+                if (ln == 0) red[cidx][warp] = r;
+            }
+        }
+        __syncthreads();
+        if ((int)threadIdx.x < a.ndot) {
+            double u = 0.0;
+            for (int k = 0; k < (int)(blockDim.x >> 5); ++k) u += red[threadIdx.x][k];
+            a.dpart[(long long)threadIdx.x * gridDim.x + blockIdx.x] = u;
         }
     }
 }
@@ -364,16 +399,26 @@ __global__ void k_gm_init(double *g, int m1, const double *beta2, double *beta, 
 __global__ void k_recip(long long n, const double *a, double *b);
 
 // ================================================================= AMG
-// coarse r_c[I] = sum_{i in I} r[i] (members ascending), bs components
+// coarse r_c[I] = sum_{i in I} r[i], bs components: 8 lanes per aggregate
+// (aggregates have at most 8 members), member loads in parallel, then a
+// fixed xor-shuffle tree inside the 8 lanes
 template <typename T>
 __global__ void k_restrict(const int *__restrict__ mptr, const int *__restrict__ mem, int nc, int bs, const T *__restrict__ r,
                            T *__restrict__ rc) {
-    const int I = blockIdx.x * blockDim.x + threadIdx.x;
-    if (I >= nc) return;
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int I = (int)(g >> 3), l = (int)(g & 7);
+    const bool live = I < nc;
+    const unsigned mask = 0xffu << (threadIdx.x & 24u);
+    if (__all_sync(0xffffffffu, !live)) return;   // whole warp past the end
+    int q = 0, beg = 0;
+    if (live) { beg = mptr[I]; q = mptr[I + 1] - beg; }
+    const int m = (live && l < q) ? mem[beg + l] : -1;
     for (int a = 0; a < bs; ++a) {
-        T s = 0;
-        for (int q = mptr[I]; q < mptr[I + 1]; ++q) s += r[(long long)mem[q] * bs + a];
-        rc[(long long)I * bs + a] = s;
+        T s = (m >= 0) ? r[(long long)m * bs + a] : T(0);
+        s += __shfl_xor_sync(mask, s, 4);
+        s += __shfl_xor_sync(mask, s, 2);
+        s += __shfl_xor_sync(mask, s, 1);
+        if (live && l == 0) rc[(long long)I * bs + a] = s;
     }
 }
 // x[i] += e_c[agg[i]]

@@ -124,6 +124,8 @@ struct nbp_ctx {
     nbp::Bufs<double> B64;
     nbp::Bufs<float> B32;
     double *full_w = nullptr;     // 4N scratch of the outer operator
+    double *dpart = nullptr;      // partials of the inner products fused into the A product
+    long long dpart_n = 0;
     nbp::GmState *hst = nullptr;  // pinned host status
     nbp_info info{};
     nbp::Prof prof;
@@ -237,6 +239,39 @@ template <typename T> static void apply_A(nbp_ctx *c, int vsel, const T *x, T *y
     do_spmv<T>(c, c->A, vsel, a, EPI_SET, lr.n_out > 0, CAT_SPMV_A0);
 }
 
+// w = A x with h = V(:, 0..ncols-1)^T w fused into the product (the first
+// Gram-Schmidt pass of the Arnoldi step); false when the fused kernel does not
+// apply (nothing launched)
+template <typename T>
+static bool apply_A_dot(nbp_ctx *c, int vsel, const T *x, T *y, const T *V, long long ldv, int ncols, double *h) {
+    const DMat &M = c->A;
+    if (ncols < 1 || ncols > 16 || !(M.tuned == 0 || (M.tuned < 0 && M.sl_ci))) return false;
+    const long long need = (long long)spmv_dot_blocks(M) * 16;
+    if (need == 0) return false;
+    if (c->dpart_n < need) {
+        dfree(c->dpart, c->s);
+        c->dpart = dmalloc<double>(need, c->s);
+        c->dpart_n = need;
+    }
+    LowRank &lr = c->lr;
+    SpmvArgs a = sargs(x, y);
+    if (lr.n_out > 0) {
+        timed(c, "A/lowrank_dots", 0.0,
+              [&] { k_lowrank_dots<T><<<lr.n_out, 256, 0, c->s>>>(lr.optr, lr.oidx, lr.oval, lr.r, x, lr.f); });
+        a.lr_rp = lr.lr_rp; a.lr_k = lr.lr_k; a.lr_c = lr.lr_c; a.lr_val = lr.lr_val; a.lr_f = lr.f;
+    }
+    a.dV = V; a.dldv = ldv; a.ndot = ncols; a.dpart = c->dpart;
+    cudaEvent_t e0;
+    prof_begin(c, e0);
+    const int nb = spmv_dot<T>(M, vsel, a, lr.n_out > 0, c->s);
+    prof_end(c, CAT_SPMV_A0, spmv_bytes<T>(M, vsel, EPI_SET) + (double)ncols * 3 * M.nbr * sizeof(T), "A/set+dot");
+    if (nb == 0) return false;   // cannot happen after the checks above
+    timed(c, "arnoldi/reduce", 0.0, [&] {
+        k_reduce_partials<<<grid_exact((long long)ncols * 32), 256, 0, c->s>>>(c->dpart, nb, ncols, h, 0);
+    });
+    return true;
+}
+
 // ------------------------------------------------------------ CGS2 Arnoldi
 template <typename T> static void mdot(nbp_ctx *c, Krylov<T> &K, const T *V, long long ldv, int ncols, const T *w, double *out) {
     cudaEvent_t e0;
@@ -288,9 +323,15 @@ static void read_state(nbp_ctx *c, const GmState *st) {
 // Restarted flexible GMRES, x_0 = 0; stops when the residual estimate
 // |g_{j+1}| <= max(rtol ||b||, atol) (confirmed on the true residual when
 // check_true) or after nmax iterations.
-template <typename T, typename Op, typename Pc>
+struct NoFusedOp {
+    template <typename T> bool operator()(const T *, T *, const T *, long long, int, double *) const { return false; }
+};
+
+// opdot(z, w, V, ldv, ncols, h): w = op(z) with h = V(:, 0..ncols-1)^T w
+// fused into it; returns false when it does not apply.
+template <typename T, typename Op, typename Pc, typename OpDot = NoFusedOp>
 static GmResult gmres(nbp_ctx *c, Krylov<T> &K, long long n, Op op, Pc pc, const T *b, T *x, double rtol, double atol,
-                      int m, int nmax, bool check_true) {
+                      int m, int nmax, bool check_true, OpDot opdot = OpDot()) {
     cudaStream_t s = c->s;
     GmResult R;
     m = std::max(1, std::min(m, std::max(nmax, 1)));
@@ -316,10 +357,13 @@ static GmResult gmres(nbp_ctx *c, Krylov<T> &K, long long n, Op op, Pc pc, const
         for (int j = 0; j < m && R.its < nmax; ++j) {
             T *vj = K.V + (size_t)j * n, *zj = K.Z + (size_t)j * n;
             pc(vj, zj);
-            op(zj, K.w);
-            // CGS2: two Gram-Schmidt passes against V(:, 0..j); for short
+            // CGS2: two Gram-Schmidt passes against V(:, 0..j); the first
+            // inner products ride on the operator when it can, and for short
             // bases each subtraction is fused with the next inner products
-            mdot<T>(c, K, K.V, n, j + 1, K.w, K.h1);
+            if (!opdot(zj, K.w, (const T *)K.V, n, j + 1, K.h1)) {
+                op(zj, K.w);
+                mdot<T>(c, K, K.V, n, j + 1, K.w, K.h1);
+            }
             if (j + 1 <= kFusedCols) {
                 maxpy_dot<T>(c, K, K.V, n, j + 1, K.h1, K.w, 0, K.h2);
                 maxpy_dot<T>(c, K, K.V, n, j + 1, K.h2, K.w, 1, K.nrm);
@@ -483,7 +527,7 @@ static void vcycle_level(nbp_ctx *c, Hier &H, int l, int vsel, const T *b, T *ou
     Level &Lc = H.L[l + 1];
     T *bc = wvec<T>(Lc, 0), *xc = wvec<T>(Lc, 1);
     timed(c, "amg/restrict", 0.0,
-          [&] { k_restrict<T><<<grid_exact(Lc.M.nbr), 256, 0, c->s>>>(L.mptr, L.mem, Lc.M.nbr, bs, r, bc); });
+          [&] { k_restrict<T><<<grid_exact((long long)Lc.M.nbr * 8), 256, 0, c->s>>>(L.mptr, L.mem, Lc.M.nbr, bs, r, bc); });
     if (H.kcycle && l + 1 < H.nlev - 1) kcycle_level<T>(c, H, l + 1, vsel, bc, xc);
     else vcycle_level<T>(c, H, l + 1, vsel, bc, xc);
     timed(c, "amg/prolong", 0.0, [&] { k_prolong<T><<<grid_exact(n), 256, 0, c->s>>>(L.agg, L.M.nbr, bs, xc, cur); });
@@ -580,10 +624,16 @@ template <typename T> static GmResult solve_A(nbp_ctx *c, int vsel, const T *s, 
             k_mul<T><<<grid_for(n), 256, 0, c->s>>>(out, x, dinv, n);
             NBP_LAUNCHED();
         };
-        return gmres<T>(c, KA<T>(c), n, op, pc, s, y, rtol, c->opt.atol, c->opt.m_A, c->opt.nmax_A, false);
+        auto opdotj = [&](const T *x, T *out, const T *V, long long ldv, int ncols, double *h) {
+            return apply_A_dot<T>(c, vsel, x, out, V, ldv, ncols, h);
+        };
+        return gmres<T>(c, KA<T>(c), n, op, pc, s, y, rtol, c->opt.atol, c->opt.m_A, c->opt.nmax_A, false, opdotj);
     }
     auto pc = [&](const T *x, T *out) { vcycle<T>(c, c->HA, vsel, x, out); };
-    return gmres<T>(c, KA<T>(c), n, op, pc, s, y, rtol, c->opt.atol, c->opt.m_A, c->opt.nmax_A, false);
+    auto opdot = [&](const T *x, T *out, const T *V, long long ldv, int ncols, double *h) {
+        return apply_A_dot<T>(c, vsel, x, out, V, ldv, ncols, h);
+    };
+    return gmres<T>(c, KA<T>(c), n, op, pc, s, y, rtol, c->opt.atol, c->opt.m_A, c->opt.nmax_A, false, opdot);
 }
 
 // Algorithm 2: y = D x_p - C A^{-1} B x_p, inner solve to delta_I
@@ -861,7 +911,7 @@ static void destroy_ctx(nbp_ctx *c) {
     dmat_free(c->A, s); dmat_free(c->B, s); dmat_free(c->C, s); dmat_free(c->D, s); dmat_free(c->Shat, s);
     free_lowrank(c->lr, s);
     hier_free(c->HA, s); hier_free(c->HS, s);
-    dfree(c->diagA, s); dfree(c->full_w, s);
+    dfree(c->diagA, s); dfree(c->full_w, s); dfree(c->dpart, s);
     c->Kout.release(s); c->KA64.release(s); c->KS64.release(s); c->KA32.release(s); c->KS32.release(s);
     c->B64.release(s); c->B32.release(s);
     cudaStreamSynchronize(s);
