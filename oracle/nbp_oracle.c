@@ -76,8 +76,9 @@ typedef struct {
     int variant;        /* 0 P_SCR (Algorithm 3), 1 upper block-triangular [[A,B],[0,S]], 2 SIMPLE */
     int amg_max_levels, amg_coarse_max, cheb_degree;
     double theta;
-    int amg_cycle;      /* 0 V-cycles; 1 K-cycle (two GCR steps on every coarse level) on
+    int amg_cycle;      /* 0 V-cycles; 1 K-cycle (two GCR steps on the coarse levels) on
                            AMG(S_hat); 2 K-cycle on both hierarchies */
+    int amg_kdepth;     /* K-cycle on coarse levels 1..amg_kdepth, V-cycles below */
 } or_options;
 
 typedef struct {
@@ -98,7 +99,7 @@ typedef struct {
     double *lu; int *piv; int nc; /* coarsest dense LU, nc = rows */
     double *bl[OR_MAXLEV], *xl[OR_MAXLEV], *rl[OR_MAXLEV], *dl[OR_MAXLEV];
     double *kr[OR_MAXLEV], *kz1[OR_MAXLEV], *kw1[OR_MAXLEV], *kz2[OR_MAXLEV], *kw2[OR_MAXLEV]; /* K-cycle */
-    int cheb_degree, cycle;
+    int cheb_degree, cycle, kdepth;
 } amg;
 
 typedef struct {
@@ -582,6 +583,7 @@ static void amg_build(amg *H, const bmat *fine, const or_options *o, int kcycle)
     H->bs = fine->br;
     H->cheb_degree = o->cheb_degree;
     H->cycle = kcycle;
+    H->kdepth = o->amg_kdepth;
     bmat_copy(&H->L[0], fine->nbr, fine->nbc, fine->br, fine->bc, fine->rp, fine->ci, fine->v);
     int l = 0;
     while (H->L[l].nbr > o->amg_coarse_max && l + 1 < o->amg_max_levels && l + 1 < OR_MAXLEV) {
@@ -703,7 +705,7 @@ static void vcycle(amg *H, int l) {
     for (int i = 0; i < M->nbr; ++i)              /* restriction P^T r, ascending i */
         if (H->agg[l][i] >= 0)
             for (int a = 0; a < bs; ++a) bc[(size_t)H->agg[l][i] * bs + a] += r[(size_t)i * bs + a];
-    if (H->cycle == 1 && l + 1 < H->nlev - 1) kcycle(H, l + 1);
+    if (H->cycle == 1 && l + 1 < H->nlev - 1 && l + 1 <= H->kdepth) kcycle(H, l + 1);
     else vcycle(H, l + 1);
     const double *xc = H->xl[l + 1];
     for (int i = 0; i < M->nbr; ++i)              /* prolongation x += P e_c */
@@ -904,6 +906,7 @@ void or_default_options(or_options *o) {
     o->pc_A = 0; o->pc_S = 0; o->variant = 0;
     o->amg_max_levels = 5; o->amg_coarse_max = 300; o->cheb_degree = 2; o->theta = 0.0064;
     o->amg_cycle = 1;
+    o->amg_kdepth = 1;
 }
 
 or_ctx *or_create(int N, const int *arp, const int *aci, const double *av, const int *brp, const int *bci,

@@ -123,6 +123,7 @@ struct Level {
 struct Hier {
     int nlev = 0, bs = 1;
     bool kcycle = false;                     // Krylov-accelerated cycle on the coarse levels
+    int kdepth = 1;                          // ... 1..kdepth
     Level L[kMaxLevels];
     double *cinv = nullptr;                  // coarsest dense inverse (nc x nc, row-major) or null
     float *cinv32 = nullptr;                 // its FP32 copy (FP32 inner solves)

@@ -528,7 +528,7 @@ static void vcycle_level(nbp_ctx *c, Hier &H, int l, int vsel, const T *b, T *ou
     T *bc = wvec<T>(Lc, 0), *xc = wvec<T>(Lc, 1);
     timed(c, "amg/restrict", 0.0,
           [&] { k_restrict<T><<<grid_exact((long long)Lc.M.nbr * 8), 256, 0, c->s>>>(L.mptr, L.mem, Lc.M.nbr, bs, r, bc); });
-    if (H.kcycle && l + 1 < H.nlev - 1) kcycle_level<T>(c, H, l + 1, vsel, bc, xc);
+    if (H.kcycle && l + 1 < H.nlev - 1 && l + 1 <= H.kdepth) kcycle_level<T>(c, H, l + 1, vsel, bc, xc);
     else vcycle_level<T>(c, H, l + 1, vsel, bc, xc);
     timed(c, "amg/prolong", 0.0, [&] { k_prolong<T><<<grid_exact(n), 256, 0, c->s>>>(L.agg, L.M.nbr, bs, xc, cur); });
     T *fin = chebyshev<T>(c, L, vsel, k, b, cur, oth, false);
@@ -883,6 +883,7 @@ static void do_setup(nbp_ctx *c) {
     amg_build(c->HS, c->Shat, c->opt, prec, s);
     c->HA.kcycle = c->opt.amg_cycle == 2;
     c->HS.kcycle = c->opt.amg_cycle >= 1;
+    c->HA.kdepth = c->HS.kdepth = c->opt.amg_kdepth;
     make_sell(c->A, prec, s);
     if (prec >= 1) {
         make_lowcopies(c->A, prec, s);
@@ -1064,13 +1065,14 @@ void nbp_default_options(nbp_options *o) {
     o->precision = 0; o->pc_A = 0; o->pc_S = 0; o->variant = 0;
     o->amg_max_levels = 5; o->amg_coarse_max = 300; o->cheb_degree = 2; o->theta = 0.0064;
     o->amg_cycle = 1;
+    o->amg_kdepth = 1;
 }
 
 static nbp_status check_options(const nbp_options *o, std::string &msg) {
     if (!(o->rtol >= 0 && o->rtol_A >= 0 && o->rtol_S >= 0 && o->rtol_I >= 0 && o->atol >= 0)) { msg = "negative tolerance"; return NBP_ERR_INVALID; }
     if (o->m < 1 || o->m_A < 1 || o->m_S < 1 || o->nmax < 1 || o->nmax_A < 1 || o->nmax_S < 1) { msg = "restart/n_max < 1"; return NBP_ERR_INVALID; }
     if (o->precision < 0 || o->precision > 2 || o->pc_A < 0 || o->pc_A > 1 || o->pc_S < 0 || o->pc_S > 1 || o->variant < 0 || o->variant > 2) { msg = "bad mode switch"; return NBP_ERR_INVALID; }
-    if (o->cheb_degree < 0 || o->cheb_degree > 8 || o->amg_max_levels < 1 || o->amg_cycle < 0 || o->amg_cycle > 2) { msg = "bad AMG option"; return NBP_ERR_INVALID; }
+    if (o->cheb_degree < 0 || o->cheb_degree > 8 || o->amg_max_levels < 1 || o->amg_cycle < 0 || o->amg_cycle > 2 || o->amg_kdepth < 1) { msg = "bad AMG option"; return NBP_ERR_INVALID; }
     return NBP_OK;
 }
 

@@ -220,13 +220,13 @@ def test_invalid_input_rejected():
         Solver(bad)
 
 
-@pytest.mark.parametrize("cycle", [1, 2])
-def test_kcycle_vcycle_vs_oracle(cycle):
+@pytest.mark.parametrize("cycle,kdepth", [(1, 1), (2, 1), (1, 3)])
+def test_kcycle_vcycle_vs_oracle(cycle, kdepth):
     """K-cycle on the coarse levels (device coefficients, graph replay) vs the oracle."""
     d = synth.generate(CASES["box9x11x23_q4"])
-    s = Solver(d, amg_coarse_max=10, amg_cycle=cycle)
+    s = Solver(d, amg_coarse_max=10, amg_cycle=cycle, amg_kdepth=kdepth)
     s.setup()
-    o = oracle.Oracle(d, amg_coarse_max=10, amg_cycle=cycle)
+    o = oracle.Oracle(d, amg_coarse_max=10, amg_cycle=cycle, amg_kdepth=kdepth)
     o.setup()
     rng = np.random.default_rng(8)
     for which, n in ((0, 3 * d["n_nodes"]), (1, d["n_nodes"])):
