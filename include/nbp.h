@@ -95,7 +95,7 @@ typedef struct {
     int32_t amg_cycle;      /* 0 V-cycle on both hierarchies; 1 (default) K-cycle on the
                                coarse levels of AMG(S_hat); 2 K-cycle on both.  Takes
                                effect at nbp_setup. */
-    int32_t amg_kdepth;     /* K-cycle on coarse levels 1..amg_kdepth (default 1), V-cycles
+    int32_t amg_kdepth;     /* K-cycle on coarse levels 1..amg_kdepth (default 99: all), V-cycles
                                below */
 } nbp_options;
 

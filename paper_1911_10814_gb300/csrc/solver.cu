@@ -1065,7 +1065,7 @@ void nbp_default_options(nbp_options *o) {
     o->precision = 0; o->pc_A = 0; o->pc_S = 0; o->variant = 0;
     o->amg_max_levels = 5; o->amg_coarse_max = 300; o->cheb_degree = 2; o->theta = 0.0064;
     o->amg_cycle = 1;
-    o->amg_kdepth = 1;
+    o->amg_kdepth = 99;
 }
 
 static nbp_status check_options(const nbp_options *o, std::string &msg) {
