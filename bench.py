@@ -47,7 +47,8 @@ def _args():
     p.add_argument("--pc-A", type=int, default=0, help="P_A: 0 AMG V-cycle (default), 1 Jacobi")
     p.add_argument("--amg-cycle", type=int, default=1, help="0 V-cycles, 1 K-cycle on AMG(S_hat), 2 K-cycle on both")
     p.add_argument("--amg-kdepth", type=int, default=99, help="K-cycle on coarse levels 1..k")
-    p.add_argument("--cheb-degree", type=int, default=2, help="Chebyshev smoothing degree")
+    p.add_argument("--cheb-degree", type=int, default=2, help="Chebyshev smoothing degree of AMG(A)")
+    p.add_argument("--cheb-degree-S", type=int, default=1, help="Chebyshev smoothing degree of AMG(S_hat)")
     p.add_argument("--workload", default="large", choices=["large", "batch"],
                    help="large: the 4.34M-unknown tangent (default); batch: 48 uneven cubes in one batched call")
     return p.parse_args()
@@ -285,7 +286,7 @@ def main():
     d = synth.generate(spec)
     t_gen = time.perf_counter() - t0
     s = Solver(d, device=dev, precision=a.precision, pc_A=a.pc_A, amg_cycle=a.amg_cycle, amg_kdepth=a.amg_kdepth,
-               cheb_degree=a.cheb_degree)
+               cheb_degree=a.cheb_degree, cheb_degree_S=a.cheb_degree_S)
     s.setup()
     b = torch.as_tensor(d["b"], device=f"cuda:{dev}")
     n = 4 * d["n_nodes"]
@@ -387,7 +388,7 @@ def main():
         "config": {"workload": spec.name, "unknowns": n, "tets": 6 * spec.nx * spec.ny * spec.nz,
                    "outlets": spec.n_out, "tolerance": 1e-8, "inner_precision": a.precision,
                    "P_A": "AMG" if a.pc_A == 0 else "Jacobi", "amg_cycle": a.amg_cycle, "amg_kdepth": a.amg_kdepth,
-                   "cheb_degree": a.cheb_degree,
+                   "cheb_degree": a.cheb_degree, "cheb_degree_S": a.cheb_degree_S,
                    "parallelism": f"replicas{ws}", "l2": "inputs larger than L2 (no flush)"},
         "fp64": ({"solve_s": info64["solve_s"], "rel_res_true": info64["rel_res_true"], **counts64} if info64 else None),
         "mixed": {"solve_s": ms / 1e3, "rel_res_true": infos[-1]["rel_res_true"], "err_vs_fp64": err_vs_fp64,

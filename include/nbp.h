@@ -97,6 +97,8 @@ typedef struct {
                                effect at nbp_setup. */
     int32_t amg_kdepth;     /* K-cycle on coarse levels 1..amg_kdepth (default 99: all), V-cycles
                                below */
+    int32_t cheb_degree_S;  /* Chebyshev degree of the AMG(S_hat) smoother, default 1
+                               (cheb_degree, default 2, is that of AMG(A)) */
 } nbp_options;
 
 typedef struct {

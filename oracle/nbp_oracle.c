@@ -79,6 +79,7 @@ typedef struct {
     int amg_cycle;      /* 0 V-cycles; 1 K-cycle (two GCR steps on the coarse levels) on
                            AMG(S_hat); 2 K-cycle on both hierarchies */
     int amg_kdepth;     /* K-cycle on coarse levels 1..amg_kdepth, V-cycles below */
+    int cheb_degree_S;  /* Chebyshev degree of the AMG(S_hat) smoother (cheb_degree: AMG(A)) */
 } or_options;
 
 typedef struct {
@@ -578,10 +579,10 @@ static double gershgorin_rho(const bmat *M, const double *dinv) {
     return rho;
 }
 
-static void amg_build(amg *H, const bmat *fine, const or_options *o, int kcycle) {
+static void amg_build(amg *H, const bmat *fine, const or_options *o, int kcycle, int degree) {
     memset(H, 0, sizeof(*H));
     H->bs = fine->br;
-    H->cheb_degree = o->cheb_degree;
+    H->cheb_degree = degree;
     H->cycle = kcycle;
     H->kdepth = o->amg_kdepth;
     bmat_copy(&H->L[0], fine->nbr, fine->nbc, fine->br, fine->bc, fine->rp, fine->ci, fine->v);
@@ -907,6 +908,7 @@ void or_default_options(or_options *o) {
     o->amg_max_levels = 5; o->amg_coarse_max = 300; o->cheb_degree = 2; o->theta = 0.0064;
     o->amg_cycle = 1;
     o->amg_kdepth = 99;
+    o->cheb_degree_S = 1;
 }
 
 or_ctx *or_create(int N, const int *arp, const int *aci, const double *av, const int *brp, const int *bci,
@@ -949,10 +951,10 @@ void or_set_resistances(or_ctx *c, const double *r) {
 int or_setup(or_ctx *c) {
     if (c->have_amgA) amg_free(&c->amgA);
     if (c->have_amgS) amg_free(&c->amgS);
-    amg_build(&c->amgA, &c->A, &c->opt, c->opt.amg_cycle == 2);
+    amg_build(&c->amgA, &c->A, &c->opt, c->opt.amg_cycle == 2, c->opt.cheb_degree);
     c->have_amgA = 1;
     build_shat(c);
-    amg_build(&c->amgS, &c->Shat, &c->opt, c->opt.amg_cycle >= 1);
+    amg_build(&c->amgS, &c->Shat, &c->opt, c->opt.amg_cycle >= 1, c->opt.cheb_degree_S);
     c->have_amgS = 1;
     return 0;
 }

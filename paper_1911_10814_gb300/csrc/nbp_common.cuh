@@ -124,6 +124,7 @@ struct Hier {
     int nlev = 0, bs = 1;
     bool kcycle = false;                     // Krylov-accelerated cycle on the coarse levels
     int kdepth = 1;                          // ... 1..kdepth
+    int cheb = 2;                            // Chebyshev smoothing degree of this hierarchy
     Level L[kMaxLevels];
     double *cinv = nullptr;                  // coarsest dense inverse (nc x nc, row-major) or null
     float *cinv32 = nullptr;                 // its FP32 copy (FP32 inner solves)

@@ -502,13 +502,13 @@ static void vcycle_level(nbp_ctx *c, Hier &H, int l, int vsel, const T *b, T *ou
     Level &L = H.L[l];
     const int bs = H.bs;
     const long long n = (long long)L.M.nbr * bs;
-    const int k = c->opt.cheb_degree;
+    const int k = H.cheb;
     if (l == H.nlev - 1) {
         if (H.cinv) {
             timed(c, "amg/coarsest_gemv", (double)H.nc * H.nc * 8.0,
                   [&] { k_dense_gemv<T><<<grid_exact((long long)H.nc * 32), 256, 0, c->s>>>(cinv_of<T>(H), H.nc, b, out); });
         } else {
-            T *res = chebyshev<T>(c, L, vsel, std::max(k, 1), b, out, wvec<T>(L, 2), true);
+            T *res = chebyshev<T>(c, L, vsel, std::max(k, 1), b, out, wvec<T>(L, 2), true);  // coarsest: smoothing only
             if (res != out) copy<T>(out, res, n, c->s);
         }
         return;
@@ -558,7 +558,7 @@ template <typename T> static void vcycle(nbp_ctx *c, Hier &H, int vsel, const T 
         T *gb = wvec<T>(L0, 0), *gx = wvec<T>(L0, 1);
         const long long n = (long long)L0.M.nbr * H.bs;
         nbp_ctx::CycleGraph &G = c->graphs[&H == &c->HS ? 1 : 0][vsel];
-        if (G.exec && G.cheb != c->opt.cheb_degree) {
+        if (G.exec && G.cheb != H.cheb) {
             cudaGraphExecDestroy(G.exec);
             G.exec = nullptr;
         }
@@ -582,7 +582,7 @@ template <typename T> static void vcycle(nbp_ctx *c, Hier &H, int vsel, const T 
             c->s = saved;
             NBP_CUDA(cudaGraphInstantiate(&G.exec, g, 0));
             NBP_CUDA(cudaGraphDestroy(g));
-            G.cheb = c->opt.cheb_degree;
+            G.cheb = H.cheb;
             G.kernels = c->prof.launches - k0;
             c->prof.launches = k0;
         }
@@ -884,6 +884,8 @@ static void do_setup(nbp_ctx *c) {
     c->HA.kcycle = c->opt.amg_cycle == 2;
     c->HS.kcycle = c->opt.amg_cycle >= 1;
     c->HA.kdepth = c->HS.kdepth = c->opt.amg_kdepth;
+    c->HA.cheb = c->opt.cheb_degree;
+    c->HS.cheb = c->opt.cheb_degree_S;
     make_sell(c->A, prec, s);
     if (prec >= 1) {
         make_lowcopies(c->A, prec, s);
@@ -1066,13 +1068,14 @@ void nbp_default_options(nbp_options *o) {
     o->amg_max_levels = 5; o->amg_coarse_max = 300; o->cheb_degree = 2; o->theta = 0.0064;
     o->amg_cycle = 1;
     o->amg_kdepth = 99;
+    o->cheb_degree_S = 1;
 }
 
 static nbp_status check_options(const nbp_options *o, std::string &msg) {
     if (!(o->rtol >= 0 && o->rtol_A >= 0 && o->rtol_S >= 0 && o->rtol_I >= 0 && o->atol >= 0)) { msg = "negative tolerance"; return NBP_ERR_INVALID; }
     if (o->m < 1 || o->m_A < 1 || o->m_S < 1 || o->nmax < 1 || o->nmax_A < 1 || o->nmax_S < 1) { msg = "restart/n_max < 1"; return NBP_ERR_INVALID; }
     if (o->precision < 0 || o->precision > 2 || o->pc_A < 0 || o->pc_A > 1 || o->pc_S < 0 || o->pc_S > 1 || o->variant < 0 || o->variant > 2) { msg = "bad mode switch"; return NBP_ERR_INVALID; }
-    if (o->cheb_degree < 0 || o->cheb_degree > 8 || o->amg_max_levels < 1 || o->amg_cycle < 0 || o->amg_cycle > 2 || o->amg_kdepth < 1) { msg = "bad AMG option"; return NBP_ERR_INVALID; }
+    if (o->cheb_degree < 0 || o->cheb_degree > 8 || o->cheb_degree_S < 0 || o->cheb_degree_S > 8 || o->amg_max_levels < 1 || o->amg_cycle < 0 || o->amg_cycle > 2 || o->amg_kdepth < 1) { msg = "bad AMG option"; return NBP_ERR_INVALID; }
     return NBP_OK;
 }
 

@@ -381,7 +381,7 @@ def test_kcycle_is_two_step_minimal_residual(tiny):
     hierarchy, composed with the level-0 smoothing and transfers."""
     import scipy.linalg as sla
     d, _ = tiny
-    o = oracle.Oracle(d, amg_max_levels=3, amg_coarse_max=10, amg_cycle=1)
+    o = oracle.Oracle(d, amg_max_levels=3, amg_coarse_max=10, amg_cycle=1, cheb_degree_S=2)
     o.setup()
     L = o.amg_levels(1)
     assert len(L) == 3
