@@ -23,8 +23,10 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <algorithm>
 #include <map>
 #include <memory>
+#include <mutex>
 #include <tuple>
 
 #include "kernels.cuh"
@@ -535,6 +537,73 @@ static void vcycle_level(nbp_ctx *c, Hier &H, int l, int vsel, const T *b, T *ou
     if (fin != out) copy<T>(out, fin, n, c->s);
 }
 
+// In-place autotuner of the coarse-level product kernels: for every level
+// below the finest, each candidate (sliced ELL, flat kernel with g/2, g, 2g
+// lanes per row) is timed inside complete AMG cycles on this hierarchy -- the
+// level's data is as warm or cold as in the solve -- and the fastest kept.
+// Decisions are cached per (hierarchy, level shape, precision) for the life
+// of the process so that every context meeting the same shapes rounds the
+// same way.
+static std::mutex g_cycle_tune_mutex;
+static std::map<std::tuple<int, int, long long, int, int>, int> g_cycle_tune;
+
+template <typename T> static void autotune_cycles(nbp_ctx *c) {
+    const int vsel = vsel_of(c->setup_precision < 0 ? c->opt.precision : c->opt.precision);
+    cudaEvent_t e0, e1;
+    NBP_CUDA(cudaEventCreate(&e0));
+    NBP_CUDA(cudaEventCreate(&e1));
+    const bool prof = c->prof.on;
+    c->prof.on = false;
+    for (int h = 0; h < 2; ++h) {
+        Hier &H = h ? c->HS : c->HA;
+        Level &L0 = H.L[0];
+        const long long n0 = (long long)L0.M.nbr * H.bs;
+        T *b = wvec<T>(L0, 0), *x = wvec<T>(L0, 1);
+        fill<T>(b, T(1), n0, c->s);
+        const int last = H.cinv ? H.nlev - 1 : H.nlev;   // the dense coarsest level has no product
+        for (int l = 1; l < last; ++l) {
+            DMat &M = H.L[l].M;
+            const auto key = std::make_tuple(h, M.nbr, (long long)M.nnz, M.br, (int)sizeof(T) * 4 + vsel);
+            {
+                std::lock_guard<std::mutex> lock(g_cycle_tune_mutex);
+                auto it = g_cycle_tune.find(key);
+                if (it != g_cycle_tune.end()) { M.tuned = it->second; continue; }
+            }
+            const int g0 = choose_group(M);
+            std::vector<int> cands;
+            if (M.sl_ci) cands.push_back(0);
+            cands.push_back(g0);
+            if (g0 > 4) cands.push_back(g0 / 2);
+            if (g0 < 32) cands.push_back(g0 * 2);
+            float best = 1e30f;
+            int arg = cands[0];
+            for (int cand : cands) {
+                M.tuned = cand;
+                vcycle_level<T>(c, H, 0, vsel, b, x);   // warm up
+                float t[3];
+                for (int r = 0; r < 3; ++r) {
+                    NBP_CUDA(cudaEventRecord(e0, c->s));
+                    vcycle_level<T>(c, H, 0, vsel, b, x);
+                    NBP_CUDA(cudaEventRecord(e1, c->s));
+                    NBP_CUDA(cudaEventSynchronize(e1));
+                    NBP_CUDA(cudaEventElapsedTime(&t[r], e0, e1));
+                }
+                std::sort(t, t + 3);
+                if (t[1] < best) { best = t[1]; arg = cand; }
+            }
+            std::lock_guard<std::mutex> lock(g_cycle_tune_mutex);
+            auto it = g_cycle_tune.find(key);
+            if (it != g_cycle_tune.end()) arg = it->second;
+            else g_cycle_tune[key] = arg;
+            M.tuned = arg;
+        }
+    }
+    c->prof.on = prof;
+    c->prof.launches = 0;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+}
+
 static void drop_graphs(nbp_ctx *c) {
     for (auto &row : c->graphs)
         for (auto &g : row) {
@@ -893,10 +962,12 @@ static void do_setup(nbp_ctx *c) {
         make_lowcopies(c->C, prec, s);
         make_lowcopies(c->D, prec, s);
     }
-    // kernel choice per matrix, timed once per setup
-    autotune_spmv(c->A, prec, s);
-    for (Hier *H : {&c->HA, &c->HS})
-        for (int l = 0; l < H->nlev; ++l) autotune_spmv(H->L[l].M, prec, s);
+    // kernel choice per matrix: the fine levels use the sliced-ELL kernel;
+    // coarse levels are tuned in place by timing whole AMG cycles
+    c->A.tuned = c->A.sl_ci ? 0 : -1;
+    for (Hier *H : {&c->HA, &c->HS}) H->L[0].M.tuned = H->L[0].M.sl_ci ? 0 : -1;
+    if (prec >= 1) autotune_cycles<float>(c);
+    else autotune_cycles<double>(c);
     NBP_CUDA(cudaStreamSynchronize(s));
     c->setup_done = true;
     c->setup_precision = prec;

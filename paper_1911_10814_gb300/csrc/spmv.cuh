@@ -20,9 +20,5 @@ int choose_group(const DMat &M);
 template <typename XT> int spmv_dot(const DMat &M, int vsel, SpmvArgs a, bool lr, cudaStream_t s);
 int spmv_dot_blocks(const DMat &M);
 
-// Times the sliced-ELL kernel and the flat kernel with several lane counts on
-// M (y = Mx, the setup precision's value and vector types) and stores the
-// fastest choice in M.tuned.
-void autotune_spmv(DMat &M, int precision, cudaStream_t s);
 
 }  // namespace nbp
