@@ -181,120 +181,4 @@ int spmv_dot_blocks(const DMat &M) { return M.sl_ci ? (int)grid_exact((long long
 template int spmv_dot<double>(const DMat &, int, SpmvArgs, bool, cudaStream_t);
 template int spmv_dot<float>(const DMat &, int, SpmvArgs, bool, cudaStream_t);
 
-template <int BS, typename VT, typename XT, int C>
-static void launch_dot(const SpmvArgs &a, bool lr, cudaStream_t s) {
-    const unsigned grid = grid_exact((long long)a.nslice * C);
-    if (lr) k_sell<BS, VT, XT, EPI_SET, true, C, true><<<grid, 256, 0, s>>>(a);
-    else k_sell<BS, VT, XT, EPI_SET, false, C, true><<<grid, 256, 0, s>>>(a);
-    NBP_LAUNCHED();
-}
-
-template <typename XT>
-int spmv_dot(const DMat &M, int vsel, SpmvArgs a, bool lr, cudaStream_t s) {
-    const bool sell_ok = M.sl_ci && M.br == 3 && M.bc == 3 && (sizeof(XT) == 8 ? M.sl_v != nullptr
-                                                                              : (vsel == 2 ? M.sl_v16 != nullptr
-                                                                                           : M.sl_v32 != nullptr));
-    if (!sell_ok || M.tuned > 0 || a.ndot < 1 || a.ndot > 16) return 0;
-    a.nbr = M.nbr;
-    a.nslice = M.nslice;
-    a.sl_ptr = M.sl_ptr;
-    a.sl_ci = M.sl_ci;
-    const int C = M.sl_c;
-    if constexpr (sizeof(XT) == 8) {
-        a.val = M.sl_v;
-        if (C == 8) launch_dot<3, double, double, 8>(a, lr, s); else launch_dot<3, double, double, 32>(a, lr, s);
-    } else if (vsel == 2) {
-        a.val = M.sl_v16;
-        if (C == 8) launch_dot<3, __nv_bfloat16, float, 8>(a, lr, s); else launch_dot<3, __nv_bfloat16, float, 32>(a, lr, s);
-    } else {
-        a.val = M.sl_v32;
-        if (C == 8) launch_dot<3, float, float, 8>(a, lr, s); else launch_dot<3, float, float, 32>(a, lr, s);
-    }
-    return (int)grid_exact((long long)M.nslice * C);
-}
-
-int spmv_dot_blocks(const DMat &M) { return M.sl_ci ? (int)grid_exact((long long)M.nslice * M.sl_c) : 0; }
-
-template int spmv_dot<double>(const DMat &, int, SpmvArgs, bool, cudaStream_t);
-template int spmv_dot<float>(const DMat &, int, SpmvArgs, bool, cudaStream_t);
-
-// Time of one launch with a cold L2 (a 256 MB buffer is written before each
-// timed launch, as the other levels' traffic does inside an AMG cycle); the
-// median of three.
-template <typename XT> static float time_choice(const DMat &M, int vsel, int G, XT *x, XT *y, char *flush,
-                                                size_t flush_bytes, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1) {
-    SpmvArgs a{};
-    a.x = x;
-    a.y = y;
-    spmv<XT>(M, vsel, a, EPI_SET, false, s, G);   // warm up the code path
-    float t[3];
-    for (int r = 0; r < 3; ++r) {
-        NBP_CUDA(cudaMemsetAsync(flush, r, flush_bytes, s));
-        NBP_CUDA(cudaEventRecord(e0, s));
-        spmv<XT>(M, vsel, a, EPI_SET, false, s, G);
-        NBP_CUDA(cudaEventRecord(e1, s));
-        NBP_CUDA(cudaEventSynchronize(e1));
-        NBP_CUDA(cudaEventElapsedTime(&t[r], e0, e1));
-    }
-    std::sort(t, t + 3);
-    return t[1];
-}
-
-// Decisions are cached per (rows, stored blocks, block size, precision) for
-// the life of the process, so every context that meets a matrix of the same
-// shape uses the same kernel (and therefore the same rounding).
-static std::mutex g_tune_mutex;
-static std::map<std::tuple<int, long long, int, int>, int> g_tune_cache;
-
-void autotune_spmv(DMat &M, int precision, cudaStream_t s) {
-    if (M.nbr == 0 || M.br != M.bc) return;
-    const auto key = std::make_tuple(M.nbr, (long long)M.nnz, M.br, precision);
-    {
-        std::lock_guard<std::mutex> lock(g_tune_mutex);
-        auto it = g_tune_cache.find(key);
-        if (it != g_tune_cache.end()) { M.tuned = it->second; return; }
-    }
-    const int vsel = precision == 2 ? 2 : (precision == 1 ? 1 : 0);
-    const long long nx = (long long)M.nbc * M.bc, ny = (long long)M.nbr * M.br;
-    cudaEvent_t e0, e1;
-    NBP_CUDA(cudaEventCreate(&e0));
-    NBP_CUDA(cudaEventCreate(&e1));
-    const int g0 = choose_group(M);
-    std::vector<int> cands = {0, g0};
-    if (g0 > 4) cands.push_back(g0 / 2);
-    if (g0 < 32) cands.push_back(g0 * 2);
-    float best = 1e30f;
-    int arg = 0;
-    const size_t flush_bytes = 256ull << 20;   // twice the L2
-    char *flush = dmalloc<char>(flush_bytes, s);
-    if (vsel == 0) {
-        double *x = dmalloc<double>(nx, s), *y = dmalloc<double>(ny, s);
-        NBP_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * nx, s));
-        for (int G : cands) {
-            if (G == 0 && !M.sl_v) continue;
-            const float t = time_choice<double>(M, vsel, G, x, y, flush, flush_bytes, s, e0, e1);
-            if (t < best) { best = t; arg = G; }
-        }
-        dfree(x, s); dfree(y, s);
-    } else {
-        float *x = dmalloc<float>(nx, s), *y = dmalloc<float>(ny, s);
-        NBP_CUDA(cudaMemsetAsync(x, 0, sizeof(float) * nx, s));
-        for (int G : cands) {
-            if (G == 0 && !(vsel == 2 ? (const void *)M.sl_v16 : (const void *)M.sl_v32)) continue;
-            if (G > 0 && !(vsel == 2 ? (const void *)M.v16 : (const void *)M.v32)) continue;
-            const float t = time_choice<float>(M, vsel, G, x, y, flush, flush_bytes, s, e0, e1);
-            if (t < best) { best = t; arg = G; }
-        }
-        dfree(x, s); dfree(y, s);
-    }
-    dfree(flush, s);
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    std::lock_guard<std::mutex> lock(g_tune_mutex);
-    auto it = g_tune_cache.find(key);
-    if (it != g_tune_cache.end()) arg = it->second;   // another context decided first
-    else g_tune_cache[key] = arg;
-    M.tuned = arg;
-}
-
 }  // namespace nbp
