@@ -227,6 +227,77 @@ __global__ void __launch_bounds__(256) k_sell(SpmvArgs a) {
     }
 }
 
+// Sliced-ELL product with two threads per block row (alternate slots, then
+// one xor shuffle), for coarse levels whose rows are few and long enough that
+// one thread per row leaves the SM under-occupied.  No rank-one or fused-dot
+// epilogue (coarse levels need neither).
+constexpr int kSell2 = 1000;   // DMat::tuned code of this kernel
+template <int BS, typename VT, typename XT, int EPI, int C>
+__global__ void __launch_bounds__(256) k_sell2(SpmvArgs a) {
+    using AT = XT;
+    constexpr int BB = BS * BS;
+    const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int row = (int)(gid >> 1), h = (int)(gid & 1);
+    const int sl = row / C, t = row % C;
+    const bool live = sl < a.nslice;
+    const long long base = live ? a.sl_ptr[sl] : 0;
+    const int w = live ? (int)((a.sl_ptr[sl + 1] - base) / C) : 0;
+    const VT *__restrict__ val = (const VT *)a.val;
+    const int *__restrict__ ci = a.sl_ci;
+    const XT *__restrict__ x = (const XT *)a.x;
+    AT acc0 = 0, acc1 = 0, acc2 = 0;
+    for (int k = h; k < w; k += 2) {
+        const long long g = base + (long long)C * k;
+        const int c = __ldg(ci + g + t);
+        const VT *v = val + g * BB + t;
+        if (BS == 1) {
+            acc0 += cvt<AT>(__ldg(v)) * __ldg(x + c);
+        } else {
+            const AT x0 = __ldg(x + 3LL * c), x1 = __ldg(x + 3LL * c + 1), x2 = __ldg(x + 3LL * c + 2);
+            acc0 += cvt<AT>(__ldg(v)) * x0 + cvt<AT>(__ldg(v + C)) * x1 + cvt<AT>(__ldg(v + 2 * C)) * x2;
+            acc1 += cvt<AT>(__ldg(v + 3 * C)) * x0 + cvt<AT>(__ldg(v + 4 * C)) * x1 + cvt<AT>(__ldg(v + 5 * C)) * x2;
+            acc2 += cvt<AT>(__ldg(v + 6 * C)) * x0 + cvt<AT>(__ldg(v + 7 * C)) * x1 + cvt<AT>(__ldg(v + 8 * C)) * x2;
+        }
+    }
+    acc0 += __shfl_xor_sync(0xffffffffu, acc0, 1);
+    if (BS > 1) {
+        acc1 += __shfl_xor_sync(0xffffffffu, acc1, 1);
+        acc2 += __shfl_xor_sync(0xffffffffu, acc2, 1);
+    }
+    if (h != 0 || row >= a.nbr) return;
+    const AT accs[3] = {acc0, acc1, acc2};
+    XT *y = (XT *)a.y;
+    if (EPI == EPI_CHEB) {
+        const XT *b = (const XT *)a.b;
+        const XT *dinv = (const XT *)a.dinv + (long long)row * BB;
+        XT *d = (XT *)a.d;
+        XT *xo = (XT *)a.xout;
+        const AT c1 = sizeof(AT) == 4 ? (AT)a.c1f : (AT)a.c1, c2 = sizeof(AT) == 4 ? (AT)a.c2f : (AT)a.c2;
+        AT r[3];
+#pragma unroll
+        for (int q = 0; q < BS; ++q) r[q] = b[(long long)row * BS + q] - accs[q];
+#pragma unroll
+        for (int q = 0; q < BS; ++q) {
+            AT tq = 0;
+#pragma unroll
+            for (int c = 0; c < BS; ++c) tq += dinv[q * BS + c] * r[c];
+            const long long idx = (long long)row * BS + q;
+            const AT dn = c1 * d[idx] + c2 * tq;
+            d[idx] = dn;
+            xo[idx] = x[idx] + dn;
+        }
+        return;
+    }
+#pragma unroll
+    for (int q = 0; q < BS; ++q) {
+        const long long idx = (long long)row * BS + q;
+        if (EPI == EPI_SET) y[idx] = accs[q];
+        else if (EPI == EPI_ADD) y[idx] += accs[q];
+        else if (EPI == EPI_SUB) y[idx] -= accs[q];
+        else y[idx] = ((const XT *)a.b)[idx] - accs[q];
+    }
+}
+
 // ============================================ deterministic reductions
 // Partial dot products of columns 0..ncols-1 of V (column j at V + j*ldv)
 // with w over a fixed grid of kReduceBlocks blocks; block b covers a fixed

@@ -210,7 +210,10 @@ static std::string mat_tag(nbp_ctx *c, const DMat &M, int epi) {
         if (t.empty()) t = "M";
     }
     const int kind = M.tuned >= 0 ? M.tuned : (M.sl_ci ? 0 : -1);
-    return t + "/" + en[epi] + (kind == 0 ? "/sell" + std::to_string(M.sl_c) : "/flat" + std::to_string(kind));
+    const std::string k = kind == 0 ? "/sell" + std::to_string(M.sl_c)
+                          : kind == kSell2 ? "/sell" + std::to_string(M.sl_c) + "x2"
+                                           : "/flat" + std::to_string(kind);
+    return t + "/" + en[epi] + k;
 }
 
 template <typename XT>
@@ -247,7 +250,7 @@ template <typename T> static void apply_A(nbp_ctx *c, int vsel, const T *x, T *y
 template <typename T>
 static bool apply_A_dot(nbp_ctx *c, int vsel, const T *x, T *y, const T *V, long long ldv, int ncols, double *h) {
     const DMat &M = c->A;
-    if (ncols < 1 || ncols > 16 || !(M.tuned == 0 || (M.tuned < 0 && M.sl_ci))) return false;
+    if (ncols < 1 || ncols > 16 || !(M.tuned == 0 || M.tuned == kSell2 || (M.tuned < 0 && M.sl_ci))) return false;
     const long long need = (long long)spmv_dot_blocks(M) * 16;
     if (need == 0) return false;
     if (c->dpart_n < need) {
@@ -571,7 +574,7 @@ template <typename T> static void autotune_cycles(nbp_ctx *c) {
             }
             const int g0 = choose_group(M);
             std::vector<int> cands;
-            if (M.sl_ci) cands.push_back(0);
+            if (M.sl_ci) { cands.push_back(0); cands.push_back(kSell2); }
             cands.push_back(g0);
             if (g0 > 4) cands.push_back(g0 / 2);
             if (g0 < 32) cands.push_back(g0 * 2);
