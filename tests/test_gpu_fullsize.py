@@ -1,0 +1,63 @@
+"""Parity at the benchmark's full size (64x64x256 box, 4,343,300 unknowns,
+Re 2000, 4 outlets) in the launch configuration bench.py times (FP32 inner /
+FP64 outer, default options): properties that hold at any size, checked by
+the oracle's own FP64 arithmetic -- the true residual of the GPU solution,
+sampled rows of the A product, bit-exact aggregates and S_hat."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_1911_10814_gb300 import Solver  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def big():
+    d = synth.generate(synth.large_mixed(64))
+    s = Solver(d, precision=1)
+    s.setup()
+    o = oracle.Oracle(d)
+    yield d, s, o
+    s.close()
+
+
+def test_fullsize_true_residual_by_oracle(big):
+    d, s, o = big
+    x, info = s.solve(torch.as_tensor(d["b"], device="cuda:0"))
+    xh = x.cpu().numpy()
+    r = d["b"] - o.apply_full(xh)
+    assert np.linalg.norm(r) / np.linalg.norm(d["b"]) <= 1e-8
+    assert info["rel_res_true"] <= 1e-8
+
+
+def test_fullsize_sampled_A_rows(big):
+    d, s, o = big
+    rng = np.random.default_rng(21)
+    x = rng.standard_normal(3 * d["n_nodes"])
+    y = s.apply_A(torch.as_tensor(x, device="cuda:0")).cpu().numpy()
+    yo = o.apply_A(x)
+    rows = rng.choice(len(y), 20000, replace=False)
+    assert np.abs(y[rows] - yo[rows]).max() <= 1e-12 * np.abs(yo).max()
+
+
+def test_fullsize_hierarchy_bit_exact(big):
+    d, s, o = big
+    o.setup()
+    for which in (0, 1):
+        G, O = s.amg_levels(which), o.amg_levels(which)
+        assert len(G) == len(O)
+        for lg, lo in zip(G, O):
+            assert np.array_equal(lg["col"], lo["col"])
+            assert np.array_equal(lg["val"], lo["val"])
+            if lo["agg"] is not None:
+                assert np.array_equal(lg["agg"], lo["agg"])
+    rp, ci, v = s.shat()
+    rpo, cio, vo = o.shat()
+    assert np.array_equal(ci, cio) and np.array_equal(v, vo)
