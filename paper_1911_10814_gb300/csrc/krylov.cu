@@ -22,7 +22,8 @@ __global__ void k_givens(double *H, int ldh, int j, const double *h1, const doub
                          double *sn, double *g, GmState *st) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     for (int i = 0; i <= j; ++i) H[(long long)i * ldh + j] = h1[i] + h2[i];
-    const double beta = sqrt(fmax(nrm2[0], 0.0));
+    const double q = nrm2[0];
+    const double beta = (q >= 0.0) ? sqrt(q) : q;   // NaN passes through (fmax would hide it)
     H[(long long)(j + 1) * ldh + j] = beta;
     for (int i = 0; i < j; ++i) {
         const double a = H[(long long)i * ldh + j], b = H[(long long)(i + 1) * ldh + j];
@@ -54,7 +55,8 @@ __global__ void k_trisolve(const double *H, int ldh, const double *g, double *y,
 }
 
 __global__ void k_gm_init(double *g, int m1, const double *beta2, double *beta, GmState *st) {
-    const double b = sqrt(fmax(beta2[0], 0.0));
+    const double q = beta2[0];
+    const double b = (q >= 0.0) ? sqrt(q) : q;       // NaN passes through (fmax would hide it)
     for (int i = threadIdx.x; i < m1; i += blockDim.x) g[i] = 0.0;
     __syncthreads();
     if (threadIdx.x == 0) {
