@@ -5,6 +5,9 @@
 // translation units that launch them.
 #pragma once
 
+#include <cstring>
+#include <type_traits>
+
 #include "nbp_common.cuh"
 
 namespace nbp {
@@ -299,31 +302,158 @@ __global__ void __launch_bounds__(256) k_sell2(SpmvArgs a) {
 }
 
 // ============================================ deterministic reductions
-// Partial dot products of columns 0..ncols-1 of V (column j at V + j*ldv)
-// with w over a fixed grid of kReduceBlocks blocks; block b covers a fixed
-// contiguous chunk.  partial layout: [col][block].
-template <typename T, int CB>
+// The Arnoldi kernels run on a fixed grid of kReduceBlocks blocks; block b
+// covers one fixed contiguous chunk of the vectors (a multiple of the 16-byte
+// vector width), writes its partial sums to partial[col][b], and the last
+// block to finish (atomic ticket) adds the partials of every column in a
+// fixed order.  Results therefore do not depend on block scheduling.
+
+// 16-byte vectors of T (float4 / double2)
+template <typename T> struct Vec16;
+template <> struct Vec16<float> { static constexpr int W = 4; using type = float4; };
+template <> struct Vec16<double> { static constexpr int W = 2; using type = double2; };
+
+template <typename T> __device__ __forceinline__ void vld(const T *p, T (&o)[Vec16<T>::W]) {
+    const typename Vec16<T>::type u = *reinterpret_cast<const typename Vec16<T>::type *>(p);
+    memcpy(o, &u, 16);
+}
+template <typename T> __device__ __forceinline__ void vst(T *p, const T (&o)[Vec16<T>::W]) {
+    typename Vec16<T>::type u;
+    memcpy(&u, o, 16);
+    *reinterpret_cast<typename Vec16<T>::type *>(p) = u;
+}
+
+// This block's chunk [lo, hi) of 0..n-1; lo is a multiple of W.
+__device__ __forceinline__ void block_chunk(long long n, int W, long long &lo, long long &hi) {
+    const long long per = ((n + gridDim.x - 1) / gridDim.x + W - 1) / W * W;
+    lo = min(n, (long long)blockIdx.x * per);
+    hi = min(n, lo + per);
+}
+
+// True in the last block of the grid to get here (after every block has
+// published its partials).  The last block resets the ticket before it ends.
+__device__ __forceinline__ bool grid_last_block(unsigned *ticket) {
+    __shared__ int s_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
+    __syncthreads();
+    return s_last != 0;
+}
+
+// out[col] = sum_b partial[col][b] (lanes over b with stride 32, then a warp
+// tree), one warp per column; run by one block.
+__device__ __forceinline__ void block_reduce_partials(const double *partial, int nb, int ncols, double *out) {
+    const int warp = threadIdx.x >> 5, ln = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int col = warp; col < ncols; col += nw) {
+        double s = 0.0;
+        for (int b = ln; b < nb; b += 32) s += __ldcg(partial + (long long)col * nb + b);
+        s = warp_sum(s);
+        if (ln == 0) out[col] = s;
+    }
+}
+
+// out[j] (+)= sum_b partial[j][b] in the same fixed order, as a kernel of
+// its own (one warp per column), for partials of kernels without a ticket.
+__global__ void k_reduce_partials(const double *__restrict__ partial, int nblocks, int ncols, double *__restrict__ out,
+                                  int accumulate);
+
+// ================================================ Givens / least squares
+struct GmState {
+    double res;      // |g_{j+1}|
+    double beta;     // h_{j+1,j}
+    int nan;         // NaN/Inf met
+    int pad;
+};
+
+// What the fused Givens update of Hessenberg column j needs (H == nullptr:
+// no update).
+struct GivensArgs {
+    double *H = nullptr;
+    int ldh = 0, j = 0;
+    const double *h1 = nullptr, *h2 = nullptr;
+    double *cs = nullptr, *sn = nullptr, *g = nullptr;
+    GmState *st = nullptr;
+};
+
+// Column j of the Hessenberg matrix: H(i,j) = h1_i + h2_i (i <= j),
+// H(j+1,j) = ||w|| (from ||w||^2 = nrm2); the previous rotations applied, a
+// new rotation chosen to zero H(j+1,j), and the right-hand side g rotated
+// (Saad 1993, FGMRES with Givens rotations).  One thread.
+__device__ __forceinline__ void givens_step(const GivensArgs &q, double nrm2) {
+    double *H = q.H;
+    const long long ldh = q.ldh;
+    const int j = q.j;
+    for (int i = 0; i <= j; ++i) H[i * ldh + j] = q.h1[i] + q.h2[i];
+    const double beta = (nrm2 >= 0.0) ? sqrt(nrm2) : nrm2;   // NaN passes through
+    H[(j + 1) * ldh + j] = beta;
+    for (int i = 0; i < j; ++i) {
+        const double a = H[i * ldh + j], b = H[(i + 1) * ldh + j];
+        H[i * ldh + j] = q.cs[i] * a + q.sn[i] * b;
+        H[(i + 1) * ldh + j] = -q.sn[i] * a + q.cs[i] * b;
+    }
+    const double a = H[j * ldh + j], b = H[(j + 1) * ldh + j];
+    const double den = hypot(a, b);
+    if (den == 0.0) { q.cs[j] = 1.0; q.sn[j] = 0.0; }
+    else { q.cs[j] = a / den; q.sn[j] = b / den; }
+    H[j * ldh + j] = den;
+    H[(j + 1) * ldh + j] = 0.0;
+    q.g[j + 1] = -q.sn[j] * q.g[j];
+    q.g[j] = q.cs[j] * q.g[j];
+    const double res = fabs(q.g[j + 1]);
+    q.st->res = res;
+    q.st->beta = beta;
+    q.st->nan = (isfinite(res) && isfinite(beta)) ? 0 : 1;
+}
+
+// out[c] = V(:, c)^T w for c < ncols (column c at V + c*ldv), over the fixed
+// grid; VEC: every pointer and ldv are 16-byte aligned.  When gv.H is set
+// (ncols == 1, w the new Arnoldi vector) the last block also applies the
+// Givens update with out[0] = ||w||^2.
+template <typename T, int CB, bool VEC>
 __global__ void __launch_bounds__(256) k_mdot(const T *__restrict__ V, long long ldv, int ncols, const T *__restrict__ w,
-                                              long long n, double *__restrict__ partial) {
+                                              long long n, double *__restrict__ partial, double *__restrict__ out,
+                                              unsigned *ticket, GivensArgs gv) {
+    constexpr int W = VEC ? Vec16<T>::W : 1;
     __shared__ double red[CB][8];
-    const long long chunk = (n + gridDim.x - 1) / gridDim.x;
-    const long long lo = (long long)blockIdx.x * chunk;
-    const long long hi = min(n, lo + chunk);
+    long long lo, hi;
+    block_chunk(n, Vec16<T>::W, lo, hi);
+    const long long nv = (hi - lo) / W;
     const int warp = threadIdx.x >> 5, ln = threadIdx.x & 31;
     for (int c0 = 0; c0 < ncols; c0 += CB) {
-        using AT = T;
-        AT acc[CB];
+        T acc[CB];
 #pragma unroll
         for (int q = 0; q < CB; ++q) acc[q] = 0;
-        for (long long t = lo + threadIdx.x; t < hi; t += blockDim.x) {
-            const AT wt = w[t];
+        for (long long i = threadIdx.x; i < nv; i += blockDim.x) {
+            const long long t = lo + i * W;
+            if constexpr (VEC) {
+                T wt[W];
+                vld(w + t, wt);
+#pragma unroll
+                for (int q = 0; q < CB; ++q)
+                    if (c0 + q < ncols) {
+                        T v[W];
+                        vld(V + (long long)(c0 + q) * ldv + t, v);
+#pragma unroll
+                        for (int e = 0; e < W; ++e) acc[q] += v[e] * wt[e];
+                    }
+            } else {
+                const T wt = w[t];
+#pragma unroll
+                for (int q = 0; q < CB; ++q)
+                    if (c0 + q < ncols) acc[q] += V[(long long)(c0 + q) * ldv + t] * wt;
+            }
+        }
+        if (VEC && threadIdx.x < hi - lo - nv * W) {   // ragged end of the last chunk
+            const long long t = lo + nv * W + threadIdx.x;
+            const T wt = w[t];
 #pragma unroll
             for (int q = 0; q < CB; ++q)
                 if (c0 + q < ncols) acc[q] += V[(long long)(c0 + q) * ldv + t] * wt;
         }
 #pragma unroll
         for (int q = 0; q < CB; ++q) {
-            double v = warp_sum((double)acc[q]);
+            const double v = warp_sum((double)acc[q]);
             if (ln == 0) red[q][warp] = v;
         }
         __syncthreads();
@@ -334,78 +464,106 @@ __global__ void __launch_bounds__(256) k_mdot(const T *__restrict__ V, long long
         }
         __syncthreads();
     }
+    if (!grid_last_block(ticket)) return;
+    block_reduce_partials(partial, gridDim.x, ncols, out);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (gv.H) givens_step(gv, out[0]);
+        *ticket = 0;
+    }
 }
 
-// out[j] (+)= sum_b partial[j][b] in a fixed order (one warp per column).
-__global__ void k_reduce_partials(const double *__restrict__ partial, int nblocks, int ncols, double *__restrict__ out,
-                                  int accumulate);
-
 // w[t] += alpha * sum_j coef[j] V[j][t]  (coef on the device, FP64)
-template <typename T>
+template <typename T, bool VEC>
 __global__ void __launch_bounds__(256) k_maxpy(const T *__restrict__ V, long long ldv, int ncols, const double *__restrict__ coef,
                                                double alpha, T *__restrict__ w, long long n) {
+    constexpr int W = VEC ? Vec16<T>::W : 1;
     __shared__ T cs[256];
+    const long long nv = n / W;
     for (int c0 = 0; c0 < ncols; c0 += 256) {
         const int cn = min(256, ncols - c0);
         __syncthreads();
         if ((int)threadIdx.x < cn) cs[threadIdx.x] = (T)(alpha * coef[c0 + threadIdx.x]);
         __syncthreads();
-        for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
-            T acc = 0;
-            int j = 0;
-            for (; j + 4 <= cn; j += 4) {
-                acc += cs[j] * V[(long long)(c0 + j) * ldv + t];
-                acc += cs[j + 1] * V[(long long)(c0 + j + 1) * ldv + t];
-                acc += cs[j + 2] * V[(long long)(c0 + j + 2) * ldv + t];
-                acc += cs[j + 3] * V[(long long)(c0 + j + 3) * ldv + t];
+        for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += (long long)gridDim.x * blockDim.x) {
+            const long long t = i * W;
+            T acc[W];
+            if constexpr (VEC) vld(w + t, acc);
+            else acc[0] = w[t];
+            for (int j = 0; j < cn; ++j) {
+                T v[W];
+                if constexpr (VEC) vld(V + (long long)(c0 + j) * ldv + t, v);
+                else v[0] = V[(long long)(c0 + j) * ldv + t];
+#pragma unroll
+                for (int e = 0; e < W; ++e) acc[e] += cs[j] * v[e];
             }
-            for (; j < cn; ++j) acc += cs[j] * V[(long long)(c0 + j) * ldv + t];
-            w[t] += acc;
+            if constexpr (VEC) vst(w + t, acc);
+            else w[t] = acc[0];
+        }
+        if (VEC && blockIdx.x == 0 && threadIdx.x < n - nv * W) {   // ragged end
+            const long long t = nv * W + threadIdx.x;
+            T acc = w[t];
+            for (int j = 0; j < cn; ++j) acc += cs[j] * V[(long long)(c0 + j) * ldv + t];
+            w[t] = acc;
         }
     }
 }
 
 // Fused CGS pass for up to MAXC columns: w_new = w - sum_j coef[j] V[j], then
-// partial dots of the same columns with w_new (norm_only = 0) or the partial
-// squared norm of w_new (norm_only = 1), V read once.  Same fixed grid and
-// chunking as k_mdot, so the partials reduce in a fixed order.
-template <typename T, int MAXC>
+// the dots of the same columns with w_new (norm_only = 0) or the squared norm
+// of w_new (norm_only = 1), V read once; partials reduced by the last block
+// into out (and, with gv.H set, the Givens update with out[0] = ||w_new||^2).
+template <typename T, int MAXC, bool VEC>
 __global__ void __launch_bounds__(256) k_maxpy_dot(const T *__restrict__ V, long long ldv, int ncols,
                                                    const double *__restrict__ coef, T *__restrict__ w, long long n,
-                                                   int norm_only, double *__restrict__ partial) {
+                                                   int norm_only, double *__restrict__ partial, double *__restrict__ out,
+                                                   unsigned *ticket, GivensArgs gv) {
+    constexpr int W = VEC ? Vec16<T>::W : 1;
     __shared__ double red[MAXC][8];
     __shared__ T cs[MAXC];
     if ((int)threadIdx.x < ncols) cs[threadIdx.x] = (T)coef[threadIdx.x];
     __syncthreads();
-    const long long chunk = (n + gridDim.x - 1) / gridDim.x;
-    const long long lo = (long long)blockIdx.x * chunk;
-    const long long hi = min(n, lo + chunk);
+    long long lo, hi;
+    block_chunk(n, Vec16<T>::W, lo, hi);
+    const long long nv = (hi - lo) / W;
     const int warp = threadIdx.x >> 5, ln = threadIdx.x & 31;
     T acc[MAXC];
 #pragma unroll
     for (int q = 0; q < MAXC; ++q) acc[q] = 0;
-    for (long long t = lo + threadIdx.x; t < hi; t += blockDim.x) {
-        T v[MAXC];
-        T s = w[t];
+    auto body = [&](long long t, auto wtag) {
+        constexpr int L = decltype(wtag)::value;
+        T v[MAXC][L], s[L];
+        if constexpr (L > 1) vld(w + t, s);
+        else s[0] = w[t];
 #pragma unroll
         for (int q = 0; q < MAXC; ++q)
             if (q < ncols) {
-                v[q] = V[(long long)q * ldv + t];
-                s -= cs[q] * v[q];
+                if constexpr (L > 1) vld(V + (long long)q * ldv + t, v[q]);
+                else v[q][0] = V[(long long)q * ldv + t];
+#pragma unroll
+                for (int e = 0; e < L; ++e) s[e] -= cs[q] * v[q][e];
             }
-        w[t] = s;
-        if (norm_only) acc[0] += s * s;
-        else {
+        if constexpr (L > 1) vst(w + t, s);
+        else w[t] = s[0];
+        if (norm_only) {
+#pragma unroll
+            for (int e = 0; e < L; ++e) acc[0] += s[e] * s[e];
+        } else {
 #pragma unroll
             for (int q = 0; q < MAXC; ++q)
-                if (q < ncols) acc[q] += v[q] * s;
+                if (q < ncols) {
+#pragma unroll
+                    for (int e = 0; e < L; ++e) acc[q] += v[q][e] * s[e];
+                }
         }
-    }
+    };
+    for (long long i = threadIdx.x; i < nv; i += blockDim.x) body(lo + i * W, std::integral_constant<int, W>());
+    if (VEC && threadIdx.x < hi - lo - nv * W) body(lo + nv * W + threadIdx.x, std::integral_constant<int, 1>());
     const int nout = norm_only ? 1 : ncols;
 #pragma unroll
     for (int q = 0; q < MAXC; ++q) {
         if (q < nout) {
-            double r = warp_sum((double)acc[q]);
+            const double r = warp_sum((double)acc[q]);
             if (ln == 0) red[q][warp] = r;
         }
     }
@@ -414,6 +572,13 @@ __global__ void __launch_bounds__(256) k_maxpy_dot(const T *__restrict__ V, long
         double u = 0.0;
         for (int k = 0; k < (int)(blockDim.x >> 5); ++k) u += red[threadIdx.x][k];
         partial[(long long)threadIdx.x * gridDim.x + blockIdx.x] = u;
+    }
+    if (!grid_last_block(ticket)) return;
+    block_reduce_partials(partial, gridDim.x, nout, out);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (gv.H) givens_step(gv, out[0]);
+        *ticket = 0;
     }
 }
 
@@ -435,8 +600,9 @@ template <typename T> __global__ void k_sub(T *z, const T *x, const T *y, long l
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         z[i] = x[i] - y[i];
 }
-// v = w / s[0] (skips when s[0] == 0)
-template <typename T> __global__ void k_scale_inv(T *v, const T *w, const double *s, long long n) {
+// v = w / s[0] (skips when s[0] == 0); VEC: v, w 16-byte aligned
+template <typename T, bool VEC> __global__ void k_scale_inv(T *v, const T *w, const double *s, long long n) {
+    constexpr int W = VEC ? Vec16<T>::W : 1;
     __shared__ T inv_s;
     __shared__ int zero;
     if (threadIdx.x == 0) {   // one FP64 division per block, not per element
@@ -447,21 +613,22 @@ template <typename T> __global__ void k_scale_inv(T *v, const T *w, const double
     __syncthreads();
     if (zero) return;
     const T inv = inv_s;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        v[i] = w[i] * inv;
+    const long long nv = n / W;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += (long long)gridDim.x * blockDim.x) {
+        if constexpr (VEC) {
+            T u[W];
+            vld(w + i * W, u);
+#pragma unroll
+            for (int e = 0; e < W; ++e) u[e] *= inv;
+            vst(v + i * W, u);
+        } else {
+            v[i] = w[i] * inv;
+        }
+    }
+    if (VEC && blockIdx.x == 0 && threadIdx.x < n - nv * W) v[nv * W + threadIdx.x] = w[nv * W + threadIdx.x] * inv;
 }
 
-// ================================================ Givens / least squares
-struct GmState {
-    double res;      // |g_{j+1}|
-    double beta;     // h_{j+1,j}
-    int nan;         // NaN/Inf met
-    int pad;
-};
-// Column j of the Hessenberg matrix from h1 + h2 (CGS2) and ||w||^2, previous
-// rotations applied, new rotation formed, g updated (Saad 1993).  One thread.
-__global__ void k_givens(double *H, int ldh, int j, const double *h1, const double *h2, const double *nrm2, double *cs,
-                         double *sn, double *g, GmState *st);
+// ============================================= least squares (GMRES end)
 // y = H(0:k,0:k)^{-1} g(0:k), upper triangular.  One thread.
 __global__ void k_trisolve(const double *H, int ldh, const double *g, double *y, int k);
 // g = [beta, 0, ...]; st->res = beta

@@ -1,5 +1,7 @@
 // krylov.cu -- non-template kernels of the Krylov layer: fixed-order partial
-// reductions and the device Givens / least-squares update of (F)GMRES.
+// reductions, the triangular solve of the GMRES least-squares problem and the
+// start of a GMRES cycle (the Givens update itself is fused into the last
+// Gram-Schmidt kernel of each Arnoldi step).
 #include "kernels.cuh"
 
 namespace nbp {
@@ -13,35 +15,6 @@ __global__ void k_reduce_partials(const double *__restrict__ partial, int nblock
     for (int b = ln; b < nblocks; b += 32) s += partial[(long long)col * nblocks + b];
     s = warp_sum(s);
     if (ln == 0) out[col] = accumulate ? out[col] + s : s;
-}
-
-// Hessenberg column j: H(i,j) = h1_i + h2_i (i <= j), H(j+1,j) = ||w||;
-// previous rotations applied, new rotation chosen to zero H(j+1,j), and the
-// right-hand side g rotated (Saad 1993, FGMRES with Givens rotations).
-__global__ void k_givens(double *H, int ldh, int j, const double *h1, const double *h2, const double *nrm2, double *cs,
-                         double *sn, double *g, GmState *st) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    for (int i = 0; i <= j; ++i) H[(long long)i * ldh + j] = h1[i] + h2[i];
-    const double q = nrm2[0];
-    const double beta = (q >= 0.0) ? sqrt(q) : q;   // NaN passes through (fmax would hide it)
-    H[(long long)(j + 1) * ldh + j] = beta;
-    for (int i = 0; i < j; ++i) {
-        const double a = H[(long long)i * ldh + j], b = H[(long long)(i + 1) * ldh + j];
-        H[(long long)i * ldh + j] = cs[i] * a + sn[i] * b;
-        H[(long long)(i + 1) * ldh + j] = -sn[i] * a + cs[i] * b;
-    }
-    const double a = H[(long long)j * ldh + j], b = H[(long long)(j + 1) * ldh + j];
-    const double den = hypot(a, b);
-    if (den == 0.0) { cs[j] = 1.0; sn[j] = 0.0; }
-    else { cs[j] = a / den; sn[j] = b / den; }
-    H[(long long)j * ldh + j] = den;
-    H[(long long)(j + 1) * ldh + j] = 0.0;
-    g[j + 1] = -sn[j] * g[j];
-    g[j] = cs[j] * g[j];
-    const double res = fabs(g[j + 1]);
-    st->res = res;
-    st->beta = beta;
-    st->nan = (isfinite(res) && isfinite(beta)) ? 0 : 1;
 }
 
 __global__ void k_trisolve(const double *H, int ldh, const double *g, double *y, int k) {

@@ -58,18 +58,20 @@ enum { CAT_SPMV = 0, CAT_SPMV_A0 = 1, CAT_ARNOLDI = 2, CAT_VCYCLE = 3, CAT_CHEB_
 
 // ------------------------------------------------------------ Krylov space
 template <typename T> struct Krylov {
-    long long n = 0;
+    long long n = 0, ld = 0;   // basis columns at V + j*ld, ld = n rounded up to 32 (128-byte columns)
     int m = 0;
     T *V = nullptr, *Z = nullptr, *w = nullptr, *r = nullptr;
     double *H = nullptr, *cs = nullptr, *sn = nullptr, *g = nullptr, *y = nullptr;
     double *h1 = nullptr, *h2 = nullptr, *nrm = nullptr, *beta = nullptr, *partial = nullptr;
+    unsigned *ticket = nullptr;   // last-block ticket of the Arnoldi reductions
     GmState *st = nullptr;
     void ensure(long long n_, int m_, cudaStream_t s) {
         if (n_ == n && m_ <= m) return;
         release(s);
         n = n_; m = m_;
-        V = dmalloc<T>((size_t)n * (m + 1), s);
-        Z = dmalloc<T>((size_t)n * m, s);
+        ld = (n + 31) / 32 * 32;
+        V = dmalloc<T>((size_t)ld * (m + 1), s);
+        Z = dmalloc<T>((size_t)ld * m, s);
         w = dmalloc<T>(n, s);
         r = dmalloc<T>(n, s);
         H = dmalloc<double>((size_t)(m + 1) * m, s);
@@ -78,12 +80,20 @@ template <typename T> struct Krylov {
         h1 = dmalloc<double>(m + 1, s); h2 = dmalloc<double>(m + 1, s);
         nrm = dmalloc<double>(1, s); beta = dmalloc<double>(1, s);
         partial = dmalloc<double>((size_t)kReduceBlocks * (m + 1), s);
+        ticket = dmalloc<unsigned>(1, s);
+        NBP_CUDA(cudaMemsetAsync(ticket, 0, sizeof(unsigned), s));
         st = dmalloc<GmState>(1, s);
     }
     void release(cudaStream_t s) {
         dfree(V, s); dfree(Z, s); dfree(w, s); dfree(r, s); dfree(H, s); dfree(cs, s); dfree(sn, s); dfree(g, s);
-        dfree(y, s); dfree(h1, s); dfree(h2, s); dfree(nrm, s); dfree(beta, s); dfree(partial, s); dfree(st, s);
+        dfree(y, s); dfree(h1, s); dfree(h2, s); dfree(nrm, s); dfree(beta, s); dfree(partial, s); dfree(ticket, s);
+        dfree(st, s);
         *this = Krylov();
+    }
+    GivensArgs givens(int j) const {
+        GivensArgs q;
+        q.H = H; q.ldh = m; q.j = j; q.h1 = h1; q.h2 = h2; q.cs = cs; q.sn = sn; q.g = g; q.st = st;
+        return q;
     }
 };
 
@@ -278,40 +288,78 @@ static bool apply_A_dot(nbp_ctx *c, int vsel, const T *x, T *y, const T *V, long
 }
 
 // ------------------------------------------------------------ CGS2 Arnoldi
-template <typename T> static void mdot(nbp_ctx *c, Krylov<T> &K, const T *V, long long ldv, int ncols, const T *w, double *out) {
+static inline bool al16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+// One wave of the fixed-grid kernel: kSMs x (resident blocks per SM, at most
+// 4), so that no block waits for a second wave; fixed per kernel, so the
+// partial sums keep one order.
+template <typename F> static unsigned one_wave(F kernel) {
+    int per_sm = 0;
+    NBP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 256, 0));
+    return (unsigned)(kSMs * std::max(1, std::min(4, per_sm)));
+}
+
+
+// out = V(:, 0..ncols-1)^T w, reduced on the device by the grid's last block
+// (which also applies the Givens update gv when gv.H is set)
+template <typename T> static void mdot(nbp_ctx *c, Krylov<T> &K, const T *V, long long ldv, int ncols, const T *w, double *out,
+                                       GivensArgs gv = GivensArgs()) {
     cudaEvent_t e0;
     prof_begin(c, e0);
-    k_mdot<T, 8><<<kReduceBlocks, 256, 0, c->s>>>(V, ldv, ncols, w, K.n, K.partial);
+    const bool vec = al16(V) && al16(w) && (ncols <= 1 || (ldv * (long long)sizeof(T)) % 16 == 0);
+    static const unsigned g1 = one_wave(k_mdot<T, 8, true>), g0 = one_wave(k_mdot<T, 8, false>);
+    if (vec) k_mdot<T, 8, true><<<g1, 256, 0, c->s>>>(V, ldv, ncols, w, K.n, K.partial, out, K.ticket, gv);
+    else k_mdot<T, 8, false><<<g0, 256, 0, c->s>>>(V, ldv, ncols, w, K.n, K.partial, out, K.ticket, gv);
     NBP_LAUNCHED();
     prof_end(c, CAT_ARNOLDI, (double)(ncols + 1) * K.n * sizeof(T), "arnoldi/mdot");
-    timed(c, "arnoldi/reduce", 0.0, [&] {
-        k_reduce_partials<<<grid_exact((long long)ncols * 32), 256, 0, c->s>>>(K.partial, kReduceBlocks, ncols, out, 0);
-    });
 }
 template <typename T> static void maxpy(nbp_ctx *c, long long n, const T *V, long long ldv, int ncols, const double *coef,
                                         double alpha, T *w) {
     cudaEvent_t e0;
     prof_begin(c, e0);
-    k_maxpy<T><<<grid_for(n, 256, 8LL * kSMs * 4), 256, 0, c->s>>>(V, ldv, ncols, coef, alpha, w, n);
+    const bool vec = al16(V) && al16(w) && (ncols <= 1 || (ldv * (long long)sizeof(T)) % 16 == 0);
+    const unsigned grid = grid_for(n / (vec ? Vec16<T>::W : 1) + 1, 256, 8LL * kSMs * 4);
+    if (vec) k_maxpy<T, true><<<grid, 256, 0, c->s>>>(V, ldv, ncols, coef, alpha, w, n);
+    else k_maxpy<T, false><<<grid, 256, 0, c->s>>>(V, ldv, ncols, coef, alpha, w, n);
     NBP_LAUNCHED();
     prof_end(c, CAT_ARNOLDI, (double)(ncols + 2) * n * sizeof(T), "arnoldi/maxpy");
 }
 
 constexpr int kFusedCols = 16;
 
+template <typename T, int MAXC, bool VEC>
+static void launch_maxpy_dot_v(nbp_ctx *c, Krylov<T> &K, const T *V, long long ldv, int ncols, const double *coef, T *w,
+                               int norm_only, double *out, GivensArgs gv) {
+    static const unsigned grid = one_wave(k_maxpy_dot<T, MAXC, VEC>);
+    k_maxpy_dot<T, MAXC, VEC><<<grid, 256, 0, c->s>>>(V, ldv, ncols, coef, w, K.n, norm_only, K.partial, out, K.ticket, gv);
+}
+template <typename T, int MAXC>
+static void launch_maxpy_dot(nbp_ctx *c, Krylov<T> &K, bool vec, const T *V, long long ldv, int ncols, const double *coef,
+                             T *w, int norm_only, double *out, GivensArgs gv) {
+    if (vec) launch_maxpy_dot_v<T, MAXC, true>(c, K, V, ldv, ncols, coef, w, norm_only, out, gv);
+    else launch_maxpy_dot_v<T, MAXC, false>(c, K, V, ldv, ncols, coef, w, norm_only, out, gv);
+}
+
 // w -= V coef (ncols <= kFusedCols columns), then out = V^T w (or ||w||^2
-// when norm_only), in one pass over V
+// when norm_only, followed by the Givens update gv), in one pass over V
 template <typename T> static void maxpy_dot(nbp_ctx *c, Krylov<T> &K, const T *V, long long ldv, int ncols,
-                                            const double *coef, T *w, int norm_only, double *out) {
+                                            const double *coef, T *w, int norm_only, double *out,
+                                            GivensArgs gv = GivensArgs()) {
     cudaEvent_t e0;
     prof_begin(c, e0);
-    k_maxpy_dot<T, kFusedCols><<<kReduceBlocks, 256, 0, c->s>>>(V, ldv, ncols, coef, w, K.n, norm_only, K.partial);
+    const bool vec = al16(V) && al16(w) && (ncols <= 1 || (ldv * (long long)sizeof(T)) % 16 == 0);
+    if (ncols <= 4) launch_maxpy_dot<T, 4>(c, K, vec, V, ldv, ncols, coef, w, norm_only, out, gv);
+    else if (ncols <= 8) launch_maxpy_dot<T, 8>(c, K, vec, V, ldv, ncols, coef, w, norm_only, out, gv);
+    else launch_maxpy_dot<T, kFusedCols>(c, K, vec, V, ldv, ncols, coef, w, norm_only, out, gv);
     NBP_LAUNCHED();
     prof_end(c, CAT_ARNOLDI, (double)(ncols + 2) * K.n * sizeof(T), "arnoldi/maxpy_dot");
-    const int nout = norm_only ? 1 : ncols;
-    timed(c, "arnoldi/reduce", 0.0, [&] {
-        k_reduce_partials<<<grid_exact((long long)nout * 32), 256, 0, c->s>>>(K.partial, kReduceBlocks, nout, out, 0);
-    });
+}
+
+template <typename T> static void scale_inv(nbp_ctx *c, T *v, const T *w, const double *sc, long long n) {
+    const bool vec = al16(v) && al16(w);
+    const unsigned grid = grid_for(n / (vec ? Vec16<T>::W : 1) + 1);
+    if (vec) k_scale_inv<T, true><<<grid, 256, 0, c->s>>>(v, w, sc, n);
+    else k_scale_inv<T, false><<<grid, 256, 0, c->s>>>(v, w, sc, n);
 }
 
 // ----------------------------------------------------------------- GMRES
@@ -356,31 +404,32 @@ static GmResult gmres(nbp_ctx *c, Krylov<T> &K, long long n, Op op, Pc pc, const
     const T *r0 = b;   // first cycle: r = b (x_0 = 0)
     while (R.its < nmax) {
         c->prof.launches++;
-        k_scale_inv<T><<<grid_for(n), 256, 0, s>>>(K.V, r0, K.beta, n);
+        scale_inv<T>(c, K.V, r0, K.beta, n);
         NBP_LAUNCHED();
         int jend = 0;
         for (int j = 0; j < m && R.its < nmax; ++j) {
-            T *vj = K.V + (size_t)j * n, *zj = K.Z + (size_t)j * n;
+            T *vj = K.V + (size_t)j * K.ld, *zj = K.Z + (size_t)j * K.ld;
             pc(vj, zj);
             // CGS2: two Gram-Schmidt passes against V(:, 0..j); the first
             // inner products ride on the operator when it can, and for short
             // bases each subtraction is fused with the next inner products
-            if (!opdot(zj, K.w, (const T *)K.V, n, j + 1, K.h1)) {
+            if (!opdot(zj, K.w, (const T *)K.V, K.ld, j + 1, K.h1)) {
                 op(zj, K.w);
-                mdot<T>(c, K, K.V, n, j + 1, K.w, K.h1);
+                mdot<T>(c, K, K.V, K.ld, j + 1, K.w, K.h1);
             }
+            // second pass; the last kernel also forms ||w|| and applies the
+            // Givens update of column j on the device
             if (j + 1 <= kFusedCols) {
-                maxpy_dot<T>(c, K, K.V, n, j + 1, K.h1, K.w, 0, K.h2);
-                maxpy_dot<T>(c, K, K.V, n, j + 1, K.h2, K.w, 1, K.nrm);
+                maxpy_dot<T>(c, K, K.V, K.ld, j + 1, K.h1, K.w, 0, K.h2);
+                maxpy_dot<T>(c, K, K.V, K.ld, j + 1, K.h2, K.w, 1, K.nrm, K.givens(j));
             } else {
-                maxpy<T>(c, n, K.V, n, j + 1, K.h1, -1.0, K.w);
-                mdot<T>(c, K, K.V, n, j + 1, K.w, K.h2);
-                maxpy<T>(c, n, K.V, n, j + 1, K.h2, -1.0, K.w);
-                mdot<T>(c, K, K.w, n, 1, K.w, K.nrm);
+                maxpy<T>(c, n, K.V, K.ld, j + 1, K.h1, -1.0, K.w);
+                mdot<T>(c, K, K.V, K.ld, j + 1, K.w, K.h2);
+                maxpy<T>(c, n, K.V, K.ld, j + 1, K.h2, -1.0, K.w);
+                mdot<T>(c, K, K.w, K.ld, 1, K.w, K.nrm, K.givens(j));
             }
-            timed(c, "arnoldi/givens", 0.0, [&] { k_givens<<<1, 1, 0, s>>>(K.H, m, j, K.h1, K.h2, K.nrm, K.cs, K.sn, K.g, K.st); });
             timed(c, "arnoldi/scale", 2.0 * n * sizeof(T),
-                  [&] { k_scale_inv<T><<<grid_for(n), 256, 0, s>>>(K.V + (size_t)(j + 1) * n, K.w, &K.st->beta, n); });
+                  [&] { scale_inv<T>(c, K.V + (size_t)(j + 1) * K.ld, K.w, &K.st->beta, n); });
             read_state(c, K.st);
             require(!c->hst->nan, NBP_ERR_NAN, "gmres: NaN/Inf in the Arnoldi process");
             res = c->hst->res;
@@ -391,7 +440,7 @@ static GmResult gmres(nbp_ctx *c, Krylov<T> &K, long long n, Op op, Pc pc, const
         c->prof.launches += 1;
         k_trisolve<<<1, 1, 0, s>>>(K.H, m, K.g, K.y, jend);
         NBP_LAUNCHED();
-        maxpy<T>(c, n, K.Z, n, jend, K.y, 1.0, x);
+        maxpy<T>(c, n, K.Z, K.ld, jend, K.y, 1.0, x);
         const bool est_conv = res <= tol;
         if (est_conv && !check_true) { R.conv = 1; break; }
         // true residual: confirmation, or the next restart vector
