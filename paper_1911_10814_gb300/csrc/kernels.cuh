@@ -659,6 +659,47 @@ __global__ void k_restrict(const int *__restrict__ mptr, const int *__restrict__
         if (live && l == 0) rc[(long long)I * bs + a] = s;
     }
 }
+// Restriction fused with the first Chebyshev step of the coarse level's
+// pre-smoothing (which starts from zero): rc = R r, then d = c2 Dinv_c rc and
+// x = d, as k_restrict followed by k_cheb_first on the coarse level computes
+// them (same operations, same order); rcopy (optional) gets a copy of rc.
+template <typename T>
+__global__ void k_restrict_first(const int *__restrict__ mptr, const int *__restrict__ mem, int nc, int bs,
+                                 const T *__restrict__ r, T *__restrict__ rc, const T *__restrict__ dinv, T c2,
+                                 T *__restrict__ d, T *__restrict__ x, T *__restrict__ rcopy) {
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int I = (int)(g >> 3), l = (int)(g & 7);
+    const bool live = I < nc;
+    const unsigned mask = 0xffu << (threadIdx.x & 24u);
+    if (__all_sync(0xffffffffu, !live)) return;
+    int q = 0, beg = 0;
+    if (live) { beg = mptr[I]; q = mptr[I + 1] - beg; }
+    const int m = (live && l < q) ? mem[beg + l] : -1;
+    T v[3] = {T(0), T(0), T(0)};   // bs <= 3; every lane of the group ends with the sums
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (a < bs) {
+            T s = (m >= 0) ? r[(long long)m * bs + a] : T(0);
+            s += __shfl_xor_sync(mask, s, 4);
+            s += __shfl_xor_sync(mask, s, 2);
+            s += __shfl_xor_sync(mask, s, 1);
+            v[a] = s;
+        }
+    }
+    if (!live || l >= bs) return;
+    // lane l < bs finishes component l of aggregate I
+    const long long t = (long long)I * bs + l;
+    const T vl = (l == 0) ? v[0] : (l == 1) ? v[1] : v[2];
+    rc[t] = vl;
+    if (rcopy) rcopy[t] = vl;
+    T s = 0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+        if (c < bs) s += dinv[(long long)I * bs * bs + l * bs + c] * v[c];
+    const T dn = c2 * s;
+    d[t] = dn;
+    x[t] = dn;
+}
 // x[i] += e_c[agg[i]]
 template <typename T>
 __global__ void k_prolong(const int *__restrict__ agg, int n, int bs, const T *__restrict__ ec, T *__restrict__ x) {
@@ -697,8 +738,8 @@ __global__ void k_dense_gemv(const T *__restrict__ Cinv, int n, const T *__restr
 // ============================================================== K-cycle
 // kd[o0] = a.b and, when c != nullptr, kd[o1] = c.d.  Each block reduces a
 // fixed contiguous chunk into kd[8 + 2 blk], and the last block to finish
-// (ticket in kd[7]) sums the block partials in index order: one launch,
-// same result whatever order the blocks run in.
+// (ticket in kd[7]) sums the block partials in a fixed order (one warp,
+// lanes over blocks): one launch, same result whatever order the blocks run in.
 constexpr int kKdotBlocks = 96;
 template <typename T>
 __global__ void __launch_bounds__(256) k_kdots(const T *__restrict__ a, const T *__restrict__ b, const T *__restrict__ c,
@@ -726,16 +767,20 @@ __global__ void __launch_bounds__(256) k_kdots(const T *__restrict__ a, const T 
         last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
     }
     __syncthreads();
-    if (last && threadIdx.x == 0) {
+    if (last && threadIdx.x < 32) {   // warp 0: lanes over blocks (stride 32), then a warp tree
         __threadfence();
         double u0 = 0.0, u1 = 0.0;
-        for (unsigned q = 0; q < gridDim.x; ++q) {
-            u0 += ((volatile double *)kd)[8 + 2 * q];
-            u1 += ((volatile double *)kd)[9 + 2 * q];
+        for (unsigned q = threadIdx.x; q < gridDim.x; q += 32) {
+            u0 += __ldcg(kd + 8 + 2 * q);
+            u1 += __ldcg(kd + 9 + 2 * q);
         }
-        kd[o0] = u0;
-        if (c) kd[o1] = u1;
-        *(unsigned int *)(kd + 7) = 0u;   // ready for the next call
+        u0 = warp_sum(u0);
+        u1 = warp_sum(u1);
+        if (threadIdx.x == 0) {
+            kd[o0] = u0;
+            if (c) kd[o1] = u1;
+            *(unsigned int *)(kd + 7) = 0u;   // ready for the next call
+        }
     }
 }
 // r -= a1 w1 with a1 = (w1.r)/(w1.w1) = kd[1]/kd[0]; a1 saved in kd[2]

@@ -495,15 +495,20 @@ static void cheb_step(nbp_ctx *c, Level &L, int vsel, const T *b, const T *x, T 
 
 // Chebyshev smoothing of degree k on level L; from x = 0 when zero_start.
 // Returns the buffer holding the result (x or alt).
+// first_done: the first step from zero (d = x = Dinv b / theta) was already
+// made by the restriction that produced b.
 template <typename T>
-static T *chebyshev(nbp_ctx *c, Level &L, int vsel, int k, const T *b, T *x, T *alt, bool zero_start) {
+static T *chebyshev(nbp_ctx *c, Level &L, int vsel, int k, const T *b, T *x, T *alt, bool zero_start,
+                    bool first_done = false) {
     const int bs = L.M.br;
     const Cheb ch = cheb_of(L.rho);
     T *d = wvec<T>(L, 4);
     double rho_old = 1.0 / ch.sigma;
     T *cur = x, *nxt = alt;
     if (k <= 0) return cur;
-    if (zero_start) {
+    if (zero_start && first_done) {
+        // d and x already hold the first step
+    } else if (zero_start) {
         timed(c, "amg/cheb_first", (double)L.M.nbr * bs * (bs + 3) * sizeof(T), [&] {
             k_cheb_first<T><<<grid_exact((long long)L.M.nbr * bs), 256, 0, c->s>>>(L.M.nbr, bs, dinv_of<T>(L), b,
                                                                                    (T)(1.0 / ch.theta), d, cur);
@@ -522,7 +527,7 @@ static T *chebyshev(nbp_ctx *c, Level &L, int vsel, int k, const T *b, T *x, T *
 }
 
 template <typename T>
-static void vcycle_level(nbp_ctx *c, Hier &H, int l, int vsel, const T *b, T *out);
+static void vcycle_level(nbp_ctx *c, Hier &H, int l, int vsel, const T *b, T *out, bool first_done = false);
 
 // K-cycle on coarse level cl (Notay's Krylov-accelerated multigrid): two GCR
 // steps on L_cl e = b, each preconditioned by one cycle on level cl; every
@@ -530,13 +535,13 @@ static void vcycle_level(nbp_ctx *c, Hier &H, int l, int vsel, const T *b, T *ou
 // CUDA graph.  x = a1 z1 + a2 z2 with a1 = (w1.b)/(w1.w1), r = b - a1 w1,
 // beta = (w2.w1)/(w1.w1), w2 -= beta w1, z2 -= beta z1, a2 = (w2.r)/(w2.w2).
 template <typename T>
-static void kcycle_level(nbp_ctx *c, Hier &H, int cl, int vsel, const T *b, T *x) {
+static void kcycle_level(nbp_ctx *c, Hier &H, int cl, int vsel, const T *b, T *x, bool first_done = false) {
     Level &L = H.L[cl];
     const long long n = (long long)L.M.nbr * H.bs;
     T *r = wvec<T>(L, 5), *z1 = wvec<T>(L, 6), *w1 = wvec<T>(L, 7), *z2 = wvec<T>(L, 8), *w2 = wvec<T>(L, 9);
     const unsigned g = grid_for(n);
-    copy<T>(r, b, n, c->s);
-    vcycle_level<T>(c, H, cl, vsel, b, z1);
+    if (!first_done) copy<T>(r, b, n, c->s);   // else the restriction wrote r
+    vcycle_level<T>(c, H, cl, vsel, b, z1, first_done);
     do_spmv<T>(c, L.M, vsel, sargs(z1, w1), EPI_SET, false);
     timed(c, "kcycle/dots", 0.0, [&] { k_kdots<T><<<kKdotBlocks, 256, 0, c->s>>>(w1, w1, w1, r, n, L.kdots, 0, 1); });
     timed(c, "kcycle/update", 0.0, [&] { k_kupd1<T><<<g, 256, 0, c->s>>>(r, w1, L.kdots, n); });
@@ -551,8 +556,10 @@ static void kcycle_level(nbp_ctx *c, Hier &H, int cl, int vsel, const T *b, T *x
 }
 
 // V(1,1)-cycle from level l with right-hand side b; result written to out.
+// first_done: the first pre-smoothing step on this level was fused into the
+// restriction from the level above (d and the smoothing iterate hold it).
 template <typename T>
-static void vcycle_level(nbp_ctx *c, Hier &H, int l, int vsel, const T *b, T *out) {
+static void vcycle_level(nbp_ctx *c, Hier &H, int l, int vsel, const T *b, T *out, bool first_done) {
     Level &L = H.L[l];
     const int bs = H.bs;
     const long long n = (long long)L.M.nbr * bs;
@@ -573,17 +580,31 @@ static void vcycle_level(nbp_ctx *c, Hier &H, int l, int vsel, const T *b, T *ou
     T *x = (k > 0) ? alt : out;
     T *other = (k > 0) ? out : alt;
     if (k <= 0) fill<T>(x, T(0), n, c->s);
-    T *cur = chebyshev<T>(c, L, vsel, k, b, x, other, true);
+    T *cur = chebyshev<T>(c, L, vsel, k, b, x, other, true, first_done);
     T *oth = (cur == out) ? alt : out;
     // residual and restriction
     T *r = wvec<T>(L, 3);
     do_spmv<T>(c, L.M, vsel, [&] { SpmvArgs a = sargs(cur, r); a.b = b; return a; }(), EPI_RES, false);
     Level &Lc = H.L[l + 1];
     T *bc = wvec<T>(Lc, 0), *xc = wvec<T>(Lc, 1);
-    timed(c, "amg/restrict", 0.0,
-          [&] { k_restrict<T><<<grid_exact((long long)Lc.M.nbr * 8), 256, 0, c->s>>>(L.mptr, L.mem, Lc.M.nbr, bs, r, bc); });
-    if (H.kcycle && l + 1 < H.nlev - 1 && l + 1 <= H.kdepth) kcycle_level<T>(c, H, l + 1, vsel, bc, xc);
-    else vcycle_level<T>(c, H, l + 1, vsel, bc, xc);
+    const bool kc = H.kcycle && l + 1 < H.nlev - 1 && l + 1 <= H.kdepth;
+    // below a smoothed coarse level, the restriction also makes that level's
+    // first smoothing step (into the buffers its cycle uses: d = w[4], the
+    // iterate w[2]) and, for a K-cycle, its copy of the right-hand side (w[5])
+    const bool fuse = k > 0 && l + 1 < H.nlev - 1;
+    if (fuse) {
+        const Cheb chc = cheb_of(Lc.rho);
+        timed(c, "amg/restrict+first", 0.0, [&] {
+            k_restrict_first<T><<<grid_exact((long long)Lc.M.nbr * 8), 256, 0, c->s>>>(
+                L.mptr, L.mem, Lc.M.nbr, bs, r, bc, dinv_of<T>(Lc), (T)(1.0 / chc.theta), wvec<T>(Lc, 4), wvec<T>(Lc, 2),
+                kc ? wvec<T>(Lc, 5) : (T *)nullptr);
+        });
+    } else {
+        timed(c, "amg/restrict", 0.0,
+              [&] { k_restrict<T><<<grid_exact((long long)Lc.M.nbr * 8), 256, 0, c->s>>>(L.mptr, L.mem, Lc.M.nbr, bs, r, bc); });
+    }
+    if (kc) kcycle_level<T>(c, H, l + 1, vsel, bc, xc, fuse);
+    else vcycle_level<T>(c, H, l + 1, vsel, bc, xc, fuse);
     timed(c, "amg/prolong", 0.0, [&] { k_prolong<T><<<grid_exact(n), 256, 0, c->s>>>(L.agg, L.M.nbr, bs, xc, cur); });
     T *fin = chebyshev<T>(c, L, vsel, k, b, cur, oth, false);
     if (fin != out) copy<T>(out, fin, n, c->s);
