@@ -40,7 +40,8 @@ def _args():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="nbp", choices=["nbp", "reference"])
     p.add_argument("--scale", type=int, default=64, help="hexes across the box width (64 = the 4.34M-unknown tangent)")
-    p.add_argument("--precision", type=int, default=1, help="inner precision of the headline solve (1 FP32, 2 BF16)")
+    p.add_argument("--precision", type=int, default=3,
+                   help="inner precision of the headline solve (1 FP32, 2 BF16, 3 FP32 operators + BF16 AMG values)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--skip-fp64", action="store_true", help="skip the FP64 comparison solve (profiling runs)")
@@ -83,16 +84,17 @@ def _source_hash():
     return hashlib.sha256(src[a:b].encode()).hexdigest()[:16]
 
 
-def _traffic_record():
+def _traffic_record(precision):
     """DRAM bytes per launch of the dominant kernel from a committed ncu
-    summary, valid only while the kernel sources are unchanged."""
+    summary, valid only while the kernel sources are unchanged and for the
+    precision mode it was captured in."""
     path = os.path.join(ROOT, "profiles", "roofline_traffic.json")
     if not os.path.exists(path):
         return None
     try:
         with open(path) as f:
             d = json.load(f)
-        if d.get("source_hash") != _source_hash():
+        if d.get("source_hash") != _source_hash() or d.get("precision", 1) != precision:
             return None
         return d
     except Exception:
@@ -255,7 +257,7 @@ def run_batch(a):
     unknowns = sum(4 * d["n_nodes"] for d in systems)
     print(json.dumps({"metric": "batched nested solves: 48 uneven tangents", "value": v, "unit": "s",
                       "instances_per_s": 48 / v, "n_gpus": 1, "steps": a.steps, "warmup": a.warmup,
-                      "higher_is_better": False, "dtype": "f32" if a.precision == 1 else "bf16", "data": "synthetic",
+                      "higher_is_better": False, "dtype": "bf16" if a.precision == 2 else "f32", "data": "synthetic",
                       "config": {"workload": "48 cubes 12^3-40^3 hexes, Re U[100,1000], 1-4 outlets, seed 3",
                                  "unknowns_total": unknowns, "tolerance": 1e-8},
                       "outer_iters_max": max(i["outer_iters"] for i in infos),
@@ -301,6 +303,12 @@ def main():
         x64, info64 = None, None
     else:
         x64, info64 = s.solve(b, precision=0)
+    # FP32 values everywhere (mode 1) on the same setup, for comparison (untimed by events;
+    # the library's own solve clock)
+    info32 = None
+    if not a.skip_fp64 and a.precision == 3:
+        for _ in range(2):
+            _, info32 = s.solve(b, precision=1)
     for _ in range(a.warmup):
         x, info = s.solve(b)
     torch.cuda.synchronize()
@@ -370,7 +378,7 @@ def main():
     avg_ms = prof[key + "_ms"] / max(prof[key + "_launches"], 1)
     bytes_per = prof[key + "_bytes"] / max(prof[key + "_launches"], 1)
     achieved = bytes_per / (avg_ms * 1e-3) / 1e9 if avg_ms > 0 else None
-    tr = _traffic_record()
+    tr = _traffic_record(a.precision)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": (achieved / peak) if achieved else None,
                 "traffic": tr.get(key) if tr else None,
@@ -384,15 +392,19 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": "s", "n_gpus": ws, "steps": a.steps, "warmup": a.warmup,
         "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32" if a.precision == 1 else "bf16", "data": "synthetic",
+        "dtype": "bf16" if a.precision == 2 else "f32", "data": "synthetic",
         "config": {"workload": spec.name, "unknowns": n, "tets": 6 * spec.nx * spec.ny * spec.nz,
                    "outlets": spec.n_out, "tolerance": 1e-8, "inner_precision": a.precision,
+                   "values": {0: "f64", 1: "f32", 2: "bf16", 3: "f32 operators, bf16 AMG hierarchies"}[a.precision],
                    "P_A": "AMG" if a.pc_A == 0 else "Jacobi", "amg_cycle": a.amg_cycle, "amg_kdepth": a.amg_kdepth,
                    "cheb_degree": a.cheb_degree, "cheb_degree_S": a.cheb_degree_S,
                    "parallelism": f"replicas{ws}", "l2": "inputs larger than L2 (no flush)"},
         "fp64": ({"solve_s": info64["solve_s"], "rel_res_true": info64["rel_res_true"], **counts64} if info64 else None),
         "mixed": {"solve_s": ms / 1e3, "rel_res_true": infos[-1]["rel_res_true"], "err_vs_fp64": err_vs_fp64,
                   **counts},
+        "fp32_values_everywhere": ({"solve_s": info32["solve_s"], "rel_res_true": info32["rel_res_true"],
+                                    **{k: info32[k] for k in ("outer_iters", "A_iters", "S_iters", "I_iters")}}
+                                   if info32 else None),
         "setup_s": info["setup_s"], "generate_s": t_gen,
         "speedup_vs_fp64": (info64["solve_s"] / (ms / 1e3)) if info64 else None,
         "roofline": roofline,

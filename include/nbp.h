@@ -80,9 +80,13 @@ typedef struct {
     double rtol, rtol_A, rtol_S, rtol_I, atol;
     int32_t m, m_A, m_S, nmax, nmax_A, nmax_S;
     int32_t precision;      /* 0 FP64 everywhere; 1 FP32 inner (values, vectors, basis);
-                               2 BF16 inner matrix values with FP32 vectors/accumulation.
+                               2 BF16 inner matrix values with FP32 vectors/accumulation;
+                               3 FP32 inner operators (A, B, C, D) and Krylov bases with
+                               BF16 values in the two AMG hierarchies only (smoothers,
+                               residuals and coarse levels of the preconditioners).
                                The outer FGMRES, Givens update, true residual and the
-                               rank-one term stay FP64 in every mode. */
+                               rank-one term stay FP64 in every mode.  Modes 2 and 3 need
+                               nbp_setup run with mode 2 or 3 (both build every copy). */
     int32_t pc_A;           /* 0 AMG V-cycle, 1 point Jacobi diag(A)^{-1} */
     int32_t pc_S;           /* 0 AMG on S_hat, 1 none */
     int32_t variant;        /* 0 P_SCR (Algorithm 3); 1 upper block-triangular [[A,B],[0,S]];

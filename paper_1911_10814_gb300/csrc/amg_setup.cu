@@ -451,7 +451,7 @@ static long long sell_layout(const DMat &m, int C, long long *&sp, cudaStream_t 
 
 void make_sell(DMat &m, int precision, cudaStream_t s) {
     if (m.br != m.bc || m.nbr == 0) return;
-    if (m.sl_ci && (precision < 1 || m.sl_v32) && (precision < 2 || m.sl_v16)) return;
+    if (m.sl_ci && (precision < 1 || m.sl_v32) && (precision < 2 || m.sl_v16)) return;   // 2, 3: FP32 and BF16
     dfree(m.sl_ptr, s); dfree(m.sl_ci, s); dfree(m.sl_v, s); dfree(m.sl_v32, s); dfree(m.sl_v16, s);
     m.sl_ptr = nullptr; m.sl_ci = nullptr; m.sl_v = nullptr; m.sl_v32 = nullptr; m.sl_v16 = nullptr;
     // 32-row slices unless their padding exceeds 10% of the stored blocks
@@ -468,7 +468,7 @@ void make_sell(DMat &m, int precision, cudaStream_t s) {
     m.sl_ci = dmalloc<int>(total, s);
     m.sl_v = dmalloc<double>(total * bb, s);
     if (precision >= 1) m.sl_v32 = dmalloc<float>(total * bb, s);
-    if (precision == 2) m.sl_v16 = dmalloc<__nv_bfloat16>(total * bb, s);
+    if (precision >= 2) m.sl_v16 = dmalloc<__nv_bfloat16>(total * bb, s);
     k_sell_fill<<<grid_exact((long long)m.nslice * C), 256, 0, s>>>(m.nbr, m.nslice, C, bb, m.rp, m.ci, m.v, m.sl_ptr,
                                                                     m.sl_ci, m.sl_v, m.sl_v32, m.sl_v16);
     NBP_LAUNCHED();
@@ -481,7 +481,7 @@ void make_lowcopies(DMat &m, int precision, cudaStream_t s) {
         k_to_f32<<<grid_for(nv), 256, 0, s>>>(m.v, m.v32, nv);
         NBP_LAUNCHED();
     }
-    if (precision == 2 && !m.v16) {
+    if (precision >= 2 && !m.v16) {
         m.v16 = dmalloc<__nv_bfloat16>(nv, s);
         k_to_bf16<<<grid_for(nv), 256, 0, s>>>(m.v, m.v16, nv);
         NBP_LAUNCHED();

@@ -156,7 +156,12 @@ struct nbp_ctx {
 namespace nbp {
 
 // ------------------------------------------------------------ small helpers
-static inline int vsel_of(int precision) { return precision == 2 ? 2 : (precision == 1 ? 1 : 0); }
+// value copy of the inner operators (0 FP64, 1 FP32, 2 BF16) per precision mode
+static inline int vsel_of(int precision) { return precision == 2 ? 2 : (precision >= 1 ? 1 : 0); }
+// value copy of the AMG hierarchies: BF16 in modes 2 and 3
+static inline int amg_vsel_of(int precision) { return precision >= 2 ? 2 : (precision == 1 ? 1 : 0); }
+// copies a precision mode needs built at setup (modes 2 and 3 need the same)
+static inline int build_level(int precision) { return precision >= 2 ? 2 : precision; }
 
 template <typename T> static void fill(T *x, T v, long long n, cudaStream_t s) {
     k_fill<T><<<grid_for(n), 256, 0, s>>>(x, v, n);
@@ -621,7 +626,7 @@ static std::mutex g_cycle_tune_mutex;
 static std::map<std::tuple<int, int, long long, int, int>, int> g_cycle_tune;
 
 template <typename T> static void autotune_cycles(nbp_ctx *c) {
-    const int vsel = vsel_of(c->setup_precision < 0 ? c->opt.precision : c->opt.precision);
+    const int vsel = amg_vsel_of(c->opt.precision);
     cudaEvent_t e0, e1;
     NBP_CUDA(cudaEventCreate(&e0));
     NBP_CUDA(cudaEventCreate(&e1));
@@ -771,7 +776,8 @@ template <typename T> static GmResult solve_A(nbp_ctx *c, int vsel, const T *s, 
         };
         return gmres<T>(c, KA<T>(c), n, op, pc, s, y, rtol, c->opt.atol, c->opt.m_A, c->opt.nmax_A, false, opdotj);
     }
-    auto pc = [&](const T *x, T *out) { vcycle<T>(c, c->HA, vsel, x, out); };
+    const int avsel = amg_vsel_of(c->opt.precision);
+    auto pc = [&](const T *x, T *out) { vcycle<T>(c, c->HA, avsel, x, out); };
     auto opdot = [&](const T *x, T *out, const T *V, long long ldv, int ncols, double *h) {
         return apply_A_dot<T>(c, vsel, x, out, V, ldv, ncols, h);
     };
@@ -804,7 +810,7 @@ template <typename T> static void apply_simple(nbp_ctx *c, int vsel, Bufs<T> &Bf
     do_spmv<T>(c, c->C, vsel, sargs(Bf.yvh, Bf.sp), EPI_SUB, false);                // step 2
     const DMat &Sh = c->HS.L[0].M;
     auto opH = [&](const T *x, T *out) { do_spmv<T>(c, Sh, vsel, sargs(x, out), EPI_SET, false); };
-    auto pcS = [&](const T *x, T *out) { vcycle<T>(c, c->HS, vsel, x, out); };
+    auto pcS = [&](const T *x, T *out) { vcycle<T>(c, c->HS, amg_vsel_of(c->opt.precision), x, out); };
     GmResult R3 = gmres<T>(c, KS<T>(c), N, opH, pcS, Bf.sp, Bf.yp, c->opt.rtol_S, c->opt.atol, c->opt.m_S, c->opt.nmax_S,
                            false);                                                   // step 3'
     c->info.S_iters += R3.its;
@@ -837,7 +843,7 @@ template <typename T> static void apply_pscr(nbp_ctx *c, const double *s, double
     auto opS = [&](const T *x, T *out) { apply_S<T>(c, vsel, x, out); };
     GmResult R3;
     if (c->opt.pc_S == 0) {
-        auto pcS = [&](const T *x, T *out) { vcycle<T>(c, c->HS, vsel, x, out); };
+        auto pcS = [&](const T *x, T *out) { vcycle<T>(c, c->HS, amg_vsel_of(c->opt.precision), x, out); };
         R3 = gmres<T>(c, KS<T>(c), N, opS, pcS, Bf.sp, Bf.yp, c->opt.rtol_S, c->opt.atol, c->opt.m_S, c->opt.nmax_S, false);
     } else {
         auto pcI = [&](const T *x, T *out) { copy<T>(out, x, N, c->s); };
@@ -864,7 +870,7 @@ static void apply_full(nbp_ctx *c, const double *x, double *y) {
 
 static void prepare_inner(nbp_ctx *c) {
     require(c->setup_done, NBP_ERR_STATE, "nbp: call nbp_setup before solving");
-    require(c->opt.precision <= c->setup_precision || c->opt.precision == 0, NBP_ERR_STATE,
+    require(build_level(c->opt.precision) <= build_level(c->setup_precision) || c->opt.precision == 0, NBP_ERR_STATE,
             "nbp: precision mode needs nbp_setup with that mode");
     const long long N = c->N;
     if (c->opt.precision == 0) {
@@ -1018,7 +1024,7 @@ static void do_setup(nbp_ctx *c) {
     auto t0 = std::chrono::steady_clock::now();
     cudaStream_t s = c->s;
     drop_graphs(c);
-    const int prec = c->opt.precision;
+    const int prec = build_level(c->opt.precision);
     if (!c->diagA) c->diagA = dmalloc<double>(3LL * c->N, s);
     amg_build(c->HA, c->A, c->opt, prec, s);
     build_shat(c->A, c->B, c->C, c->D, c->lr, c->N, c->Shat, c->diagA, s);
@@ -1043,7 +1049,7 @@ static void do_setup(nbp_ctx *c) {
     else autotune_cycles<double>(c);
     NBP_CUDA(cudaStreamSynchronize(s));
     c->setup_done = true;
-    c->setup_precision = prec;
+    c->setup_precision = c->opt.precision;
     c->setup_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     if (c->tctx) { c->tctx->setup_done = false; }
 }
@@ -1218,7 +1224,7 @@ void nbp_default_options(nbp_options *o) {
 static nbp_status check_options(const nbp_options *o, std::string &msg) {
     if (!(o->rtol >= 0 && o->rtol_A >= 0 && o->rtol_S >= 0 && o->rtol_I >= 0 && o->atol >= 0)) { msg = "negative tolerance"; return NBP_ERR_INVALID; }
     if (o->m < 1 || o->m_A < 1 || o->m_S < 1 || o->nmax < 1 || o->nmax_A < 1 || o->nmax_S < 1) { msg = "restart/n_max < 1"; return NBP_ERR_INVALID; }
-    if (o->precision < 0 || o->precision > 2 || o->pc_A < 0 || o->pc_A > 1 || o->pc_S < 0 || o->pc_S > 1 || o->variant < 0 || o->variant > 2) { msg = "bad mode switch"; return NBP_ERR_INVALID; }
+    if (o->precision < 0 || o->precision > 3 || o->pc_A < 0 || o->pc_A > 1 || o->pc_S < 0 || o->pc_S > 1 || o->variant < 0 || o->variant > 2) { msg = "bad mode switch"; return NBP_ERR_INVALID; }
     if (o->cheb_degree < 0 || o->cheb_degree > 8 || o->cheb_degree_S < 0 || o->cheb_degree_S > 8 || o->amg_max_levels < 1 || o->amg_cycle < 0 || o->amg_cycle > 2 || o->amg_kdepth < 1) { msg = "bad AMG option"; return NBP_ERR_INVALID; }
     return NBP_OK;
 }
@@ -1382,7 +1388,7 @@ nbp_status nbp_apply_A(nbp_ctx *c, const void *x, void *y, int32_t precision) {
     begin_call(c);
     if (precision == 0) apply_A<double>(c, 0, (const double *)x, (double *)y);
     else {
-        require(c->setup_done && c->setup_precision >= precision, NBP_ERR_STATE, "nbp_apply_A: setup with that precision first");
+        require(c->setup_done && build_level(c->setup_precision) >= precision, NBP_ERR_STATE, "nbp_apply_A: setup with that precision first");
         apply_A<float>(c, vsel_of(precision), (const float *)x, (float *)y);
     }
     NBP_CUDA(cudaStreamSynchronize(c->s));

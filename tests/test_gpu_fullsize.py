@@ -1,6 +1,6 @@
 """Parity at the benchmark's full size (64x64x256 box, 4,343,300 unknowns,
 Re 2000, 4 outlets) in the launch configuration bench.py times (FP32 inner /
-FP64 outer, default options): properties that hold at any size, checked by
+FP64 outer with BF16 AMG values, default options): properties that hold at any size, checked by
 the oracle's own FP64 arithmetic -- the true residual of the GPU solution,
 sampled rows of the A product, bit-exact aggregates and S_hat."""
 import numpy as np
@@ -21,7 +21,7 @@ from paper_1911_10814_gb300 import Solver  # noqa: E402
 @pytest.fixture(scope="module")
 def big():
     d = synth.generate(synth.large_mixed(64))
-    s = Solver(d, precision=1)
+    s = Solver(d, precision=3)   # the benchmark's mode: FP32 operators, BF16 AMG values
     s.setup()
     o = oracle.Oracle(d)
     yield d, s, o
@@ -35,6 +35,16 @@ def test_fullsize_true_residual_by_oracle(big):
     r = d["b"] - o.apply_full(xh)
     assert np.linalg.norm(r) / np.linalg.norm(d["b"]) <= 1e-8
     assert info["rel_res_true"] <= 1e-8
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_fullsize_other_modes_true_residual(big, prec):
+    # a setup in mode 3 holds every value copy: modes 1 and 2 run on it too
+    d, s, o = big
+    x, info = s.solve(torch.as_tensor(d["b"], device="cuda:0"), precision=prec)
+    xh = x.cpu().numpy()
+    r = d["b"] - o.apply_full(xh)
+    assert np.linalg.norm(r) / np.linalg.norm(d["b"]) <= 1e-8
 
 
 def test_fullsize_sampled_A_rows(big):

@@ -160,7 +160,7 @@ def test_nested_solve_iteration_counts_match_oracle(case):
     assert abs(info["S_iters"] - oinfo.S_iters) <= max(2, 0.1 * oinfo.S_iters)
 
 
-@pytest.mark.parametrize("prec", [1, 2])
+@pytest.mark.parametrize("prec", [1, 2, 3])
 def test_nested_solve_mixed(prec):
     d = synth.generate(CASES["box9x11x23_q4"])
     s = Solver(d, precision=prec)
