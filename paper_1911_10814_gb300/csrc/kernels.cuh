@@ -121,6 +121,39 @@ __global__ void __launch_bounds__(256) k_bspmv(SpmvArgs a) {
     }
 }
 
+// Slots p0, p0 + step, ... of the paired BF16 layout (DMat::sl2_ptr) of one
+// row: per pair, one int2 of columns and one bf16x2 per component; the two
+// slots are added in slot order, as the unpaired loop adds them.
+template <int BS, int C>
+__device__ __forceinline__ void sell_pairs(const SpmvArgs &a, long long base2, int np, int t, int p0, int step,
+                                           const float *__restrict__ x, float &acc0, float &acc1, float &acc2) {
+    constexpr int BB = BS * BS;
+    const __nv_bfloat162 *__restrict__ val = (const __nv_bfloat162 *)a.val;
+    const int2 *__restrict__ ci = (const int2 *)a.sl_ci;
+    for (int p = p0; p < np; p += step) {
+        const long long g = base2 + (long long)C * p;
+        const int2 c = __ldg(ci + g + t);
+        const __nv_bfloat162 *v = val + g * BB + t;
+        if (BS == 1) {
+            const float2 m = __bfloat1622float2(__ldg(v));
+            acc0 += m.x * __ldg(x + c.x);
+            acc0 += m.y * __ldg(x + c.y);
+        } else {
+            const float xa0 = __ldg(x + 3LL * c.x), xa1 = __ldg(x + 3LL * c.x + 1), xa2 = __ldg(x + 3LL * c.x + 2);
+            const float xb0 = __ldg(x + 3LL * c.y), xb1 = __ldg(x + 3LL * c.y + 1), xb2 = __ldg(x + 3LL * c.y + 2);
+            float2 m[9];
+#pragma unroll
+            for (int q = 0; q < 9; ++q) m[q] = __bfloat1622float2(__ldg(v + q * C));
+            acc0 += m[0].x * xa0 + m[1].x * xa1 + m[2].x * xa2;
+            acc1 += m[3].x * xa0 + m[4].x * xa1 + m[5].x * xa2;
+            acc2 += m[6].x * xa0 + m[7].x * xa1 + m[8].x * xa2;
+            acc0 += m[0].y * xb0 + m[1].y * xb1 + m[2].y * xb2;
+            acc1 += m[3].y * xb0 + m[4].y * xb1 + m[5].y * xb2;
+            acc2 += m[6].y * xb0 + m[7].y * xb1 + m[8].y * xb2;
+        }
+    }
+}
+
 // Sliced-ELL product for square BS x BS blocks: one thread per block row, C
 // rows per slice (C = 32: a warp per slice; C = 8 for matrices whose row
 // lengths vary, to cut padding).  Every load of values and columns by the C
@@ -141,18 +174,22 @@ __global__ void __launch_bounds__(256) k_sell(SpmvArgs a) {
     const int *__restrict__ ci = a.sl_ci;
     const XT *__restrict__ x = (const XT *)a.x;
     AT acc0 = 0, acc1 = 0, acc2 = 0;
+    if constexpr (std::is_same<VT, __nv_bfloat16>::value) {   // paired layout: w counts slots, even
+        sell_pairs<BS, C>(a, base / 2, w / 2, t, 0, 1, x, acc0, acc1, acc2);
+    } else {
 #pragma unroll 2
-    for (int k = 0; k < w; ++k) {
-        const long long g = base + (long long)C * k;
-        const int c = __ldg(ci + g + t);
-        const VT *v = val + g * BB + t;
-        if (BS == 1) {
-            acc0 += cvt<AT>(__ldg(v)) * __ldg(x + c);
-        } else {
-            const AT x0 = __ldg(x + 3LL * c), x1 = __ldg(x + 3LL * c + 1), x2 = __ldg(x + 3LL * c + 2);
-            acc0 += cvt<AT>(__ldg(v)) * x0 + cvt<AT>(__ldg(v + C)) * x1 + cvt<AT>(__ldg(v + 2 * C)) * x2;
-            acc1 += cvt<AT>(__ldg(v + 3 * C)) * x0 + cvt<AT>(__ldg(v + 4 * C)) * x1 + cvt<AT>(__ldg(v + 5 * C)) * x2;
-            acc2 += cvt<AT>(__ldg(v + 6 * C)) * x0 + cvt<AT>(__ldg(v + 7 * C)) * x1 + cvt<AT>(__ldg(v + 8 * C)) * x2;
+        for (int k = 0; k < w; ++k) {
+            const long long g = base + (long long)C * k;
+            const int c = __ldg(ci + g + t);
+            const VT *v = val + g * BB + t;
+            if (BS == 1) {
+                acc0 += cvt<AT>(__ldg(v)) * __ldg(x + c);
+            } else {
+                const AT x0 = __ldg(x + 3LL * c), x1 = __ldg(x + 3LL * c + 1), x2 = __ldg(x + 3LL * c + 2);
+                acc0 += cvt<AT>(__ldg(v)) * x0 + cvt<AT>(__ldg(v + C)) * x1 + cvt<AT>(__ldg(v + 2 * C)) * x2;
+                acc1 += cvt<AT>(__ldg(v + 3 * C)) * x0 + cvt<AT>(__ldg(v + 4 * C)) * x1 + cvt<AT>(__ldg(v + 5 * C)) * x2;
+                acc2 += cvt<AT>(__ldg(v + 6 * C)) * x0 + cvt<AT>(__ldg(v + 7 * C)) * x1 + cvt<AT>(__ldg(v + 8 * C)) * x2;
+            }
         }
     }
     if (!DOT && row >= a.nbr) return;
@@ -249,17 +286,21 @@ __global__ void __launch_bounds__(256) k_sell2(SpmvArgs a) {
     const int *__restrict__ ci = a.sl_ci;
     const XT *__restrict__ x = (const XT *)a.x;
     AT acc0 = 0, acc1 = 0, acc2 = 0;
-    for (int k = h; k < w; k += 2) {
-        const long long g = base + (long long)C * k;
-        const int c = __ldg(ci + g + t);
-        const VT *v = val + g * BB + t;
-        if (BS == 1) {
-            acc0 += cvt<AT>(__ldg(v)) * __ldg(x + c);
-        } else {
-            const AT x0 = __ldg(x + 3LL * c), x1 = __ldg(x + 3LL * c + 1), x2 = __ldg(x + 3LL * c + 2);
-            acc0 += cvt<AT>(__ldg(v)) * x0 + cvt<AT>(__ldg(v + C)) * x1 + cvt<AT>(__ldg(v + 2 * C)) * x2;
-            acc1 += cvt<AT>(__ldg(v + 3 * C)) * x0 + cvt<AT>(__ldg(v + 4 * C)) * x1 + cvt<AT>(__ldg(v + 5 * C)) * x2;
-            acc2 += cvt<AT>(__ldg(v + 6 * C)) * x0 + cvt<AT>(__ldg(v + 7 * C)) * x1 + cvt<AT>(__ldg(v + 8 * C)) * x2;
+    if constexpr (std::is_same<VT, __nv_bfloat16>::value) {   // paired layout: the two threads take alternate pairs
+        sell_pairs<BS, C>(a, base / 2, w / 2, t, h, 2, x, acc0, acc1, acc2);
+    } else {
+        for (int k = h; k < w; k += 2) {
+            const long long g = base + (long long)C * k;
+            const int c = __ldg(ci + g + t);
+            const VT *v = val + g * BB + t;
+            if (BS == 1) {
+                acc0 += cvt<AT>(__ldg(v)) * __ldg(x + c);
+            } else {
+                const AT x0 = __ldg(x + 3LL * c), x1 = __ldg(x + 3LL * c + 1), x2 = __ldg(x + 3LL * c + 2);
+                acc0 += cvt<AT>(__ldg(v)) * x0 + cvt<AT>(__ldg(v + C)) * x1 + cvt<AT>(__ldg(v + 2 * C)) * x2;
+                acc1 += cvt<AT>(__ldg(v + 3 * C)) * x0 + cvt<AT>(__ldg(v + 4 * C)) * x1 + cvt<AT>(__ldg(v + 5 * C)) * x2;
+                acc2 += cvt<AT>(__ldg(v + 6 * C)) * x0 + cvt<AT>(__ldg(v + 7 * C)) * x1 + cvt<AT>(__ldg(v + 8 * C)) * x2;
+            }
         }
     }
     acc0 += __shfl_xor_sync(0xffffffffu, acc0, 1);

@@ -130,6 +130,8 @@ static void launch_sell(const DMat &M, int vsel, SpmvArgs a, int epi, bool lr, c
         launch_sell_c<BS, double, double>(M, a, epi, lr, s, two);
     } else if (vsel == 2) {
         require(M.sl_v16 != nullptr, NBP_ERR_STATE, "spmv: BF16 sliced values not built");
+        a.sl_ptr = M.sl2_ptr;   // paired layout
+        a.sl_ci = M.sl2_ci;
         a.val = M.sl_v16;
         launch_sell_c<BS, __nv_bfloat16, float>(M, a, epi, lr, s, two);
     } else {
@@ -186,6 +188,8 @@ int spmv_dot(const DMat &M, int vsel, SpmvArgs a, bool lr, cudaStream_t s) {
         a.val = M.sl_v;
         if (C == 8) launch_dot<3, double, double, 8>(a, lr, s); else launch_dot<3, double, double, 32>(a, lr, s);
     } else if (vsel == 2) {
+        a.sl_ptr = M.sl2_ptr;   // paired layout
+        a.sl_ci = M.sl2_ci;
         a.val = M.sl_v16;
         if (C == 8) launch_dot<3, __nv_bfloat16, float, 8>(a, lr, s); else launch_dot<3, __nv_bfloat16, float, 32>(a, lr, s);
     } else {
