@@ -36,10 +36,6 @@ struct SpmvArgs {
     float c1f, c2f;         // the same, pre-rounded for FP32 vectors (no FP64 work per element)
     const int *lr_rp, *lr_k, *lr_c;   // rank-one epilogue (EPI_SET only)
     const double *lr_val, *lr_f;
-    const void *dV;                   // fused inner products (k_sell, EPI_SET): columns of V ...
-    long long dldv;                   // ... with this stride,
-    int ndot;                         // ... this many (<= 16),
-    double *dpart;                    // ... per-block partials [col][block]
     int nslice;                       // sliced-ELL layout (k_sell): slices of C rows
     const long long *sl_ptr;
     const int *sl_ci;
@@ -159,17 +155,15 @@ __device__ __forceinline__ void sell_pairs(const SpmvArgs &a, long long base2, i
 // lengths vary, to cut padding).  Every load of values and columns by the C
 // threads of a slice is one contiguous segment (C x value bytes).  Same
 // epilogues as k_bspmv (a.rp unused; a.sl_* describe the slices).
-template <int BS, typename VT, typename XT, int EPI, bool LR, int C, bool DOT = false>
+template <int BS, typename VT, typename XT, int EPI, bool LR, int C>
 __global__ void __launch_bounds__(256) k_sell(SpmvArgs a) {
     using AT = XT;
     constexpr int BB = BS * BS;
-    constexpr int MAXD = 16;
     const int row = blockIdx.x * blockDim.x + threadIdx.x;
     const int sl = row / C, t = row % C;
-    if (!DOT && sl >= a.nslice) return;
-    const bool live = sl < a.nslice;
-    const long long base = live ? a.sl_ptr[sl] : 0;
-    const int w = live ? (int)((a.sl_ptr[sl + 1] - base) / C) : 0;
+    if (sl >= a.nslice) return;
+    const long long base = a.sl_ptr[sl];
+    const int w = (int)((a.sl_ptr[sl + 1] - base) / C);
     const VT *__restrict__ val = (const VT *)a.val;
     const int *__restrict__ ci = a.sl_ci;
     const XT *__restrict__ x = (const XT *)a.x;
@@ -192,8 +186,7 @@ __global__ void __launch_bounds__(256) k_sell(SpmvArgs a) {
             }
         }
     }
-    if (!DOT && row >= a.nbr) return;
-    const bool own = row < a.nbr;
+    if (row >= a.nbr) return;
     AT accs[3] = {acc0, acc1, acc2};
     XT *y = (XT *)a.y;
     if (EPI == EPI_CHEB) {
@@ -217,60 +210,32 @@ __global__ void __launch_bounds__(256) k_sell(SpmvArgs a) {
         }
         return;
     }
-    if (own) {
 #pragma unroll
-        for (int q = 0; q < BS; ++q) {
-            const long long idx = (long long)row * BS + q;
-            AT s = accs[q];
-            if (EPI == EPI_SET) {
-                if (LR) {
-                    double tt = 0.0;
-                    for (int e = a.lr_rp[row]; e < a.lr_rp[row + 1]; ++e)
-                        if (a.lr_c[e] == q) tt += a.lr_f[a.lr_k[e]] * a.lr_val[e];
-                    s = (AT)((double)s + tt);
-                }
-                y[idx] = s;
-            } else if (EPI == EPI_ADD) {
-                y[idx] += s;
-            } else if (EPI == EPI_SUB) {
-                y[idx] -= s;
-            } else {
-                y[idx] = ((const XT *)a.b)[idx] - s;
+    for (int q = 0; q < BS; ++q) {
+        const long long idx = (long long)row * BS + q;
+        AT s = accs[q];
+        if (EPI == EPI_SET) {
+            if (LR) {
+                double tt = 0.0;
+                for (int e = a.lr_rp[row]; e < a.lr_rp[row + 1]; ++e)
+                    if (a.lr_c[e] == q) tt += a.lr_f[a.lr_k[e]] * a.lr_val[e];
+                s = (AT)((double)s + tt);
             }
-            accs[q] = s;
-        }
-    }
-    if constexpr (DOT) {
-        // partial inner products of y with columns 0..ndot-1 of V (the first
-        // Gram-Schmidt pass of the Arnoldi step that follows this product)
-        __shared__ double red[MAXD][8];
-        const XT *V = (const XT *)a.dV;
-        const int warp = threadIdx.x >> 5, ln = threadIdx.x & 31;
-#pragma unroll
-        for (int cidx = 0; cidx < MAXD; ++cidx) {
-            if (cidx < a.ndot) {
-                AT p = 0;
-                if (own) {
-#pragma unroll
-                    for (int q = 0; q < BS; ++q) p += accs[q] * V[(long long)cidx * a.dldv + (long long)row * BS + q];
-                }
-                const double r = warp_sum((double)p);
-                if (ln == 0) red[cidx][warp] = r;
-            }
-        }
-        __syncthreads();
-        if ((int)threadIdx.x < a.ndot) {
-            double u = 0.0;
-            for (int k = 0; k < (int)(blockDim.x >> 5); ++k) u += red[threadIdx.x][k];
-            a.dpart[(long long)threadIdx.x * gridDim.x + blockIdx.x] = u;
+            y[idx] = s;
+        } else if (EPI == EPI_ADD) {
+            y[idx] += s;
+        } else if (EPI == EPI_SUB) {
+            y[idx] -= s;
+        } else {
+            y[idx] = ((const XT *)a.b)[idx] - s;
         }
     }
 }
 
 // Sliced-ELL product with two threads per block row (alternate slots, then
 // one xor shuffle), for coarse levels whose rows are few and long enough that
-// one thread per row leaves the SM under-occupied.  No rank-one or fused-dot
-// epilogue (coarse levels need neither).
+// one thread per row leaves the SM under-occupied.  No rank-one epilogue
+// (coarse levels need none).
 constexpr int kSell2 = 1000;   // DMat::tuned code of this kernel
 template <int BS, typename VT, typename XT, int EPI, int C>
 __global__ void __launch_bounds__(256) k_sell2(SpmvArgs a) {
@@ -393,11 +358,6 @@ __device__ __forceinline__ void block_reduce_partials(const double *partial, int
         if (ln == 0) out[col] = s;
     }
 }
-
-// out[j] (+)= sum_b partial[j][b] in the same fixed order, as a kernel of
-// its own (one warp per column), for partials of kernels without a ticket.
-__global__ void k_reduce_partials(const double *__restrict__ partial, int nblocks, int ncols, double *__restrict__ out,
-                                  int accumulate);
 
 // ================================================ Givens / least squares
 struct GmState {
@@ -751,11 +711,13 @@ __global__ void k_prolong(const int *__restrict__ agg, int n, int bs, const T *_
     if (I >= 0) x[t] += ec[(long long)I * bs + a];
 }
 // Chebyshev first step from x = 0: d = c2 Dinv b; x = d
+// (bcopy != nullptr: b is also copied there, for a cycle replayed on fixed buffers)
 template <typename T>
 __global__ void k_cheb_first(int nbr, int bs, const T *__restrict__ dinv, const T *__restrict__ b, T c2, T *__restrict__ d,
-                             T *__restrict__ x) {
+                             T *__restrict__ x, T *__restrict__ bcopy) {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (long long)nbr * bs) return;
+    if (bcopy) bcopy[t] = b[t];
     const int i = (int)(t / bs), a = (int)(t - (long long)i * bs);
     T s = 0;
     for (int c = 0; c < bs; ++c) s += dinv[(long long)i * bs * bs + a * bs + c] * b[(long long)i * bs + c];

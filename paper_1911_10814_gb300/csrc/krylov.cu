@@ -1,21 +1,10 @@
-// krylov.cu -- non-template kernels of the Krylov layer: fixed-order partial
-// reductions, the triangular solve of the GMRES least-squares problem and the
-// start of a GMRES cycle (the Givens update itself is fused into the last
-// Gram-Schmidt kernel of each Arnoldi step).
+// krylov.cu -- non-template kernels of the Krylov layer: the triangular
+// solve of the GMRES least-squares problem and the start of a GMRES cycle
+// (the Givens update itself is fused into the last Gram-Schmidt kernel of
+// each Arnoldi step).
 #include "kernels.cuh"
 
 namespace nbp {
-
-__global__ void k_reduce_partials(const double *__restrict__ partial, int nblocks, int ncols, double *__restrict__ out,
-                                  int accumulate) {
-    const int col = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int ln = threadIdx.x & 31;
-    if (col >= ncols) return;
-    double s = 0.0;
-    for (int b = ln; b < nblocks; b += 32) s += partial[(long long)col * nblocks + b];
-    s = warp_sum(s);
-    if (ln == 0) out[col] = accumulate ? out[col] + s : s;
-}
 
 __global__ void k_trisolve(const double *H, int ldh, const double *g, double *y, int k) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;

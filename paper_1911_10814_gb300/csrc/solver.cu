@@ -136,8 +136,6 @@ struct nbp_ctx {
     nbp::Bufs<double> B64;
     nbp::Bufs<float> B32;
     double *full_w = nullptr;     // 4N scratch of the outer operator
-    double *dpart = nullptr;      // partials of the inner products fused into the A product
-    long long dpart_n = 0;
     nbp::GmState *hst = nullptr;  // pinned host status
     nbp_info info{};
     nbp::Prof prof;
@@ -259,39 +257,6 @@ template <typename T> static void apply_A(nbp_ctx *c, int vsel, const T *x, T *y
     do_spmv<T>(c, c->A, vsel, a, EPI_SET, lr.n_out > 0, CAT_SPMV_A0);
 }
 
-// w = A x with h = V(:, 0..ncols-1)^T w fused into the product (the first
-// Gram-Schmidt pass of the Arnoldi step); false when the fused kernel does not
-// apply (nothing launched)
-template <typename T>
-static bool apply_A_dot(nbp_ctx *c, int vsel, const T *x, T *y, const T *V, long long ldv, int ncols, double *h) {
-    const DMat &M = c->A;
-    if (ncols < 1 || ncols > 16 || !(M.tuned == 0 || M.tuned == kSell2 || (M.tuned < 0 && M.sl_ci))) return false;
-    const long long need = (long long)spmv_dot_blocks(M) * 16;
-    if (need == 0) return false;
-    if (c->dpart_n < need) {
-        dfree(c->dpart, c->s);
-        c->dpart = dmalloc<double>(need, c->s);
-        c->dpart_n = need;
-    }
-    LowRank &lr = c->lr;
-    SpmvArgs a = sargs(x, y);
-    if (lr.n_out > 0) {
-        timed(c, "A/lowrank_dots", 0.0,
-              [&] { k_lowrank_dots<T><<<lr.n_out, 256, 0, c->s>>>(lr.optr, lr.oidx, lr.oval, lr.r, x, lr.f); });
-        a.lr_rp = lr.lr_rp; a.lr_k = lr.lr_k; a.lr_c = lr.lr_c; a.lr_val = lr.lr_val; a.lr_f = lr.f;
-    }
-    a.dV = V; a.dldv = ldv; a.ndot = ncols; a.dpart = c->dpart;
-    cudaEvent_t e0;
-    prof_begin(c, e0);
-    const int nb = spmv_dot<T>(M, vsel, a, lr.n_out > 0, c->s);
-    prof_end(c, CAT_SPMV_A0, spmv_bytes<T>(M, vsel, EPI_SET) + (double)ncols * 3 * M.nbr * sizeof(T), "A/set+dot");
-    if (nb == 0) return false;   // cannot happen after the checks above
-    timed(c, "arnoldi/reduce", 0.0, [&] {
-        k_reduce_partials<<<grid_exact((long long)ncols * 32), 256, 0, c->s>>>(c->dpart, nb, ncols, h, 0);
-    });
-    return true;
-}
-
 // ------------------------------------------------------------ CGS2 Arnoldi
 static inline bool al16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
@@ -381,15 +346,9 @@ static void read_state(nbp_ctx *c, const GmState *st) {
 // Restarted flexible GMRES, x_0 = 0; stops when the residual estimate
 // |g_{j+1}| <= max(rtol ||b||, atol) (confirmed on the true residual when
 // check_true) or after nmax iterations.
-struct NoFusedOp {
-    template <typename T> bool operator()(const T *, T *, const T *, long long, int, double *) const { return false; }
-};
-
-// opdot(z, w, V, ldv, ncols, h): w = op(z) with h = V(:, 0..ncols-1)^T w
-// fused into it; returns false when it does not apply.
-template <typename T, typename Op, typename Pc, typename OpDot = NoFusedOp>
+template <typename T, typename Op, typename Pc>
 static GmResult gmres(nbp_ctx *c, Krylov<T> &K, long long n, Op op, Pc pc, const T *b, T *x, double rtol, double atol,
-                      int m, int nmax, bool check_true, OpDot opdot = OpDot()) {
+                      int m, int nmax, bool check_true) {
     cudaStream_t s = c->s;
     GmResult R;
     m = std::max(1, std::min(m, std::max(nmax, 1)));
@@ -418,10 +377,8 @@ static GmResult gmres(nbp_ctx *c, Krylov<T> &K, long long n, Op op, Pc pc, const
             // CGS2: two Gram-Schmidt passes against V(:, 0..j); the first
             // inner products ride on the operator when it can, and for short
             // bases each subtraction is fused with the next inner products
-            if (!opdot(zj, K.w, (const T *)K.V, K.ld, j + 1, K.h1)) {
-                op(zj, K.w);
-                mdot<T>(c, K, K.V, K.ld, j + 1, K.w, K.h1);
-            }
+            op(zj, K.w);
+            mdot<T>(c, K, K.V, K.ld, j + 1, K.w, K.h1);
             // second pass; the last kernel also forms ||w|| and applies the
             // Givens update of column j on the device
             if (j + 1 <= kFusedCols) {
@@ -516,7 +473,7 @@ static T *chebyshev(nbp_ctx *c, Level &L, int vsel, int k, const T *b, T *x, T *
     } else if (zero_start) {
         timed(c, "amg/cheb_first", (double)L.M.nbr * bs * (bs + 3) * sizeof(T), [&] {
             k_cheb_first<T><<<grid_exact((long long)L.M.nbr * bs), 256, 0, c->s>>>(L.M.nbr, bs, dinv_of<T>(L), b,
-                                                                                   (T)(1.0 / ch.theta), d, cur);
+                                                                                   (T)(1.0 / ch.theta), d, cur, nullptr);
         });
     } else {
         cheb_step<T>(c, L, vsel, b, cur, nxt, d, 0.0, 1.0 / ch.theta);
@@ -608,6 +565,8 @@ static void vcycle_level(nbp_ctx *c, Hier &H, int l, int vsel, const T *b, T *ou
         timed(c, "amg/restrict", 0.0,
               [&] { k_restrict<T><<<grid_exact((long long)Lc.M.nbr * 8), 256, 0, c->s>>>(L.mptr, L.mem, Lc.M.nbr, bs, r, bc); });
     }
+    // (a prolongation fused into the coarse level's last kernel, as a scatter
+    // over each aggregate's members, was slower: uncoalesced fine updates)
     if (kc) kcycle_level<T>(c, H, l + 1, vsel, bc, xc, fuse);
     else vcycle_level<T>(c, H, l + 1, vsel, bc, xc, fuse);
     timed(c, "amg/prolong", 0.0, [&] { k_prolong<T><<<grid_exact(n), 256, 0, c->s>>>(L.agg, L.M.nbr, bs, xc, cur); });
@@ -704,6 +663,9 @@ template <typename T> static void vcycle(nbp_ctx *c, Hier &H, int vsel, const T 
         Level &L0 = H.L[0];
         T *gb = wvec<T>(L0, 0), *gx = wvec<T>(L0, 1);
         const long long n = (long long)L0.M.nbr * H.bs;
+        // with a smoothed level 0, the copy of b into the replay buffer and
+        // the first smoothing step from zero are one kernel outside the graph
+        const bool first_in = H.cheb > 0 && H.nlev > 1;
         nbp_ctx::CycleGraph &G = c->graphs[&H == &c->HS ? 1 : 0][vsel];
         if (G.exec && G.cheb != H.cheb) {
             cudaGraphExecDestroy(G.exec);
@@ -718,7 +680,7 @@ template <typename T> static void vcycle(nbp_ctx *c, Hier &H, int vsel, const T 
             cudaGraph_t g = nullptr;
             NBP_CUDA(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
             try {
-                vcycle_level<T>(c, H, 0, vsel, gb, gx);
+                vcycle_level<T>(c, H, 0, vsel, gb, gx, first_in);
             } catch (...) {
                 cudaStreamEndCapture(c->cap, &g);
                 if (g) cudaGraphDestroy(g);
@@ -733,7 +695,15 @@ template <typename T> static void vcycle(nbp_ctx *c, Hier &H, int vsel, const T 
             G.kernels = c->prof.launches - k0;
             c->prof.launches = k0;
         }
-        copy<T>(gb, b, n, c->s);
+        if (first_in) {
+            const Cheb ch = cheb_of(L0.rho);
+            c->prof.launches++;
+            k_cheb_first<T><<<grid_exact(n), 256, 0, c->s>>>(L0.M.nbr, H.bs, dinv_of<T>(L0), b, (T)(1.0 / ch.theta),
+                                                             wvec<T>(L0, 4), wvec<T>(L0, 2), gb);
+            NBP_LAUNCHED();
+        } else {
+            copy<T>(gb, b, n, c->s);
+        }
         NBP_CUDA(cudaGraphLaunch(G.exec, c->s));
         copy<T>(x, gx, n, c->s);
         c->prof.launches += G.kernels;
@@ -771,17 +741,11 @@ template <typename T> static GmResult solve_A(nbp_ctx *c, int vsel, const T *s, 
             k_mul<T><<<grid_for(n), 256, 0, c->s>>>(out, x, dinv, n);
             NBP_LAUNCHED();
         };
-        auto opdotj = [&](const T *x, T *out, const T *V, long long ldv, int ncols, double *h) {
-            return apply_A_dot<T>(c, vsel, x, out, V, ldv, ncols, h);
-        };
-        return gmres<T>(c, KA<T>(c), n, op, pc, s, y, rtol, c->opt.atol, c->opt.m_A, c->opt.nmax_A, false, opdotj);
+        return gmres<T>(c, KA<T>(c), n, op, pc, s, y, rtol, c->opt.atol, c->opt.m_A, c->opt.nmax_A, false);
     }
     const int avsel = amg_vsel_of(c->opt.precision);
     auto pc = [&](const T *x, T *out) { vcycle<T>(c, c->HA, avsel, x, out); };
-    auto opdot = [&](const T *x, T *out, const T *V, long long ldv, int ncols, double *h) {
-        return apply_A_dot<T>(c, vsel, x, out, V, ldv, ncols, h);
-    };
-    return gmres<T>(c, KA<T>(c), n, op, pc, s, y, rtol, c->opt.atol, c->opt.m_A, c->opt.nmax_A, false, opdot);
+    return gmres<T>(c, KA<T>(c), n, op, pc, s, y, rtol, c->opt.atol, c->opt.m_A, c->opt.nmax_A, false);
 }
 
 // Algorithm 2: y = D x_p - C A^{-1} B x_p, inner solve to delta_I
@@ -1064,7 +1028,7 @@ static void destroy_ctx(nbp_ctx *c) {
     dmat_free(c->A, s); dmat_free(c->B, s); dmat_free(c->C, s); dmat_free(c->D, s); dmat_free(c->Shat, s);
     free_lowrank(c->lr, s);
     hier_free(c->HA, s); hier_free(c->HS, s);
-    dfree(c->diagA, s); dfree(c->full_w, s); dfree(c->dpart, s);
+    dfree(c->diagA, s); dfree(c->full_w, s);
     c->Kout.release(s); c->KA64.release(s); c->KS64.release(s); c->KA32.release(s); c->KS32.release(s);
     c->B64.release(s); c->B32.release(s);
     cudaStreamSynchronize(s);

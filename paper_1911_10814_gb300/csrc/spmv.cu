@@ -165,43 +165,4 @@ void spmv(const DMat &M, int vsel, SpmvArgs a, int epi, bool lr, cudaStream_t s,
 template void spmv<double>(const DMat &, int, SpmvArgs, int, bool, cudaStream_t, int);
 template void spmv<float>(const DMat &, int, SpmvArgs, int, bool, cudaStream_t, int);
 
-template <int BS, typename VT, typename XT, int C>
-static void launch_dot(const SpmvArgs &a, bool lr, cudaStream_t s) {
-    const unsigned grid = grid_exact((long long)a.nslice * C);
-    if (lr) k_sell<BS, VT, XT, EPI_SET, true, C, true><<<grid, 256, 0, s>>>(a);
-    else k_sell<BS, VT, XT, EPI_SET, false, C, true><<<grid, 256, 0, s>>>(a);
-    NBP_LAUNCHED();
-}
-
-template <typename XT>
-int spmv_dot(const DMat &M, int vsel, SpmvArgs a, bool lr, cudaStream_t s) {
-    const bool sell_ok = M.sl_ci && M.br == 3 && M.bc == 3 && (sizeof(XT) == 8 ? M.sl_v != nullptr
-                                                                              : (vsel == 2 ? M.sl_v16 != nullptr
-                                                                                           : M.sl_v32 != nullptr));
-    if (!sell_ok || (M.tuned > 0 && M.tuned != kSell2) || a.ndot < 1 || a.ndot > 16) return 0;
-    a.nbr = M.nbr;
-    a.nslice = M.nslice;
-    a.sl_ptr = M.sl_ptr;
-    a.sl_ci = M.sl_ci;
-    const int C = M.sl_c;
-    if constexpr (sizeof(XT) == 8) {
-        a.val = M.sl_v;
-        if (C == 8) launch_dot<3, double, double, 8>(a, lr, s); else launch_dot<3, double, double, 32>(a, lr, s);
-    } else if (vsel == 2) {
-        a.sl_ptr = M.sl2_ptr;   // paired layout
-        a.sl_ci = M.sl2_ci;
-        a.val = M.sl_v16;
-        if (C == 8) launch_dot<3, __nv_bfloat16, float, 8>(a, lr, s); else launch_dot<3, __nv_bfloat16, float, 32>(a, lr, s);
-    } else {
-        a.val = M.sl_v32;
-        if (C == 8) launch_dot<3, float, float, 8>(a, lr, s); else launch_dot<3, float, float, 32>(a, lr, s);
-    }
-    return (int)grid_exact((long long)M.nslice * C);
-}
-
-int spmv_dot_blocks(const DMat &M) { return M.sl_ci ? (int)grid_exact((long long)M.nslice * M.sl_c) : 0; }
-
-template int spmv_dot<double>(const DMat &, int, SpmvArgs, bool, cudaStream_t);
-template int spmv_dot<float>(const DMat &, int, SpmvArgs, bool, cudaStream_t);
-
 }  // namespace nbp

@@ -13,12 +13,5 @@ void spmv(const DMat &M, int vsel, SpmvArgs a, int epi, bool lr, cudaStream_t s,
 
 int choose_group(const DMat &M);
 
-// y = M x (3x3 blocks, sliced ELL) with the partial inner products of y and
-// columns 0..a.ndot-1 of a.dV fused into the epilogue (a.dpart gets
-// [col][block] partials).  Returns the number of blocks (partials per column)
-// or 0 when the fused path does not apply (then nothing was launched).
-template <typename XT> int spmv_dot(const DMat &M, int vsel, SpmvArgs a, bool lr, cudaStream_t s);
-int spmv_dot_blocks(const DMat &M);
-
 
 }  // namespace nbp
