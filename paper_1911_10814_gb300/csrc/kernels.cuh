@@ -347,15 +347,35 @@ __device__ __forceinline__ bool grid_last_block(unsigned *ticket) {
     return s_last != 0;
 }
 
-// out[col] = sum_b partial[col][b] (lanes over b with stride 32, then a warp
-// tree), one warp per column; run by one block.
+// out[col] = sum_b partial[col][b] for col < ncols, run by one whole block:
+// thread t adds partials b = t, t + blockDim, ... of up to 8 columns at a time
+// (all loads independent), then a warp tree and a fixed sum over the warps --
+// one order whatever the scheduling.
 __device__ __forceinline__ void block_reduce_partials(const double *partial, int nb, int ncols, double *out) {
+    __shared__ double red[8][32];
     const int warp = threadIdx.x >> 5, ln = threadIdx.x & 31, nw = blockDim.x >> 5;
-    for (int col = warp; col < ncols; col += nw) {
-        double s = 0.0;
-        for (int b = ln; b < nb; b += 32) s += __ldcg(partial + (long long)col * nb + b);
-        s = warp_sum(s);
-        if (ln == 0) out[col] = s;
+    for (int c0 = 0; c0 < ncols; c0 += 8) {
+        double acc[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) acc[q] = 0.0;
+#pragma unroll 4
+        for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                if (c0 + q < ncols) acc[q] += __ldcg(partial + (long long)(c0 + q) * nb + b);
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const double v = warp_sum(acc[q]);
+            if (ln == 0) red[q][warp] = v;
+        }
+        __syncthreads();
+        if ((int)threadIdx.x < 8 && c0 + (int)threadIdx.x < ncols) {
+            double u = 0.0;
+            for (int w = 0; w < nw; ++w) u += red[threadIdx.x][w];
+            out[c0 + threadIdx.x] = u;
+        }
+        __syncthreads();
     }
 }
 
@@ -454,8 +474,10 @@ __global__ void __launch_bounds__(256) k_mdot(const T *__restrict__ V, long long
         }
 #pragma unroll
         for (int q = 0; q < CB; ++q) {
-            const double v = warp_sum((double)acc[q]);
-            if (ln == 0) red[q][warp] = v;
+            if (c0 + q < ncols) {   // uniform over the block
+                const double v = warp_sum((double)acc[q]);
+                if (ln == 0) red[q][warp] = v;
+            }
         }
         __syncthreads();
         if (threadIdx.x < CB && c0 + (int)threadIdx.x < ncols) {
