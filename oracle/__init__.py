@@ -91,6 +91,8 @@ def _load():
             ("or_get_info", [vp, ctypes.POINTER(Info)]), ("or_destroy", [vp]),
             ("or_chebyshev", [ctypes.c_int, ctypes.c_int, _ip, _ip, _dp, ctypes.c_double, ctypes.c_int, _dp, _dp,
                               ctypes.c_int]),
+            ("or_rcr_step", [ctypes.c_int] + [_dp] * 7 + [ctypes.c_double, ctypes.c_int, ctypes.c_double,
+                                                          ctypes.c_double, _dp, _dp, _dp]),
         ]:
             f = getattr(lib, name)
             f.argtypes = args
@@ -305,6 +307,27 @@ def chebyshev(rowptr, col, val, bs, rho, k, b, x0=None):
     x = np.zeros(n * bs) if x0 is None else _d(x0).copy()
     lib.or_chebyshev(n, bs, _pi(rp), _pi(ci), _pd(v), rho, k, _pd(b), _pd(x), int(x0 is None))
     return x
+
+
+def rcr_step(Rp, C, Rd, Pd, Pi_n, Q_n, Q_np1, dt, nts, eps_abs=1e-8, eps_rel=1e-5):
+    """RCR outlets, one time step (Algorithm 1) and the difference-quotient
+    stiffness m^k (Sec. 2.5).  Arrays of n_out values; returns
+    (P_np1, Pi_np1, m)."""
+    lib = _load()
+    arrs = [_d(np.atleast_1d(a)) for a in (Rp, C, Rd, Pd, Pi_n, Q_n, Q_np1)]
+    n = len(arrs[0])
+    assert all(len(a) == n for a in arrs)
+    P, Pi, m = np.zeros(n), np.zeros(n), np.zeros(n)
+    lib.or_rcr_step(n, *[_pd(a) for a in arrs], float(dt), int(nts), float(eps_abs), float(eps_rel), _pd(P), _pd(Pi),
+                    _pd(m))
+    return P, Pi, m
+
+
+def outlet_flows(sysd: dict, v):
+    """Q^k = a^k . v (the flow rate through outlet k, Sec. 2.5), v the 3N velocity dofs."""
+    ptr, idx, val = sysd["out_ptr"], sysd["out_idx"], sysd["out_val"]
+    v = _d(v)
+    return np.array([float(np.dot(val[ptr[k]:ptr[k + 1]], v[idx[ptr[k]:ptr[k + 1]]])) for k in range(len(ptr) - 1)])
 
 
 # --------------------------------------------------------------- dense forms

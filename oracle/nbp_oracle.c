@@ -46,6 +46,12 @@
  *   - Chebyshev smoothing of degree k on D_b^{-1} A (D_b = block diagonal),
  *     interval [rho/10, rho] with rho the Gershgorin bound of D_b^{-1} A
  *     (largest absolute row sum) (Saad, Iterative Methods, Alg. 12.1).
+ *   - RCR (three-element Windkessel) outlets, Sec. 2.1 / 2.4: one time step
+ *     of dPi/dt = -Pi/(R_d C) + Q/C, P = R_p Q + Pi + P_d by the
+ *     fourth-order Runge-Kutta scheme of Algorithm 1 (n_ts substeps, Q
+ *     linear in time), and the stiffness m^k = dP_{n+1}/dQ_{n+1} by the
+ *     central difference quotient of Sec. 2.5 (eps = max(eps_abs,
+ *     eps_rel |Q|)).
  *
  * Vectors: x = [x_v (3N, node-interleaved); x_p (N)].
  * Build with -ffp-contract=off so that no multiply-add is fused.
@@ -1015,4 +1021,46 @@ void or_destroy(or_ctx *c) {
     free(c->out_ptr); free(c->out_idx); free(c->out_val); free(c->r); free(c->diagA);
     free(c->wv1); free(c->wv2); free(c->wv3); free(c->wp1); free(c->wp2); free(c->wp3); free(c->wp4);
     free(c);
+}
+
+/* ------------------------------------------------------------ RCR outlets */
+/* right-hand side of the distal-pressure ODE (Sec. 2.1, RCR circuit) */
+static double rcr_rhs(double Pi, double Q, double Rd, double C) { return -Pi / (Rd * C) + Q / C; }
+
+/* Algorithm 1: Pi over [t_n, t_n + dt] in n_ts equal substeps h, Q linear
+ * from Q_n to Q_np1 (Q_{n,m} = (1 - m/n_ts) Q_n + (m/n_ts) Q_np1); stages
+ * K1..K4 with the intermediate flows 2/3 Q_m + 1/3 Q_{m+1} and
+ * 1/3 Q_m + 2/3 Q_{m+1}; weights 1/8, 3/8, 3/8, 1/8.  Returns
+ * P_{n+1} = R_p Q_np1 + Pi_{n,n_ts} + P_d and the end value of Pi. */
+static double rcr_G(double Rp, double C, double Rd, double Pd, double Pi_n, double Q_n, double Q_np1, double dt,
+                    int nts, double *Pi_end) {
+    const double h = dt / nts;
+    double Pi = Pi_n;
+    for (int m = 0; m < nts; ++m) {
+        const double Qa = (1.0 - (double)m / nts) * Q_n + ((double)m / nts) * Q_np1;
+        const double Qb = (1.0 - (double)(m + 1) / nts) * Q_n + ((double)(m + 1) / nts) * Q_np1;
+        const double K1 = rcr_rhs(Pi, Qa, Rd, C);
+        const double K2 = rcr_rhs(Pi + K1 * h / 3.0, 2.0 * Qa / 3.0 + Qb / 3.0, Rd, C);
+        const double K3 = rcr_rhs(Pi - K1 * h / 3.0 + K2 * h, Qa / 3.0 + 2.0 * Qb / 3.0, Rd, C);
+        const double K4 = rcr_rhs(Pi + K1 * h - K2 * h + K3 * h, Qb, Rd, C);
+        Pi = Pi + K1 * h / 8.0 + 3.0 * K2 * h / 8.0 + 3.0 * K3 * h / 8.0 + K4 * h / 8.0;
+    }
+    if (Pi_end) *Pi_end = Pi;
+    return Rp * Q_np1 + Pi + Pd;
+}
+
+/* One step for n_out outlets: P_np1 = G(Pi_n, Q_n, Q_np1), Pi_np1 its end
+ * state, and m = (G(.., Q_np1 + eps/2) - G(.., Q_np1 - eps/2)) / eps with
+ * eps = max(eps_abs, eps_rel |Q_np1|) (Sec. 2.5, difference approximation
+ * of m^k). */
+void or_rcr_step(int n_out, const double *Rp, const double *C, const double *Rd, const double *Pd, const double *Pi_n,
+                 const double *Q_n, const double *Q_np1, double dt, int nts, double eps_abs, double eps_rel,
+                 double *P_np1, double *Pi_np1, double *m) {
+    for (int k = 0; k < n_out; ++k) {
+        P_np1[k] = rcr_G(Rp[k], C[k], Rd[k], Pd[k], Pi_n[k], Q_n[k], Q_np1[k], dt, nts, &Pi_np1[k]);
+        const double eps = fmax(eps_abs, eps_rel * fabs(Q_np1[k]));
+        const double Pp = rcr_G(Rp[k], C[k], Rd[k], Pd[k], Pi_n[k], Q_n[k], Q_np1[k] + eps / 2.0, dt, nts, NULL);
+        const double Pm = rcr_G(Rp[k], C[k], Rd[k], Pd[k], Pi_n[k], Q_n[k], Q_np1[k] - eps / 2.0, dt, nts, NULL);
+        m[k] = (Pp - Pm) / eps;
+    }
 }

@@ -69,6 +69,7 @@ def _load():
         lib.synth_state.argtypes = [P, dp]; lib.synth_state.restype = None
         lib.synth_assemble.argtypes = [P, dp, ip, ip, dp, dp, dp, dp, dp]; lib.synth_assemble.restype = ctypes.c_int
         lib.synth_rhs.argtypes = [P, dp]; lib.synth_rhs.restype = None
+        lib.synth_outlets.argtypes = [P, ip, ip, dp]; lib.synth_outlets.restype = ctypes.c_long
         lib.synth_uniforms.argtypes = [ctypes.c_uint64, ctypes.c_long, dp]; lib.synth_uniforms.restype = None
         lib.synth_element_tangent.argtypes = [P, dp, dp, dp]; lib.synth_element_tangent.restype = None
         lib.synth_backflow_tangent.argtypes = [P, dp, dp, dp]; lib.synth_backflow_tangent.restype = None
@@ -143,28 +144,48 @@ def generate(spec: MeshSpec) -> dict:
     B = np.empty((nnz, 3), dtype=np.float64)
     C = np.empty((nnz, 3), dtype=np.float64)
     D = np.empty(nnz, dtype=np.float64)
-    avec = np.empty((max(spec.n_out, 1), 3 * N), dtype=np.float64)
-    rc = lib.synth_assemble(ctypes.byref(p), _dp(vel), _ip(rowptr), _ip(col), _dp(A), _dp(B), _dp(C), _dp(D),
-                            _dp(avec))
+    rc = lib.synth_assemble(ctypes.byref(p), _dp(vel), _ip(rowptr), _ip(col), _dp(A), _dp(B), _dp(C), _dp(D), None)
     if rc != 0:
         raise RuntimeError("synth_assemble: element node missing from pattern")
     b = np.empty(4 * N, dtype=np.float64)
     lib.synth_rhs(ctypes.byref(p), _dp(b))
-    out_ptr = [0]
-    out_idx, out_val = [], []
-    for k in range(spec.n_out):
-        nzk = np.nonzero(avec[k])[0]
-        out_idx.append(nzk.astype(np.int32))
-        out_val.append(avec[k][nzk])
-        out_ptr.append(out_ptr[-1] + len(nzk))
+    out_ptr, out_idx, out_val = outlets(spec)
     r = np.asarray(spec.R, dtype=np.float64) * spec.alpha_f_gamma_dt
     return dict(
         spec=spec, n_nodes=N, rowptr=rowptr, col=col, A=A, B=B, C=C, D=D, vel=vel,
-        out_ptr=np.asarray(out_ptr, dtype=np.int32),
-        out_idx=np.concatenate(out_idx) if out_idx else np.zeros(0, np.int32),
-        out_val=np.concatenate(out_val) if out_val else np.zeros(0, np.float64),
-        r=r, b=b,
+        out_ptr=out_ptr, out_idx=out_idx, out_val=out_val, r=r, b=b,
     )
+
+
+def outlets(spec: MeshSpec):
+    """Sparse outlet vectors a^k (out_ptr, out_idx, out_val) of `spec`."""
+    lib = _load()
+    p = spec.params()
+    out_ptr = np.zeros(spec.n_out + 1, dtype=np.int32)
+    cnt = lib.synth_outlets(ctypes.byref(p), _ip(out_ptr), None, None)
+    if cnt < 0:
+        raise ValueError("synth_outlets: more outlets than outlet triangles")
+    out_idx = np.zeros(cnt, dtype=np.int32)
+    out_val = np.zeros(cnt, dtype=np.float64)
+    lib.synth_outlets(ctypes.byref(p), _ip(out_ptr), _ip(out_idx), _dp(out_val))
+    return out_ptr, out_idx, out_val
+
+
+def outlets_dense(spec: MeshSpec) -> np.ndarray:
+    """Dense outlet vectors (n_out, 3N) as assembled with the tangent (tests)."""
+    lib = _load()
+    p = spec.params()
+    N = lib.synth_num_nodes(ctypes.byref(p))
+    nnz = lib.synth_pattern(ctypes.byref(p), None, None)
+    rowptr = np.empty(N + 1, dtype=np.int32)
+    col = np.empty(nnz, dtype=np.int32)
+    lib.synth_pattern(ctypes.byref(p), _ip(rowptr), _ip(col))
+    vel = np.empty(3 * N, dtype=np.float64)
+    lib.synth_state(ctypes.byref(p), _dp(vel))
+    A = np.empty((nnz, 3, 3)); B = np.empty((nnz, 3)); C = np.empty((nnz, 3)); D = np.empty(nnz)
+    avec = np.empty((max(spec.n_out, 1), 3 * N), dtype=np.float64)
+    lib.synth_assemble(ctypes.byref(p), _dp(vel), _ip(rowptr), _ip(col), _dp(A), _dp(B), _dp(C), _dp(D), _dp(avec))
+    return avec[:spec.n_out]
 
 
 def element_tangent(spec: MeshSpec, X: np.ndarray, vel: np.ndarray) -> np.ndarray:

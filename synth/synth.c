@@ -46,7 +46,8 @@ typedef struct {
     double Re, rho, mu, dt, rho_inf;
     double pert;      /* relative perturbation amplitude (0.05) */
     uint64_t seed;
-    int n_out;        /* 1..4 outlet pieces on the z = Lz face */
+    int n_out;        /* outlet pieces on the z = Lz face: 1..4 (halves, thirds,
+                         quadrants) or up to 2 nx ny patches of consecutive triangles */
 } synth_params;
 
 static inline uint64_t sm64_next(uint64_t *s) {
@@ -372,13 +373,18 @@ static inline int find_col(const int32_t *col, int32_t beg, int32_t end, int32_t
     return -1;
 }
 
-/* Outlet piece of a top-face point (x, y in [0,1]) for n_out pieces:
- * 1 whole face, 2 halves in x, 3 thirds in x, 4 quadrants. */
-static inline int outlet_piece(int n_out, double x, double y) {
+/* Outlet piece of a top-face triangle with centroid (x, y in [0,1]) for
+ * n_out pieces: 1 whole face, 2 halves in x, 3 thirds in x, 4 quadrants;
+ * more than 4 (many-outlet stress cases): n_out patches of consecutive
+ * triangles, triangle t of T (loop order: squares row by row, two
+ * triangles each) in patch floor(t n_out / T), every patch non-empty when
+ * n_out <= T. */
+static inline int outlet_piece(int n_out, double x, double y, long t, long T) {
     if (n_out <= 1) return 0;
     if (n_out == 2) return x >= 0.5;
     if (n_out == 3) { int k = (int)(3.0 * x); return k > 2 ? 2 : k; }
-    return (x >= 0.5) + 2 * (y >= 0.5);
+    if (n_out == 4) return (x >= 0.5) + 2 * (y >= 0.5);
+    return (int)((t * (long)n_out) / T);
 }
 
 /* Assemble the tangent on the shared pattern (rowptr/col from synth_pattern).
@@ -501,7 +507,7 @@ int synth_assemble(const synth_params *p, const double *vel, const int32_t *rowp
                         cy += (hj + ((tri[t][v] >> 1) & 1)) * hy;
                     }
                     cx /= 3.0 * p->Lx; cy /= 3.0 * p->Ly;
-                    int kk = outlet_piece(p->n_out, cx, cy);
+                    int kk = outlet_piece(p->n_out, cx, cy, 2L * ((long)hj * p->nx + hi) + t, 2L * p->nx * p->ny);
                     for (int v = 0; v < 3; ++v) {
                         int bi = hi + (tri[t][v] & 1), bj = hj + ((tri[t][v] >> 1) & 1);
                         if (is_dirichlet(p, bi, bj, p->nz)) continue;
@@ -512,6 +518,60 @@ int synth_assemble(const synth_params *p, const double *vel, const int32_t *rowp
             }
     }
     return bad ? -1 : 0;
+}
+
+/* Outlet vectors in sparse form, the same values as the dense avec of
+ * synth_assemble (same triangles, same summation order): outlet k has
+ * entries out_idx/out_val[out_ptr[k] .. out_ptr[k+1]-1], unknown indices
+ * 3g + 2 (z component) ascending, Dirichlet nodes left out.  With out_idx ==
+ * NULL only out_ptr is filled.  Returns the entry count, or -1 when
+ * n_out exceeds the 2 nx ny outlet triangles. */
+long synth_outlets(const synth_params *p, int32_t *out_ptr, int32_t *out_idx, double *out_val) {
+    const int n_out = p->n_out > 0 ? p->n_out : 0;
+    const long nf = (long)(p->nx + 1) * (p->ny + 1);
+    if (n_out > 2L * p->nx * p->ny) return -1;
+    double *acc = (double *)calloc((size_t)n_out * (size_t)nf, sizeof(double));
+    unsigned char *hit = (unsigned char *)calloc((size_t)n_out * (size_t)nf, 1);
+    if ((n_out && !acc) || (n_out && !hit)) { free(acc); free(hit); return -1; }
+    const double hx = p->Lx / p->nx, hy = p->Ly / p->ny;
+    const double area = 0.5 * hx * hy;
+    for (int hj = 0; hj < p->ny; ++hj)
+        for (int hi = 0; hi < p->nx; ++hi) {
+            static const int tri[2][3] = {{0, 1, 3}, {0, 2, 3}};
+            for (int t = 0; t < 2; ++t) {
+                double cx = 0.0, cy = 0.0;
+                for (int v = 0; v < 3; ++v) {
+                    cx += (hi + (tri[t][v] & 1)) * hx;
+                    cy += (hj + ((tri[t][v] >> 1) & 1)) * hy;
+                }
+                cx /= 3.0 * p->Lx; cy /= 3.0 * p->Ly;
+                int kk = outlet_piece(p->n_out, cx, cy, 2L * ((long)hj * p->nx + hi) + t, 2L * p->nx * p->ny);
+                for (int v = 0; v < 3; ++v) {
+                    int bi = hi + (tri[t][v] & 1), bj = hj + ((tri[t][v] >> 1) & 1);
+                    if (is_dirichlet(p, bi, bj, p->nz)) continue;
+                    long f = (long)bj * (p->nx + 1) + bi;
+                    acc[(size_t)kk * nf + f] += area / 3.0;
+                    hit[(size_t)kk * nf + f] = 1;
+                }
+            }
+        }
+    long cnt = 0;
+    for (int k = 0; k < n_out; ++k) {
+        if (out_ptr) out_ptr[k] = (int32_t)cnt;
+        for (long f = 0; f < nf; ++f) {
+            if (!hit[(size_t)k * nf + f] || acc[(size_t)k * nf + f] == 0.0) continue;
+            if (out_idx) {
+                int bi = (int)(f % (p->nx + 1)), bj = (int)(f / (p->nx + 1));
+                out_idx[cnt] = (int32_t)(3 * nid(p, bi, bj, p->nz) + 2);
+                out_val[cnt] = acc[(size_t)k * nf + f];
+            }
+            ++cnt;
+        }
+    }
+    if (out_ptr) out_ptr[n_out] = (int32_t)cnt;
+    free(acc);
+    free(hit);
+    return cnt;
 }
 
 /* Right-hand side: uniform [-1, 1] on all 4N unknowns, ordered [x_v (3N, node

@@ -441,3 +441,89 @@ def test_simple_preconditioner_identity(tiny):
     o.set_options(rtol_A=1e-3, rtol_S=1e-2)
     x, info, rc = o.solve(d["b"])
     assert rc == 0 and np.linalg.norm(d["b"] - F @ x) <= 1e-8 * np.linalg.norm(d["b"])
+
+
+# ------------------------------------------------------------ RCR outlets
+def _rcr_exact(Rp, C, Rd, Pd, Pi_n, Q_n, Q_np1, T):
+    """Closed form of one step of dPi/dt = -Pi/tau + Q(t)/C (tau = Rd C) with
+    Q linear on [0, T]: Pi(T) = Pi_n e + (Q_n/C)(I0 - I1) + (Q_np1/C) I1,
+    e = exp(-T/tau), I0 = tau (1 - e), I1 = tau - tau^2 (1 - e)/T; and
+    dP/dQ_np1 = Rp + I1/C."""
+    tau = Rd * C
+    e = np.exp(-T / tau)
+    I0 = tau * (1.0 - e)
+    I1 = tau - tau * tau * (1.0 - e) / T
+    Pi = Pi_n * e + Q_n / C * (I0 - I1) + Q_np1 / C * I1
+    return Rp * Q_np1 + Pi + Pd, Pi, Rp + I1 / C
+
+
+def test_rcr_step_fourth_order_to_the_exact_solution():
+    """Algorithm 1 is a fourth-order Runge-Kutta scheme: against the closed
+    form of the linear RCR ODE the error falls by ~2^4 per halving of h."""
+    Rp, C, Rd, Pd, Pi_n, Q_n, Q_np1, T = 120.0, 1e-3, 1.0, 3.0, 5.0, 0.4, 0.9, 1e-3   # tau = T
+    Pex, Piex, _ = _rcr_exact(Rp, C, Rd, Pd, Pi_n, Q_n, Q_np1, T)
+    errs = []
+    for nts in (4, 8, 16, 32):   # h / tau = 1/4 .. 1/32 (asymptotic range)
+        P, Pi, _ = oracle.rcr_step([Rp], [C], [Rd], [Pd], [Pi_n], [Q_n], [Q_np1], T, nts)
+        assert abs(P[0] - Rp * Q_np1 - Pi[0] - Pd) <= 1e-12 * abs(P[0])
+        errs.append(abs(Pi[0] - Piex))
+    for a, b in zip(errs, errs[1:]):
+        assert 15.0 <= a / b <= 19.0
+    P, _, _ = oracle.rcr_step([Rp], [C], [Rd], [Pd], [Pi_n], [Q_n], [Q_np1], T, 64)
+    assert abs(P[0] - Pex) <= 1e-10 * abs(Pex)
+
+
+def test_rcr_stiffness_is_the_derivative_of_the_step():
+    """The model is affine in Q_{n+1}, so the difference quotient of Sec. 2.5
+    equals dP/dQ_{n+1} of the RK4 map for any eps, and tends to the exact
+    Rp + I1/C as h -> 0."""
+    rng = np.random.default_rng(31)
+    n = 50
+    Rp = 10 ** rng.uniform(1, 3, n); C = 10 ** rng.uniform(-5, -3, n); Rd = 10 ** rng.uniform(2, 4, n)
+    Pd = rng.uniform(0, 10, n); Pi_n = rng.uniform(0, 100, n); Q_n = rng.uniform(-1, 1, n); Q_np1 = rng.uniform(-1, 1, n)
+    T = 1e-3
+    P, _, m = oracle.rcr_step(Rp, C, Rd, Pd, Pi_n, Q_n, Q_np1, T, 64)
+    _, _, m_big = oracle.rcr_step(Rp, C, Rd, Pd, Pi_n, Q_n, Q_np1, T, 64, eps_abs=1e-2, eps_rel=0.0)
+    exact = np.array([_rcr_exact(*a, T)[2] for a in zip(Rp, C, Rd, Pd, Pi_n, Q_n, Q_np1)])
+    # a wide step: only the RK4 truncation (h / tau <= 0.013 here) is left
+    assert np.max(np.abs(m_big - exact) / exact) <= 1e-9
+    # the paper's step eps = max(1e-8, 1e-5 |Q|): plus the rounding of P over eps
+    eps = np.maximum(1e-8, 1e-5 * np.abs(Q_np1))
+    bound = 16 * np.finfo(float).eps * (np.abs(P) + np.abs(Rp * eps)) / eps + 1e-9 * exact
+    assert np.all(np.abs(m - exact) <= bound)
+
+
+def test_rcr_fixed_point_and_resistance_limit():
+    """At the steady state Pi = Rd Q with constant Q nothing moves:
+    P = (Rp + Rd) Q + Pd.  As C -> 0+ the RCR model reduces to a resistance
+    Rp + Rd (Sec. 2.1), so m^k -> Rp + Rd."""
+    Rp, Rd, Q, Pd = 200.0, 1800.0, 0.3, 7.0
+    P, Pi, _ = oracle.rcr_step([Rp], [1e-3], [Rd], [Pd], [Rd * Q], [Q], [Q], 1e-3, 5)
+    assert abs(P[0] - ((Rp + Rd) * Q + Pd)) <= 1e-13 * abs(P[0])
+    assert abs(Pi[0] - Rd * Q) <= 1e-13 * Rd * Q
+    # tau = 1e-6 s: h = dt / 4000 keeps explicit RK4 stable (h / tau = 0.25)
+    _, _, m = oracle.rcr_step([Rp], [1e-9], [1000.0], [0.0], [0.0], [0.1], [0.2], 1e-3, 4000)
+    assert abs(m[0] - (Rp + 1000.0)) <= 2e-3 * (Rp + 1000.0)
+
+
+def test_many_outlet_patches_cover_the_outlet_face():
+    """The many-outlet split (772 patches of consecutive outlet triangles,
+    the patient-model outlet count of Sec. 4) partitions the outlet face:
+    every patch is non-empty and the patch vectors sum to the whole-face
+    outlet vector a = int N_A n dGamma."""
+    many = synth.MeshSpec(32, 32, 16, R=tuple([1e3] * 772), name="box32_o772")
+    one = synth.MeshSpec(32, 32, 16, R=(1e3,), name="box32_o1")
+    ptr, idx, val = synth.outlets(many)
+    assert np.all(np.diff(ptr) > 0)
+    tot = np.zeros(3 * many.n_nodes)
+    np.add.at(tot, idx, val)
+    p1, i1, v1 = synth.outlets(one)
+    whole = np.zeros(3 * one.n_nodes)
+    whole[i1] = v1
+    assert np.max(np.abs(tot - whole)) <= 1e-15 * np.max(np.abs(whole)) * 8
+    # sparse outlet vectors equal the dense ones assembled with the tangent
+    dense = synth.outlets_dense(synth.large_mixed(8))
+    p4, i4, v4 = synth.outlets(synth.large_mixed(8))
+    for k in range(4):
+        nz = np.nonzero(dense[k])[0]
+        assert np.array_equal(nz, i4[p4[k]:p4[k + 1]]) and np.array_equal(dense[k][nz], v4[p4[k]:p4[k + 1]])
