@@ -50,14 +50,24 @@ def _args():
     p.add_argument("--amg-kdepth", type=int, default=99, help="K-cycle on coarse levels 1..k")
     p.add_argument("--cheb-degree", type=int, default=2, help="Chebyshev smoothing degree of AMG(A)")
     p.add_argument("--cheb-degree-S", type=int, default=1, help="Chebyshev smoothing degree of AMG(S_hat)")
+    p.add_argument("--outlets", type=int, default=0,
+                   help="split the outlet face into this many patches (many-outlet stress case, e.g. 772)")
     p.add_argument("--workload", default="large", choices=["large", "batch"],
                    help="large: the 4.34M-unknown tangent (default); batch: 48 uneven cubes in one batched call")
     return p.parse_args()
 
 
-def _spec(scale):
+def _spec(scale, outlets=0):
+    """The 4.34M-unknown Re-2000 box (4 quadrant outlets); with outlets > 0 its
+    outlet face split into that many patches, R_k log-uniform in [1e2, 1e5]."""
+    import dataclasses
     import synth
-    return synth.large_mixed(scale)
+    spec = synth.large_mixed(scale)
+    if outlets:
+        u = synth.uniforms(outlets ^ 0x5EED, outlets)
+        R = tuple(float(10.0 ** (2.0 + 3.0 * x)) for x in u)
+        spec = dataclasses.replace(spec, R=R, name=f"{spec.name[:spec.name.rindex('_')]}_o{outlets}")
+    return spec
 
 
 def _peaks():
@@ -201,7 +211,7 @@ def run_reference(a):
         return
     import synth
     import oracle
-    d = synth.generate(_spec(a.scale))
+    d = synth.generate(_spec(a.scale, a.outlets))
     counts_path = os.path.join(ROOT, "profiles", "nested_solve_counts.json")
     with open(counts_path) as f:
         counts = json.load(f)["fp64"]
@@ -283,7 +293,7 @@ def main():
     import synth
     from paper_1911_10814_gb300 import Solver
 
-    spec = _spec(a.scale)
+    spec = _spec(a.scale, a.outlets)
     t0 = time.perf_counter()
     d = synth.generate(spec)
     t_gen = time.perf_counter() - t0

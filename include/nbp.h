@@ -259,6 +259,56 @@ nbp_status nbp_apply_A_noalloc(int32_t n_nodes, const int32_t *a_rowptr, const i
                                int32_t n_out, const int32_t *out_ptr, const int32_t *out_idx, const double *out_val,
                                const double *r, const double *x, double *y, void *stream);
 
+/* ------------------------------------------------------------ RCR outlets
+ * Three-element Windkessel (RCR) outlet model, paper Sec. 2.1 (RCR circuit
+ * equations): dPi^k/dt = -Pi^k / (R_d^k C^k) + Q^k / C^k and
+ * P^k = R_p^k Q^k + Pi^k + P_d^k, with Pi^k the pressure drop across the
+ * distal resistor and Q^k the flow through outlet k.  Parameters and the
+ * state at t_n of n_out outlets, each a DEVICE array of n_out doubles owned
+ * by the caller (read during the call only). */
+typedef struct {
+    const double *Rp, *C, *Rd;  /* proximal resistance, compliance, distal resistance (> 0) */
+    const double *Pd;           /* distal reference pressure P_d at t_{n+1} */
+    const double *Pi_n, *Q_n;   /* Pi and Q at t_n */
+    double eps_abs, eps_rel;    /* difference step eps = max(eps_abs, eps_rel |Q_{n+1}|) for m^k;
+                                   Sec. 2.5 fixes 1e-8 and 1e-5 (non-negative, not both zero) */
+} nbp_rcr;
+
+/* One time step of n_out RCR outlets (Algorithm 1): Pi from t_n to
+ * t_{n+1} = t_n + dt in nts equal substeps of the four-stage Runge-Kutta
+ * scheme, with Q linear in time from Q_n to Q_np1; P_np1 = R_p Q_np1 +
+ * Pi_{n+1} + P_d.  m^k = dP_{n+1}/dQ_{n+1} by the central difference
+ * quotient of Sec. 2.5 (two more steps at Q_np1 +- eps/2).  Q_np1: DEVICE
+ * array of n_out flows; outputs P_np1, Pi_np1, m: DEVICE arrays of n_out
+ * doubles, each may be NULL.  One thread per outlet, queued on `stream`
+ * (NULL: legacy default stream); returns without synchronising.  Errors:
+ * NBP_ERR_INVALID (n_out < 0, nts < 1, dt <= 0, a missing parameter
+ * array), NBP_ERR_CUDA (launch).  Explicit RK4 needs dt / nts below about
+ * 2.8 R_d C for stability; the caller picks nts. */
+nbp_status nbp_rcr_step(int32_t n_out, const nbp_rcr *p, const double *Q_np1, double dt, int32_t nts,
+                        double *P_np1, double *Pi_np1, double *m, void *stream);
+
+/* Flow rates through the context's outlets, Q^k = a^k . v (Sec. 2.5: Q^k is
+ * the integral of v . n over outlet k and a^k_{Ai} the integral of N_A n_i,
+ * the outlet vectors given to nbp_create).  v: DEVICE array of the 3N
+ * velocity dofs; Q: DEVICE array of n_out doubles.  Fixed-order
+ * reductions (bitwise repeatable).  Synchronises the context stream.
+ * Errors: NBP_ERR_INVALID (null pointer), NBP_ERR_CUDA. */
+nbp_status nbp_outlet_flows(nbp_ctx *ctx, const double *v, double *Q);
+
+/* The outlet coupling of one Newton iteration (Sec. 2.5): Q_{n+1}^k =
+ * a^k . v_np1, the RCR step and m^k as in nbp_rcr_step, and the context's
+ * rank-one weights set to r_k = scale m^k (scale = alpha_f gamma dt gives
+ * the matrix K of Sec. 2.5), all on the device: Q and m make no host round
+ * trip before the weights are in place.  p describes the context's n_out
+ * outlets in order.  Outputs (DEVICE, n_out doubles each, may be NULL):
+ * Q_np1, P_np1, Pi_np1, m.  Like nbp_set_resistances, S_hat keeps the
+ * weights of the last nbp_setup (call it again if P_S should track them).
+ * Synchronises the context stream.  Errors: NBP_ERR_INVALID, NBP_ERR_NAN
+ * (a non-finite m^k; the weights are then left unchanged), NBP_ERR_CUDA. */
+nbp_status nbp_rcr_update(nbp_ctx *ctx, const nbp_rcr *p, const double *v_np1, double dt, int32_t nts, double scale,
+                          double *Q_np1, double *P_np1, double *Pi_np1, double *m);
+
 #ifdef __cplusplus
 }
 #endif

@@ -163,6 +163,7 @@ class Oracle:
             args += [_pi(a), _pi(b), _pd(c)]
         args += [self.n_out, _pi(optr), _pi(oidx), _pd(oval), _pd(r)]
         self.ctx = lib.or_create(*args)
+        self._ready = False   # hierarchies built (setup) -- the solves need them
         self.set_options(**opts)
 
     def __del__(self):
@@ -191,6 +192,13 @@ class Oracle:
 
     def setup(self):
         self.lib.or_setup(self.ctx)
+        self._ready = True
+
+    def _ensure_setup(self):
+        # the solves and cycles use the AMG hierarchies; building them on
+        # first use keeps a forgotten setup() from reaching unbuilt data
+        if not self._ready:
+            self.setup()
 
     # -- operators
     def _apply(self, fn, x, n_out):
@@ -215,20 +223,24 @@ class Oracle:
         return self._apply(self.lib.or_apply_full, x, 4 * self.N)
 
     def apply_S(self, x):
-        """Algorithm 2 (needs setup())."""
+        """Algorithm 2 (builds the hierarchies first if setup() was not called)."""
+        self._ensure_setup()
         return self._apply(self.lib.or_apply_S, x, self.N)
 
     def apply_pscr(self, s):
-        """Algorithm 3 (needs setup())."""
+        """Algorithm 3 (builds the hierarchies first if setup() was not called)."""
+        self._ensure_setup()
         return self._apply(self.lib.or_apply_pscr, s, 4 * self.N)
 
     def vcycle(self, which, b):
+        self._ensure_setup()
         b = _d(b)
         x = np.zeros_like(b)
         self.lib.or_vcycle(self.ctx, which, _pd(b), _pd(x))
         return x
 
     def solve_A(self, b, rtol):
+        self._ensure_setup()
         b = _d(b)
         x = np.zeros_like(b)
         its = ctypes.c_int(0)
@@ -236,6 +248,8 @@ class Oracle:
         return x, its.value, rc
 
     def gmres_A(self, b, rtol, m, nmax, use_pc):
+        if use_pc:
+            self._ensure_setup()
         b = _d(b)
         x = np.zeros_like(b)
         its = ctypes.c_int(0)
@@ -245,6 +259,7 @@ class Oracle:
         return x, its.value, rel.value, rc
 
     def solve(self, b):
+        self._ensure_setup()
         b = _d(b)
         x = np.zeros_like(b)
         info = Info()

@@ -31,6 +31,7 @@
 
 #include "kernels.cuh"
 #include "spmv.cuh"
+#include "rcr.cuh"
 
 namespace nbp {
 
@@ -136,6 +137,8 @@ struct nbp_ctx {
     nbp::Bufs<double> B64;
     nbp::Bufs<float> B32;
     double *full_w = nullptr;     // 4N scratch of the outer operator
+    double *rcr_buf = nullptr;    // RCR update: Q, m and the new weights when the caller keeps none (3 n_out)
+    int *rcr_bad = nullptr;       // RCR update: non-finite m^k seen
     nbp::GmState *hst = nullptr;  // pinned host status
     nbp_info info{};
     nbp::Prof prof;
@@ -1028,7 +1031,7 @@ static void destroy_ctx(nbp_ctx *c) {
     dmat_free(c->A, s); dmat_free(c->B, s); dmat_free(c->C, s); dmat_free(c->D, s); dmat_free(c->Shat, s);
     free_lowrank(c->lr, s);
     hier_free(c->HA, s); hier_free(c->HS, s);
-    dfree(c->diagA, s); dfree(c->full_w, s);
+    dfree(c->diagA, s); dfree(c->full_w, s); dfree(c->rcr_buf, s); dfree(c->rcr_bad, s);
     c->Kout.release(s); c->KA64.release(s); c->KS64.release(s); c->KA32.release(s); c->KS32.release(s);
     c->B64.release(s); c->B32.release(s);
     cudaStreamSynchronize(s);
@@ -1248,6 +1251,53 @@ nbp_status nbp_set_resistances(nbp_ctx *c, const double *r) {
         NBP_CUDA(cudaMemcpyAsync(c->tctx->lr.r, c->lr.r, sizeof(double) * c->lr.n_out, cudaMemcpyDeviceToDevice, c->s));
         c->tctx->setup_done = false;
     }
+    return NBP_OK;
+    NBP_API_END(c)
+}
+
+nbp_status nbp_outlet_flows(nbp_ctx *c, const double *v, double *Q) {
+    NBP_API_BEGIN(c)
+    begin_call(c);
+    require(v && (Q || c->lr.n_out == 0), NBP_ERR_INVALID, "nbp_outlet_flows: null pointer");
+    launch_outlet_flows(c->lr.n_out, c->lr.optr, c->lr.oidx, c->lr.oval, v, Q, c->s);
+    NBP_CUDA(cudaStreamSynchronize(c->s));
+    return NBP_OK;
+    NBP_API_END(c)
+}
+
+nbp_status nbp_rcr_update(nbp_ctx *c, const nbp_rcr *p, const double *v_np1, double dt, int32_t nts, double scale,
+                          double *Q_np1, double *P_np1, double *Pi_np1, double *m) {
+    NBP_API_BEGIN(c)
+    begin_call(c);
+    const int n = c->lr.n_out;
+    if (n == 0) return NBP_OK;
+    require(v_np1 && rcr_params_ok(p) && nts >= 1 && dt > 0.0 && std::isfinite(scale), NBP_ERR_INVALID,
+            "nbp_rcr_update: bad arguments");
+    if (!c->rcr_buf) {
+        c->rcr_buf = dmalloc<double>(3LL * n, c->s);
+        c->rcr_bad = dmalloc<int>(1, c->s);
+    }
+    double *Q = Q_np1 ? Q_np1 : c->rcr_buf;
+    double *mk = m ? m : c->rcr_buf + n;
+    double *rnew = c->rcr_buf + 2LL * n;
+    NBP_CUDA(cudaMemsetAsync(c->rcr_bad, 0, sizeof(int), c->s));
+    launch_outlet_flows(n, c->lr.optr, c->lr.oidx, c->lr.oval, v_np1, Q, c->s);
+    launch_rcr_step(n, *p, Q, dt, nts, P_np1, Pi_np1, mk, rnew, scale, c->rcr_bad, c->s);
+    int bad = 0;
+    std::vector<double> r(n);
+    NBP_CUDA(cudaMemcpyAsync(&bad, c->rcr_bad, sizeof(int), cudaMemcpyDeviceToHost, c->s));
+    NBP_CUDA(cudaMemcpyAsync(r.data(), rnew, sizeof(double) * n, cudaMemcpyDeviceToHost, c->s));
+    NBP_CUDA(cudaStreamSynchronize(c->s));
+    require(!bad, NBP_ERR_NAN, "nbp_rcr_update: non-finite stiffness m^k");
+    // install the weights (device copy in stream order; host copy for the transposed context)
+    NBP_CUDA(cudaMemcpyAsync(c->lr.r, rnew, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->s));
+    c->lr.r_host = r;
+    if (c->tctx) {
+        c->tctx->lr.r_host = r;
+        NBP_CUDA(cudaMemcpyAsync(c->tctx->lr.r, rnew, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->s));
+        c->tctx->setup_done = false;
+    }
+    NBP_CUDA(cudaStreamSynchronize(c->s));
     return NBP_OK;
     NBP_API_END(c)
 }

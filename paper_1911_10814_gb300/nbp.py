@@ -70,6 +70,12 @@ class nbp_profile_info(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class nbp_rcr(ctypes.Structure):
+    _fields_ = [("Rp", ctypes.c_void_p), ("C", ctypes.c_void_p), ("Rd", ctypes.c_void_p), ("Pd", ctypes.c_void_p),
+                ("Pi_n", ctypes.c_void_p), ("Q_n", ctypes.c_void_p), ("eps_abs", ctypes.c_double),
+                ("eps_rel", ctypes.c_double)]
+
+
 STATUS = {0: "NBP_OK", 1: "NBP_ERR_INVALID", 2: "NBP_ERR_CUDA", 3: "NBP_ERR_OOM", 4: "NBP_NOT_CONVERGED",
           5: "NBP_ERR_BREAKDOWN", 6: "NBP_ERR_NAN", 7: "NBP_ERR_TIMEOUT", 8: "NBP_ERR_STATE"}
 
@@ -106,6 +112,9 @@ SIGNATURES = {
     "nbp_batch_destroy": (ctypes.c_int, [_vp]),
     "nbp_batch_last_error": (ctypes.c_char_p, [_vp]),
     "nbp_apply_A_noalloc": (ctypes.c_int, [_i32, _vp, _vp, _vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "nbp_rcr_step": (ctypes.c_int, [_i32, ctypes.POINTER(nbp_rcr), _vp, _d, _i32, _vp, _vp, _vp, _vp]),
+    "nbp_outlet_flows": (ctypes.c_int, [_vp, _vp, _vp]),
+    "nbp_rcr_update": (ctypes.c_int, [_vp, ctypes.POINTER(nbp_rcr), _vp, _d, _i32, _d, _vp, _vp, _vp, _vp]),
 }
 
 
@@ -146,6 +155,34 @@ def default_options(**kw) -> nbp_options:
 
 def _ptr(t):
     return ctypes.c_void_p(t.data_ptr())
+
+
+def _optr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def rcr_params(Rp, C, Rd, Pd, Pi_n, Q_n, eps_abs=1e-8, eps_rel=1e-5) -> nbp_rcr:
+    """nbp_rcr over CUDA float64 tensors (n_out each); keep the tensors alive
+    while the structure is used."""
+    p = nbp_rcr()
+    p.Rp, p.C, p.Rd, p.Pd, p.Pi_n, p.Q_n = (t.data_ptr() for t in (Rp, C, Rd, Pd, Pi_n, Q_n))
+    p.eps_abs, p.eps_rel = float(eps_abs), float(eps_rel)
+    return p
+
+
+def rcr_step(Rp, C, Rd, Pd, Pi_n, Q_n, Q_np1, dt, nts, eps_abs=1e-8, eps_rel=1e-5, stream=None):
+    """One RCR time step of n_out outlets on the GPU (nbp_rcr_step); CUDA
+    float64 tensors in, (P_np1, Pi_np1, m) out (stream-ordered, not synchronised)."""
+    import torch
+    n = Q_np1.numel()
+    P, Pi, m = (torch.empty(n, dtype=torch.float64, device=Q_np1.device) for _ in range(3))
+    p = rcr_params(Rp, C, Rd, Pd, Pi_n, Q_n, eps_abs, eps_rel)
+    s = stream if stream is not None else torch.cuda.current_stream(Q_np1.device)
+    st = load().nbp_rcr_step(n, ctypes.byref(p), _ptr(Q_np1), float(dt), int(nts), _ptr(P), _ptr(Pi), _ptr(m),
+                             ctypes.c_void_p(s.cuda_stream))
+    if st != 0:
+        raise NbpError(st, "nbp_rcr_step failed")
+    return P, Pi, m
 
 
 def _system(sysd, dev, keep):
@@ -405,6 +442,22 @@ class Solver:
         v = np.zeros(max(z, 1))
         self._check(self.lib.nbp_shat_get(self.ctx, rp.ctypes.data, ci.ctypes.data, v.ctypes.data))
         return rp, ci[:z], v[:z]
+
+    def outlet_flows(self, v):
+        """Q^k = a^k . v for the 3N velocity dofs v (CUDA float64)."""
+        Q = self.zeros(self.n_out)
+        self._check(self.lib.nbp_outlet_flows(self.ctx, _ptr(v), _ptr(Q)))
+        return Q
+
+    def rcr_update(self, rcr: dict, v_np1, dt, nts, scale, eps_abs=1e-8, eps_rel=1e-5):
+        """Outlet coupling of one Newton iteration (nbp_rcr_update): rcr holds
+        CUDA float64 tensors Rp, C, Rd, Pd, Pi_n, Q_n; the weights r_k =
+        scale m^k are installed in the context.  Returns dict Q, P, Pi, m."""
+        p = rcr_params(rcr["Rp"], rcr["C"], rcr["Rd"], rcr["Pd"], rcr["Pi_n"], rcr["Q_n"], eps_abs, eps_rel)
+        out = {k: self.zeros(self.n_out) for k in ("Q", "P", "Pi", "m")}
+        self._check(self.lib.nbp_rcr_update(self.ctx, ctypes.byref(p), _ptr(v_np1), float(dt), int(nts), float(scale),
+                                             _ptr(out["Q"]), _ptr(out["P"]), _ptr(out["Pi"]), _ptr(out["m"])))
+        return out
 
     def profile(self, enable=True):
         self._check(self.lib.nbp_profile(self.ctx, int(enable)))

@@ -527,3 +527,12 @@ def test_many_outlet_patches_cover_the_outlet_face():
     for k in range(4):
         nz = np.nonzero(dense[k])[0]
         assert np.array_equal(nz, i4[p4[k]:p4[k + 1]]) and np.array_equal(dense[k][nz], v4[p4[k]:p4[k + 1]])
+
+
+def test_solve_without_explicit_setup_builds_the_hierarchies(tiny):
+    """The oracle's solves need the AMG hierarchies; a solve called before
+    setup() builds them instead of reading unbuilt data."""
+    d, (A, B, C, D, F) = tiny
+    o = oracle.Oracle(d)
+    x, info, rc = o.solve(d["b"])
+    assert rc == 0 and np.linalg.norm(d["b"] - F @ x) <= 1e-8 * np.linalg.norm(d["b"])
