@@ -334,10 +334,14 @@ def main():
     e0.record(stream)
     infos = []
     launches = 0
+    host_wait, host_syncs = 0.0, 0
     for _ in range(a.steps):
         x, info = s.solve(b)
         infos.append(info)
-        launches += s.profile_info()["kernel_launches"]
+        pi = s.profile_info()
+        launches += pi["kernel_launches"]
+        host_wait += pi["host_wait_s"]
+        host_syncs += pi["host_syncs"]
     e1.record(stream)
     torch.cuda.synchronize()
     barrier()
@@ -419,9 +423,11 @@ def main():
         "speedup_vs_fp64": (info64["solve_s"] / (ms / 1e3)) if info64 else None,
         "roofline": roofline,
         "kernel_breakdown_ms_per_solve": {k: [round(v[1] / a.steps, 2), round(v[2] / max(v[1], 1e-9) / 1e6, 1)]
-                                          for k, v in sorted(breakdown.items(), key=lambda kv: -kv[1][1])[:24]},
+                                          for k, v in sorted(breakdown.items(), key=lambda kv: -kv[1][1])[:40]},
         "clocks": ck,
         "gpu_launches": int(prof["kernel_launches"]),
+        "host": {"syncs_per_solve": host_syncs / a.steps, "wait_s_per_solve": host_wait / a.steps,
+                 "note": "host blocked in stream syncs (one small state read per Krylov iteration)"},
         "e2e": e2e,
     }
     if rank == 0 and ws == 1 and not a.no_cpu_baseline:

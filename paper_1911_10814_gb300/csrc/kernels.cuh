@@ -232,17 +232,19 @@ __global__ void __launch_bounds__(256) k_sell(SpmvArgs a) {
     }
 }
 
-// Sliced-ELL product with two threads per block row (alternate slots, then
-// one xor shuffle), for coarse levels whose rows are few and long enough that
-// one thread per row leaves the SM under-occupied.  No rank-one epilogue
-// (coarse levels need none).
-constexpr int kSell2 = 1000;   // DMat::tuned code of this kernel
-template <int BS, typename VT, typename XT, int EPI, int C>
-__global__ void __launch_bounds__(256) k_sell2(SpmvArgs a) {
+// Sliced-ELL product with T threads per block row (T = 2, 4, 8: thread h
+// takes slots h, h + T, ..., then an xor-shuffle tree over the T lanes), for
+// coarse levels whose rows are few, so that one thread per row leaves the
+// SMs with little memory parallelism.  No rank-one epilogue (coarse levels
+// need none).
+constexpr int kSellMT = 1000;   // DMat::tuned code kSellMT + T selects this kernel with T threads per row
+__host__ __device__ inline bool is_sellm(int g) { return g == kSellMT + 2 || g == kSellMT + 4 || g == kSellMT + 8; }
+template <int BS, typename VT, typename XT, int EPI, int C, int T>
+__global__ void __launch_bounds__(256) k_sellm(SpmvArgs a) {
     using AT = XT;
     constexpr int BB = BS * BS;
     const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const int row = (int)(gid >> 1), h = (int)(gid & 1);
+    const int row = (int)(gid / T), h = (int)(gid % T);
     const int sl = row / C, t = row % C;
     const bool live = sl < a.nslice;
     const long long base = live ? a.sl_ptr[sl] : 0;
@@ -252,9 +254,9 @@ __global__ void __launch_bounds__(256) k_sell2(SpmvArgs a) {
     const XT *__restrict__ x = (const XT *)a.x;
     AT acc0 = 0, acc1 = 0, acc2 = 0;
     if constexpr (std::is_same<VT, __nv_bfloat16>::value) {   // paired layout: the two threads take alternate pairs
-        sell_pairs<BS, C>(a, base / 2, w / 2, t, h, 2, x, acc0, acc1, acc2);
+        sell_pairs<BS, C>(a, base / 2, w / 2, t, h, T, x, acc0, acc1, acc2);
     } else {
-        for (int k = h; k < w; k += 2) {
+        for (int k = h; k < w; k += T) {
             const long long g = base + (long long)C * k;
             const int c = __ldg(ci + g + t);
             const VT *v = val + g * BB + t;
@@ -268,10 +270,13 @@ __global__ void __launch_bounds__(256) k_sell2(SpmvArgs a) {
             }
         }
     }
-    acc0 += __shfl_xor_sync(0xffffffffu, acc0, 1);
-    if (BS > 1) {
-        acc1 += __shfl_xor_sync(0xffffffffu, acc1, 1);
-        acc2 += __shfl_xor_sync(0xffffffffu, acc2, 1);
+#pragma unroll
+    for (int o = T / 2; o > 0; o >>= 1) {
+        acc0 += __shfl_xor_sync(0xffffffffu, acc0, o);
+        if (BS > 1) {
+            acc1 += __shfl_xor_sync(0xffffffffu, acc1, o);
+            acc2 += __shfl_xor_sync(0xffffffffu, acc2, o);
+        }
     }
     if (h != 0 || row >= a.nbr) return;
     const AT accs[3] = {acc0, acc1, acc2};

@@ -94,7 +94,7 @@ struct DMat {
     long long *sl2_ptr = nullptr;
     int *sl2_ci = nullptr;
     __nv_bfloat16 *sl_v16 = nullptr;
-    int tuned = -1;                  // autotuned kernel: -1 untuned, 0 sliced ELL, >0 flat with that many lanes per row
+    int tuned = -1;                  // autotuned kernel: -1 untuned, 0 sliced ELL, 1000 + T sliced ELL with T threads per row, other > 0 flat with that many lanes per row
     int bb() const { return br * bc; }
 };
 

@@ -227,7 +227,7 @@ static std::string mat_tag(nbp_ctx *c, const DMat &M, int epi) {
     }
     const int kind = M.tuned >= 0 ? M.tuned : (M.sl_ci ? 0 : -1);
     const std::string k = kind == 0 ? "/sell" + std::to_string(M.sl_c)
-                          : kind == kSell2 ? "/sell" + std::to_string(M.sl_c) + "x2"
+                          : is_sellm(kind) ? "/sell" + std::to_string(M.sl_c) + "x" + std::to_string(kind - kSellMT)
                                            : "/flat" + std::to_string(kind);
     return t + "/" + en[epi] + k;
 }
@@ -611,7 +611,8 @@ template <typename T> static void autotune_cycles(nbp_ctx *c) {
             }
             const int g0 = choose_group(M);
             std::vector<int> cands;
-            if (M.sl_ci) { cands.push_back(0); cands.push_back(kSell2); }
+            if (M.sl_ci)
+                for (int cand : {0, kSellMT + 2, kSellMT + 4, kSellMT + 8}) cands.push_back(cand);
             cands.push_back(g0);
             if (g0 > 4) cands.push_back(g0 / 2);
             if (g0 < 32) cands.push_back(g0 * 2);

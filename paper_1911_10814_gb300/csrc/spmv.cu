@@ -95,25 +95,34 @@ static void launch_sell_epi(const SpmvArgs &a, int epi, bool lr, cudaStream_t s)
     NBP_LAUNCHED();
 }
 
-template <int BS, typename VT, typename XT, int C>
-static void launch_sell2_epi(const SpmvArgs &a, int epi, cudaStream_t s) {
-    const unsigned grid = grid_exact((long long)a.nslice * C * 2);
+template <int BS, typename VT, typename XT, int C, int T>
+static void launch_sellm_epi(const SpmvArgs &a, int epi, cudaStream_t s) {
+    const unsigned grid = grid_exact((long long)a.nslice * C * T);
     switch (epi) {
-    case EPI_SET: k_sell2<BS, VT, XT, EPI_SET, C><<<grid, 256, 0, s>>>(a); break;
-    case EPI_ADD: k_sell2<BS, VT, XT, EPI_ADD, C><<<grid, 256, 0, s>>>(a); break;
-    case EPI_SUB: k_sell2<BS, VT, XT, EPI_SUB, C><<<grid, 256, 0, s>>>(a); break;
-    case EPI_RES: k_sell2<BS, VT, XT, EPI_RES, C><<<grid, 256, 0, s>>>(a); break;
-    case EPI_CHEB: k_sell2<BS, VT, XT, EPI_CHEB, C><<<grid, 256, 0, s>>>(a); break;
+    case EPI_SET: k_sellm<BS, VT, XT, EPI_SET, C, T><<<grid, 256, 0, s>>>(a); break;
+    case EPI_ADD: k_sellm<BS, VT, XT, EPI_ADD, C, T><<<grid, 256, 0, s>>>(a); break;
+    case EPI_SUB: k_sellm<BS, VT, XT, EPI_SUB, C, T><<<grid, 256, 0, s>>>(a); break;
+    case EPI_RES: k_sellm<BS, VT, XT, EPI_RES, C, T><<<grid, 256, 0, s>>>(a); break;
+    case EPI_CHEB: k_sellm<BS, VT, XT, EPI_CHEB, C, T><<<grid, 256, 0, s>>>(a); break;
     default: throw Error{NBP_ERR_INVALID, "spmv: unknown epilogue"};
     }
     NBP_LAUNCHED();
 }
 
+template <int BS, typename VT, typename XT, int C>
+static void launch_sellm_t(const SpmvArgs &a, int epi, cudaStream_t s, int T) {
+    if (T == 8) launch_sellm_epi<BS, VT, XT, C, 8>(a, epi, s);
+    else if (T == 4) launch_sellm_epi<BS, VT, XT, C, 4>(a, epi, s);
+    else launch_sellm_epi<BS, VT, XT, C, 2>(a, epi, s);
+}
+
+// T threads per row (T = 1: the one-thread kernel, which also has the
+// rank-one epilogue)
 template <int BS, typename VT, typename XT>
-static void launch_sell_c(const DMat &M, const SpmvArgs &a, int epi, bool lr, cudaStream_t s, bool two) {
-    if (two && !lr) {
-        if (M.sl_c == 8) launch_sell2_epi<BS, VT, XT, 8>(a, epi, s);
-        else launch_sell2_epi<BS, VT, XT, 32>(a, epi, s);
+static void launch_sell_c(const DMat &M, const SpmvArgs &a, int epi, bool lr, cudaStream_t s, int T) {
+    if (T > 1 && !lr) {
+        if (M.sl_c == 8) launch_sellm_t<BS, VT, XT, 8>(a, epi, s, T);
+        else launch_sellm_t<BS, VT, XT, 32>(a, epi, s, T);
         return;
     }
     if (M.sl_c == 8) launch_sell_epi<BS, VT, XT, 8>(a, epi, lr, s);
@@ -121,23 +130,23 @@ static void launch_sell_c(const DMat &M, const SpmvArgs &a, int epi, bool lr, cu
 }
 
 template <int BS, typename XT>
-static void launch_sell(const DMat &M, int vsel, SpmvArgs a, int epi, bool lr, cudaStream_t s, bool two) {
+static void launch_sell(const DMat &M, int vsel, SpmvArgs a, int epi, bool lr, cudaStream_t s, int T) {
     a.nslice = M.nslice;
     a.sl_ptr = M.sl_ptr;
     a.sl_ci = M.sl_ci;
     if constexpr (sizeof(XT) == 8) {
         a.val = M.sl_v;
-        launch_sell_c<BS, double, double>(M, a, epi, lr, s, two);
+        launch_sell_c<BS, double, double>(M, a, epi, lr, s, T);
     } else if (vsel == 2) {
         require(M.sl_v16 != nullptr, NBP_ERR_STATE, "spmv: BF16 sliced values not built");
         a.sl_ptr = M.sl2_ptr;   // paired layout
         a.sl_ci = M.sl2_ci;
         a.val = M.sl_v16;
-        launch_sell_c<BS, __nv_bfloat16, float>(M, a, epi, lr, s, two);
+        launch_sell_c<BS, __nv_bfloat16, float>(M, a, epi, lr, s, T);
     } else {
         require(M.sl_v32 != nullptr, NBP_ERR_STATE, "spmv: FP32 sliced values not built");
         a.val = M.sl_v32;
-        launch_sell_c<BS, float, float>(M, a, epi, lr, s, two);
+        launch_sell_c<BS, float, float>(M, a, epi, lr, s, T);
     }
 }
 
@@ -149,10 +158,11 @@ void spmv(const DMat &M, int vsel, SpmvArgs a, int epi, bool lr, cudaStream_t s,
     if (a.nbr == 0) return;
     const bool sell_ok = M.sl_ci && M.br == M.bc && (sizeof(XT) == 8 ? M.sl_v != nullptr : true);
     if (G < 0) G = (M.tuned >= 0) ? M.tuned : (sell_ok ? 0 : choose_group(M));
-    if ((G == 0 || G == kSell2) && !sell_ok) G = choose_group(M);
-    if (sell_ok && (G == 0 || G == kSell2)) {
-        if (M.br == 3) launch_sell<3, XT>(M, vsel, a, epi, lr, s, G == kSell2);
-        else launch_sell<1, XT>(M, vsel, a, epi, lr, s, G == kSell2);
+    if ((G == 0 || is_sellm(G)) && !sell_ok) G = choose_group(M);
+    if (sell_ok && (G == 0 || is_sellm(G))) {
+        const int T = G == 0 ? 1 : G - kSellMT;
+        if (M.br == 3) launch_sell<3, XT>(M, vsel, a, epi, lr, s, T);
+        else launch_sell<1, XT>(M, vsel, a, epi, lr, s, T);
         return;
     }
     if (M.br == 3 && M.bc == 3) launch_vt<3, 3, XT>(M, vsel, a, G, epi, lr, s);

@@ -7,7 +7,8 @@ namespace nbp {
 // Launch y = epilogue(M x) on stream s.  vsel selects the value copy
 // (0 FP64, 1 FP32, 2 BF16); XT is the vector type (double needs vsel 0).
 // G: -1 = the autotuned choice (else sliced ELL when built); 0 = sliced ELL;
-// > 0 = flat kernel with G lanes per block row.
+// kSellMT + T = sliced ELL with T threads per row (T = 2, 4, 8); other > 0 =
+// flat kernel with G lanes per block row.
 template <typename XT>
 void spmv(const DMat &M, int vsel, SpmvArgs a, int epi, bool lr, cudaStream_t s, int G = -1);
 
