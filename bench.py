@@ -409,7 +409,7 @@ def main():
         "dtype": "bf16" if a.precision == 2 else "f32", "data": "synthetic",
         "config": {"workload": spec.name, "unknowns": n, "tets": 6 * spec.nx * spec.ny * spec.nz,
                    "outlets": spec.n_out, "tolerance": 1e-8, "inner_precision": a.precision,
-                   "values": {0: "f64", 1: "f32", 2: "bf16", 3: "f32 operators, bf16 AMG hierarchies"}[a.precision],
+                   "values": {0: "f64", 1: "f32", 2: "bf16", 3: "f32 operators, bf16 AMG hierarchies"}.get(a.precision, str(a.precision)),
                    "P_A": "AMG" if a.pc_A == 0 else "Jacobi", "amg_cycle": a.amg_cycle, "amg_kdepth": a.amg_kdepth,
                    "cheb_degree": a.cheb_degree, "cheb_degree_S": a.cheb_degree_S,
                    "parallelism": f"replicas{ws}", "l2": "inputs larger than L2 (no flush)"},
