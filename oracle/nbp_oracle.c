@@ -44,8 +44,13 @@
  *                 left out of every aggregate (zero row of P);
  *       coarsest  dense LU with partial pivoting.
  *   - Chebyshev smoothing of degree k on D_b^{-1} A (D_b = block diagonal),
- *     interval [rho/10, rho] with rho the Gershgorin bound of D_b^{-1} A
- *     (largest absolute row sum) (Saad, Iterative Methods, Alg. 12.1).
+ *     interval [rho/10, rho] (Saad, Iterative Methods, Alg. 12.1), rho the
+ *     smaller of the Gershgorin bound of D_b^{-1} A (largest absolute row
+ *     sum) and 1.1 x the spectral radius of the Hessenberg matrix of 20
+ *     Arnoldi steps on D_b^{-1} A from the vector of ones (the largest Ritz
+ *     value magnitude, an estimate of the largest eigenvalue magnitude from
+ *     below; the factor 1.1 keeps rho above it).  The Hessenberg spectral
+ *     radius is lim ||H^m||^(1/m) (Gelfand), taken by repeated squaring.
  *   - RCR (three-element Windkessel) outlets, Sec. 2.1 / 2.4: one time step
  *     of dPi/dt = -Pi/(R_d C) + Q/C, P = R_p Q + Pi + P_d by the
  *     fourth-order Runge-Kutta scheme of Algorithm 1 (n_ts substeps, Q
@@ -585,6 +590,82 @@ static double gershgorin_rho(const bmat *M, const double *dinv) {
     return rho;
 }
 
+/* Spectral radius of the k x k matrix H (row-major) by Gelfand's formula
+ * rho = lim ||H^m||_F^(1/m), with m = 2^40 reached by squaring; each square
+ * is renormalised and the scale carried as a logarithm. */
+static double spectral_radius_gelfand(int k, const double *H) {
+    double *M = dvec((size_t)k * k), *T = dvec((size_t)k * k);
+    double s = 0.0;
+    for (int i = 0; i < k * k; ++i) s += H[i] * H[i];
+    s = sqrt(s);
+    if (s == 0.0) { free(M); free(T); return 0.0; }
+    for (int i = 0; i < k * k; ++i) M[i] = H[i] / s;
+    double logscale = log(s);   /* H^(2^q) = exp(logscale) M */
+    const int Q = 40;
+    for (int q = 0; q < Q; ++q) {
+        for (int i = 0; i < k; ++i)
+            for (int j = 0; j < k; ++j) {
+                double t = 0.0;
+                for (int l = 0; l < k; ++l) t += M[i * k + l] * M[l * k + j];
+                T[i * k + j] = t;
+            }
+        double n2 = 0.0;
+        for (int i = 0; i < k * k; ++i) n2 += T[i] * T[i];
+        const double n = sqrt(n2);
+        if (n == 0.0) { free(M); free(T); return 0.0; }   /* nilpotent */
+        for (int i = 0; i < k * k; ++i) M[i] = T[i] / n;
+        logscale = 2.0 * logscale + log(n);
+    }
+    free(M); free(T);
+    return exp(logscale / ldexp(1.0, Q));
+}
+
+/* 20 Arnoldi steps (classical Gram-Schmidt, two passes) on D_b^{-1} A from
+ * the normalised vector of ones; returns the spectral radius of the square
+ * Hessenberg matrix (stops early on an invariant subspace). */
+#define RHO_ARNOLDI_STEPS 20
+static double arnoldi_rho(const bmat *M, const double *dinv) {
+    const int bs = M->br, nb = bs * bs, n = M->nbr * bs, K = RHO_ARNOLDI_STEPS;
+    double *V = dvec((size_t)n * (K + 1)), *w = dvec(n), *t = dvec(n);
+    double Hk[RHO_ARNOLDI_STEPS * RHO_ARNOLDI_STEPS];
+    memset(Hk, 0, sizeof(Hk));
+    for (int i = 0; i < n; ++i) V[i] = 1.0 / sqrt((double)n);
+    int k = K;
+    for (int j = 0; j < K; ++j) {
+        spmv(M, V + (size_t)j * n, t);
+        for (int r = 0; r < M->nbr; ++r)          /* w = D_b^{-1} (A v_j) */
+            for (int a = 0; a < bs; ++a) {
+                double u = 0.0;
+                for (int c = 0; c < bs; ++c) u += dinv[(size_t)r * nb + a * bs + c] * t[(size_t)r * bs + c];
+                w[(size_t)r * bs + a] = u;
+            }
+        for (int pass = 0; pass < 2; ++pass) {
+            double h[RHO_ARNOLDI_STEPS + 1];
+            for (int i = 0; i <= j; ++i) {
+                double u = 0.0;
+                for (int e = 0; e < n; ++e) u += V[(size_t)i * n + e] * w[e];
+                h[i] = u;
+            }
+            for (int i = 0; i <= j; ++i) {
+                for (int e = 0; e < n; ++e) w[e] -= h[i] * V[(size_t)i * n + e];
+                Hk[i * K + j] += h[i];
+            }
+        }
+        double nrm = 0.0;
+        for (int e = 0; e < n; ++e) nrm += w[e] * w[e];
+        nrm = sqrt(nrm);
+        if (j + 1 < K) Hk[(j + 1) * K + j] = nrm;
+        if (nrm == 0.0) { k = j + 1; break; }
+        for (int e = 0; e < n; ++e) V[(size_t)(j + 1) * n + e] = w[e] / nrm;
+    }
+    double Hs[RHO_ARNOLDI_STEPS * RHO_ARNOLDI_STEPS];
+    for (int i = 0; i < k; ++i)
+        for (int j = 0; j < k; ++j) Hs[i * k + j] = Hk[i * K + j];
+    const double r = spectral_radius_gelfand(k, Hs);
+    free(V); free(w); free(t);
+    return r;
+}
+
 static void amg_build(amg *H, const bmat *fine, const or_options *o, int kcycle, int degree) {
     memset(H, 0, sizeof(*H));
     H->bs = fine->br;
@@ -611,7 +692,9 @@ static void amg_build(amg *H, const bmat *fine, const or_options *o, int kcycle,
         if (k + 1 < H->nlev) {
             H->dinv[k] = dvec((size_t)n * bs * bs);
             block_diag_inv(&H->L[k], H->dinv[k]);
-            H->rho[k] = gershgorin_rho(&H->L[k], H->dinv[k]);
+            const double g = gershgorin_rho(&H->L[k], H->dinv[k]);
+            const double a = 1.1 * arnoldi_rho(&H->L[k], H->dinv[k]);
+            H->rho[k] = a < g ? a : g;
         }
     }
     /* coarsest: dense LU */

@@ -237,6 +237,52 @@ def _cheb_closed_form(Ad, Dinv, rho, k, b):
     return (np.eye(n) - Q) @ np.linalg.solve(Ad, b)
 
 
+def _cheb_rho(DA, steps=20):
+    """min(Gershgorin bound, 1.1 x largest |Ritz value| of `steps` Arnoldi
+    steps (CGS2) from the vector of ones), the eigenvalues of the Hessenberg
+    matrix taken by LAPACK."""
+    n = DA.shape[0]
+    V = np.zeros((n, steps + 1))
+    H = np.zeros((steps + 1, steps))
+    V[:, 0] = 1.0 / np.sqrt(n)
+    k = steps
+    for j in range(steps):
+        w = DA @ V[:, j]
+        for _ in range(2):
+            h = V[:, :j + 1].T @ w
+            w = w - V[:, :j + 1] @ h
+            H[:j + 1, j] += h
+        H[j + 1, j] = np.linalg.norm(w)
+        if H[j + 1, j] == 0.0:
+            k = j + 1
+            break
+        V[:, j + 1] = w / H[j + 1, j]
+    ritz = np.abs(np.linalg.eigvals(H[:k, :k])).max()
+    return min(np.abs(DA).sum(axis=1).max(), 1.1 * ritz)
+
+
+def test_chebyshev_bound_covers_the_spectrum(tiny):
+    """The Chebyshev interval's upper end lies above every eigenvalue
+    magnitude of D_b^{-1} A (dense eigenvalues), on both hierarchies and
+    every smoothed level, and below the Gershgorin bound."""
+    d, _ = tiny
+    o = oracle.Oracle(d)
+    o.setup()
+    for which, bs in ((0, 3), (1, 1)):
+        L = o.amg_levels(which)
+        for lev in L[:-1]:
+            n = len(lev["rowptr"]) - 1
+            Ad = oracle.dense_block(lev["rowptr"], lev["col"], lev["val"], bs, bs, n, n)
+            Db = np.zeros_like(Ad)
+            for i in range(n):
+                Db[bs * i:bs * i + bs, bs * i:bs * i + bs] = Ad[bs * i:bs * i + bs, bs * i:bs * i + bs]
+            DA = np.linalg.inv(Db) @ Ad
+            lam = np.abs(np.linalg.eigvals(DA)).max()
+            assert lev["rho"] >= lam
+            assert lev["rho"] <= np.abs(DA).sum(axis=1).max() * (1 + 1e-14)
+            assert np.isclose(lev["rho"], _cheb_rho(DA), rtol=1e-9)
+
+
 @pytest.mark.parametrize("k", [1, 2, 3])
 def test_chebyshev_matches_closed_form(tiny, k):
     """Chebyshev smoother (Saad, Alg. 12.1) vs its residual polynomial."""
@@ -250,8 +296,7 @@ def test_chebyshev_matches_closed_form(tiny, k):
     for i in range(n):
         Db[3 * i:3 * i + 3, 3 * i:3 * i + 3] = Ad[3 * i:3 * i + 3, 3 * i:3 * i + 3]
     Dinv = np.linalg.inv(Db)
-    rho = np.abs(Dinv @ Ad).sum(axis=1).max()          # Gershgorin bound of D^{-1}A
-    assert np.isclose(rho, L[0]["rho"], rtol=1e-13)
+    assert np.isclose(_cheb_rho(Dinv @ Ad), L[0]["rho"], rtol=1e-9)
     b = np.random.default_rng(4).standard_normal(3 * n)
     x = oracle.chebyshev(L[0]["rowptr"], L[0]["col"], L[0]["val"], 3, L[0]["rho"], k, b)
     assert _rel(x, _cheb_closed_form(Ad, Dinv, L[0]["rho"], k, b)) <= 1e-10
