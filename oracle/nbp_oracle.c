@@ -45,12 +45,13 @@
  *       coarsest  dense LU with partial pivoting.
  *   - Chebyshev smoothing of degree k on D_b^{-1} A (D_b = block diagonal),
  *     interval [rho/10, rho] (Saad, Iterative Methods, Alg. 12.1), rho the
- *     smaller of the Gershgorin bound of D_b^{-1} A (largest absolute row
- *     sum) and 1.1 x the spectral radius of the Hessenberg matrix of 20
- *     Arnoldi steps on D_b^{-1} A from the vector of ones (the largest Ritz
- *     value magnitude, an estimate of the largest eigenvalue magnitude from
- *     below; the factor 1.1 keeps rho above it).  The Hessenberg spectral
- *     radius is lim ||H^m||^(1/m) (Gelfand), taken by repeated squaring.
+ *     Gershgorin bound of D_b^{-1} A (largest absolute row sum); on the
+ *     levels of AMG(A) the smaller of that bound and 1.1 x the spectral
+ *     radius of the Hessenberg matrix of 20 Arnoldi steps on D_b^{-1} A from
+ *     the vector of ones (the largest Ritz value magnitude, an estimate of
+ *     the largest eigenvalue magnitude from below; the factor 1.1 keeps rho
+ *     above it).  The Hessenberg spectral radius is lim ||H^m||^(1/m)
+ *     (Gelfand), taken by repeated squaring.
  *   - RCR (three-element Windkessel) outlets, Sec. 2.1 / 2.4: one time step
  *     of dPi/dt = -Pi/(R_d C) + Q/C, P = R_p Q + Pi + P_d by the
  *     fourth-order Runge-Kutta scheme of Algorithm 1 (n_ts substeps, Q
@@ -666,7 +667,9 @@ static double arnoldi_rho(const bmat *M, const double *dinv) {
     return r;
 }
 
-static void amg_build(amg *H, const bmat *fine, const or_options *o, int kcycle, int degree) {
+/* tight_rho: Chebyshev bound from the Arnoldi estimate (AMG(A)); else the
+ * Gershgorin bound (AMG(S_hat)) */
+static void amg_build(amg *H, const bmat *fine, const or_options *o, int kcycle, int degree, int tight_rho) {
     memset(H, 0, sizeof(*H));
     H->bs = fine->br;
     H->cheb_degree = degree;
@@ -693,7 +696,7 @@ static void amg_build(amg *H, const bmat *fine, const or_options *o, int kcycle,
             H->dinv[k] = dvec((size_t)n * bs * bs);
             block_diag_inv(&H->L[k], H->dinv[k]);
             const double g = gershgorin_rho(&H->L[k], H->dinv[k]);
-            const double a = 1.1 * arnoldi_rho(&H->L[k], H->dinv[k]);
+            const double a = tight_rho ? 1.1 * arnoldi_rho(&H->L[k], H->dinv[k]) : g;
             H->rho[k] = a < g ? a : g;
         }
     }
@@ -1040,10 +1043,10 @@ void or_set_resistances(or_ctx *c, const double *r) {
 int or_setup(or_ctx *c) {
     if (c->have_amgA) amg_free(&c->amgA);
     if (c->have_amgS) amg_free(&c->amgS);
-    amg_build(&c->amgA, &c->A, &c->opt, c->opt.amg_cycle == 2, c->opt.cheb_degree);
+    amg_build(&c->amgA, &c->A, &c->opt, c->opt.amg_cycle == 2, c->opt.cheb_degree, 1);
     c->have_amgA = 1;
     build_shat(c);
-    amg_build(&c->amgS, &c->Shat, &c->opt, c->opt.amg_cycle >= 1, c->opt.cheb_degree_S);
+    amg_build(&c->amgS, &c->Shat, &c->opt, c->opt.amg_cycle >= 1, c->opt.cheb_degree_S, 0);
     c->have_amgS = 1;
     return 0;
 }

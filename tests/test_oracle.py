@@ -263,8 +263,9 @@ def _cheb_rho(DA, steps=20):
 
 def test_chebyshev_bound_covers_the_spectrum(tiny):
     """The Chebyshev interval's upper end lies above every eigenvalue
-    magnitude of D_b^{-1} A (dense eigenvalues), on both hierarchies and
-    every smoothed level, and below the Gershgorin bound."""
+    magnitude of D_b^{-1} A (dense eigenvalues) on every smoothed level:
+    the Arnoldi estimate (x 1.1, capped by Gershgorin) on AMG(A), the
+    Gershgorin bound on AMG(S_hat)."""
     d, _ = tiny
     o = oracle.Oracle(d)
     o.setup()
@@ -279,8 +280,9 @@ def test_chebyshev_bound_covers_the_spectrum(tiny):
             DA = np.linalg.inv(Db) @ Ad
             lam = np.abs(np.linalg.eigvals(DA)).max()
             assert lev["rho"] >= lam
-            assert lev["rho"] <= np.abs(DA).sum(axis=1).max() * (1 + 1e-14)
-            assert np.isclose(lev["rho"], _cheb_rho(DA), rtol=1e-9)
+            gers = np.abs(DA).sum(axis=1).max()
+            assert lev["rho"] <= gers * (1 + 1e-14)
+            assert np.isclose(lev["rho"], _cheb_rho(DA) if which == 0 else gers, rtol=1e-9)
 
 
 @pytest.mark.parametrize("k", [1, 2, 3])
