@@ -988,6 +988,95 @@ static void free_lowrank(LowRank &lr, cudaStream_t s) {
     lr = LowRank();
 }
 
+// ------------------------------------------------ Chebyshev interval bound
+// Spectral radius of the k x k matrix H (row-major) as lim ||H^m||_F^(1/m)
+// (Gelfand), m = 2^40 reached by renormalised squaring, the scale carried as
+// a logarithm.
+static double gelfand_radius(int k, const std::vector<double> &H) {
+    std::vector<double> M(H), T((size_t)k * k);
+    double f = 0.0;
+    for (double v : M) f += v * v;
+    f = std::sqrt(f);
+    if (f == 0.0) return 0.0;
+    for (double &v : M) v /= f;
+    double lg = std::log(f);
+    const int Q = 40;
+    for (int q = 0; q < Q; ++q) {
+        for (int i = 0; i < k; ++i)
+            for (int j = 0; j < k; ++j) {
+                double t = 0.0;
+                for (int l = 0; l < k; ++l) t += M[(size_t)i * k + l] * M[(size_t)l * k + j];
+                T[(size_t)i * k + j] = t;
+            }
+        double n2 = 0.0;
+        for (double v : T) n2 += v * v;
+        const double nn = std::sqrt(n2);
+        if (nn == 0.0) return 0.0;
+        for (size_t i = 0; i < T.size(); ++i) M[i] = T[i] / nn;
+        lg = 2.0 * lg + std::log(nn);
+    }
+    return std::exp(lg / std::ldexp(1.0, Q));
+}
+
+// Upper end of level l's Chebyshev interval: min(Gershgorin bound (from
+// setup), 1.1 x the spectral radius of the Hessenberg matrix of 20 Arnoldi
+// steps (CGS2, FP64) on D_b^{-1} A from the normalised vector of ones).  The
+// Gershgorin bound overestimates |lambda_max| 1.6-2x on these tangents, which
+// weakens every smoothing step; the Ritz value approaches |lambda_max| from
+// below and the factor 1.1 keeps the bound above it.  Used on AMG(A) only:
+// on AMG(S_hat), smoothed with degree 1 (damped Jacobi with weight 1/theta),
+// the tighter bound over-relaxes the top of the nonsymmetric spectrum and
+// costs S-iterations (measured), so that hierarchy keeps Gershgorin.
+constexpr int kRhoSteps = 20;
+static void refine_rho(nbp_ctx *c, Hier &H, int l) {
+    Level &L = H.L[l];
+    if (!L.dinv) return;
+    const long long n = (long long)L.M.nbr * H.bs;
+    cudaStream_t s = c->s;
+    Krylov<double> K;
+    K.ensure(n, kRhoSteps, s);
+    fill<double>(K.V, 1.0 / std::sqrt((double)n), n, s);
+    std::vector<double> Hk((size_t)kRhoSteps * kRhoSteps, 0.0), h1(kRhoSteps + 1), h2(kRhoSteps + 1);
+    int k = kRhoSteps;
+    for (int j = 0; j < kRhoSteps; ++j) {
+        do_spmv<double>(c, L.M, 0, sargs(K.V + (size_t)j * K.ld, K.w), EPI_SET, false);   // w = A v_j
+        c->prof.launches++;
+        k_cheb_first<double><<<grid_exact(n), 256, 0, s>>>(L.M.nbr, H.bs, L.dinv, K.w, 1.0, K.r, K.r, nullptr);
+        NBP_LAUNCHED();                                                                   // r = D_b^{-1} w
+        mdot<double>(c, K, K.V, K.ld, j + 1, K.r, K.h1);
+        maxpy<double>(c, n, K.V, K.ld, j + 1, K.h1, -1.0, K.r);
+        mdot<double>(c, K, K.V, K.ld, j + 1, K.r, K.h2);
+        maxpy<double>(c, n, K.V, K.ld, j + 1, K.h2, -1.0, K.r);
+        mdot<double>(c, K, K.r, K.ld, 1, K.r, K.nrm);
+        double nrm2 = 0.0;
+        NBP_CUDA(cudaMemcpyAsync(h1.data(), K.h1, sizeof(double) * (j + 1), cudaMemcpyDeviceToHost, s));
+        NBP_CUDA(cudaMemcpyAsync(h2.data(), K.h2, sizeof(double) * (j + 1), cudaMemcpyDeviceToHost, s));
+        NBP_CUDA(cudaMemcpyAsync(&nrm2, K.nrm, sizeof(double), cudaMemcpyDeviceToHost, s));
+        NBP_CUDA(cudaStreamSynchronize(s));
+        for (int i = 0; i <= j; ++i) Hk[(size_t)i * kRhoSteps + j] = h1[i] + h2[i];
+        const double nrm = std::sqrt(std::max(nrm2, 0.0));
+        if (j + 1 < kRhoSteps) Hk[(size_t)(j + 1) * kRhoSteps + j] = nrm;
+        if (!(nrm > 0.0)) { k = j + 1; break; }
+        if (j + 1 < kRhoSteps) {
+            NBP_CUDA(cudaMemcpyAsync(K.beta, &nrm, sizeof(double), cudaMemcpyHostToDevice, s));
+            scale_inv<double>(c, K.V + (size_t)(j + 1) * K.ld, K.r, K.beta, n);
+            NBP_LAUNCHED();
+        }
+    }
+    std::vector<double> Hs((size_t)k * k);
+    for (int i = 0; i < k; ++i)
+        for (int j = 0; j < k; ++j) Hs[(size_t)i * k + j] = Hk[(size_t)i * kRhoSteps + j];
+    const double est = 1.1 * gelfand_radius(k, Hs);
+    NBP_CUDA(cudaStreamSynchronize(s));
+    K.release(s);
+    if (std::isfinite(est) && est < L.rho) L.rho = est;
+}
+
+static void refine_rhos(nbp_ctx *c, Hier &H) {
+    for (int l = 0; l < H.nlev; ++l)
+        if (l < H.nlev - 1 || !H.cinv) refine_rho(c, H, l);
+}
+
 static void do_setup(nbp_ctx *c) {
     auto t0 = std::chrono::steady_clock::now();
     cudaStream_t s = c->s;
@@ -995,8 +1084,9 @@ static void do_setup(nbp_ctx *c) {
     const int prec = build_level(c->opt.precision);
     if (!c->diagA) c->diagA = dmalloc<double>(3LL * c->N, s);
     amg_build(c->HA, c->A, c->opt, prec, s);
+    refine_rhos(c, c->HA);
     build_shat(c->A, c->B, c->C, c->D, c->lr, c->N, c->Shat, c->diagA, s);
-    amg_build(c->HS, c->Shat, c->opt, prec, s);
+    amg_build(c->HS, c->Shat, c->opt, prec, s);   // AMG(S_hat) keeps the Gershgorin bound (see refine_rho)
     c->HA.kcycle = c->opt.amg_cycle == 2;
     c->HS.kcycle = c->opt.amg_cycle >= 1;
     c->HA.kdepth = c->HS.kdepth = c->opt.amg_kdepth;

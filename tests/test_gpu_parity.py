@@ -90,9 +90,9 @@ def test_amg_hierarchy_bit_exact(case):
             assert np.array_equal(lg["rowptr"], lo["rowptr"])
             assert np.array_equal(lg["col"], lo["col"])
             assert np.array_equal(lg["val"], lo["val"])
-            if lo["agg"] is not None:   # smoothed levels: Gershgorin bounds to rounding
+            if lo["agg"] is not None:   # smoothed levels: Chebyshev bounds (Arnoldi in FP64) to rounding
                 assert np.array_equal(lg["agg"], lo["agg"])
-                assert lg["rho"] == pytest.approx(lo["rho"], rel=1e-12)
+                assert lg["rho"] == pytest.approx(lo["rho"], rel=1e-9)
 
 
 def test_shat_bit_exact(case):
