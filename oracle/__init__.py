@@ -89,8 +89,8 @@ def _load():
             ("or_amg_level_get", [vp, ctypes.c_int, ctypes.c_int, _ip, _ip, _dp, _ip]),
             ("or_shat_get", [vp, _ip, _ip, _dp]), ("or_diag_A", [vp, _dp]),
             ("or_get_info", [vp, ctypes.POINTER(Info)]), ("or_destroy", [vp]),
-            ("or_chebyshev", [ctypes.c_int, ctypes.c_int, _ip, _ip, _dp, ctypes.c_double, ctypes.c_int, _dp, _dp,
-                              ctypes.c_int]),
+            ("or_chebyshev", [ctypes.c_int, ctypes.c_int, _ip, _ip, _dp, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                              _dp, _dp, ctypes.c_int]),
             ("or_rcr_step", [ctypes.c_int] + [_dp] * 7 + [ctypes.c_double, ctypes.c_int, ctypes.c_double,
                                                           ctypes.c_double, _dp, _dp, _dp]),
         ]:
@@ -314,13 +314,14 @@ def aggregate(rowptr, col, val, bs, theta):
     return nc, agg
 
 
-def chebyshev(rowptr, col, val, bs, rho, k, b, x0=None):
+def chebyshev(rowptr, col, val, bs, rho, k, b, x0=None, lodiv=10.0):
+    """k Chebyshev steps on D_b^{-1} A over [rho / lodiv, rho]."""
     lib = _load()
     rp, ci, v = _i(rowptr), _i(col), _d(val).reshape(-1)
     n = len(rp) - 1
     b = _d(b)
     x = np.zeros(n * bs) if x0 is None else _d(x0).copy()
-    lib.or_chebyshev(n, bs, _pi(rp), _pi(ci), _pd(v), rho, k, _pd(b), _pd(x), int(x0 is None))
+    lib.or_chebyshev(n, bs, _pi(rp), _pi(ci), _pd(v), rho, float(lodiv), k, _pd(b), _pd(x), int(x0 is None))
     return x
 
 

@@ -44,7 +44,8 @@
  *                 left out of every aggregate (zero row of P);
  *       coarsest  dense LU with partial pivoting.
  *   - Chebyshev smoothing of degree k on D_b^{-1} A (D_b = block diagonal),
- *     interval [rho/10, rho] (Saad, Iterative Methods, Alg. 12.1), rho the
+ *     interval [rho/10, rho] on AMG(A) and [rho/3, rho] on AMG(S_hat)
+ *     (Saad, Iterative Methods, Alg. 12.1), rho the
  *     Gershgorin bound of D_b^{-1} A (largest absolute row sum); on the
  *     levels of AMG(A) the smaller of that bound and 1.1 x the spectral
  *     radius of the Hessenberg matrix of 20 Arnoldi steps on D_b^{-1} A from
@@ -113,6 +114,7 @@ typedef struct {
     double *bl[OR_MAXLEV], *xl[OR_MAXLEV], *rl[OR_MAXLEV], *dl[OR_MAXLEV];
     double *kr[OR_MAXLEV], *kz1[OR_MAXLEV], *kw1[OR_MAXLEV], *kz2[OR_MAXLEV], *kw2[OR_MAXLEV]; /* K-cycle */
     int cheb_degree, cycle, kdepth;
+    double cheb_lo;         /* Chebyshev interval [rho / cheb_lo, rho] */
 } amg;
 
 typedef struct {
@@ -669,8 +671,10 @@ static double arnoldi_rho(const bmat *M, const double *dinv) {
 
 /* tight_rho: Chebyshev bound from the Arnoldi estimate (AMG(A)); else the
  * Gershgorin bound (AMG(S_hat)) */
-static void amg_build(amg *H, const bmat *fine, const or_options *o, int kcycle, int degree, int tight_rho) {
+static void amg_build(amg *H, const bmat *fine, const or_options *o, int kcycle, int degree, int tight_rho,
+                      double lodiv) {
     memset(H, 0, sizeof(*H));
+    H->cheb_lo = lodiv;
     H->bs = fine->br;
     H->cheb_degree = degree;
     H->cycle = kcycle;
@@ -726,10 +730,10 @@ static void amg_free(amg *H) {
 
 /* Chebyshev smoothing, degree k, on D^{-1} A x = D^{-1} b, interval
  * [rho/10, 1.1 rho]; x updated in place (Saad, Alg. 12.1). */
-static void chebyshev(const bmat *M, const double *dinv, double rho, int k, const double *b, double *x,
+static void chebyshev(const bmat *M, const double *dinv, double rho, double lodiv, int k, const double *b, double *x,
                       double *r, double *d, int x_is_zero) {
     int n = M->nbr * M->br;
-    double lmax = rho, lmin = rho / 10.0;
+    double lmax = rho, lmin = rho / lodiv;
     double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin);
     double sigma = theta / delta, rho_old = 1.0 / sigma;
     double *t = dvec(n);
@@ -788,7 +792,7 @@ static void vcycle(amg *H, int l) {
     double *b = H->bl[l], *x = H->xl[l], *r = H->rl[l], *d = H->dl[l];
     if (l == H->nlev - 1) { dense_lu_solve(H->nc, H->lu, H->piv, b, x); return; }
     for (int i = 0; i < n; ++i) x[i] = 0.0;
-    chebyshev(M, H->dinv[l], H->rho[l], H->cheb_degree, b, x, r, d, 1);
+    chebyshev(M, H->dinv[l], H->rho[l], H->cheb_lo, H->cheb_degree, b, x, r, d, 1);
     double *t = dvec(n);
     spmv(M, x, t);
     for (int i = 0; i < n; ++i) r[i] = b[i] - t[i];
@@ -804,7 +808,7 @@ static void vcycle(amg *H, int l) {
     for (int i = 0; i < M->nbr; ++i)              /* prolongation x += P e_c */
         if (H->agg[l][i] >= 0)
             for (int a = 0; a < bs; ++a) x[(size_t)i * bs + a] += xc[(size_t)H->agg[l][i] * bs + a];
-    chebyshev(M, H->dinv[l], H->rho[l], H->cheb_degree, b, x, r, d, 0);
+    chebyshev(M, H->dinv[l], H->rho[l], H->cheb_lo, H->cheb_degree, b, x, r, d, 0);
     free(t);
 }
 
@@ -1043,10 +1047,10 @@ void or_set_resistances(or_ctx *c, const double *r) {
 int or_setup(or_ctx *c) {
     if (c->have_amgA) amg_free(&c->amgA);
     if (c->have_amgS) amg_free(&c->amgS);
-    amg_build(&c->amgA, &c->A, &c->opt, c->opt.amg_cycle == 2, c->opt.cheb_degree, 1);
+    amg_build(&c->amgA, &c->A, &c->opt, c->opt.amg_cycle == 2, c->opt.cheb_degree, 1, 10.0);
     c->have_amgA = 1;
     build_shat(c);
-    amg_build(&c->amgS, &c->Shat, &c->opt, c->opt.amg_cycle >= 1, c->opt.cheb_degree_S, 0);
+    amg_build(&c->amgS, &c->Shat, &c->opt, c->opt.amg_cycle >= 1, c->opt.cheb_degree_S, 0, 3.0);
     c->have_amgS = 1;
     return 0;
 }
@@ -1082,13 +1086,13 @@ int or_strength_and_aggregate(int nbr, int bs, const int *rp, const int *ci, con
 }
 
 /* Chebyshev smoother, exposed for pin tests: x <- smoothed x (x in/out) */
-void or_chebyshev(int nbr, int bs, const int *rp, const int *ci, const double *v, double rho, int k, const double *b,
-                  double *x, int x_is_zero) {
+void or_chebyshev(int nbr, int bs, const int *rp, const int *ci, const double *v, double rho, double lodiv, int k,
+                  const double *b, double *x, int x_is_zero) {
     bmat M = {nbr, nbr, bs, bs, (int *)rp, (int *)ci, (double *)v};
     int n = nbr * bs;
     double *dinv = dvec((size_t)nbr * bs * bs), *r = dvec(n), *d = dvec(n);
     block_diag_inv(&M, dinv);
-    chebyshev(&M, dinv, rho, k, b, x, r, d, x_is_zero);
+    chebyshev(&M, dinv, rho, lodiv, k, b, x, r, d, x_is_zero);
     free(dinv); free(r); free(d);
 }
 

@@ -218,9 +218,10 @@ def test_galerkin_matches_dense_triple_product(tiny):
         assert np.abs(P.T @ A0 @ P - A1).max() <= 1e-14 * np.abs(A1).max()
 
 
-def _cheb_closed_form(Ad, Dinv, rho, k, b):
-    """x = (I - q(D^{-1}A)) A^{-1} b, q(t) = T_k((theta - t)/delta) / T_k(theta/delta)."""
-    lmax, lmin = rho, rho / 10.0
+def _cheb_closed_form(Ad, Dinv, rho, k, b, lodiv=10.0):
+    """x = (I - q(D^{-1}A)) A^{-1} b, q(t) = T_k((theta - t)/delta) / T_k(theta/delta),
+    interval [rho / lodiv, rho] (10 on AMG(A), 3 on AMG(S_hat))."""
+    lmax, lmin = rho, rho / lodiv
     th, de = 0.5 * (lmax + lmin), 0.5 * (lmax - lmin)
     n = Ad.shape[0]
     X = (th * np.eye(n) - Dinv @ Ad) / de
@@ -447,7 +448,7 @@ def test_kcycle_is_two_step_minimal_residual(tiny):
     def smoother(l):
         A = mats[l]
         Dinv = np.diag(1.0 / np.diag(A))
-        return _cheb_closed_form(A, Dinv, L[l]["rho"], 2, None)
+        return _cheb_closed_form(A, Dinv, L[l]["rho"], 2, None, lodiv=3.0)
 
     def two_grid(l, b):
         A, P, S = mats[l], Ps[l], smoother(l)
