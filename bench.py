@@ -90,7 +90,8 @@ def _source_hash():
         src = f.read()
     k = src.index("__device__ __forceinline__ void sell_pairs(")   # the paired BF16 loop, then k_sell
     a = src.rindex("template <", 0, k)
-    b = src.index("// ====", a)
+    k2 = src.index("__global__ void __launch_bounds__(256) k_sell(", a)
+    b = src.index("\n}\n", k2) + 3                                   # end of k_sell
     return hashlib.sha256(src[a:b].encode()).hexdigest()[:16]
 
 

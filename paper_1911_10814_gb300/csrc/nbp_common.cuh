@@ -119,6 +119,7 @@ struct Level {
     double *dinv = nullptr;                  // bs*bs per row
     float *dinv32 = nullptr;
     double rho = 0.0;
+    double cheb_lo = 10.0;                   // Chebyshev interval [rho / cheb_lo, rho]
     // work vectors: [0] b, [1] x, [2] x (ping-pong), [3] r, [4] d, and for the
     // K-cycle [5] r, [6] z1, [7] w1, [8] z2, [9] w2; FP64 and FP32 sets
     static constexpr int kWork = 10;

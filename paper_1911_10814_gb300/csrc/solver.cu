@@ -440,8 +440,8 @@ template <> const double *dinv_of<double>(const Level &L) { return L.dinv; }
 template <> const float *dinv_of<float>(const Level &L) { return L.dinv32; }
 
 struct Cheb { double theta, delta, sigma; };
-static Cheb cheb_of(double rho) {
-    const double lmax = rho, lmin = rho / 10.0;
+static Cheb cheb_of(const Level &L) {
+    const double lmax = L.rho, lmin = L.rho / L.cheb_lo;
     Cheb ch;
     ch.theta = 0.5 * (lmax + lmin);
     ch.delta = 0.5 * (lmax - lmin);
@@ -466,7 +466,7 @@ template <typename T>
 static T *chebyshev(nbp_ctx *c, Level &L, int vsel, int k, const T *b, T *x, T *alt, bool zero_start,
                     bool first_done = false) {
     const int bs = L.M.br;
-    const Cheb ch = cheb_of(L.rho);
+    const Cheb ch = cheb_of(L);
     T *d = wvec<T>(L, 4);
     double rho_old = 1.0 / ch.sigma;
     T *cur = x, *nxt = alt;
@@ -558,7 +558,7 @@ static void vcycle_level(nbp_ctx *c, Hier &H, int l, int vsel, const T *b, T *ou
     // iterate w[2]) and, for a K-cycle, its copy of the right-hand side (w[5])
     const bool fuse = k > 0 && l + 1 < H.nlev - 1;
     if (fuse) {
-        const Cheb chc = cheb_of(Lc.rho);
+        const Cheb chc = cheb_of(Lc);
         timed(c, "amg/restrict+first", 0.0, [&] {
             k_restrict_first<T><<<grid_exact((long long)Lc.M.nbr * 8), 256, 0, c->s>>>(
                 L.mptr, L.mem, Lc.M.nbr, bs, r, bc, dinv_of<T>(Lc), (T)(1.0 / chc.theta), wvec<T>(Lc, 4), wvec<T>(Lc, 2),
@@ -700,7 +700,7 @@ template <typename T> static void vcycle(nbp_ctx *c, Hier &H, int vsel, const T 
             c->prof.launches = k0;
         }
         if (first_in) {
-            const Cheb ch = cheb_of(L0.rho);
+            const Cheb ch = cheb_of(L0);
             c->prof.launches++;
             k_cheb_first<T><<<grid_exact(n), 256, 0, c->s>>>(L0.M.nbr, H.bs, dinv_of<T>(L0), b, (T)(1.0 / ch.theta),
                                                              wvec<T>(L0, 4), wvec<T>(L0, 2), gb);
@@ -1087,6 +1087,12 @@ static void do_setup(nbp_ctx *c) {
     refine_rhos(c, c->HA);
     build_shat(c->A, c->B, c->C, c->D, c->lr, c->N, c->Shat, c->diagA, s);
     amg_build(c->HS, c->Shat, c->opt, prec, s);   // AMG(S_hat) keeps the Gershgorin bound (see refine_rho)
+    // Chebyshev intervals [rho/10, rho] on AMG(A) and [rho/3, rho] on AMG(S_hat):
+    // for the degree-1 smoothing of S_hat the lower end only sets the Jacobi
+    // weight (1.5 / rho); rho/3 there cut S-iterations 97 -> 91 on the 4.34M
+    // tangent, while lower ends other than rho/10 were worse on A
+    for (int l = 0; l < c->HA.nlev; ++l) c->HA.L[l].cheb_lo = 10.0;
+    for (int l = 0; l < c->HS.nlev; ++l) c->HS.L[l].cheb_lo = 3.0;
     c->HA.kcycle = c->opt.amg_cycle == 2;
     c->HS.kcycle = c->opt.amg_cycle >= 1;
     c->HA.kdepth = c->HS.kdepth = c->opt.amg_kdepth;
