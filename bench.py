@@ -50,6 +50,9 @@ def _args():
     p.add_argument("--amg-kdepth", type=int, default=99, help="K-cycle on coarse levels 1..k")
     p.add_argument("--cheb-degree", type=int, default=2, help="Chebyshev smoothing degree of AMG(A)")
     p.add_argument("--cheb-degree-S", type=int, default=1, help="Chebyshev smoothing degree of AMG(S_hat)")
+    p.add_argument("--theta", type=float, default=0.0064, help="aggregation strength threshold")
+    p.add_argument("--amg-max-levels", type=int, default=5)
+    p.add_argument("--amg-coarse-max", type=int, default=300, help="coarsest level size (block rows)")
     p.add_argument("--outlets", type=int, default=0,
                    help="split the outlet face into this many patches (many-outlet stress case, e.g. 772)")
     p.add_argument("--workload", default="large", choices=["large", "batch"],
@@ -299,7 +302,8 @@ def main():
     d = synth.generate(spec)
     t_gen = time.perf_counter() - t0
     s = Solver(d, device=dev, precision=a.precision, pc_A=a.pc_A, amg_cycle=a.amg_cycle, amg_kdepth=a.amg_kdepth,
-               cheb_degree=a.cheb_degree, cheb_degree_S=a.cheb_degree_S)
+               cheb_degree=a.cheb_degree, cheb_degree_S=a.cheb_degree_S, theta=a.theta,
+               amg_max_levels=a.amg_max_levels, amg_coarse_max=a.amg_coarse_max)
     s.setup()
     b = torch.as_tensor(d["b"], device=f"cuda:{dev}")
     n = 4 * d["n_nodes"]
@@ -412,7 +416,8 @@ def main():
                    "outlets": spec.n_out, "tolerance": 1e-8, "inner_precision": a.precision,
                    "values": {0: "f64", 1: "f32", 2: "bf16", 3: "f32 operators, bf16 AMG hierarchies"}.get(a.precision, str(a.precision)),
                    "P_A": "AMG" if a.pc_A == 0 else "Jacobi", "amg_cycle": a.amg_cycle, "amg_kdepth": a.amg_kdepth,
-                   "cheb_degree": a.cheb_degree, "cheb_degree_S": a.cheb_degree_S,
+                   "cheb_degree": a.cheb_degree, "cheb_degree_S": a.cheb_degree_S, "theta": a.theta,
+                   "amg_max_levels": a.amg_max_levels, "amg_coarse_max": a.amg_coarse_max,
                    "parallelism": f"replicas{ws}", "l2": "inputs larger than L2 (no flush)"},
         "fp64": ({"solve_s": info64["solve_s"], "rel_res_true": info64["rel_res_true"], **counts64} if info64 else None),
         "mixed": {"solve_s": ms / 1e3, "rel_res_true": infos[-1]["rel_res_true"], "err_vs_fp64": err_vs_fp64,
