@@ -530,6 +530,10 @@ long synth_outlets(const synth_params *p, int32_t *out_ptr, int32_t *out_idx, do
     const int n_out = p->n_out > 0 ? p->n_out : 0;
     const long nf = (long)(p->nx + 1) * (p->ny + 1);
     if (n_out > 2L * p->nx * p->ny) return -1;
+    if (n_out == 0) {   /* no outlets: nothing to assemble */
+        if (out_ptr) out_ptr[0] = 0;
+        return 0;
+    }
     double *acc = (double *)calloc((size_t)n_out * (size_t)nf, sizeof(double));
     unsigned char *hit = (unsigned char *)calloc((size_t)n_out * (size_t)nf, 1);
     if ((n_out && !acc) || (n_out && !hit)) { free(acc); free(hit); return -1; }

@@ -257,3 +257,38 @@ def test_simple_variant_solves_and_matches_oracle():
     assert _rel(s2.apply_pscr(_t(sv)).cpu().numpy(), o2.apply_pscr(sv)) <= 1e-7
     s.close()
     s2.close()
+
+
+def test_zero_rhs_gives_zero_solution():
+    """b = 0: the nested solve returns x = 0 at once (||b|| = 0 meets every
+    tolerance) in every precision mode."""
+    d = synth.generate(synth.tiny())
+    s = Solver(d, precision=3)
+    s.setup()
+    b = torch.zeros(4 * d["n_nodes"], dtype=torch.float64, device=DEV)
+    for prec in (0, 1, 3):
+        x, info = s.solve(b, precision=prec)
+        assert float(torch.abs(x).max()) == 0.0 and info["outer_iters"] == 0
+    s.close()
+
+
+@pytest.mark.parametrize("prec", [0, 2])
+def test_no_outlets(prec):
+    """A tangent without outlet coupling (n_out = 0, no rank-one term): the
+    A product, S_hat and the nested solve against the oracle."""
+    spec = synth.MeshSpec(7, 9, 13, Lz=2.0, Re=200.0, seed=8, R=(), name="box7x9x13_o0")
+    d = synth.generate(spec)
+    assert len(d["out_ptr"]) == 1
+    s = Solver(d, precision=prec)
+    s.setup()
+    o = oracle.Oracle(d, rtol=1e-12)
+    x = np.random.default_rng(2).standard_normal(3 * d["n_nodes"])
+    y = s.apply_A(_t(x)).cpu().numpy()
+    yo = o.apply_A(x)
+    assert np.max(np.abs(y - yo)) <= 1e-12 * np.max(np.abs(yo))
+    xs, info = s.solve(_t(d["b"]))
+    xh = xs.cpu().numpy()
+    assert np.linalg.norm(d["b"] - o.apply_full(xh)) <= 1e-8 * np.linalg.norm(d["b"])
+    xo, _, _ = o.solve(d["b"])
+    assert _rel(xh, xo) <= (1e-6 if prec == 0 else 1e-5)
+    s.close()

@@ -131,3 +131,9 @@ def test_tiny_tangent_structure():
     assert d["out_ptr"][-1] == 7 * 7  # interior outlet nodes of the 9x9 top face
     assert np.all(np.isfinite(d["A"])) and np.all(np.isfinite(d["b"]))
     assert np.all(np.abs(d["b"]) <= 1.0)
+
+
+def test_no_outlet_spec():
+    """A spec without outlets gives empty outlet arrays (and no stray writes)."""
+    d = synth.generate(synth.MeshSpec(5, 6, 7, R=(), name="box5x6x7_o0"))
+    assert list(d["out_ptr"]) == [0] and len(d["out_idx"]) == 0 and len(d["r"]) == 0
