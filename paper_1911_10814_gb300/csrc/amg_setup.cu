@@ -473,7 +473,7 @@ static long long sell_layout(const DMat &m, int C, long long *&sp, cudaStream_t 
 }
 
 void make_sell(DMat &m, int precision, cudaStream_t s) {
-    if (m.br != m.bc || m.nbr == 0) return;
+    if (m.nbr == 0) return;
     if (m.sl_ci && (precision < 1 || m.sl_v32) && (precision < 2 || m.sl_v16)) return;   // 2, 3: FP32 and BF16
     dfree(m.sl_ptr, s); dfree(m.sl_ci, s); dfree(m.sl_v, s); dfree(m.sl_v32, s); dfree(m.sl_v16, s);
     dfree(m.sl2_ptr, s); dfree(m.sl2_ci, s);

@@ -232,6 +232,52 @@ __global__ void __launch_bounds__(256) k_sell(SpmvArgs a) {
     }
 }
 
+// Sliced-ELL product for the rectangular coupling blocks (B: 3x1, C: 1x3):
+// one thread per block row, slot values component-major as in k_sell (value
+// q = r BC + c of the C slots at (slot base) * BR BC + C q + t).  Epilogues
+// SET / ADD / SUB; FP64 or FP32 values.
+template <int BR, int BC, typename VT, typename XT, int EPI, int C>
+__global__ void __launch_bounds__(256) k_sellr(SpmvArgs a) {
+    using AT = XT;
+    constexpr int BB = BR * BC;
+    const int row = blockIdx.x * blockDim.x + threadIdx.x;
+    const int sl = row / C, t = row % C;
+    if (sl >= a.nslice) return;
+    const long long base = a.sl_ptr[sl];
+    const int w = (int)((a.sl_ptr[sl + 1] - base) / C);
+    const VT *__restrict__ val = (const VT *)a.val;
+    const int *__restrict__ ci = a.sl_ci;
+    const XT *__restrict__ x = (const XT *)a.x;
+    AT acc[BR];
+#pragma unroll
+    for (int r = 0; r < BR; ++r) acc[r] = 0;
+#pragma unroll 2
+    for (int k = 0; k < w; ++k) {
+        const long long g = base + (long long)C * k;
+        const int c = __ldg(ci + g + t);
+        const VT *v = val + g * BB + t;
+        AT xs[BC];
+#pragma unroll
+        for (int cc = 0; cc < BC; ++cc) xs[cc] = __ldg(x + (long long)BC * c + cc);
+#pragma unroll
+        for (int r = 0; r < BR; ++r) {
+            AT u = 0;
+#pragma unroll
+            for (int cc = 0; cc < BC; ++cc) u += cvt<AT>(__ldg(v + (r * BC + cc) * C)) * xs[cc];
+            acc[r] += u;
+        }
+    }
+    if (row >= a.nbr) return;
+    XT *y = (XT *)a.y;
+#pragma unroll
+    for (int r = 0; r < BR; ++r) {
+        const long long idx = (long long)row * BR + r;
+        if (EPI == EPI_SET) y[idx] = acc[r];
+        else if (EPI == EPI_ADD) y[idx] += acc[r];
+        else y[idx] -= acc[r];
+    }
+}
+
 // Sliced-ELL product with T threads per block row (T = 2, 4, 8: thread h
 // takes slots h, h + T, ..., then an xor-shuffle tree over the T lanes), for
 // coarse levels whose rows are few, so that one thread per row leaves the

@@ -1099,6 +1099,7 @@ static void do_setup(nbp_ctx *c) {
     c->HA.cheb = c->opt.cheb_degree;
     c->HS.cheb = c->opt.cheb_degree_S;
     make_sell(c->A, prec, s);
+    for (DMat *M : {&c->B, &c->C, &c->D}) make_sell(*M, prec, s);   // the coupling products too
     if (prec >= 1) {
         make_lowcopies(c->A, prec, s);
         make_lowcopies(c->B, prec, s);
@@ -1108,6 +1109,7 @@ static void do_setup(nbp_ctx *c) {
     // kernel choice per matrix: the fine levels use the sliced-ELL kernel;
     // coarse levels are tuned in place by timing whole AMG cycles
     c->A.tuned = c->A.sl_ci ? 0 : -1;
+    for (DMat *M : {&c->B, &c->C, &c->D}) M->tuned = M->sl_ci ? 0 : -1;
     for (Hier *H : {&c->HA, &c->HS}) H->L[0].M.tuned = H->L[0].M.sl_ci ? 0 : -1;
     if (prec >= 1) autotune_cycles<float>(c);
     else autotune_cycles<double>(c);

@@ -150,12 +150,47 @@ static void launch_sell(const DMat &M, int vsel, SpmvArgs a, int epi, bool lr, c
     }
 }
 
+template <int BR, int BC, typename VT, typename XT, int C>
+static void launch_sellr_epi(const SpmvArgs &a, int epi, cudaStream_t s) {
+    const unsigned grid = grid_exact((long long)a.nslice * C);
+    switch (epi) {
+    case EPI_SET: k_sellr<BR, BC, VT, XT, EPI_SET, C><<<grid, 256, 0, s>>>(a); break;
+    case EPI_ADD: k_sellr<BR, BC, VT, XT, EPI_ADD, C><<<grid, 256, 0, s>>>(a); break;
+    case EPI_SUB: k_sellr<BR, BC, VT, XT, EPI_SUB, C><<<grid, 256, 0, s>>>(a); break;
+    default: throw Error{NBP_ERR_INVALID, "spmv: rectangular blocks take SET, ADD or SUB"};
+    }
+    NBP_LAUNCHED();
+}
+
+// rectangular blocks (3x1, 1x3) on their sliced-ELL copy, FP64 or FP32 values
+template <int BR, int BC, typename XT>
+static void launch_sellr(const DMat &M, int vsel, SpmvArgs a, int epi, cudaStream_t s) {
+    a.nslice = M.nslice;
+    a.sl_ptr = M.sl_ptr;
+    a.sl_ci = M.sl_ci;
+    if constexpr (sizeof(XT) == 8) {
+        a.val = M.sl_v;
+        if (M.sl_c == 8) launch_sellr_epi<BR, BC, double, double, 8>(a, epi, s);
+        else launch_sellr_epi<BR, BC, double, double, 32>(a, epi, s);
+    } else {
+        a.val = M.sl_v32;
+        if (M.sl_c == 8) launch_sellr_epi<BR, BC, float, float, 8>(a, epi, s);
+        else launch_sellr_epi<BR, BC, float, float, 32>(a, epi, s);
+    }
+}
+
 template <typename XT>
 void spmv(const DMat &M, int vsel, SpmvArgs a, int epi, bool lr, cudaStream_t s, int G) {
     a.nbr = M.nbr;
     a.rp = M.rp;
     a.ci = M.ci;
     if (a.nbr == 0) return;
+    // rectangular coupling blocks: sliced ELL for FP64 / FP32 values (BF16: flat kernel)
+    if (M.br != M.bc && M.sl_ci && G <= 0 && epi <= EPI_SUB && vsel != 2 &&
+        (sizeof(XT) == 8 ? M.sl_v != nullptr : M.sl_v32 != nullptr)) {
+        if (M.br == 3 && M.bc == 1) { launch_sellr<3, 1, XT>(M, vsel, a, epi, s); return; }
+        if (M.br == 1 && M.bc == 3) { launch_sellr<1, 3, XT>(M, vsel, a, epi, s); return; }
+    }
     const bool sell_ok = M.sl_ci && M.br == M.bc && (sizeof(XT) == 8 ? M.sl_v != nullptr : true);
     if (G < 0) G = (M.tuned >= 0) ? M.tuned : (sell_ok ? 0 : choose_group(M));
     if ((G == 0 || is_sellm(G)) && !sell_ok) G = choose_group(M);
