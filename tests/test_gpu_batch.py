@@ -21,15 +21,16 @@ def _t(a):
     return torch.as_tensor(np.ascontiguousarray(a), device="cuda:0")
 
 
-def test_small_batch_matches_single_solves():
+@pytest.mark.parametrize("prec", [1, 3])
+def test_small_batch_matches_single_solves(prec):
     specs = synth.batch(count=6, seed=7, smin=5, smax=11)
     systems = [synth.generate(sp) for sp in specs]
-    B = BatchSolver(systems, precision=1)
+    B = BatchSolver(systems, precision=prec)
     B.setup()
     xs, infos = B.solve([_t(d["b"]) for d in systems])
     torch.cuda.synchronize()
     for d, x, info in zip(systems, xs, infos):
-        s = Solver(d, precision=1)
+        s = Solver(d, precision=prec)
         s.setup()
         x1, info1 = s.solve(_t(d["b"]))
         assert torch.equal(x, x1)

@@ -184,10 +184,11 @@ def test_block_triangular_two_iterations():
     s.close()
 
 
-def test_adjoint_matches_oracle():
+@pytest.mark.parametrize("prec", [0, 3])
+def test_adjoint_matches_oracle(prec):
     spec = CASES["box9x11x23_q4"]
     d = synth.generate(spec)
-    s = Solver(d, rtol=1e-12)
+    s = Solver(d, rtol=1e-12, precision=prec)
     s.setup()
     x, _ = s.solve(_t(d["b"]))
     xh = x.cpu().numpy()
@@ -197,7 +198,7 @@ def test_adjoint_matches_oracle():
     g[:nv] = rng.standard_normal(nv)
     lam, dldr, info = s.adjoint(_t(g), x)
     lam_o, dldr_o, _ = oracle.adjoint(d, g, xh, rtol=1e-12)
-    assert _rel(lam.cpu().numpy(), lam_o) <= 1e-6
+    assert _rel(lam.cpu().numpy(), lam_o) <= (1e-6 if prec == 0 else 1e-5)
     assert np.allclose(dldr, dldr_o, rtol=1e-5, atol=0)
     s.close()
 
