@@ -185,8 +185,11 @@ nbp_status nbp_vcycle(nbp_ctx *ctx, int32_t which, const double *b, double *x);
 /* Hierarchy introspection (after nbp_setup).  nbp_amg_level_sizes returns the
  * number of levels; rows/nnz (HOST arrays of length >= levels) get the block
  * rows and stored blocks of each level.  nbp_amg_level_get copies level l to
- * HOST arrays: rowptr (rows+1), col (nnz), val (nnz*bs*bs doubles) and the
- * aggregate map to level l+1 (rows; -1 = left out), any of which may be NULL. */
+ * HOST arrays: rowptr (rows+1), col (nnz), val (nnz*bs*bs doubles), the
+ * aggregate map to level l+1 (rows; -1 = left out) and rho, the upper end of
+ * the level's Chebyshev interval (AMG(A): min of the Gershgorin bound of
+ * D_b^{-1} A and 1.1 x the spectral radius of a 20-step Arnoldi Hessenberg
+ * matrix; AMG(S_hat): the Gershgorin bound), any of which may be NULL. */
 int32_t nbp_amg_level_sizes(nbp_ctx *ctx, int32_t which, int32_t *rows, int64_t *nnz, int32_t max_levels);
 nbp_status nbp_amg_level_get(nbp_ctx *ctx, int32_t which, int32_t l, int32_t *rowptr, int32_t *col, double *val,
                              int32_t *agg, double *rho);
