@@ -46,6 +46,7 @@ def _args():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--skip-fp64", action="store_true", help="skip the FP64 comparison solve (profiling runs)")
     p.add_argument("--pc-A", type=int, default=0, help="P_A: 0 AMG V-cycle (default), 1 Jacobi")
+    p.add_argument("--variant", type=int, default=0, help="0 P_SCR (Algorithm 3), 1 block-triangular, 2 SIMPLE")
     p.add_argument("--amg-cycle", type=int, default=1, help="0 V-cycles, 1 K-cycle on AMG(S_hat), 2 K-cycle on both")
     p.add_argument("--amg-kdepth", type=int, default=99, help="K-cycle on coarse levels 1..k")
     p.add_argument("--cheb-degree", type=int, default=2, help="Chebyshev smoothing degree of AMG(A)")
@@ -301,7 +302,8 @@ def main():
     t0 = time.perf_counter()
     d = synth.generate(spec)
     t_gen = time.perf_counter() - t0
-    s = Solver(d, device=dev, precision=a.precision, pc_A=a.pc_A, amg_cycle=a.amg_cycle, amg_kdepth=a.amg_kdepth,
+    s = Solver(d, device=dev, precision=a.precision, pc_A=a.pc_A, variant=a.variant, amg_cycle=a.amg_cycle,
+               amg_kdepth=a.amg_kdepth,
                cheb_degree=a.cheb_degree, cheb_degree_S=a.cheb_degree_S, theta=a.theta,
                amg_max_levels=a.amg_max_levels, amg_coarse_max=a.amg_coarse_max)
     s.setup()
@@ -415,7 +417,8 @@ def main():
         "config": {"workload": spec.name, "unknowns": n, "tets": 6 * spec.nx * spec.ny * spec.nz,
                    "outlets": spec.n_out, "tolerance": 1e-8, "inner_precision": a.precision,
                    "values": {0: "f64", 1: "f32", 2: "bf16", 3: "f32 operators, bf16 AMG hierarchies"}.get(a.precision, str(a.precision)),
-                   "P_A": "AMG" if a.pc_A == 0 else "Jacobi", "amg_cycle": a.amg_cycle, "amg_kdepth": a.amg_kdepth,
+                   "P_A": "AMG" if a.pc_A == 0 else "Jacobi", "variant": ["P_SCR", "block-triangular", "SIMPLE"][a.variant],
+                   "amg_cycle": a.amg_cycle, "amg_kdepth": a.amg_kdepth,
                    "cheb_degree": a.cheb_degree, "cheb_degree_S": a.cheb_degree_S, "theta": a.theta,
                    "amg_max_levels": a.amg_max_levels, "amg_coarse_max": a.amg_coarse_max,
                    "parallelism": f"replicas{ws}", "l2": "inputs larger than L2 (no flush)"},
