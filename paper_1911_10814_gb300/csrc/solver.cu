@@ -403,7 +403,7 @@ static GmResult gmres(nbp_ctx *c, Krylov<T> &K, long long n, Op op, Pc pc, const
             if (res <= tol || c->hst->beta == 0.0) break;
         }
         c->prof.launches += 1;
-        k_trisolve<<<1, 1, 0, s>>>(K.H, m, K.g, K.y, jend);
+        k_trisolve<<<1, 1, 0, s>>>(K.H, K.m, K.g, K.y, jend);   // H is laid out with the allocated restart length
         NBP_LAUNCHED();
         maxpy<T>(c, n, K.Z, K.ld, jend, K.y, 1.0, x);
         const bool est_conv = res <= tol;

@@ -241,6 +241,32 @@ def test_kcycle_vcycle_vs_oracle(cycle, kdepth):
     s.close()
 
 
+@pytest.mark.parametrize("prec", [0, 3])
+def test_restarted_solves_match_oracle(prec):
+    """GMRES(4) at every level (outer, A and S solves all restart) on a context
+    whose Krylov spaces were first sized by a GMRES(200) solve: the smaller
+    restart length reuses the larger allocation."""
+    d = synth.generate(CASES["box9x11x23_q4"])
+    s = Solver(d, precision=prec)
+    s.setup()
+    s.solve(_t(d["b"]))
+    x, info = s.solve(_t(d["b"]), m=4, m_A=4, m_S=4)
+    xh = x.cpu().numpy()
+    o = oracle.Oracle(d, m=4, m_A=4, m_S=4)
+    o.setup()
+    xo, oinfo, rc = o.solve(d["b"])
+    assert rc == 0 and oinfo.outer_iters > 4 and oinfo.A_iters > 4 * oinfo.n_A_solves
+    assert np.linalg.norm(d["b"] - o.apply_full(xh)) / np.linalg.norm(d["b"]) <= 1e-8
+    assert info["rel_res_true"] <= 1e-8
+    if prec == 0:
+        assert abs(info["outer_iters"] - oinfo.outer_iters) <= 1
+        assert abs(info["S_iters"] - oinfo.S_iters) <= max(2, 0.1 * oinfo.S_iters)
+    o.set_options(rtol=1e-12)
+    xt, _, _ = o.solve(d["b"])
+    assert _rel(xh, xt) <= 1e-5
+    s.close()
+
+
 def test_simple_variant_solves_and_matches_oracle():
     d = synth.generate(CASES["box9x11x23_q4"])
     s = Solver(d, variant=2)

@@ -376,6 +376,34 @@ def test_gmres_iterate_is_krylov_minimiser(tiny):
         assert abs(rel - np.linalg.norm(b - A @ x) / np.linalg.norm(b)) <= 1e-10
 
 
+def test_restarted_gmres_is_cyclewise_minimiser(tiny):
+    """GMRES(m) restarted (Saad & Schultz): each cycle of m steps minimises
+    ||b - A x|| over x_c + K_m(A, b - A x_c) from the cycle's start x_c;
+    brute force by dense least squares, cycle after cycle."""
+    d, (A, B, C, D, F) = tiny
+    o = oracle.Oracle(d)
+    b = np.random.default_rng(17).standard_normal(3 * d["n_nodes"])
+    for m in (1, 2, 3):
+        x, its, rel, rc = o.gmres_A(b, 1e-30, m, 6, 0)
+        assert its == 6
+        xr = np.zeros_like(b)
+        for _ in range(6 // m):
+            r = b - A @ xr
+            K = np.empty((len(b), m))
+            v = r / np.linalg.norm(r)
+            for j in range(m):
+                K[:, j] = v
+                v = A @ v
+                for i in range(j + 1):
+                    v -= (K[:, i] @ v) * K[:, i]
+                v /= np.linalg.norm(v)
+            Q, _ = np.linalg.qr(K)
+            y, *_ = np.linalg.lstsq(A @ Q, r, rcond=None)
+            xr = xr + Q @ y
+        assert _rel(x, xr) <= 1e-8
+        assert abs(rel - np.linalg.norm(b - A @ x) / np.linalg.norm(b)) <= 1e-10
+
+
 @pytest.fixture(scope="module")
 def tiny4():
     spec = synth.MeshSpec(8, 8, 8, Re=100.0, seed=0, R=(1e2, 1e3, 3e3, 1e4), name="cube8_re100_q4")
