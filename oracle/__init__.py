@@ -10,7 +10,13 @@ Schur product), Algorithm 3 (P_SCR^{-1}), S_hat = D - C diag(A)^{-1} B, an
 aggregation AMG and a dense LU.  ``dense_*`` helpers below build the same
 operators as dense numpy arrays for the pins on tiny cases.
 
-Parity status per function (see the pins in tests/test_oracle.py):
+``vms_oracle.c`` is the residual of the VMS / generalized-alpha P1-P1
+discretisation (Sec. 2.3-2.4) and its consistent tangent (Sec. 2.5), the
+tangent taken exactly by dual numbers; ``newton_step`` below is the
+predictor multi-corrector of Sec. 2.5 around the oracle's nested solve.
+
+Parity status per function (see the pins in tests/test_oracle.py and
+tests/test_vms_oracle.py):
   apply_A/apply_full .... pinned (dense products)
   solve (FGMRES+P_SCR) .. pinned (dense LU solve; exact-inner 1-iteration and
                           block-triangular 2-iteration closed forms)
@@ -21,6 +27,12 @@ Parity status per function (see the pins in tests/test_oracle.py):
   Galerkin .............. pinned (dense P^T A P)
   Chebyshev ............. pinned (dense polynomial in D^{-1}A)
   V-cycle ............... pinned (two-level exact-coarse identity)
+  VMS residual/tangent .. pinned (P1 mass/stiffness/divergence closed forms on
+                          one element; the generator's analytic tangent;
+                          central differences; the divergence theorem; node
+                          order invariance of the metric G)
+  newton_step ........... pinned (generalized-alpha update identity; the
+                          residual of the accepted state below tolerance)
 """
 from __future__ import annotations
 
@@ -32,6 +44,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "nbp_oracle.c")
+_SRCS = [_SRC, os.path.join(_HERE, "vms_oracle.c")]
 _LIB_PATH = os.path.join(_HERE, "_nbp_oracle.so")
 _lib = None
 
@@ -58,12 +71,30 @@ class Info(ctypes.Structure):
     ]
 
 
+class VmsPhys(ctypes.Structure):
+    """Physical and stabilisation constants of the VMS residual (Sec. 2.3-2.4)."""
+    _fields_ = [("rho", ctypes.c_double), ("mu", ctypes.c_double), ("dt", ctypes.c_double),
+                ("rho_inf", ctypes.c_double), ("beta", ctypes.c_double), ("CI", ctypes.c_double),
+                ("CT", ctypes.c_double)]
+
+
+def vms_phys(spec, beta: float = 0.2) -> VmsPhys:
+    """Constants of a generator spec: backflow beta = 0.2, C_I = 36, C_T = 4 (Sec. 2.3)."""
+    return VmsPhys(spec.rho, spec.mu, spec.dt, spec.rho_inf, beta, 36.0, 4.0)
+
+
+def gen_alpha(rho_inf: float):
+    """(alpha_m, alpha_f, gamma) from rho_inf (Sec. 2.4.1)."""
+    return 0.5 * (3.0 - rho_inf) / (1.0 + rho_inf), 1.0 / (1.0 + rho_inf), 1.0 / (1.0 + rho_inf)
+
+
 def build(force: bool = False) -> str:
     """Compile the oracle (gcc, FP64, no fused multiply-add)."""
-    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+    stale = not os.path.exists(_LIB_PATH) or any(os.path.getmtime(_LIB_PATH) < os.path.getmtime(f) for f in _SRCS)
+    if force or stale:
         tmp = _LIB_PATH + f".{os.getpid()}.tmp"
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
-                               _SRC, "-o", tmp, "-lm"])
+                               *_SRCS, "-o", tmp, "-lm"])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -110,6 +141,9 @@ def _load():
             ("or_shat_nnz", [vp], ctypes.c_int),
             ("or_strength_and_aggregate", [ctypes.c_int, ctypes.c_int, _ip, _ip, _dp, ctypes.c_double, _ip],
              ctypes.c_int),
+            ("or_vms_assemble", [ctypes.c_int, _dp, ctypes.c_int, _ip, ctypes.c_int, _ip, ctypes.c_void_p,
+                                 ctypes.POINTER(VmsPhys), _dp, _dp, _dp, _dp, ctypes.c_int, _ip, _ip, _dp, _dp, _ip, _ip,
+                                 _dp, _dp, _dp, _dp, _dp], ctypes.c_int),
         ]:
             f = getattr(lib, name)
             f.argtypes = args
@@ -427,3 +461,92 @@ def adjoint(sysd: dict, g, x, **opts):
         val = oval[optr[k]:optr[k + 1]]
         dLdr[k] = -(lam[:nv][idx] @ val) * (np.asarray(x)[:nv][idx] @ val)
     return lam, dLdr, info
+
+
+# ------------------------------------------------- VMS residual and Newton step
+def vms_assemble(mesh: dict, sysd: dict, phys: VmsPhys, vd, v, p, P=None, vtau=None, residual=True, tangent=True):
+    """Residual R (4N) and/or tangent blocks at (vdot_{n+alpha_m}, v_{n+alpha_f},
+    p_{n+alpha_f}) with outlet pressures P (P^k_{n+alpha_f}); tau at vtau (default v).
+    Returns dict(R=..., A=(nnz,3,3), B=(nnz,3), C=(nnz,3), D=(nnz,))."""
+    lib = _load()
+    N = sysd["n_nodes"]
+    rp, col = _i(sysd["rowptr"]), _i(sysd["col"])
+    nnz = int(rp[N])
+    X, tets, tris = _d(mesh["X"]).reshape(-1), _i(mesh["tets"]).reshape(-1), _i(mesh["tris"]).reshape(-1)
+    dirn = np.ascontiguousarray(mesh["dir"], dtype=np.uint8)
+    vd, v, p = _d(vd), _d(v), _d(p)
+    vt = _d(vtau) if vtau is not None else None
+    optr, oidx, oval = _i(sysd["out_ptr"]), _i(sysd["out_idx"]), _d(sysd["out_val"])
+    n_out = len(optr) - 1
+    Pk = _d(P) if P is not None else np.zeros(max(n_out, 1))
+    out = {}
+    R = np.zeros(4 * N) if residual else None
+    A = np.zeros((nnz, 3, 3)) if tangent else None
+    B = np.zeros((nnz, 3)) if tangent else None
+    C = np.zeros((nnz, 3)) if tangent else None
+    D = np.zeros(nnz) if tangent else None
+    nul = ctypes.POINTER(ctypes.c_double)()
+    rc = lib.or_vms_assemble(N, _pd(X), len(mesh["tets"]), _pi(tets), len(mesh["tris"]), _pi(tris),
+                             dirn.ctypes.data_as(ctypes.c_void_p), ctypes.byref(phys), _pd(vd), _pd(v), _pd(p),
+                             _pd(vt) if vt is not None else nul, n_out, _pi(optr), _pi(oidx), _pd(oval), _pd(Pk),
+                             _pi(rp), _pi(col), _pd(R) if residual else nul, _pd(A) if tangent else nul,
+                             _pd(B) if tangent else nul, _pd(C) if tangent else nul, _pd(D) if tangent else nul)
+    if rc != 0:
+        raise RuntimeError("or_vms_assemble: element couples nodes absent from the pattern")
+    if residual:
+        out["R"] = R
+    if tangent:
+        out.update(A=A, B=B, C=C, D=D)
+    return out
+
+
+def newton_step(mesh: dict, sysd: dict, phys: VmsPhys, y_n, yd_n, rcr: dict, tol_R=1e-6, tol_A=1e-6, l_max=20,
+                **solve_opts):
+    """One time step by the predictor multi-corrector of Sec. 2.5 around the
+    oracle's nested solve.  y = [v (3N); p (N)], yd its time derivative;
+    rcr = dict(Rp, C, Rd, Pd, Pi, nts) per outlet (Pi = Pi^k_n).
+    Readings: ||R_(0)|| is the residual at the predictor (the first residual
+    evaluated); velocity increments at Dirichlet nodes are set to zero.
+    Returns dict(y, yd, Pi, P, iters (linear solves), res (residual norms))."""
+    N = sysd["n_nodes"]
+    am, af, gm = gen_alpha(phys.rho_inf)
+    dt = phys.dt
+    y_n, yd_n = _d(y_n), _d(yd_n)
+    dmask = np.repeat(np.asarray(mesh["dir"], dtype=bool), 3)
+    y1 = y_n.copy()
+    yd1 = (gm - 1.0) / gm * yd_n                                   # predictor
+    n_out = len(sysd["out_ptr"]) - 1
+    Rp, Cc, Rd, Pd = (np.asarray(rcr[k], dtype=np.float64) for k in ("Rp", "C", "Rd", "Pd"))
+    Pi_n = np.asarray(rcr["Pi"], dtype=np.float64)
+    Q_n = outlet_flows(sysd, y_n[:3 * N]) if n_out else np.zeros(0)
+    P_n = Rp * Q_n + Pi_n + Pd
+    res, r0, lin = [], None, []
+    P1 = Pi1 = np.zeros(n_out)
+    for l in range(1, l_max + 1):
+        Q1 = outlet_flows(sysd, y1[:3 * N]) if n_out else np.zeros(0)                   # step 1
+        if n_out:
+            P1, Pi1, m = rcr_step(Rp, Cc, Rd, Pd, Pi_n, Q_n, Q1, dt, int(rcr["nts"]))   # steps 2-3
+        else:
+            m = np.zeros(0)
+        yaf = y_n + af * (y1 - y_n)                                                      # step 4
+        ydam = yd_n + am * (yd1 - yd_n)
+        Paf = (1.0 - af) * P_n + af * P1                                                 # step 5
+        R = vms_assemble(mesh, sysd, phys, ydam[:3 * N], yaf[:3 * N], yaf[3 * N:], Paf, tangent=False)["R"]  # 6
+        nr = float(np.linalg.norm(R))
+        res.append(nr)
+        if r0 is None:
+            r0 = nr
+        if (r0 > 0 and nr / r0 <= tol_R) or nr <= tol_A:                                 # step 7
+            return dict(y=y1, yd=yd1, Pi=Pi1, P=P1, iters=l - 1, res=res, lin=lin)
+        T = vms_assemble(mesh, sysd, phys, ydam[:3 * N], yaf[:3 * N], yaf[3 * N:], Paf, residual=False)  # step 8
+        sl = dict(sysd, A=T["A"], B=T["B"], C=T["C"], D=T["D"], r=af * gm * dt * m)
+        o = Oracle(sl, **solve_opts)
+        o.setup()
+        dx, info, rc = o.solve(-R)                                                       # step 9
+        if rc != 0:
+            raise RuntimeError(f"newton_step: nested solve failed (status {rc})")
+        lin.append(info.outer_iters)
+        dx[:3 * N][dmask] = 0.0
+        yd1 = yd1 + dx                                                                   # step 10
+        y1 = y1 + gm * dt * dx
+    raise RuntimeError("newton_step: no convergence in l_max corrector iterations")

@@ -73,6 +73,8 @@ def _load():
         lib.synth_uniforms.argtypes = [ctypes.c_uint64, ctypes.c_long, dp]; lib.synth_uniforms.restype = None
         lib.synth_element_tangent.argtypes = [P, dp, dp, dp]; lib.synth_element_tangent.restype = None
         lib.synth_backflow_tangent.argtypes = [P, dp, dp, dp]; lib.synth_backflow_tangent.restype = None
+        u8 = ctypes.POINTER(ctypes.c_uint8)
+        lib.synth_mesh.argtypes = [P, dp, ip, ip, ip, u8]; lib.synth_mesh.restype = None
         _lib = lib
     return _lib
 
@@ -155,6 +157,26 @@ def generate(spec: MeshSpec) -> dict:
         spec=spec, n_nodes=N, rowptr=rowptr, col=col, A=A, B=B, C=C, D=D, vel=vel,
         out_ptr=out_ptr, out_idx=out_idx, out_val=out_val, r=r, b=b,
     )
+
+
+def mesh(spec: MeshSpec) -> dict:
+    """Explicit mesh arrays of the box: X (N, 3) coordinates, tets (E, 4) node
+    ids, outlet triangles tris (T, 3) on z = Lz (outward +e_z orientation) with
+    their outlet piece tri_out (T,), and the Dirichlet flag dir (N,) of every
+    node (walls and inlet: velocity prescribed)."""
+    lib = _load()
+    p = spec.params()
+    N = spec.n_nodes
+    E = 6 * spec.nx * spec.ny * spec.nz
+    T = 2 * spec.nx * spec.ny
+    X = np.empty((N, 3), dtype=np.float64)
+    tets = np.empty((E, 4), dtype=np.int32)
+    tris = np.empty((T, 3), dtype=np.int32)
+    tri_out = np.empty(T, dtype=np.int32)
+    dirn = np.empty(N, dtype=np.uint8)
+    lib.synth_mesh(ctypes.byref(p), _dp(X), _ip(tets), _ip(tris), _ip(tri_out),
+                   dirn.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)))
+    return dict(X=X, tets=tets, tris=tris, tri_out=tri_out, dir=dirn)
 
 
 def outlets(spec: MeshSpec):

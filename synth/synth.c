@@ -578,6 +578,54 @@ long synth_outlets(const synth_params *p, int32_t *out_ptr, int32_t *out_idx, do
     return cnt;
 }
 
+/* Mesh arrays of the box (input data for a residual/tangent assembler):
+ *   X        3N node coordinates (node ids as everywhere: x fastest);
+ *   tets     4 node ids per tet, 6 nx ny nz tets (hex (hi, hj, hk) in x-fastest
+ *            order, Kuhn tet t of that hex at 6 h + t, nodes in kuhn_tet order);
+ *   tris     3 node ids per outlet triangle on z = Lz, 2 nx ny triangles
+ *            (square (hi, hj) row by row, two triangles each), ordered so that
+ *            (x1 - x0) x (x2 - x0) points out of the box (+e_z);
+ *   tri_out  the outlet piece of each triangle (the partition of synth_outlets);
+ *   dir      1 for each node whose velocity is prescribed (walls, inlet).
+ * Any pointer may be NULL. */
+void synth_mesh(const synth_params *p, double *X, int32_t *tets, int32_t *tris, int32_t *tri_out, uint8_t *dir) {
+    const double hx = p->Lx / p->nx, hy = p->Ly / p->ny, hz = p->Lz / p->nz;
+    for (int k = 0; k <= p->nz; ++k)
+        for (int j = 0; j <= p->ny; ++j)
+            for (int i = 0; i <= p->nx; ++i) {
+                long a = nid(p, i, j, k);
+                if (X) { X[3 * a] = i * hx; X[3 * a + 1] = j * hy; X[3 * a + 2] = k * hz; }
+                if (dir) dir[a] = (uint8_t)is_dirichlet(p, i, j, k);
+            }
+    if (tets) {
+        long e = 0;
+        for (int hk = 0; hk < p->nz; ++hk)
+            for (int hj = 0; hj < p->ny; ++hj)
+                for (int hi = 0; hi < p->nx; ++hi)
+                    for (int t = 0; t < 6; ++t, ++e) {
+                        int c[4];
+                        kuhn_tet(t, c);
+                        for (int v = 0; v < 4; ++v)
+                            tets[4 * e + v] = (int32_t)nid(p, hi + (c[v] & 1), hj + ((c[v] >> 1) & 1), hk + ((c[v] >> 2) & 1));
+                    }
+    }
+    /* corner codes bx + 2 by on the top face; both triangles counter-clockwise seen from +z */
+    static const int tri[2][3] = {{0, 1, 3}, {0, 3, 2}};
+    for (int hj = 0; hj < p->ny; ++hj)
+        for (int hi = 0; hi < p->nx; ++hi)
+            for (int t = 0; t < 2; ++t) {
+                long f = 2L * ((long)hj * p->nx + hi) + t;
+                double cx = 0.0, cy = 0.0;
+                for (int v = 0; v < 3; ++v) {
+                    int bi = hi + (tri[t][v] & 1), bj = hj + ((tri[t][v] >> 1) & 1);
+                    if (tris) tris[3 * f + v] = (int32_t)nid(p, bi, bj, p->nz);
+                    cx += bi * hx; cy += bj * hy;
+                }
+                cx /= 3.0 * p->Lx; cy /= 3.0 * p->Ly;
+                if (tri_out) tri_out[f] = p->n_out > 0 ? outlet_piece(p->n_out, cx, cy, f, 2L * p->nx * p->ny) : -1;
+            }
+}
+
 /* Right-hand side: uniform [-1, 1] on all 4N unknowns, ordered [x_v (3N, node
  * interleaved); x_p (N)], drawn from a stream seeded with seed ^ 0xB0B. */
 void synth_rhs(const synth_params *p, double *b) {
