@@ -312,6 +312,117 @@ nbp_status nbp_outlet_flows(nbp_ctx *ctx, const double *v, double *Q);
 nbp_status nbp_rcr_update(nbp_ctx *ctx, const nbp_rcr *p, const double *v_np1, double dt, int32_t nts, double scale,
                           double *Q_np1, double *P_np1, double *Pi_np1, double *m);
 
+/* --------------------------------------------- tangent values in place
+ * Replaces the values of A, B, C, D (DEVICE arrays in the layout and on the
+ * pattern given to nbp_create: 9, 3, 3, 1 values per entry), e.g. with the
+ * tangent of a new Newton iteration.  Copies them, drops every copy built
+ * from the old values (precision copies, sliced-ELL layouts, AMG, S_hat, the
+ * transposed context of the adjoint): call nbp_setup again before solving.
+ * No paper counterpart as an entry point (the tangent is reassembled every
+ * iteration in Sec. 2.5, step 8).  Errors: NBP_ERR_INVALID (null array, a
+ * non-finite value: nothing is replaced), NBP_ERR_CUDA. */
+nbp_status nbp_set_values(nbp_ctx *ctx, const double *a_val, const double *b_val, const double *c_val,
+                          const double *d_val);
+
+/* ------------------------------------ VMS residual, tangent, Newton step
+ * On-device assembly for the P1-P1 residual-based VMS formulation with
+ * generalized-alpha time stepping (paper Sec. 2.3-2.5):
+ *   residual  R_m = R_m^vol + R_m^bc + R_m^bf and R_p (Sec. 2.3, B_m^vol,
+ *             B_m^bc, B_m^bf, B_p), fine scales v', p' and tau_M, tau_C, G
+ *             as defined there; the outlet traction is R_m^bc = sum_k P_k a^k
+ *             with the context's outlet vectors a^k;
+ *   tangent   A = F (+ K, kept as the context's rank-one term), B, C, D of
+ *             Sec. 2.5: the exact derivative of the residual with respect to
+ *             (vdot_{n+1}, pdot_{n+1}), with tau_M and tau_C held fixed.
+ * Readings: P1 elements (the viscous second derivatives in v' vanish), no
+ * body force, degree-2 4-point rule on tets and the 3-point rule at the
+ * barycentric points (2/3, 1/6, 1/6) on outlet triangles; a Dirichlet node
+ * prescribes all three velocity components: its momentum residual rows are
+ * zero, its tangent rows and columns in A keep the diagonal entry only, its
+ * B rows and C columns are zero, and Newton increments leave it unchanged.
+ * Unknowns as in nbp_solve: x = [v (3N, node-interleaved); p (N)]. */
+typedef struct nbp_vms nbp_vms;
+
+typedef struct {
+    int32_t n_nodes;          /* must equal the context's N */
+    int32_t n_tets, n_tris;
+    const double *X;          /* HOST, 3N node coordinates */
+    const int32_t *tets;      /* HOST, 4 node ids per tet (any vertex order) */
+    const int32_t *tris;      /* HOST, 3 node ids per Neumann (outlet) triangle, ordered so that
+                                 (x1 - x0) x (x2 - x0) points out of the domain */
+    const uint8_t *dir;       /* HOST, N flags: 1 = velocity prescribed (Dirichlet) */
+} nbp_mesh;
+
+typedef struct {
+    double rho, mu;           /* density, dynamic viscosity */
+    double dt;                /* time step Delta t_n */
+    double rho_inf;           /* generalized-alpha spectral radius (Sec. 2.4.1), in [0, 1] */
+    double beta;              /* backflow coefficient (0.2 in Sec. 2.3) */
+    double CI, CT;            /* 36 and 4 for linear tets (Sec. 2.3) */
+    int32_t tangent_fp32;     /* 1: tangent arithmetic in FP32 (written as FP64 values); 0: FP64 */
+} nbp_vms_params;
+
+/* Binds a mesh to a context (its pattern must contain every pair of nodes
+ * sharing a tet or an outlet triangle; A, B, C, D share one pattern).  Host
+ * arrays are copied; the gather maps (node -> incident elements, pattern
+ * slot -> element blocks, ascending element order) are built on the host
+ * once.  The handle uses the context's stream and must be destroyed before
+ * the context.  Errors: NBP_ERR_INVALID (sizes, node ids, parameters, a pair
+ * absent from the pattern), NBP_ERR_OOM, NBP_ERR_CUDA. */
+nbp_status nbp_vms_create(nbp_vms **vms, nbp_ctx *ctx, const nbp_mesh *mesh, const nbp_vms_params *par);
+nbp_status nbp_vms_destroy(nbp_vms *vms);
+
+/* R (DEVICE, 4N) at vd = vdot_{n+alpha_m} (3N), v = v_{n+alpha_f} (3N),
+ * p = p_{n+alpha_f} (N), outlet pressures P (DEVICE, n_out; may be NULL
+ * without outlets), tau evaluated at vtau (DEVICE 3N, NULL: v).  Every row is
+ * a fixed-order sum (bitwise repeatable).  Synchronises the context stream.
+ * Errors: NBP_ERR_INVALID, NBP_ERR_CUDA. */
+nbp_status nbp_vms_residual(nbp_vms *vms, const double *vd, const double *v, const double *p, const double *vtau,
+                            const double *P, double *R);
+
+/* Tangent values on the context's pattern (DEVICE a_val 9 nnz, b_val 3 nnz,
+ * c_val 3 nnz, d_val nnz) at the same state as nbp_vms_residual.  Does not
+ * touch the context (see nbp_set_values).  Synchronises the context stream.
+ * Errors: NBP_ERR_INVALID, NBP_ERR_CUDA. */
+nbp_status nbp_vms_tangent(nbp_vms *vms, const double *vd, const double *v, const double *p, const double *vtau,
+                           double *a_val, double *b_val, double *c_val, double *d_val);
+
+typedef struct {
+    double tol_R, tol_A;      /* stopping rule ||R_(l)|| / ||R_(0)|| <= tol_R or ||R_(l)|| <= tol_A (1e-6 in Sec. 2.5) */
+    int32_t l_max;            /* corrector iterations (20 in Sec. 2.5) */
+    int32_t nts;              /* RK4 substeps of the outlet model per time step */
+} nbp_newton_opts;
+
+typedef struct {
+    int32_t iters;            /* tangent solves made */
+    int32_t converged;        /* the stopping rule was met */
+    int32_t unconverged_solves; /* nested solves that stopped at their iteration limit */
+    double res0, res;         /* ||R_(0)|| (at the predictor) and the last ||R|| */
+    int64_t outer_iters, A_iters, S_iters, I_iters;   /* summed over the solves */
+    double residual_s, tangent_s, setup_s, solve_s, total_s;   /* wall seconds per phase */
+} nbp_newton_info;
+
+/* One time step by the predictor multi-corrector of Sec. 2.5: predictor
+ * y = y_n, ydot = (gamma - 1) / gamma ydot_n; then per corrector l: outlet
+ * flows Q^k = a^k . v, the RCR step and m^k (Algorithm 1 and the difference
+ * quotient, as nbp_rcr_step; rcr->Q_n is ignored: Q_n is computed from y_n),
+ * the alpha stages, the residual with P_{n+alpha_f} = (1 - alpha_f) P_n +
+ * alpha_f P_{n+1} (P_n = R_p Q_n + Pi_n + P_d), the stopping rule, the
+ * tangent installed in the context with r_k = alpha_f gamma dt m^k, a new
+ * nbp_setup, the nested solve of [[A, B], [C, D]] dydot = -R with the
+ * context's options, and ydot += dydot, y += gamma dt dydot.  ||R_(0)|| is
+ * the residual at the predictor (reading).  y_n, yd_n: DEVICE 4N inputs;
+ * y, yd: DEVICE 4N outputs (distinct from the inputs); Pi_np1: DEVICE n_out
+ * (may be NULL): Pi^k at t_{n+1} from the accepted state.  rcr: the outlet
+ * parameters (DEVICE arrays, as nbp_rcr_step; may be NULL without outlets).
+ * The context's values and weights are left at the last tangent.  Returns
+ * NBP_OK when the stopping rule is met, NBP_NOT_CONVERGED after l_max
+ * corrector solves (y, yd hold the last iterate).  Errors: NBP_ERR_INVALID,
+ * NBP_ERR_NAN (non-finite residual or m^k), the nested solve's errors,
+ * NBP_ERR_CUDA. */
+nbp_status nbp_newton_step(nbp_vms *vms, const nbp_rcr *rcr, const double *y_n, const double *yd_n, double *y,
+                           double *yd, double *Pi_np1, const nbp_newton_opts *opts, nbp_newton_info *info);
+
 #ifdef __cplusplus
 }
 #endif

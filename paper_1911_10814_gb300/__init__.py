@@ -6,4 +6,4 @@ include/nbp.h); ``nbp`` is its ctypes binding and ``autograd`` the
 torch.autograd.Function around the solve and its adjoint.
 """
 from . import build  # noqa: F401
-from .nbp import BatchSolver, Solver, default_options, load, NbpError, rcr_step  # noqa: F401
+from .nbp import BatchSolver, Solver, Vms, default_options, load, NbpError, rcr_step  # noqa: F401

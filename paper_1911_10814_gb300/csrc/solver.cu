@@ -32,6 +32,7 @@
 #include "kernels.cuh"
 #include "spmv.cuh"
 #include "rcr.cuh"
+#include "vms.cuh"
 
 namespace nbp {
 
@@ -1709,5 +1710,431 @@ nbp_status nbp_batch_destroy(nbp_batch *B) {
 }
 
 const char *nbp_batch_last_error(const nbp_batch *B) { return B ? B->err.c_str() : "null batch"; }
+
+}  // extern "C"
+
+// ============================================ VMS assembly and Newton time step
+// The predictor multi-corrector of Sec. 2.5 around the nested solve: residual
+// and tangent assembled on the device (vms.cu), the RCR outlet coupling on the
+// device (rcr.cu), the tangent values installed in the context in place and
+// the preconditioner rebuilt for every corrector (the tangent changes).
+namespace nbp {
+
+constexpr int kNormBlocks = 1024;
+
+__global__ void k_sumsq_part(long long n, const double *x, double *part) {
+    __shared__ double sh[256];
+    double acc = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        acc += x[i] * x[i];
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+__global__ void k_sum_parts(int n, const double *part, double *out) {
+    __shared__ double sh[256];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) acc += part[i];
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = sh[0];
+}
+// predictor (Sec. 2.5): y = y_n, ydot = (gamma - 1) / gamma ydot_n
+__global__ void k_newton_predict(long long n, const double *y_n, const double *yd_n, double coef, double *y, double *yd) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        y[i] = y_n[i];
+        yd[i] = coef * yd_n[i];
+    }
+}
+// intermediate stages (Sec. 2.5 step 4)
+__global__ void k_newton_stage(long long n, const double *y_n, const double *yd_n, const double *y, const double *yd,
+                               double af, double am, double *yaf, double *ydam) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        yaf[i] = y_n[i] + af * (y[i] - y_n[i]);
+        ydam[i] = yd_n[i] + am * (yd[i] - yd_n[i]);
+    }
+}
+// update (Sec. 2.5 step 10) with the velocity increments of Dirichlet nodes set to zero
+__global__ void k_newton_update(int N, const uint8_t *dir, const double *dx, double gdt, double *y, double *yd) {
+    const long long n = 4LL * N;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const double d = (i < 3LL * N && dir[i / 3]) ? 0.0 : dx[i];
+        yd[i] += d;
+        y[i] += gdt * d;
+    }
+}
+__global__ void k_negate(long long n, const double *x, double *y) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        y[i] = -x[i];
+}
+// P^k_n = R_p Q_n + Pi_n + P_d (Algorithm 1's output relation at t_n)
+__global__ void k_outlet_pn(int n, const double *Rp, const double *Pi, const double *Pd, const double *Q, double *Pn) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) Pn[k] = Rp[k] * Q[k] + Pi[k] + Pd[k];
+}
+// P^k_{n+alpha_f} = (1 - alpha_f) P^k_n + alpha_f P^k_{n+1} (Sec. 2.5 step 5)
+__global__ void k_outlet_paf(int n, const double *Pn, const double *P1, double af, double *Paf) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) Paf[k] = (1.0 - af) * Pn[k] + af * P1[k];
+}
+
+// the value-derived copies of a matrix (precision copies, sliced-ELL layouts)
+static void drop_value_copies(DMat &m, cudaStream_t s) {
+    dfree(m.v32, s); dfree(m.v16, s);
+    dfree(m.sl_ptr, s); dfree(m.sl_ci, s); dfree(m.sl_v, s); dfree(m.sl_v32, s); dfree(m.sl_v16, s);
+    dfree(m.sl2_ptr, s); dfree(m.sl2_ci, s);
+    m.v32 = nullptr; m.v16 = nullptr;
+    m.sl_ptr = nullptr; m.sl_ci = nullptr; m.sl_v = nullptr; m.sl_v32 = nullptr; m.sl_v16 = nullptr;
+    m.sl2_ptr = nullptr; m.sl2_ci = nullptr;
+}
+
+// new values of A, B, C, D are in place: everything built from them is stale
+static void values_changed(nbp_ctx *c) {
+    for (DMat *M : {&c->A, &c->B, &c->C, &c->D}) drop_value_copies(*M, c->s);
+    drop_graphs(c);
+    c->setup_done = false;
+    if (c->tctx) {
+        destroy_ctx(c->tctx);
+        c->tctx = nullptr;
+    }
+}
+
+static double norm2(const double *x, long long n, double *part, cudaStream_t s) {
+    k_sumsq_part<<<kNormBlocks, 256, 0, s>>>(n, x, part);
+    k_sum_parts<<<1, 256, 0, s>>>(kNormBlocks, part, part + kNormBlocks);
+    NBP_LAUNCHED();
+    return std::sqrt(readback(part + kNormBlocks, s));
+}
+
+}  // namespace nbp
+
+struct nbp_vms {
+    nbp_ctx *ctx = nullptr;
+    nbp::VmsDev m;
+    nbp::VmsConst k;
+    double *yaf = nullptr, *ydam = nullptr, *R = nullptr, *dx = nullptr, *rhs = nullptr;   // 4N each
+    double *ob = nullptr;        // outlet scratch: Q_n, Q, P_n, P, Pi, m, r, P_af (8 n_out)
+    int *bad = nullptr;
+    double *part = nullptr;      // norm partials
+};
+
+#define VMS_BEGIN(v)                     \
+    if (!(v) || !(v)->ctx) return NBP_ERR_INVALID; \
+    nbp_ctx *c = (v)->ctx;               \
+    try {
+#define VMS_END NBP_API_END(c)
+
+namespace nbp {
+
+static void vms_free(nbp_vms *v) {
+    if (!v) return;
+    cudaStream_t s = v->ctx ? v->ctx->s : nullptr;
+    VmsDev &m = v->m;
+    for (void *p : {(void *)m.X, (void *)m.tets, (void *)m.tris, (void *)m.dir, (void *)m.n2t_ptr, (void *)m.n2t,
+                    (void *)m.n2f_ptr, (void *)m.n2f, (void *)m.sl_ptr, (void *)m.sl_src, (void *)m.fl_ptr,
+                    (void *)m.fl_src, (void *)m.slot_row, (void *)m.Re, (void *)m.Rf, m.Ke, m.Kf, (void *)v->yaf,
+                    (void *)v->ydam, (void *)v->R, (void *)v->dx, (void *)v->rhs, (void *)v->ob, (void *)v->bad,
+                    (void *)v->part})
+        dfree(p, s);
+    if (s) cudaStreamSynchronize(s);
+    delete v;
+}
+
+template <typename T> static T *upload(const std::vector<T> &h, cudaStream_t s) {
+    T *d = dmalloc<T>(h.size(), s);
+    if (!h.empty()) NBP_CUDA(cudaMemcpyAsync(d, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice, s));
+    return d;
+}
+
+// CSR of (node -> local incidences) in ascending element order: entries w e + la
+static void incidence(int N, int E, int w, const int32_t *el, std::vector<int> &ptr, std::vector<int> &idx) {
+    ptr.assign(N + 1, 0);
+    for (long long q = 0; q < (long long)E * w; ++q) ptr[el[q] + 1]++;
+    for (int A = 0; A < N; ++A) ptr[A + 1] += ptr[A];
+    idx.resize((size_t)E * w);
+    std::vector<int> pos(ptr.begin(), ptr.end() - 1);
+    for (int e = 0; e < E; ++e)
+        for (int a = 0; a < w; ++a) idx[pos[el[(size_t)e * w + a]]++] = w * e + a;
+}
+
+// CSR of (pattern slot -> element blocks), ascending element order: entries
+// w^2 e + w la + lb for every local pair (la, lb) of every element
+static void slot_map(int N, const std::vector<int> &rp, const std::vector<int> &ci, int E, int w, const int32_t *el,
+                     std::vector<int> &ptr, std::vector<int> &src) {
+    const long long nnz = rp[N];
+    std::vector<int> slot((size_t)E * w * w);
+    ptr.assign(nnz + 1, 0);
+    for (int e = 0; e < E; ++e)
+        for (int a = 0; a < w; ++a) {
+            const int A = el[(size_t)e * w + a];
+            for (int b = 0; b < w; ++b) {
+                const int B = el[(size_t)e * w + b];
+                const int *lo = ci.data() + rp[A], *hi = ci.data() + rp[A + 1];
+                const int *f = std::lower_bound(lo, hi, B);
+                require(f != hi && *f == B, NBP_ERR_INVALID,
+                        "nbp_vms_create: an element couples two nodes absent from the solver's pattern");
+                const int sl = (int)(f - ci.data());
+                slot[((size_t)e * w + a) * w + b] = sl;
+                ptr[sl + 1]++;
+            }
+        }
+    for (long long q = 0; q < nnz; ++q) ptr[q + 1] += ptr[q];
+    src.resize((size_t)E * w * w);
+    std::vector<int> pos(ptr.begin(), ptr.end() - 1);
+    for (int e = 0; e < E; ++e)
+        for (int a = 0; a < w; ++a)
+            for (int b = 0; b < w; ++b) src[pos[slot[((size_t)e * w + a) * w + b]]++] = w * w * e + w * a + b;
+}
+
+static void vms_buffers(nbp_vms *v) {
+    if (v->yaf) return;
+    nbp_ctx *c = v->ctx;
+    const long long n = 4LL * c->N;
+    v->yaf = dmalloc<double>(n, c->s);
+    v->ydam = dmalloc<double>(n, c->s);
+    v->R = dmalloc<double>(n, c->s);
+    v->dx = dmalloc<double>(n, c->s);
+    v->rhs = dmalloc<double>(n, c->s);
+    v->ob = dmalloc<double>(8LL * std::max(c->lr.n_out, 1), c->s);
+    v->bad = dmalloc<int>(1, c->s);
+}
+
+static void vms_residual_ctx(nbp_vms *v, const double *vd, const double *vel, const double *p, const double *vtau,
+                             const double *P, double *R) {
+    nbp_ctx *c = v->ctx;
+    const LowRank &lr = c->lr;
+    vms_residual(v->m, v->k, vd, vel, p, vtau, lr.n_out, lr.lr_rp, lr.lr_k, lr.lr_c, lr.lr_val, P, R, c->s);
+}
+
+}  // namespace nbp
+
+extern "C" {
+
+nbp_status nbp_set_values(nbp_ctx *c, const double *a_val, const double *b_val, const double *c_val,
+                          const double *d_val) {
+    NBP_API_BEGIN(c)
+    begin_call(c);
+    require(a_val && b_val && c_val && d_val, NBP_ERR_INVALID, "nbp_set_values: null array");
+    const DMat *M[4] = {&c->A, &c->B, &c->C, &c->D};
+    const double *src[4] = {a_val, b_val, c_val, d_val};
+    int *bad = dmalloc<int>(1, c->s);
+    NBP_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), c->s));
+    for (int q = 0; q < 4; ++q) {
+        const long long nv = M[q]->nnz * M[q]->bb();
+        if (nv == 0) continue;
+        k_finite<<<grid_for(nv), 256, 0, c->s>>>(src[q], nv, bad);
+        NBP_LAUNCHED();
+    }
+    const int b = readback(bad, c->s);
+    dfree(bad, c->s);
+    require(b == 0, NBP_ERR_INVALID, "nbp_set_values: non-finite value");
+    for (int q = 0; q < 4; ++q) {
+        const long long nv = M[q]->nnz * M[q]->bb();
+        if (nv) NBP_CUDA(cudaMemcpyAsync(M[q]->v, src[q], sizeof(double) * nv, cudaMemcpyDeviceToDevice, c->s));
+    }
+    values_changed(c);
+    NBP_CUDA(cudaStreamSynchronize(c->s));
+    return NBP_OK;
+    NBP_API_END(c)
+}
+
+nbp_status nbp_vms_create(nbp_vms **out, nbp_ctx *c, const nbp_mesh *mesh, const nbp_vms_params *par) {
+    if (!out) return NBP_ERR_INVALID;
+    *out = nullptr;
+    NBP_API_BEGIN(c)
+    begin_call(c);
+    require(mesh && par, NBP_ERR_INVALID, "nbp_vms_create: null argument");
+    require(mesh->n_nodes == c->N, NBP_ERR_INVALID, "nbp_vms_create: mesh and context node counts differ");
+    require(mesh->n_tets >= 0 && mesh->n_tris >= 0, NBP_ERR_INVALID, "nbp_vms_create: negative element count");
+    require(mesh->X && mesh->dir && (mesh->tets || mesh->n_tets == 0) && (mesh->tris || mesh->n_tris == 0),
+            NBP_ERR_INVALID, "nbp_vms_create: null mesh array");
+    require(par->rho > 0 && par->mu > 0 && par->dt > 0 && par->rho_inf >= 0 && par->rho_inf <= 1 && par->beta >= 0 &&
+                par->CI > 0 && par->CT > 0,
+            NBP_ERR_INVALID, "nbp_vms_create: bad physical parameters");
+    const int N = c->N, E = mesh->n_tets, T = mesh->n_tris;
+    for (long long q = 0; q < 4LL * E; ++q)
+        require(mesh->tets[q] >= 0 && mesh->tets[q] < N, NBP_ERR_INVALID, "nbp_vms_create: tet node out of range");
+    for (long long q = 0; q < 3LL * T; ++q)
+        require(mesh->tris[q] >= 0 && mesh->tris[q] < N, NBP_ERR_INVALID, "nbp_vms_create: triangle node out of range");
+    std::unique_ptr<nbp_vms, void (*)(nbp_vms *)> v(new nbp_vms(), vms_free);
+    v->ctx = c;
+    cudaStream_t s = c->s;
+    // the solver's (shared) pattern on the host
+    const long long nnz = c->A.nnz;
+    require(c->B.nnz == nnz && c->C.nnz == nnz && c->D.nnz == nnz, NBP_ERR_INVALID,
+            "nbp_vms_create: A, B, C, D must share one pattern");
+    std::vector<int> rp(N + 1), ci(nnz);
+    NBP_CUDA(cudaMemcpyAsync(rp.data(), c->A.rp, sizeof(int) * (N + 1), cudaMemcpyDeviceToHost, s));
+    NBP_CUDA(cudaMemcpyAsync(ci.data(), c->A.ci, sizeof(int) * nnz, cudaMemcpyDeviceToHost, s));
+    NBP_CUDA(cudaStreamSynchronize(s));
+    std::vector<int> n2t_ptr, n2t, n2f_ptr, n2f, sl_ptr, sl_src, fl_ptr, fl_src, slot_row(nnz);
+    incidence(N, E, 4, mesh->tets, n2t_ptr, n2t);
+    incidence(N, T, 3, mesh->tris, n2f_ptr, n2f);
+    slot_map(N, rp, ci, E, 4, mesh->tets, sl_ptr, sl_src);
+    slot_map(N, rp, ci, T, 3, mesh->tris, fl_ptr, fl_src);
+    for (int A = 0; A < N; ++A)
+        for (int q = rp[A]; q < rp[A + 1]; ++q) slot_row[q] = A;
+    VmsDev &m = v->m;
+    m.N = N; m.E = E; m.T = T; m.nnz = nnz;
+    m.X = upload(std::vector<double>(mesh->X, mesh->X + 3LL * N), s);
+    m.tets = upload(std::vector<int>(mesh->tets, mesh->tets + 4LL * E), s);
+    m.tris = upload(std::vector<int>(mesh->tris, mesh->tris + 3LL * T), s);
+    m.dir = upload(std::vector<uint8_t>(mesh->dir, mesh->dir + N), s);
+    m.n2t_ptr = upload(n2t_ptr, s); m.n2t = upload(n2t, s);
+    m.n2f_ptr = upload(n2f_ptr, s); m.n2f = upload(n2f, s);
+    m.sl_ptr = upload(sl_ptr, s); m.sl_src = upload(sl_src, s);
+    m.fl_ptr = upload(fl_ptr, s); m.fl_src = upload(fl_src, s);
+    m.slot_row = upload(slot_row, s);
+    m.col = c->A.ci;
+    m.tangent_fp32 = par->tangent_fp32 ? 1 : 0;
+    const size_t tb = m.tangent_fp32 ? sizeof(float) : sizeof(double);
+    m.Re = dmalloc<double>(16LL * std::max(E, 1), s);
+    m.Rf = dmalloc<double>(9LL * std::max(T, 1), s);
+    m.Ke = dmalloc<char>(256LL * std::max(E, 1) * tb, s);
+    m.Kf = dmalloc<char>(81LL * std::max(T, 1) * tb, s);
+    v->part = dmalloc<double>(kNormBlocks + 1, s);
+    VmsConst &k = v->k;
+    k.rho = par->rho; k.mu = par->mu; k.dt = par->dt; k.beta = par->beta; k.CI = par->CI; k.CT = par->CT;
+    k.am = 0.5 * (3.0 - par->rho_inf) / (1.0 + par->rho_inf);
+    k.af = 1.0 / (1.0 + par->rho_inf);
+    k.gm = 1.0 / (1.0 + par->rho_inf);
+    k.c = k.af * k.gm * par->dt;
+    NBP_CUDA(cudaStreamSynchronize(s));
+    *out = v.release();
+    return NBP_OK;
+    NBP_API_END(c)
+}
+
+nbp_status nbp_vms_destroy(nbp_vms *v) {
+    if (!v) return NBP_ERR_INVALID;
+    if (v->ctx) cudaSetDevice(v->ctx->dev);
+    vms_free(v);
+    return NBP_OK;
+}
+
+nbp_status nbp_vms_residual(nbp_vms *v, const double *vd, const double *vel, const double *p, const double *vtau,
+                            const double *P, double *R) {
+    VMS_BEGIN(v)
+    begin_call(c);
+    require(vd && vel && p && R && (P || c->lr.n_out == 0), NBP_ERR_INVALID, "nbp_vms_residual: null array");
+    vms_residual_ctx(v, vd, vel, p, vtau, P, R);
+    NBP_CUDA(cudaStreamSynchronize(c->s));
+    return NBP_OK;
+    VMS_END
+}
+
+nbp_status nbp_vms_tangent(nbp_vms *v, const double *vd, const double *vel, const double *p, const double *vtau,
+                           double *a_val, double *b_val, double *c_val, double *d_val) {
+    VMS_BEGIN(v)
+    begin_call(c);
+    require(vd && vel && p && a_val && b_val && c_val && d_val, NBP_ERR_INVALID, "nbp_vms_tangent: null array");
+    vms_tangent(v->m, v->k, vd, vel, p, vtau, a_val, b_val, c_val, d_val, c->s);
+    NBP_CUDA(cudaStreamSynchronize(c->s));
+    return NBP_OK;
+    VMS_END
+}
+
+nbp_status nbp_newton_step(nbp_vms *v, const nbp_rcr *rcr, const double *y_n, const double *yd_n, double *y,
+                           double *yd, double *Pi_np1, const nbp_newton_opts *o, nbp_newton_info *info) {
+    VMS_BEGIN(v)
+    begin_call(c);
+    using clk = std::chrono::steady_clock;
+    const auto t_all = clk::now();
+    require(y_n && yd_n && y && yd && o, NBP_ERR_INVALID, "nbp_newton_step: null argument");
+    require(o->l_max >= 1 && o->nts >= 1 && o->tol_R >= 0 && o->tol_A >= 0, NBP_ERR_INVALID,
+            "nbp_newton_step: bad options");
+    const int n_out = c->lr.n_out;
+    nbp_rcr chk{};
+    if (rcr) {
+        chk = *rcr;
+        chk.Q_n = chk.Rp;   // Q_n is computed here from y_n, not read
+    }
+    require(n_out == 0 || (rcr && rcr_params_ok(&chk)), NBP_ERR_INVALID, "nbp_newton_step: RCR parameters missing");
+    vms_buffers(v);
+    cudaStream_t s = c->s;
+    const int N = c->N;
+    const long long n = 4LL * N;
+    const VmsConst &k = v->k;
+    double *Qn = v->ob, *Q1 = v->ob + n_out, *Pn = v->ob + 2 * n_out, *P1 = v->ob + 3 * n_out;
+    double *Pi1 = v->ob + 4 * n_out, *mk = v->ob + 5 * n_out, *rnew = v->ob + 6 * n_out, *Paf = v->ob + 7 * n_out;
+    nbp_newton_info inf{};
+    k_newton_predict<<<grid_for(n), 256, 0, s>>>(n, y_n, yd_n, (k.gm - 1.0) / k.gm, y, yd);
+    NBP_LAUNCHED();
+    nbp_rcr rl{};
+    if (n_out) {
+        rl = *rcr;
+        rl.Q_n = Qn;
+        launch_outlet_flows(n_out, c->lr.optr, c->lr.oidx, c->lr.oval, y_n, Qn, s);
+        k_outlet_pn<<<(n_out + 127) / 128, 128, 0, s>>>(n_out, rcr->Rp, rcr->Pi_n, rcr->Pd, Qn, Pn);
+        NBP_LAUNCHED();
+    }
+    double r0 = -1.0;
+    for (int l = 1; l <= o->l_max; ++l) {
+        auto t0 = clk::now();
+        if (n_out) {                                                                      // steps 1-3
+            NBP_CUDA(cudaMemsetAsync(v->bad, 0, sizeof(int), s));
+            launch_outlet_flows(n_out, c->lr.optr, c->lr.oidx, c->lr.oval, y, Q1, s);
+            launch_rcr_step(n_out, rl, Q1, k.dt, o->nts, P1, Pi1, mk, rnew, k.c, v->bad, s);
+            k_outlet_paf<<<(n_out + 127) / 128, 128, 0, s>>>(n_out, Pn, P1, k.af, Paf);   // step 5
+            NBP_LAUNCHED();
+        }
+        k_newton_stage<<<grid_for(n), 256, 0, s>>>(n, y_n, yd_n, y, yd, k.af, k.am, v->yaf, v->ydam);   // step 4
+        NBP_LAUNCHED();
+        vms_residual_ctx(v, v->ydam, v->yaf, v->yaf + 3LL * N, nullptr, n_out ? Paf : nullptr, v->R);   // step 6
+        const double nr = norm2(v->R, n, v->part, s);
+        inf.residual_s += std::chrono::duration<double>(clk::now() - t0).count();
+        require(std::isfinite(nr), NBP_ERR_NAN, "nbp_newton_step: non-finite residual");
+        if (r0 < 0) r0 = nr;
+        inf.res0 = r0;
+        inf.res = nr;
+        if ((r0 > 0 && nr / r0 <= o->tol_R) || nr <= o->tol_A) { inf.converged = 1; break; }   // step 7
+        t0 = clk::now();
+        vms_tangent(v->m, k, v->ydam, v->yaf, v->yaf + 3LL * N, nullptr, c->A.v, c->B.v, c->C.v, c->D.v, s);   // step 8
+        values_changed(c);
+        if (n_out) {
+            int bad = readback(v->bad, s);
+            require(!bad, NBP_ERR_NAN, "nbp_newton_step: non-finite outlet stiffness m^k");
+            std::vector<double> r(n_out);
+            NBP_CUDA(cudaMemcpyAsync(c->lr.r, rnew, sizeof(double) * n_out, cudaMemcpyDeviceToDevice, s));
+            NBP_CUDA(cudaMemcpyAsync(r.data(), rnew, sizeof(double) * n_out, cudaMemcpyDeviceToHost, s));
+            NBP_CUDA(cudaStreamSynchronize(s));
+            c->lr.r_host = r;
+        }
+        NBP_CUDA(cudaStreamSynchronize(s));
+        inf.tangent_s += std::chrono::duration<double>(clk::now() - t0).count();
+        t0 = clk::now();
+        do_setup(c);
+        inf.setup_s += std::chrono::duration<double>(clk::now() - t0).count();
+        t0 = clk::now();
+        k_negate<<<grid_for(n), 256, 0, s>>>(n, v->R, v->rhs);
+        NBP_LAUNCHED();
+        nbp_info si{};
+        const nbp_status st = solve_common(c, v->rhs, v->dx, nullptr, &si);   // step 9
+        require(st == NBP_OK || st == NBP_NOT_CONVERGED, st, "nbp_newton_step: nested solve failed");
+        inf.unconverged_solves += (st != NBP_OK);
+        inf.outer_iters += si.outer_iters;
+        inf.A_iters += si.A_iters;
+        inf.S_iters += si.S_iters;
+        inf.I_iters += si.I_iters;
+        k_newton_update<<<grid_for(n), 256, 0, s>>>(N, v->m.dir, v->dx, k.gm * k.dt, y, yd);   // step 10
+        NBP_LAUNCHED();
+        inf.iters = l;
+        inf.solve_s += std::chrono::duration<double>(clk::now() - t0).count();
+    }
+    if (Pi_np1 && n_out) NBP_CUDA(cudaMemcpyAsync(Pi_np1, Pi1, sizeof(double) * n_out, cudaMemcpyDeviceToDevice, s));
+    NBP_CUDA(cudaStreamSynchronize(s));
+    inf.total_s = std::chrono::duration<double>(clk::now() - t_all).count();
+    if (info) *info = inf;
+    return inf.converged ? NBP_OK : NBP_NOT_CONVERGED;
+    VMS_END
+}
 
 }  // extern "C"

@@ -76,6 +76,33 @@ class nbp_rcr(ctypes.Structure):
                 ("eps_rel", ctypes.c_double)]
 
 
+class nbp_mesh(ctypes.Structure):
+    _fields_ = [("n_nodes", ctypes.c_int32), ("n_tets", ctypes.c_int32), ("n_tris", ctypes.c_int32),
+                ("X", ctypes.c_void_p), ("tets", ctypes.c_void_p), ("tris", ctypes.c_void_p), ("dir", ctypes.c_void_p)]
+
+
+class nbp_vms_params(ctypes.Structure):
+    _fields_ = [("rho", ctypes.c_double), ("mu", ctypes.c_double), ("dt", ctypes.c_double),
+                ("rho_inf", ctypes.c_double), ("beta", ctypes.c_double), ("CI", ctypes.c_double),
+                ("CT", ctypes.c_double), ("tangent_fp32", ctypes.c_int32)]
+
+
+class nbp_newton_opts(ctypes.Structure):
+    _fields_ = [("tol_R", ctypes.c_double), ("tol_A", ctypes.c_double), ("l_max", ctypes.c_int32),
+                ("nts", ctypes.c_int32)]
+
+
+class nbp_newton_info(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("converged", ctypes.c_int32), ("unconverged_solves", ctypes.c_int32),
+                ("res0", ctypes.c_double), ("res", ctypes.c_double),
+                ("outer_iters", ctypes.c_int64), ("A_iters", ctypes.c_int64), ("S_iters", ctypes.c_int64),
+                ("I_iters", ctypes.c_int64), ("residual_s", ctypes.c_double), ("tangent_s", ctypes.c_double),
+                ("setup_s", ctypes.c_double), ("solve_s", ctypes.c_double), ("total_s", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 STATUS = {0: "NBP_OK", 1: "NBP_ERR_INVALID", 2: "NBP_ERR_CUDA", 3: "NBP_ERR_OOM", 4: "NBP_NOT_CONVERGED",
           5: "NBP_ERR_BREAKDOWN", 6: "NBP_ERR_NAN", 7: "NBP_ERR_TIMEOUT", 8: "NBP_ERR_STATE"}
 
@@ -115,6 +142,13 @@ SIGNATURES = {
     "nbp_rcr_step": (ctypes.c_int, [_i32, ctypes.POINTER(nbp_rcr), _vp, _d, _i32, _vp, _vp, _vp, _vp]),
     "nbp_outlet_flows": (ctypes.c_int, [_vp, _vp, _vp]),
     "nbp_rcr_update": (ctypes.c_int, [_vp, ctypes.POINTER(nbp_rcr), _vp, _d, _i32, _d, _vp, _vp, _vp, _vp]),
+    "nbp_set_values": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "nbp_vms_create": (ctypes.c_int, [ctypes.POINTER(_vp), _vp, ctypes.POINTER(nbp_mesh), ctypes.POINTER(nbp_vms_params)]),
+    "nbp_vms_destroy": (ctypes.c_int, [_vp]),
+    "nbp_vms_residual": (ctypes.c_int, [_vp] * 7),
+    "nbp_vms_tangent": (ctypes.c_int, [_vp] * 9),
+    "nbp_newton_step": (ctypes.c_int, [_vp, ctypes.POINTER(nbp_rcr), _vp, _vp, _vp, _vp, _vp,
+                                       ctypes.POINTER(nbp_newton_opts), ctypes.POINTER(nbp_newton_info)]),
 }
 
 
@@ -459,6 +493,11 @@ class Solver:
                                              _ptr(out["Q"]), _ptr(out["P"]), _ptr(out["Pi"]), _ptr(out["m"])))
         return out
 
+    def set_values(self, A, B, C, D):
+        """New tangent values (CUDA float64 tensors on the context's pattern,
+        9, 3, 3, 1 per entry); call setup() again before solving."""
+        self._check(self.lib.nbp_set_values(self.ctx, _ptr(A), _ptr(B), _ptr(C), _ptr(D)))
+
     def profile(self, enable=True):
         self._check(self.lib.nbp_profile(self.ctx, int(enable)))
 
@@ -470,3 +509,68 @@ class Solver:
     def profile_report(self):
         import json
         return json.loads(self.lib.nbp_profile_report(self.ctx).decode())
+
+
+class Vms:
+    """On-device VMS residual, tangent and Newton time step bound to a Solver
+    (nbp_vms_*, Sec. 2.3-2.5).  mesh: dict X (N,3), tets (E,4), tris (T,3),
+    dir (N,) as host numpy arrays.  Close it before the Solver."""
+
+    def __init__(self, solver: "Solver", mesh: dict, rho, mu, dt, rho_inf, beta=0.2, CI=36.0, CT=4.0,
+                 tangent_fp32=True):
+        self.s = solver
+        self.lib = solver.lib
+        self.N = solver.N
+        X = np.ascontiguousarray(mesh["X"], dtype=np.float64)
+        tets = np.ascontiguousarray(mesh["tets"], dtype=np.int32)
+        tris = np.ascontiguousarray(mesh["tris"], dtype=np.int32).reshape(-1, 3)
+        dirn = np.ascontiguousarray(mesh["dir"], dtype=np.uint8)
+        m = nbp_mesh(self.N, len(tets), len(tris), X.ctypes.data, tets.ctypes.data,
+                     tris.ctypes.data if len(tris) else None, dirn.ctypes.data)
+        par = nbp_vms_params(rho, mu, dt, rho_inf, beta, CI, CT, 1 if tangent_fp32 else 0)
+        h = ctypes.c_void_p()
+        solver._check(self.lib.nbp_vms_create(ctypes.byref(h), solver.ctx, ctypes.byref(m), ctypes.byref(par)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.nbp_vms_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def residual(self, vd, v, p, P=None, vtau=None):
+        """R (4N) at vdot_{n+alpha_m}, v_{n+alpha_f}, p_{n+alpha_f}; P the outlet pressures."""
+        R = self.s.zeros(4 * self.N)
+        self.s._check(self.lib.nbp_vms_residual(self.h, _ptr(vd), _ptr(v), _ptr(p), _ptr(vtau) if vtau is not None else None,
+                                                 _ptr(P) if P is not None else None, _ptr(R)))
+        return R
+
+    def tangent(self, vd, v, p, nnz, vtau=None):
+        """Tangent values (A 9 nnz, B 3 nnz, C 3 nnz, D nnz) at the same state."""
+        out = {k: self.s.zeros(w * nnz) for k, w in (("A", 9), ("B", 3), ("C", 3), ("D", 1))}
+        self.s._check(self.lib.nbp_vms_tangent(self.h, _ptr(vd), _ptr(v), _ptr(p),
+                                                _ptr(vtau) if vtau is not None else None,
+                                                _ptr(out["A"]), _ptr(out["B"]), _ptr(out["C"]), _ptr(out["D"])))
+        return out
+
+    def newton_step(self, y_n, yd_n, rcr: dict = None, tol_R=1e-6, tol_A=1e-6, l_max=20, nts=10, eps_abs=1e-8,
+                    eps_rel=1e-5, allow_not_converged=False):
+        """One predictor multi-corrector time step (nbp_newton_step).  rcr:
+        CUDA float64 tensors Rp, C, Rd, Pd, Pi (Pi^k_n).  Returns (y, ydot, Pi_np1, info)."""
+        y = self.s.zeros(4 * self.N)
+        yd = self.s.zeros(4 * self.N)
+        Pi = self.s.zeros(max(self.s.n_out, 1))
+        p = None
+        if rcr is not None:
+            p = rcr_params(rcr["Rp"], rcr["C"], rcr["Rd"], rcr["Pd"], rcr["Pi"], rcr["Pi"], eps_abs, eps_rel)
+        o = nbp_newton_opts(tol_R, tol_A, l_max, nts)
+        info = nbp_newton_info()
+        st = self.lib.nbp_newton_step(self.h, ctypes.byref(p) if p is not None else None, _ptr(y_n), _ptr(yd_n),
+                                      _ptr(y), _ptr(yd), _ptr(Pi), ctypes.byref(o), ctypes.byref(info))
+        self.s._check(st, (0, 4) if allow_not_converged else (0,))
+        return y, yd, Pi[:self.s.n_out], info.as_dict()
