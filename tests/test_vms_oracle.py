@@ -207,3 +207,29 @@ def test_newton_step_update_identity_and_convergence(small):
     # Dirichlet velocities keep their prescribed values
     dm = np.repeat(m["dir"] == 1, 3)
     assert np.array_equal(out["y"][:3 * N][dm], y_n[:3 * N][dm])
+
+
+def test_newton_quadratic_from_consistent_start():
+    """From a consistent start (outlet model at rest, uniform pressure equal
+    to the outlet pressure, smooth Poiseuille velocity) each corrector
+    roughly squares the relative residual, as Newton's method with the
+    exact Jacobian of the residual does (tau held fixed: it moves little
+    between correctors here), over successive time steps."""
+    sp = synth.MeshSpec(4, 4, 12, Lz=3.0, Re=500.0, seed=2, R=(1e3,) * 4, pert=0.0, name="box4x4x12_eq")
+    d, m, ph = synth.generate(sp), synth.mesh(sp), oracle.vms_phys(sp)
+    N = d["n_nodes"]
+    R = np.asarray(sp.R)
+    Q0 = oracle.outlet_flows(d, d["vel"])
+    rc = dict(Rp=0.1 * R, Rd=0.9 * R, C=0.1 / R, Pd=np.zeros(4), Pi=0.9 * R * Q0, nts=10)
+    y = np.concatenate([d["vel"], np.full(N, float(np.mean(R * Q0)))])
+    yd = np.zeros(4 * N)
+    for _ in range(3):
+        out = oracle.newton_step(m, d, ph, y, yd, rc, tol_R=1e-9, tol_A=1e-14, rtol=1e-12)
+        res = np.asarray(out["res"])
+        assert 2 <= out["iters"] <= 4
+        rate = res[1:] / res[:-1]
+        # a linearly convergent iteration keeps its rate; Newton's rate falls
+        # with the residual itself (here by 1e-3 or more per corrector)
+        for a, b in zip(rate[:-1], rate[1:]):
+            assert b <= 1e-2 * a
+        y, yd, rc = out["y"], out["yd"], dict(rc, Pi=out["Pi"])
