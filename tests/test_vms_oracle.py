@@ -229,7 +229,8 @@ def test_newton_quadratic_from_consistent_start():
         assert 2 <= out["iters"] <= 4
         rate = res[1:] / res[:-1]
         # a linearly convergent iteration keeps its rate; Newton's rate falls
-        # with the residual itself (here by 1e-3 or more per corrector)
+        # with the residual itself (rate_{l+1} ~ K res_l / res_0; here by about
+        # 1e-2 per corrector): at least tenfold
         for a, b in zip(rate[:-1], rate[1:]):
-            assert b <= 1e-2 * a
+            assert b <= 0.1 * a
         y, yd, rc = out["y"], out["yd"], dict(rc, Pi=out["Pi"])
