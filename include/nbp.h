@@ -370,6 +370,18 @@ typedef struct {
  * the context.  Errors: NBP_ERR_INVALID (sizes, node ids, parameters, a pair
  * absent from the pattern), NBP_ERR_OOM, NBP_ERR_CUDA. */
 nbp_status nbp_vms_create(nbp_vms **vms, nbp_ctx *ctx, const nbp_mesh *mesh, const nbp_vms_params *par);
+
+/* The host step of nbp_vms_create, on HOST arrays and without any device
+ * work: for n_el elements of w = 4 (tets) or 3 (triangles) nodes each (el),
+ * inc_ptr (n_nodes + 1) / inc (w n_el) list for every node the entries
+ * w e + a of the elements e having it as local node a, ascending e; and
+ * slot_ptr (nnz + 1) / slot_src (w^2 n_el) list for every pattern slot
+ * (row A, column B of rowptr/col) the entries w^2 e + w a + b with
+ * el[e][a] = A and el[e][b] = B, ascending e.  No paper counterpart (the
+ * deterministic assembly order).  Errors: NBP_ERR_INVALID (bad arguments, a
+ * node id out of range, a pair absent from the pattern), NBP_ERR_OOM. */
+nbp_status nbp_vms_maps(int32_t n_nodes, const int32_t *rowptr, const int32_t *col, int32_t n_el, int32_t w,
+                        const int32_t *el, int32_t *inc_ptr, int32_t *inc, int32_t *slot_ptr, int32_t *slot_src);
 nbp_status nbp_vms_destroy(nbp_vms *vms);
 
 /* R (DEVICE, 4N) at vd = vdot_{n+alpha_m} (3N), v = v_{n+alpha_f} (3N),

@@ -1946,6 +1946,30 @@ nbp_status nbp_set_values(nbp_ctx *c, const double *a_val, const double *b_val, 
     NBP_API_END(c)
 }
 
+nbp_status nbp_vms_maps(int32_t n_nodes, const int32_t *rowptr, const int32_t *col, int32_t n_el, int32_t w,
+                        const int32_t *el, int32_t *inc_ptr, int32_t *inc, int32_t *slot_ptr, int32_t *slot_src) {
+    try {
+        require(n_nodes >= 0 && n_el >= 0 && (w == 3 || w == 4) && rowptr && col && (el || n_el == 0) && inc_ptr &&
+                    inc && slot_ptr && slot_src,
+                NBP_ERR_INVALID, "nbp_vms_maps: bad arguments");
+        for (long long q = 0; q < (long long)n_el * w; ++q)
+            require(el[q] >= 0 && el[q] < n_nodes, NBP_ERR_INVALID, "nbp_vms_maps: node id out of range");
+        const long long nnz = rowptr[n_nodes];
+        std::vector<int> rp(rowptr, rowptr + n_nodes + 1), ci(col, col + nnz), ip, ix, sp, ss;
+        incidence(n_nodes, n_el, w, el, ip, ix);
+        slot_map(n_nodes, rp, ci, n_el, w, el, sp, ss);
+        std::copy(ip.begin(), ip.end(), inc_ptr);
+        std::copy(ix.begin(), ix.end(), inc);
+        std::copy(sp.begin(), sp.end(), slot_ptr);
+        std::copy(ss.begin(), ss.end(), slot_src);
+        return NBP_OK;
+    } catch (const nbp::Error &e) {
+        return e.st;
+    } catch (const std::exception &) {
+        return NBP_ERR_OOM;
+    }
+}
+
 nbp_status nbp_vms_create(nbp_vms **out, nbp_ctx *c, const nbp_mesh *mesh, const nbp_vms_params *par) {
     if (!out) return NBP_ERR_INVALID;
     *out = nullptr;

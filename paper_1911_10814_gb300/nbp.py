@@ -145,6 +145,7 @@ SIGNATURES = {
     "nbp_set_values": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "nbp_vms_create": (ctypes.c_int, [ctypes.POINTER(_vp), _vp, ctypes.POINTER(nbp_mesh), ctypes.POINTER(nbp_vms_params)]),
     "nbp_vms_destroy": (ctypes.c_int, [_vp]),
+    "nbp_vms_maps": (ctypes.c_int, [_i32, _vp, _vp, _i32, _i32, _vp, _vp, _vp, _vp, _vp]),
     "nbp_vms_residual": (ctypes.c_int, [_vp] * 7),
     "nbp_vms_tangent": (ctypes.c_int, [_vp] * 9),
     "nbp_newton_step": (ctypes.c_int, [_vp, ctypes.POINTER(nbp_rcr), _vp, _vp, _vp, _vp, _vp,
