@@ -368,7 +368,9 @@ typedef struct {
  * slot -> element blocks, ascending element order) are built on the host
  * once.  The handle uses the context's stream and must be destroyed before
  * the context.  Errors: NBP_ERR_INVALID (sizes, node ids, parameters, a pair
- * absent from the pattern), NBP_ERR_OOM, NBP_ERR_CUDA. */
+ * absent from the pattern, a degenerate element: |det| of a tet at most 1e-12
+ * of its longest edge cubed, twice the area of a triangle at most 1e-12 of
+ * its longest edge squared), NBP_ERR_OOM, NBP_ERR_CUDA. */
 nbp_status nbp_vms_create(nbp_vms **vms, nbp_ctx *ctx, const nbp_mesh *mesh, const nbp_vms_params *par);
 
 /* The host step of nbp_vms_create, on HOST arrays and without any device

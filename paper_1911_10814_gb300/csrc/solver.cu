@@ -1988,6 +1988,43 @@ nbp_status nbp_vms_create(nbp_vms **out, nbp_ctx *c, const nbp_mesh *mesh, const
         require(mesh->tets[q] >= 0 && mesh->tets[q] < N, NBP_ERR_INVALID, "nbp_vms_create: tet node out of range");
     for (long long q = 0; q < 3LL * T; ++q)
         require(mesh->tris[q] >= 0 && mesh->tris[q] < N, NBP_ERR_INVALID, "nbp_vms_create: triangle node out of range");
+    // degenerate elements (the shape-function gradients would divide by a zero
+    // volume or area): |det| must exceed 1e-12 of the cube (square) of the
+    // longest edge
+    auto edge = [&](int a, int b, int r) { return mesh->X[3LL * b + r] - mesh->X[3LL * a + r]; };
+    for (long long e = 0; e < E; ++e) {
+        const int32_t *t = mesh->tets + 4 * e;
+        double d[3][3], lmax = 0.0;
+        for (int k = 0; k < 3; ++k)
+            for (int r = 0; r < 3; ++r) d[k][r] = edge(t[0], t[k + 1], r);
+        for (int a = 0; a < 4; ++a)
+            for (int b = a + 1; b < 4; ++b) {
+                double l2 = 0.0;
+                for (int r = 0; r < 3; ++r) l2 += edge(t[a], t[b], r) * edge(t[a], t[b], r);
+                lmax = std::max(lmax, std::sqrt(l2));
+            }
+        const double det = d[0][0] * (d[1][1] * d[2][2] - d[1][2] * d[2][1]) -
+                           d[0][1] * (d[1][0] * d[2][2] - d[1][2] * d[2][0]) +
+                           d[0][2] * (d[1][0] * d[2][1] - d[1][1] * d[2][0]);
+        require(std::isfinite(det) && std::fabs(det) > 1e-12 * lmax * lmax * lmax, NBP_ERR_INVALID,
+                "nbp_vms_create: degenerate tet " + std::to_string(e));
+    }
+    for (long long f = 0; f < T; ++f) {
+        const int32_t *t = mesh->tris + 3 * f;
+        double c[3], l2max = 0.0;
+        for (int r = 0; r < 3; ++r)
+            c[r] = edge(t[0], t[1], (r + 1) % 3) * edge(t[0], t[2], (r + 2) % 3) -
+                   edge(t[0], t[1], (r + 2) % 3) * edge(t[0], t[2], (r + 1) % 3);
+        for (int a = 0; a < 3; ++a)
+            for (int b = a + 1; b < 3; ++b) {
+                double l2 = 0.0;
+                for (int r = 0; r < 3; ++r) l2 += edge(t[a], t[b], r) * edge(t[a], t[b], r);
+                l2max = std::max(l2max, l2);
+            }
+        const double area2 = std::sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
+        require(std::isfinite(area2) && area2 > 1e-12 * l2max, NBP_ERR_INVALID,
+                "nbp_vms_create: degenerate outlet triangle " + std::to_string(f));
+    }
     std::unique_ptr<nbp_vms, void (*)(nbp_vms *)> v(new nbp_vms(), vms_free);
     v->ctx = c;
     cudaStream_t s = c->s;

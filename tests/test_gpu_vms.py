@@ -193,3 +193,22 @@ def test_pattern_mismatch_rejected(case):
     with pytest.raises(Exception):
         Vms(s, bad, SPEC.rho, SPEC.mu, SPEC.dt, SPEC.rho_inf)
     s.close()
+
+
+def test_degenerate_elements_rejected(case):
+    """A tet with a repeated vertex (zero volume) or a collinear outlet triangle
+    is refused when the mesh is bound (its node pairs are in the pattern, so
+    only the degeneracy check can refuse it)."""
+    d, m, ph = case
+    s = Solver(d)
+    t = m["tets"][0]
+    flat = dict(m, tets=np.vstack([m["tets"], [[t[0], t[1], t[2], t[0]]]]).astype(np.int32))
+    with pytest.raises(Exception):
+        Vms(s, flat, SPEC.rho, SPEC.mu, SPEC.dt, SPEC.rho_inf)
+    f = m["tris"][0]
+    line = dict(m, tris=np.vstack([m["tris"], [[f[0], f[1], f[1]]]]).astype(np.int32))
+    with pytest.raises(Exception):
+        Vms(s, line, SPEC.rho, SPEC.mu, SPEC.dt, SPEC.rho_inf)
+    vm = Vms(s, m, SPEC.rho, SPEC.mu, SPEC.dt, SPEC.rho_inf)   # the mesh itself binds
+    vm.close()
+    s.close()
