@@ -47,3 +47,30 @@ def test_no_cpu_fallback_without_gpu():
     from paper_1911_10814_gb300 import Solver
     with pytest.raises(RuntimeError):
         Solver(synth.generate(synth.tiny()))
+
+
+def test_ctypes_mirrors_match_the_header_layout(tmp_path):
+    """Every structure the binding passes through the C ABI has the size and
+    field offsets the header gives it (a C program built against
+    include/nbp.h prints them)."""
+    import subprocess
+    from paper_1911_10814_gb300 import nbp
+    mirrors = [nbp.nbp_system, nbp.nbp_options, nbp.nbp_info, nbp.nbp_profile_info, nbp.nbp_rcr, nbp.nbp_mesh,
+               nbp.nbp_vms_params, nbp.nbp_newton_opts, nbp.nbp_newton_info]
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "nbp.h"', "int main(void) {"]
+    for cls in mirrors:
+        name = cls.__name__
+        lines.append(f'    printf("{name} %zu\\n", sizeof({name}));')
+        for f, _ in cls._fields_:
+            lines.append(f'    printf("{name}.{f} %zu\\n", offsetof({name}, {f}));')
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    got = dict(line.rsplit(" ", 1) for line in subprocess.check_output([str(exe)], text=True).splitlines())
+    for cls in mirrors:
+        name = cls.__name__
+        assert int(got[name]) == ctypes.sizeof(cls), name
+        for f, _ in cls._fields_:
+            assert int(got[f"{name}.{f}"]) == getattr(cls, f).offset, f"{name}.{f}"
