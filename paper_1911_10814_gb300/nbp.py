@@ -11,6 +11,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import weakref
 
 import numpy as np
 
@@ -361,6 +362,9 @@ class Solver:
         return st
 
     def close(self):
+        # handles bound to this context (Vms) go first: they hold its pointer
+        for child in list(getattr(self, "_children", ())):
+            child.close()
         if getattr(self, "ctx", None):
             self.lib.nbp_destroy(self.ctx)
             self.ctx = None
@@ -532,6 +536,9 @@ class Vms:
         h = ctypes.c_void_p()
         solver._check(self.lib.nbp_vms_create(ctypes.byref(h), solver.ctx, ctypes.byref(m), ctypes.byref(par)))
         self.h = h
+        if not hasattr(solver, "_children"):
+            solver._children = weakref.WeakSet()
+        solver._children.add(self)
 
     def close(self):
         if getattr(self, "h", None):
