@@ -212,3 +212,19 @@ def test_degenerate_elements_rejected(case):
     vm = Vms(s, m, SPEC.rho, SPEC.mu, SPEC.dt, SPEC.rho_inf)   # the mesh itself binds
     vm.close()
     s.close()
+
+
+def test_set_values_refuses_non_finite(case):
+    """A NaN in the new values is refused before anything is replaced: the
+    context keeps its values and its setup, and solves as before."""
+    d, m, ph = case
+    s = Solver(d)
+    s.setup()
+    x0, _ = s.solve(_t(d["b"]))
+    A = np.ravel(d["A"]).copy()
+    A[7] = np.nan
+    with pytest.raises(Exception):
+        s.set_values(_t(A), _t(np.ravel(d["B"])), _t(np.ravel(d["C"])), _t(np.ravel(d["D"])))
+    x1, _ = s.solve(_t(d["b"]))
+    assert torch.equal(x0, x1)
+    s.close()
