@@ -322,6 +322,7 @@ class Solver:
         self.N = int(sysd["n_nodes"])
         self.n_out = len(sysd["out_ptr"]) - 1
         rp, col = sysd["rowptr"], sysd["col"]
+        self.nnz = len(col)   # entries of the shared pattern (the time-step tangent's layout)
         keep = []
 
         def dev(a, dt):
@@ -558,8 +559,10 @@ class Vms:
                                                  _ptr(P) if P is not None else None, _ptr(R)))
         return R
 
-    def tangent(self, vd, v, p, nnz, vtau=None):
-        """Tangent values (A 9 nnz, B 3 nnz, C 3 nnz, D nnz) at the same state."""
+    def tangent(self, vd, v, p, nnz=None, vtau=None):
+        """Tangent values (A 9 nnz, B 3 nnz, C 3 nnz, D nnz) at the same state
+        (nnz: entries of the solver's pattern, by default the Solver's)."""
+        nnz = self.s.nnz if nnz is None else nnz
         out = {k: self.s.zeros(w * nnz) for k, w in (("A", 9), ("B", 3), ("C", 3), ("D", 1))}
         self.s._check(self.lib.nbp_vms_tangent(self.h, _ptr(vd), _ptr(v), _ptr(p),
                                                 _ptr(vtau) if vtau is not None else None,
