@@ -61,7 +61,10 @@
  *     eps_rel |Q|)).
  *
  * Vectors: x = [x_v (3N, node-interleaved); x_p (N)].
- * Build with -ffp-contract=off so that no multiply-add is fused.
+ * Build with -ffp-contract=off so that no multiply-add is fused, and with
+ * -fopenmp: threads share only loops with independent iterations, and every
+ * sum keeps one fixed order, so the results do not depend on the thread
+ * count (OpenMP static scheduling with fixed-order reductions).
  */
 #include <math.h>
 #include <stdint.h>
@@ -70,6 +73,12 @@
 #include <string.h>
 
 #define OR_MAXLEV 12
+/* Loops whose iterations are independent (the rows of a sparse product,
+ * elementwise vector updates, the prolongation, the restriction's per-
+ * aggregate sums) run on all cores with OpenMP (static schedule) once they
+ * exceed this length.  Every sum keeps one fixed order (inner products: see
+ * dot()), so a result is the same bit for bit at any thread count. */
+#define OR_PAR_MIN 32768
 /* handshake rounds per matching pass; a round that adds no pair leaves the
  * state unchanged, so extra rounds after convergence are no-ops */
 #define MATCH_ROUNDS 64
@@ -140,9 +149,31 @@ static void *xmalloc(size_t n) {
 }
 static double *dvec(size_t n) { return (double *)calloc(n ? n : 1, sizeof(double)); }
 
+/* Inner product in a fixed order: a sequential sum over each run of
+ * OR_DOT_BLOCK consecutive entries, then the run sums added in ascending
+ * order.  The runs may be summed by different threads; the order, and so the
+ * result, is the same at any thread count (a vector of at most OR_DOT_BLOCK
+ * entries is one plain sequential sum). */
+#define OR_DOT_BLOCK 4096
 static double dot(int n, const double *a, const double *b) {
+    const int nb = (n + OR_DOT_BLOCK - 1) / OR_DOT_BLOCK;
+    if (nb <= 1) {
+        double s = 0.0;
+        for (int i = 0; i < n; ++i) s += a[i] * b[i];
+        return s;
+    }
+    double *part = (double *)malloc(sizeof(double) * (size_t)nb);
+    if (!part) { fprintf(stderr, "oracle: out of memory\n"); abort(); }
+#pragma omp parallel for schedule(static) if ((n) > OR_PAR_MIN)
+    for (int k = 0; k < nb; ++k) {
+        const int lo = k * OR_DOT_BLOCK, hi = lo + OR_DOT_BLOCK < n ? lo + OR_DOT_BLOCK : n;
+        double s = 0.0;
+        for (int i = lo; i < hi; ++i) s += a[i] * b[i];
+        part[k] = s;
+    }
     double s = 0.0;
-    for (int i = 0; i < n; ++i) s += a[i] * b[i];
+    for (int k = 0; k < nb; ++k) s += part[k];
+    free(part);
     return s;
 }
 static double nrm2(int n, const double *a) { return sqrt(dot(n, a, a)); }
@@ -162,6 +193,7 @@ static void bmat_free(bmat *m) { free(m->rp); free(m->ci); free(m->v); memset(m,
 /* y = M x (block sparse product, plain row loop) */
 static void spmv(const bmat *M, const double *x, double *y) {
     int br = M->br, bc = M->bc, bs = br * bc;
+#pragma omp parallel for schedule(static) if ((M->nbr) > OR_PAR_MIN)
     for (int i = 0; i < M->nbr; ++i) {
         double acc[3] = {0.0, 0.0, 0.0};
         for (int e = M->rp[i]; e < M->rp[i + 1]; ++e) {
@@ -196,9 +228,11 @@ void or_apply_full(or_ctx *c, const double *x, double *y) {
     double *yv = y, *yp = y + nv;
     or_apply_A(c, xv, yv);
     spmv(&c->B, xp, c->wv1);
+#pragma omp parallel for schedule(static) if ((nv) > OR_PAR_MIN)
     for (int i = 0; i < nv; ++i) yv[i] += c->wv1[i];
     spmv(&c->C, xv, yp);
     spmv(&c->D, xp, c->wp1);
+#pragma omp parallel for schedule(static) if ((np) > OR_PAR_MIN)
     for (int i = 0; i < np; ++i) yp[i] += c->wp1[i];
 }
 
@@ -220,6 +254,7 @@ static int fgmres(int n, linop op, void *opc, linop pc, void *pcc, const double 
     double *H = dvec((size_t)(m + 1) * m);
     double *cs = dvec(m), *sn = dvec(m), *g = dvec(m + 1), *y = dvec(m);
     double *r = dvec(n), *w = dvec(n);
+#pragma omp parallel for schedule(static) if ((n) > OR_PAR_MIN)
     for (int i = 0; i < n; ++i) { x[i] = 0.0; r[i] = b[i]; }
     double bnorm = nrm2(n, b);
     double tol = fmax(rtol * bnorm, atol);
@@ -227,6 +262,7 @@ static int fgmres(int n, linop op, void *opc, linop pc, void *pcc, const double 
     int its = 0, conv = (beta <= tol);
     double rel_true = (bnorm > 0) ? 1.0 : 0.0;
     while (!conv && its < nmax) {
+        #pragma omp parallel for schedule(static) if ((n) > OR_PAR_MIN)
         for (int i = 0; i < n; ++i) V[i] = r[i] / beta;
         memset(g, 0, sizeof(double) * (m + 1));
         g[0] = beta;
@@ -238,6 +274,7 @@ static int fgmres(int n, linop op, void *opc, linop pc, void *pcc, const double 
             for (int i = 0; i <= j; ++i) {           /* modified Gram-Schmidt */
                 double h = dot(n, w, V + (size_t)i * n);
                 H[i * m + j] = h;
+                #pragma omp parallel for schedule(static) if ((n) > OR_PAR_MIN)
                 for (int t = 0; t < n; ++t) w[t] -= h * V[(size_t)i * n + t];
             }
             double hn = nrm2(n, w);
@@ -258,8 +295,10 @@ static int fgmres(int n, linop op, void *opc, linop pc, void *pcc, const double 
             res = fabs(g[j + 1]);
             ++its;
             jend = j + 1;
-            if (hn != 0.0)
+            if (hn != 0.0) {
+                #pragma omp parallel for schedule(static) if ((n) > OR_PAR_MIN)
                 for (int t = 0; t < n; ++t) V[(size_t)(j + 1) * n + t] = w[t] / hn;
+            }
             if (res <= tol || hn == 0.0) break;
         }
         /* back substitution H y = g */
@@ -268,12 +307,15 @@ static int fgmres(int n, linop op, void *opc, linop pc, void *pcc, const double 
             for (int k = i + 1; k < jend; ++k) s -= H[i * m + k] * y[k];
             y[i] = (H[i * m + i] != 0.0) ? s / H[i * m + i] : 0.0;
         }
-        for (int i = 0; i < jend; ++i)
+        for (int i = 0; i < jend; ++i) {
+            #pragma omp parallel for schedule(static) if ((n) > OR_PAR_MIN)
             for (int t = 0; t < n; ++t) x[t] += y[i] * Z[(size_t)i * n + t];
+        }
         int est_conv = (res <= tol);
         if (est_conv && !check_true) { conv = 1; break; }
         /* true residual: restart vector, or the confirmation of convergence */
         op(opc, x, w);
+        #pragma omp parallel for schedule(static) if ((n) > OR_PAR_MIN)
         for (int t = 0; t < n; ++t) r[t] = b[t] - w[t];
         beta = nrm2(n, r);
         res = beta;
@@ -536,6 +578,7 @@ static void block_diag_inv(const bmat *M, double *dinv) {
 
 static void apply_dinv(int n, int bs, const double *dinv, const double *r, double *z) {
     int nb = bs * bs;
+#pragma omp parallel for schedule(static) if ((n) > OR_PAR_MIN)
     for (int i = 0; i < n; ++i)
         for (int a = 0; a < bs; ++a) {
             double s = 0.0;
@@ -687,6 +730,16 @@ static void amg_build(amg *H, const bmat *fine, const or_options *o, int kcycle,
         int nc = aggregate(&H->L[l], o->theta, H->agg[l]);
         if (nc >= n || nc == 0) { free(H->agg[l]); H->agg[l] = NULL; break; }
         galerkin(&H->L[l], H->agg[l], nc, &H->L[l + 1]);
+        H->mptr[l] = (int *)calloc((size_t)nc + 1, sizeof(int));   /* members of each aggregate, ascending */
+        H->mem[l] = (int *)xmalloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
+        for (int i = 0; i < n; ++i) if (H->agg[l][i] >= 0) H->mptr[l][H->agg[l][i] + 1]++;
+        for (int I = 0; I < nc; ++I) H->mptr[l][I + 1] += H->mptr[l][I];
+        {
+            int *fillp = (int *)xmalloc(sizeof(int) * (size_t)(nc > 0 ? nc : 1));
+            memcpy(fillp, H->mptr[l], sizeof(int) * (size_t)nc);
+            for (int i = 0; i < n; ++i) if (H->agg[l][i] >= 0) H->mem[l][fillp[H->agg[l][i]]++] = i;
+            free(fillp);
+        }
         ++l;
     }
     H->nlev = l + 1;
@@ -721,7 +774,7 @@ static void amg_build(amg *H, const bmat *fine, const or_options *o, int kcycle,
 static void amg_free(amg *H) {
     for (int k = 0; k < H->nlev; ++k) {
         bmat_free(&H->L[k]);
-        free(H->agg[k]); free(H->dinv[k]); free(H->bl[k]); free(H->xl[k]); free(H->rl[k]); free(H->dl[k]);
+        free(H->agg[k]); free(H->mptr[k]); free(H->mem[k]); free(H->dinv[k]); free(H->bl[k]); free(H->xl[k]); free(H->rl[k]); free(H->dl[k]);
         free(H->kr[k]); free(H->kz1[k]); free(H->kw1[k]); free(H->kz2[k]); free(H->kw2[k]);
     }
     free(H->lu); free(H->piv);
@@ -738,16 +791,24 @@ static void chebyshev(const bmat *M, const double *dinv, double rho, double lodi
     double sigma = theta / delta, rho_old = 1.0 / sigma;
     double *t = dvec(n);
     if (x_is_zero) memcpy(r, b, sizeof(double) * n);
-    else { spmv(M, x, t); for (int i = 0; i < n; ++i) r[i] = b[i] - t[i]; }
+    else {
+        spmv(M, x, t);
+#pragma omp parallel for schedule(static) if ((n) > OR_PAR_MIN)
+        for (int i = 0; i < n; ++i) r[i] = b[i] - t[i];
+    }
     apply_dinv(M->nbr, M->br, dinv, r, t);
+#pragma omp parallel for schedule(static) if ((n) > OR_PAR_MIN)
     for (int i = 0; i < n; ++i) d[i] = t[i] / theta;
     for (int it = 0; it < k; ++it) {
+        #pragma omp parallel for schedule(static) if ((n) > OR_PAR_MIN)
         for (int i = 0; i < n; ++i) x[i] += d[i];
         if (it + 1 == k) break;
         spmv(M, x, t);
+        #pragma omp parallel for schedule(static) if ((n) > OR_PAR_MIN)
         for (int i = 0; i < n; ++i) r[i] = b[i] - t[i];
         double rho_new = 1.0 / (2.0 * sigma - rho_old);
         apply_dinv(M->nbr, M->br, dinv, r, t);
+        #pragma omp parallel for schedule(static) if ((n) > OR_PAR_MIN)
         for (int i = 0; i < n; ++i) d[i] = rho_new * rho_old * d[i] + (2.0 * rho_new / delta) * t[i];
         rho_old = rho_new;
     }
@@ -772,16 +833,19 @@ static void kcycle(amg *H, int c) {
     spmv(M, z1, w1);
     double ww = dot(n, w1, w1);
     double a1 = (ww > 0.0) ? dot(n, w1, r) / ww : 0.0;
+#pragma omp parallel for schedule(static) if ((n) > OR_PAR_MIN)
     for (int i = 0; i < n; ++i) r[i] = r[i] - a1 * w1[i];
     memcpy(b, r, sizeof(double) * n);               /* z2 = cycle(r_1) */
     vcycle(H, c);
     memcpy(z2, H->xl[c], sizeof(double) * n);
     spmv(M, z2, w2);
     double beta = (ww > 0.0) ? dot(n, w2, w1) / ww : 0.0;
+#pragma omp parallel for schedule(static) if ((n) > OR_PAR_MIN)
     for (int i = 0; i < n; ++i) { w2[i] = w2[i] - beta * w1[i]; z2[i] = z2[i] - beta * z1[i]; }
     double w22 = dot(n, w2, w2);
     double a2 = (w22 > 0.0) ? dot(n, w2, r) / w22 : 0.0;
     double *x = H->xl[c];
+#pragma omp parallel for schedule(static) if ((n) > OR_PAR_MIN)
     for (int i = 0; i < n; ++i) x[i] = a1 * z1[i] + a2 * z2[i];
 }
 
@@ -791,20 +855,27 @@ static void vcycle(amg *H, int l) {
     int n = M->nbr * H->bs, bs = H->bs;
     double *b = H->bl[l], *x = H->xl[l], *r = H->rl[l], *d = H->dl[l];
     if (l == H->nlev - 1) { dense_lu_solve(H->nc, H->lu, H->piv, b, x); return; }
+#pragma omp parallel for schedule(static) if ((n) > OR_PAR_MIN)
     for (int i = 0; i < n; ++i) x[i] = 0.0;
     chebyshev(M, H->dinv[l], H->rho[l], H->cheb_lo, H->cheb_degree, b, x, r, d, 1);
     double *t = dvec(n);
     spmv(M, x, t);
+#pragma omp parallel for schedule(static) if ((n) > OR_PAR_MIN)
     for (int i = 0; i < n; ++i) r[i] = b[i] - t[i];
     int nc = H->L[l + 1].nbr;
     double *bc = H->bl[l + 1];
-    memset(bc, 0, sizeof(double) * (size_t)nc * bs);
-    for (int i = 0; i < M->nbr; ++i)              /* restriction P^T r, ascending i */
-        if (H->agg[l][i] >= 0)
-            for (int a = 0; a < bs; ++a) bc[(size_t)H->agg[l][i] * bs + a] += r[(size_t)i * bs + a];
+    const int *mp = H->mptr[l], *mb = H->mem[l];
+#pragma omp parallel for schedule(static) if ((nc) > OR_PAR_MIN)
+    for (int I = 0; I < nc; ++I)                  /* restriction P^T r: members in ascending i */
+        for (int a = 0; a < bs; ++a) {
+            double s = 0.0;
+            for (int t = mp[I]; t < mp[I + 1]; ++t) s += r[(size_t)mb[t] * bs + a];
+            bc[(size_t)I * bs + a] = s;
+        }
     if (H->cycle == 1 && l + 1 < H->nlev - 1 && l + 1 <= H->kdepth) kcycle(H, l + 1);
     else vcycle(H, l + 1);
     const double *xc = H->xl[l + 1];
+#pragma omp parallel for schedule(static) if ((M->nbr) > OR_PAR_MIN)
     for (int i = 0; i < M->nbr; ++i)              /* prolongation x += P e_c */
         if (H->agg[l][i] >= 0)
             for (int a = 0; a < bs; ++a) x[(size_t)i * bs + a] += xc[(size_t)H->agg[l][i] * bs + a];
@@ -900,7 +971,12 @@ static void build_shat(or_ctx *c) {
 static void op_A(void *ctx, const double *x, double *y) { or_apply_A((or_ctx *)ctx, x, y); }
 static void pc_A(void *ctx, const double *x, double *y) {
     or_ctx *c = (or_ctx *)ctx;
-    if (c->opt.pc_A == 1) { for (int i = 0; i < 3 * c->N; ++i) y[i] = x[i] / c->diagA[i]; return; }
+    if (c->opt.pc_A == 1) {
+        const int n = 3 * c->N;
+#pragma omp parallel for schedule(static) if ((n) > OR_PAR_MIN)
+        for (int i = 0; i < n; ++i) y[i] = x[i] / c->diagA[i];
+        return;
+    }
     amg_apply(&c->amgA, x, y);
 }
 static void pc_S(void *ctx, const double *x, double *y) {
@@ -925,6 +1001,7 @@ void or_apply_S(or_ctx *c, const double *xp, double *y) {
     or_solve_A(c, xbar, xtil, c->opt.rtol_I, &its);        /* line 3 */
     c->info.I_iters += its; c->info.n_I_solves++;
     spmv(&c->C, xtil, cx);                                 /* line 4 */
+#pragma omp parallel for schedule(static) if ((N) > OR_PAR_MIN)
     for (int i = 0; i < N; ++i) y[i] = xhat[i] - cx[i];    /* line 5 */
     free(xhat); free(xbar); free(xtil); free(cx);
 }
@@ -972,6 +1049,7 @@ void or_apply_pscr(or_ctx *c, const double *s, double *y) {
     fgmres(N, op_S, c, pc_S, c, sp2, yp, c->opt.rtol_S, c->opt.atol, c->opt.m_S, c->opt.nmax_S, 0, &its, &rel, NULL); /* step 3 */
     c->info.S_iters += its; c->info.n_S_solves++;
     spmv(&c->B, yp, t);                                            /* step 4 */
+#pragma omp parallel for schedule(static) if ((nv) > OR_PAR_MIN)
     for (int i = 0; i < nv; ++i) sv2[i] = sv[i] - t[i];
     or_solve_A(c, sv2, yv, c->opt.rtol_A, &its);                   /* step 5 */
     c->info.A_iters += its; c->info.n_A_solves++;
