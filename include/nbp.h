@@ -253,11 +253,15 @@ const char *nbp_batch_last_error(const nbp_batch *batch);
  * here), outlet k as out_idx/out_val[out_ptr[k] .. out_ptr[k+1]-1] over
  * velocity dofs with indices unique within one outlet, r (n_out weights), x
  * and y (3N doubles).  Work is queued on `stream` and the call returns
- * without synchronising; NBP_ERR_CUDA reports a failed launch.  The first
- * call on a device looks up the device address of the fixed array, so make
- * that first call before any stream capture.  Every call shares the array:
- * each call overwrites the entries it uses before reading them, and calls
- * that overlap on the GPU (on unordered streams) race on it. */
+ * without synchronising; NBP_ERR_CUDA reports a failed launch.  Every call
+ * looks up the device address of the fixed array on the current device (no
+ * address is cached, so a device reset between calls is safe); the first
+ * call on a device also sets up the library's device code there, so make
+ * that first call before any stream capture.  A call launches three kernels
+ * whatever n_out (one kernel adds every outlet's terms, in ascending k).
+ * Every call shares the array: each call overwrites the entries it uses
+ * before reading them, and calls that overlap on the GPU (on unordered
+ * streams) race on it. */
 nbp_status nbp_apply_A_noalloc(int32_t n_nodes, const int32_t *a_rowptr, const int32_t *a_col, const double *a_val,
                                int32_t n_out, const int32_t *out_ptr, const int32_t *out_idx, const double *out_val,
                                const double *r, const double *x, double *y, void *stream);

@@ -4,8 +4,6 @@
 // callers that forbid allocation after start-up, and callers that hold no
 // library context.  The per-outlet inner products that the regular path keeps
 // in context-owned device memory live here in a fixed file-scope device array.
-#include <mutex>
-
 #include "kernels.cuh"
 
 namespace nbp {
@@ -19,36 +17,32 @@ constexpr int kNoAllocMaxOutlets = 1024;
 // calls that overlap on the GPU (different streams, no ordering) race on it.
 static __device__ __align__(256) double g_noalloc_f[kNoAllocMaxOutlets];
 
-// y[idx] += f[k] * val over outlet k (indices unique within one outlet; one
-// launch per outlet in ascending k keeps the sums in a fixed order)
-__global__ void k_noalloc_scatter(const int *__restrict__ optr, const int *__restrict__ oidx, const double *__restrict__ oval,
-                                  const double *__restrict__ f, int k, double *__restrict__ y) {
-    const int beg = optr[k], end = optr[k + 1];
-    for (int q = beg + blockIdx.x * blockDim.x + threadIdx.x; q < end; q += gridDim.x * blockDim.x)
-        y[oidx[q]] += f[k] * oval[q];
+// y[idx] += f[k] * val for every outlet k in ascending order, by one block:
+// the entries of one outlet have distinct indices, so its threads never touch
+// the same y entry, and the barrier between outlets keeps each y entry's
+// additions in ascending k (a fixed order, one launch for any n_out).
+__global__ void __launch_bounds__(1024) k_noalloc_scatter(const int *__restrict__ optr, const int *__restrict__ oidx,
+                                                          const double *__restrict__ oval, const double *__restrict__ f,
+                                                          int n_out, double *__restrict__ y) {
+    for (int k = 0; k < n_out; ++k) {
+        const int beg = optr[k], end = optr[k + 1];
+        const double fk = f[k];
+        for (int q = beg + threadIdx.x; q < end; q += blockDim.x) y[oidx[q]] += fk * oval[q];
+        __syncthreads();
+    }
 }
 
 namespace {
-constexpr int kMaxDevices = 64;
-std::mutex g_mutex;
-double *g_scratch[kMaxDevices] = {nullptr};
-
-// Device address of the scratch array for the current device.  In host code
+// Device address of the scratch array on the current device.  In host code
 // the array's name is only a host-side stand-in, so the address is looked up
-// once per device with that device current.
+// with the device current -- on every call, so that a context torn down and
+// made again (a device reset) never leaves a stale address behind.  The
+// lookup queues no work on any stream.
 cudaError_t scratch_for_current_device(double **out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_f);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_mutex);
-    if (!g_scratch[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_f);
-        if (e != cudaSuccess) return e;
-        g_scratch[dev] = (double *)p;
-    }
-    *out = g_scratch[dev];
+    *out = (double *)p;
     return cudaSuccess;
 }
 }  // namespace
@@ -80,8 +74,8 @@ extern "C" nbp_status nbp_apply_A_noalloc(int32_t n_nodes, const int32_t *a_rowp
     const long long threads = (long long)n_nodes * 16;
     k_bspmv<3, 3, 16, double, double, EPI_SET, false><<<grid_exact(threads), 256, 0, s>>>(a);
     if (cudaGetLastError() != cudaSuccess) return NBP_ERR_CUDA;
-    for (int k = 0; k < n_out; ++k) {
-        k_noalloc_scatter<<<64, 256, 0, s>>>(out_ptr, out_idx, out_val, f, k, y);
+    if (n_out > 0) {
+        k_noalloc_scatter<<<1, 1024, 0, s>>>(out_ptr, out_idx, out_val, f, n_out, y);
         if (cudaGetLastError() != cudaSuccess) return NBP_ERR_CUDA;
     }
     return NBP_OK;
