@@ -44,6 +44,8 @@ def _args():
                    help="inner precision of the headline solve (1 FP32, 2 BF16, 3 FP32 operators + BF16 AMG values)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-extras", action="store_true",
+                   help="skip the adjoint (32x32x128 box) and 48-tangent batch measurements of the default run")
     p.add_argument("--skip-fp64", action="store_true", help="skip the FP64 comparison solve (profiling runs)")
     p.add_argument("--pc-A", type=int, default=0, help="P_A: 0 AMG V-cycle (default), 1 Jacobi")
     p.add_argument("--variant", type=int, default=0, help="0 P_SCR (Algorithm 3), 1 block-triangular, 2 SIMPLE")
@@ -184,34 +186,237 @@ def _dist():
     return ws, rank, local
 
 
-def cpu_oracle_sample(d, counts, budget_s=20.0):
-    """Time the oracle on a bounded sample of the same workload: inner
-    GMRES(m_A) iterations with the AMG V-cycle on the full-size A (the unit
-    that dominates a nested solve), then scale to one solve with the
-    iteration counts of the measured solve.  Oracle setup is not timed."""
+GOLDEN = os.path.join(ROOT, "tests", "golden", "fullsize_box64x64x256_re2000_q4.json")
+
+
+def golden_error(x, spec_name, n):
+    """Relative error of a solution against the oracle's 1e-12 solution of the
+    same tangent, on the 8192 stored entries (and the norms), when the stored
+    record is for this workload; else None."""
+    if not os.path.exists(GOLDEN):
+        return None
+    with open(GOLDEN) as f:
+        g = json.load(f)
+    if g.get("workload") != spec_name or g.get("unknowns") != n:
+        return None
+    import torch
+    idx = torch.as_tensor(np.asarray(g["idx"], dtype=np.int64), device=x.device)
+    xs = x[idx].cpu().numpy()
+    xo = np.asarray(g["x"])
+    return {"sampled_rel_err": float(np.linalg.norm(xs - xo) / np.linalg.norm(xo)),
+            "norm2_rel_diff": abs(float(x.norm()) - g["norm2"]) / g["norm2"], "samples": len(xo),
+            "oracle_rtol": g["rtol"]}
+
+
+def family_rates(breakdown):
+    """Achieved GB/s (algorithmic bytes / CUDA-event time) of kernel families
+    from the per-tag breakdown {tag: [launches, ms, bytes]}: the sparse
+    products with the AMG transfers, the CGS2 Arnoldi kernels, everything."""
+    fam = {"spmv_family": lambda t: t.split("/")[0] in ("A", "B", "C", "D") or t[:2] in ("HA", "HS")
+           or t.startswith("amg/restrict") or t == "amg/prolong",
+           "arnoldi": lambda t: t.startswith("arnoldi/"),
+           "all_kernels": lambda t: True}
+    out = {}
+    for k, sel in fam.items():
+        ms = sum(v[1] for t, v in breakdown.items() if sel(t))
+        by = sum(v[2] for t, v in breakdown.items() if sel(t))
+        out[k] = {"GBs": by / (ms * 1e-3) / 1e9 if ms > 0 else None, "ms": ms}
+    return out
+
+
+def adjoint_extra():
+    """Adjoint workload: the 32x32x128 box (561,924 unknowns, Re 300, 4
+    outlets), L = sum_k (a^k . u - q_k)^2; forward nested solve and transposed
+    nested adjoint solve (FP64 outer / FP32 inner, outer tolerance 1e-12) timed
+    on the device, and dL/dr_k checked against central differences
+    (h = 1e-6 r_k) of FP64 forward solves at 1e-13."""
+    import torch
+    import synth
+    from paper_1911_10814_gb300 import Solver
+    spec = synth.adjoint_case()
+    d = synth.generate(spec)
+    N, nv = d["n_nodes"], 3 * d["n_nodes"]
+    n_out = len(d["out_ptr"]) - 1
+    A = torch.zeros((n_out, nv), dtype=torch.float64)
+    for k in range(n_out):
+        sl = slice(d["out_ptr"][k], d["out_ptr"][k + 1])
+        A[k, torch.as_tensor(d["out_idx"][sl], dtype=torch.long)] = torch.as_tensor(d["out_val"][sl])
+    A = A.to("cuda:0")
+    s = Solver(d, precision=1, rtol=1e-12)
+    t0 = time.perf_counter()
+    s.setup()
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t0
+    b = torch.as_tensor(d["b"], device="cuda:0")
+    x0, _ = s.solve(b)
+    q = torch.as_tensor((2 * synth.uniforms(4 ^ 0xA11, n_out) - 1) * np.abs((A @ x0[:nv]).cpu().numpy()).max(),
+                        device="cuda:0")
+    times = []
+    for _ in range(3):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        x, finfo = s.solve(b)
+        gx = torch.zeros_like(x)
+        gx[:nv] = 2.0 * (A.T @ (A @ x[:nv] - q))
+        lam, dldr, ainfo = s.adjoint(gx, x)
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+    g = np.asarray(dldr)
+
+    def loss(rv):
+        s.set_resistances(rv)
+        xx, _ = s.solve(b, precision=0, rtol=1e-13, allow_not_converged=True)
+        return float(((A @ xx[:nv] - q) ** 2).sum())
+
+    errs = []
+    for k in range(n_out):
+        h = 1e-6 * d["r"][k]
+        rp, rm = d["r"].copy(), d["r"].copy()
+        rp[k] += h
+        rm[k] -= h
+        fd = (loss(rp) - loss(rm)) / (2 * h)
+        errs.append(abs(g[k] - fd) / abs(fd))
+    s.close()
+    return {"workload": spec.name, "unknowns": 4 * N, "forward_plus_adjoint_s": float(np.median(times)),
+            "forward_solve_s": finfo["solve_s"], "adjoint_solve_s": ainfo["solve_s"], "setup_s": t_setup,
+            "outer_tolerance": 1e-12, "inner_precision": "fp32",
+            "grad_rel_err_vs_central_fd_max": float(max(errs)), "fd_step": "1e-6 r_k, FP64 solves at 1e-13"}
+
+
+def batch_extra(precision, steps=3):
+    """48 uneven cubes (12^3-40^3 hexes, Re U[100,1000], 1-4 outlets, seed 3)
+    in one nbp_batch_solve, FP64 outer / inner precision mode `precision`."""
+    import torch
+    import synth
+    from paper_1911_10814_gb300 import BatchSolver
+    systems = [synth.generate(sp) for sp in synth.batch()]
+    B = BatchSolver(systems, precision=precision)
+    t0 = time.perf_counter()
+    B.setup()
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t0
+    bs = [torch.as_tensor(d["b"], device="cuda:0") for d in systems]
+    B.solve(bs)
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        xs, infos = B.solve(bs)
+        torch.cuda.synchronize()
+        ts.append(time.perf_counter() - t0)
+    B.close()
+    v = float(np.median(ts))
+    return {"workload": "48 cubes 12^3-40^3 hexes, Re U[100,1000], 1-4 outlets, seed 3",
+            "unknowns_total": int(sum(4 * d["n_nodes"] for d in systems)), "batch_solve_s": v,
+            "instances_per_s": 48.0 / v, "setup_s": t_setup, "inner_precision": precision,
+            "outer_iters_max": int(max(i["outer_iters"] for i in infos)),
+            "rel_res_true_max": float(max(i["rel_res_true"] for i in infos))}
+
+
+def _wall(f, reps=1):
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        f()
+    return (time.perf_counter() - t0) / reps
+
+
+def oracle_phase_times(o, d):
+    """Time the oracle's building blocks on the full tangent (about 10-20 s of
+    CPU work): the AMG(A) and AMG(S_hat) cycles, the A, B, C, D and full
+    tangent products, and the cost of one Gram-Schmidt column on a 3N vector
+    (from an unpreconditioned GMRES(12) on A: 12 A products plus
+    12*13/2 + 1.5*12 vector columns of modified Gram-Schmidt, norms, basis
+    scaling and the final update)."""
+    N = d["n_nodes"]
+    rng = np.random.default_rng(0)
+    bv, bp, b = rng.standard_normal(3 * N), rng.standard_normal(N), rng.standard_normal(4 * N)
+    t = {"pcA": _wall(lambda: o.vcycle(0, bv)), "pcS": _wall(lambda: o.vcycle(1, bp)),
+         "A": _wall(lambda: o.apply_A(bv)), "B": _wall(lambda: o.apply_B(bp)), "C": _wall(lambda: o.apply_C(bv)),
+         "D": _wall(lambda: o.apply_D(bp)), "full": _wall(lambda: o.apply_full(b))}
+    t12 = _wall(lambda: o.gmres_A(bv, 1e-30, 12, 12, 0))
+    t["col3N"] = max(t12 - 12 * t["A"], 0.0) / (12 * 13 / 2 + 1.5 * 12)
+    return t
+
+
+def oracle_model(t, counts, outer_solves=1):
+    """Seconds of one oracle nested solve from its building blocks and the
+    iteration counts of the solve (Algorithms 2-3 inside FGMRES):
+      A- and I-iterations: one AMG(A) cycle + one A product each;
+      S-iterations: the B, D, C products of Algorithm 2 and one AMG(S_hat)
+        cycle (the inner A-solve is counted in the I-iterations);
+      outer iterations: one full tangent product, the C and B products of
+        Algorithm 3, and one more full product for the true residual;
+      Gram-Schmidt at every level: a solve of J iterations on vectors of
+        length L costs (J(J+1)/2 + 1.5 J) columns of L entries, each column
+        timed on 3N entries and scaled by L / 3N; the A-solves number two per
+        outer iteration, the I-solves one per S-iteration, the S-solves one
+        per outer iteration."""
+    o_, a_, s_, i_ = counts["outer_iters"], counts["A_iters"], counts["S_iters"], counts["I_iters"]
+
+    def gs(its, solves, scale):
+        if solves <= 0 or its <= 0:
+            return 0.0
+        J = its / solves
+        return solves * (J * (J + 1) / 2 + 1.5 * J) * t["col3N"] * scale
+
+    parts = {
+        "A_I_iterations": (a_ + i_) * (t["pcA"] + t["A"]),
+        "S_iterations": s_ * (t["pcS"] + t["B"] + t["C"] + t["D"]),
+        "outer_iterations": o_ * (t["full"] + t["B"] + t["C"]) + outer_solves * t["full"],
+        "gram_schmidt": gs(a_, 2 * o_, 1.0) + gs(i_, s_, 1.0) + gs(s_, o_, 1.0 / 3.0) + gs(o_, outer_solves, 4.0 / 3.0),
+    }
+    return sum(parts.values()), parts
+
+
+def _threads():
+    return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+
+
+def cpu_oracle_sample(d, counts, validate_scale=32):
+    """The oracle (all host cores, OpenMP with fixed-order sums) on a bounded
+    sample of the workload: its building blocks timed on the full tangent,
+    combined by the iteration counts of the measured solve (oracle_model).
+    The model is checked in the same run against a complete oracle solve of
+    a smaller box of the same family (timed whole, setup excluded)."""
     import oracle
+    import synth
     o = oracle.Oracle(d)
     t0 = time.perf_counter()
     o.setup()
     t_setup = time.perf_counter() - t0
-    nv = 3 * d["n_nodes"]
-    b = np.random.default_rng(0).standard_normal(nv)
-    its_s = 3
     t0 = time.perf_counter()
-    _, its, _, _ = o.gmres_A(b, 1e-30, its_s, its_s, 1)
-    t_it = (time.perf_counter() - t0) / max(its, 1)
-    # S-level and outer iterations each add one operator application of the
-    # same order as an A-iteration (B, C, D products + V-cycle on S_hat, or the
-    # full tangent product): counted as one A-iteration equivalent each.
-    units = counts["A_iters"] + counts["I_iters"] + counts["S_iters"] + counts["outer_iters"]
-    return {"value": t_it * units, "unit": "s", "cores": 1, "kind": "oracle",
-            "sample": f"{its} oracle GMRES(m_A)+AMG iterations on the full 4.34M-unknown tangent "
-                      f"({t_it:.3f} s/iteration), scaled by {units} iteration equivalents of one nested solve; "
-                      f"oracle setup {t_setup:.1f} s untimed"}
+    t = oracle_phase_times(o, d)
+    t_sample = time.perf_counter() - t0
+    v, parts = oracle_model(t, counts)
+    del o
+    check = None
+    if validate_scale:
+        dv = synth.generate(synth.large_mixed(validate_scale))
+        ov = oracle.Oracle(dv)
+        ov.setup()
+        t0 = time.perf_counter()
+        _, info, _ = ov.solve(dv["b"])
+        measured = time.perf_counter() - t0
+        cv = {"outer_iters": info.outer_iters, "A_iters": info.A_iters, "S_iters": info.S_iters,
+              "I_iters": info.I_iters}
+        model_v, _ = oracle_model(oracle_phase_times(ov, dv), cv)
+        check = {"workload": synth.large_mixed(validate_scale).name, "unknowns": 4 * dv["n_nodes"],
+                 "measured_solve_s": measured, "model_s": model_v, "model_over_measured": model_v / measured,
+                 "iters": cv}
+        del ov
+    return {"value": v, "unit": "s", "cores": _threads(), "kind": "oracle",
+            "sample": f"oracle building blocks timed on the full 4.34M-unknown tangent ({t_sample:.1f} s: AMG(A) and "
+                      f"AMG(S_hat) cycles, A/B/C/D/full products, a Gram-Schmidt column), combined by the measured "
+                      f"solve's iteration counts {counts}; oracle setup {t_setup:.1f} s untimed",
+            "parts_s": {k: round(x, 3) for k, x in parts.items()}, "phase_s": {k: round(x, 5) for k, x in t.items()},
+            "model_check": check}
 
 
 def run_reference(a):
-    """Reference arm: the FP64 CPU oracle on the same workload (rank 0 only)."""
+    """Reference arm: the FP64 CPU oracle on the same workload (rank 0 only).
+    Each step times the oracle's building blocks on the full tangent and
+    combines them by the iteration counts of the oracle's own full-size solve
+    (oracle_model)."""
     ws, rank, _ = _dist()
     if rank != 0:
         return
@@ -223,27 +428,22 @@ def run_reference(a):
         counts = json.load(f)["fp64"]
     o = oracle.Oracle(d)
     o.setup()
-    nv = 3 * d["n_nodes"]
-    b = np.random.default_rng(0).standard_normal(nv)
-    units = counts["A_iters"] + counts["I_iters"] + counts["S_iters"] + counts["outer_iters"]
-    its_s = 2
     for _ in range(a.warmup):
-        o.gmres_A(b, 1e-30, its_s, its_s, 1)
+        oracle_model(oracle_phase_times(o, d), counts)
     ts = []
     for _ in range(a.steps):
-        t0 = time.perf_counter()
-        _, its, _, _ = o.gmres_A(b, 1e-30, its_s, its_s, 1)
-        ts.append((time.perf_counter() - t0) / its * units)
+        ts.append(oracle_model(oracle_phase_times(o, d), counts)[0])
     v = float(np.mean(ts))
     line = {"metric": METRIC, "value": v, "unit": "s", "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
             "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": {"workload": synth.large_mixed(a.scale).name, "unknowns": 4 * d["n_nodes"],
                        "tolerance": 1e-8, "l2": "inputs larger than L2"},
-            "cpu_baseline": {"value": v, "unit": "s", "cores": 1, "kind": "oracle",
-                             "sample": f"per step {its_s} oracle GMRES(m_A)+AMG iterations on the full tangent, "
-                                       f"scaled by {units} iteration equivalents of one nested solve "
-                                       f"(counts from profiles/nested_solve_counts.json)"},
+            "cpu_baseline": {"value": v, "unit": "s", "cores": _threads(), "kind": "oracle",
+                             "sample": "per step the oracle's building blocks (AMG cycles, A/B/C/D/full products, a "
+                                       "Gram-Schmidt column) timed on the full tangent, combined by the iteration "
+                                       f"counts {counts} of the oracle's own full-size solve "
+                                       "(profiles/nested_solve_counts.json)"},
             "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -451,6 +651,7 @@ def main():
         e2e_s = (time.perf_counter() - t0) / a.steps / ws
         e2e = {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": n * 8, "d2h_bytes_per_step": n * 8}
 
+    fams = family_rates({k: v for k, v in breakdown.items()})
     peak, peak_kind = _peaks()
     # the dominant single kernel: whichever fine-level A kernel took more total time
     if prof["cheb0_ms"] >= prof["a0_ms"]:
@@ -467,8 +668,10 @@ def main():
                 "kernel": kname, "algorithmic_bytes_per_launch": bytes_per, "avg_launch_us": avg_ms * 1e3,
                 "share_of_spmv_time": prof[key + "_ms"] / prof["spmv_ms"] if prof["spmv_ms"] else None,
                 "peak_kind": peak_kind,
-                "spmv_family_GBs": prof["spmv_bytes"] / (prof["spmv_ms"] * 1e-3) / 1e9 if prof["spmv_ms"] else None,
-                "arnoldi_GBs": prof["arnoldi_bytes"] / (prof["arnoldi_ms"] * 1e-3) / 1e9 if prof["arnoldi_ms"] else None}
+                "spmv_family_GBs": fams["spmv_family"]["GBs"], "arnoldi_GBs": fams["arnoldi"]["GBs"],
+                "all_kernels_GBs": fams["all_kernels"]["GBs"],
+                "family_note": "algorithmic bytes / CUDA-event time summed per family: sparse products and AMG "
+                               "transfers; CGS2 Arnoldi kernels; every timed kernel of the solve"}
     counts = {k: infos[-1][k] for k in ("outer_iters", "A_iters", "S_iters", "I_iters")}
     counts64 = {k: info64[k] for k in ("outer_iters", "A_iters", "S_iters", "I_iters")} if info64 else counts
     line = {
@@ -500,6 +703,15 @@ def main():
                  "note": "host blocked in stream syncs (one small state read per Krylov iteration)"},
         "e2e": e2e,
     }
+    line["err_vs_oracle"] = {"mixed": golden_error(x, spec.name, n),
+                             "fp64": golden_error(x64, spec.name, n) if x64 is not None else None}
+    s.close()
+    if rank == 0 and ws == 1 and not a.no_extras:
+        for key, f in (("adjoint", adjoint_extra), ("batch", lambda: batch_extra(a.precision))):
+            try:
+                line[key] = f()
+            except Exception as ex:   # report, never hide
+                line[key] = {"error": repr(ex)}
     if rank == 0 and ws == 1 and not a.no_cpu_baseline:
         try:
             line["cpu_baseline"] = cpu_oracle_sample(d, counts64)
@@ -507,7 +719,6 @@ def main():
             line["cpu_baseline"] = {"value": None, "error": repr(ex)}
     if rank == 0:
         print(json.dumps(line), flush=True)
-    s.close()
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

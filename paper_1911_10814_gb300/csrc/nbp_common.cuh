@@ -102,6 +102,7 @@ struct DMat {
 // entries lr_rp[i]..lr_rp[i+1]-1 of block row i hold (outlet k, component c, value).
 struct LowRank {
     int n_out = 0;
+    int no = 0;                              // entries over all outlets
     int *optr = nullptr, *oidx = nullptr;    // per-outlet sparse vectors (device)
     double *oval = nullptr;
     double *r = nullptr;                     // device copy of r_k

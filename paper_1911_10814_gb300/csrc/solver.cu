@@ -199,19 +199,6 @@ template <class F> static void timed(nbp_ctx *c, const char *tag, double bytes, 
     prof_end(c, CAT_OTHER, bytes, tag);
 }
 
-// algorithmic bytes of one block-sparse product
-template <typename XT> static double spmv_bytes(const DMat &M, int vsel, int epi) {
-    const double vb = vsel == 0 ? 8.0 : (vsel == 1 ? 4.0 : 2.0);
-    double b = (double)M.nnz * M.bb() * vb + (double)M.nnz * 4.0 + (double)(M.nbr + 1) * 4.0;
-    const double xs = sizeof(XT);
-    const double nx = (double)M.nbc * M.bc, ny = (double)M.nbr * M.br;
-    b += nx * xs;
-    if (epi == EPI_SET) b += ny * xs;
-    else if (epi == EPI_ADD || epi == EPI_SUB || epi == EPI_RES) b += 2.0 * ny * xs;
-    else b += 5.0 * ny * xs + (double)M.nbr * M.br * M.br * xs;   // Chebyshev: b, d in/out, xout, dinv
-    return b;
-}
-
 static std::string mat_tag(nbp_ctx *c, const DMat &M, int epi) {
     static const char *en[] = {"set", "add", "sub", "res", "cheb"};
     std::string t;
@@ -233,12 +220,15 @@ static std::string mat_tag(nbp_ctx *c, const DMat &M, int epi) {
     return t + "/" + en[epi] + k;
 }
 
+// extra_bytes: algorithmic bytes of a fused epilogue that the product's own
+// count leaves out (the rank-one term)
 template <typename XT>
-static void do_spmv(nbp_ctx *c, const DMat &M, int vsel, SpmvArgs a, int epi, bool lr, int cat = CAT_SPMV) {
+static void do_spmv(nbp_ctx *c, const DMat &M, int vsel, SpmvArgs a, int epi, bool lr, int cat = CAT_SPMV,
+                    double extra_bytes = 0.0) {
     cudaEvent_t e0;
     prof_begin(c, e0);
-    spmv<XT>(M, vsel, a, epi, lr, c->s);
-    prof_end(c, cat, spmv_bytes<XT>(M, vsel, epi), c->prof.on ? mat_tag(c, M, epi) : std::string());
+    const double bytes = spmv<XT>(M, vsel, a, epi, lr, c->s) + extra_bytes;
+    prof_end(c, cat, bytes, c->prof.on ? mat_tag(c, M, epi) : std::string());
 }
 
 static SpmvArgs sargs(const void *x, void *y) {
@@ -258,7 +248,10 @@ template <typename T> static void apply_A(nbp_ctx *c, int vsel, const T *x, T *y
         NBP_LAUNCHED();
         a.lr_rp = lr.lr_rp; a.lr_k = lr.lr_k; a.lr_c = lr.lr_c; a.lr_val = lr.lr_val; a.lr_f = lr.f;
     }
-    do_spmv<T>(c, c->A, vsel, a, EPI_SET, lr.n_out > 0, CAT_SPMV_A0);
+    // rank-one epilogue: the per-row list pointers, each (outlet, component,
+    // value) entry once and the n_out factors
+    const double lr_bytes = lr.n_out > 0 ? (double)(c->N + 1) * 4.0 + (double)lr.no * 16.0 + lr.n_out * 8.0 : 0.0;
+    do_spmv<T>(c, c->A, vsel, a, EPI_SET, lr.n_out > 0, CAT_SPMV_A0, lr_bytes);
 }
 
 // ------------------------------------------------------------ CGS2 Arnoldi
@@ -506,19 +499,21 @@ static void kcycle_level(nbp_ctx *c, Hier &H, int cl, int vsel, const T *b, T *x
     const long long n = (long long)L.M.nbr * H.bs;
     T *r = wvec<T>(L, 5), *z1 = wvec<T>(L, 6), *w1 = wvec<T>(L, 7), *z2 = wvec<T>(L, 8), *w2 = wvec<T>(L, 9);
     const unsigned g = grid_for(n);
+    const double vn = (double)n * sizeof(T);   // bytes of one level vector
     if (!first_done) copy<T>(r, b, n, c->s);   // else the restriction wrote r
     vcycle_level<T>(c, H, cl, vsel, b, z1, first_done);
     do_spmv<T>(c, L.M, vsel, sargs(z1, w1), EPI_SET, false);
-    timed(c, "kcycle/dots", 0.0, [&] { k_kdots<T><<<kKdotBlocks, 256, 0, c->s>>>(w1, w1, w1, r, n, L.kdots, 0, 1); });
-    timed(c, "kcycle/update", 0.0, [&] { k_kupd1<T><<<g, 256, 0, c->s>>>(r, w1, L.kdots, n); });
+    // algorithmic bytes: each distinct vector an update or a pair of dots reads or writes, once
+    timed(c, "kcycle/dots", 2.0 * vn, [&] { k_kdots<T><<<kKdotBlocks, 256, 0, c->s>>>(w1, w1, w1, r, n, L.kdots, 0, 1); });
+    timed(c, "kcycle/update", 3.0 * vn, [&] { k_kupd1<T><<<g, 256, 0, c->s>>>(r, w1, L.kdots, n); });
     vcycle_level<T>(c, H, cl, vsel, r, z2);
     do_spmv<T>(c, L.M, vsel, sargs(z2, w2), EPI_SET, false);
-    timed(c, "kcycle/dots", 0.0, [&] {
+    timed(c, "kcycle/dots", 2.0 * vn, [&] {
         k_kdots<T><<<kKdotBlocks, 256, 0, c->s>>>(w2, w1, (const T *)nullptr, (const T *)nullptr, n, L.kdots, 3, 3);
     });
-    timed(c, "kcycle/update", 0.0, [&] { k_kupd2<T><<<g, 256, 0, c->s>>>(w2, z2, w1, z1, L.kdots, n); });
-    timed(c, "kcycle/dots", 0.0, [&] { k_kdots<T><<<kKdotBlocks, 256, 0, c->s>>>(w2, w2, w2, r, n, L.kdots, 4, 5); });
-    timed(c, "kcycle/update", 0.0, [&] { k_kupd3<T><<<g, 256, 0, c->s>>>(x, z1, z2, L.kdots, n); });
+    timed(c, "kcycle/update", 6.0 * vn, [&] { k_kupd2<T><<<g, 256, 0, c->s>>>(w2, z2, w1, z1, L.kdots, n); });
+    timed(c, "kcycle/dots", 2.0 * vn, [&] { k_kdots<T><<<kKdotBlocks, 256, 0, c->s>>>(w2, w2, w2, r, n, L.kdots, 4, 5); });
+    timed(c, "kcycle/update", 3.0 * vn, [&] { k_kupd3<T><<<g, 256, 0, c->s>>>(x, z1, z2, L.kdots, n); });
 }
 
 // V(1,1)-cycle from level l with right-hand side b; result written to out.
@@ -532,7 +527,7 @@ static void vcycle_level(nbp_ctx *c, Hier &H, int l, int vsel, const T *b, T *ou
     const int k = H.cheb;
     if (l == H.nlev - 1) {
         if (H.cinv) {
-            timed(c, "amg/coarsest_gemv", (double)H.nc * H.nc * 8.0,
+            timed(c, "amg/coarsest_gemv", ((double)H.nc * H.nc + 2.0 * H.nc) * sizeof(T),
                   [&] { k_dense_gemv<T><<<grid_exact((long long)H.nc * 32), 256, 0, c->s>>>(cinv_of<T>(H), H.nc, b, out); });
         } else {
             T *res = chebyshev<T>(c, L, vsel, std::max(k, 1), b, out, wvec<T>(L, 2), true);  // coarsest: smoothing only
@@ -558,22 +553,30 @@ static void vcycle_level(nbp_ctx *c, Hier &H, int l, int vsel, const T *b, T *ou
     // first smoothing step (into the buffers its cycle uses: d = w[4], the
     // iterate w[2]) and, for a K-cycle, its copy of the right-hand side (w[5])
     const bool fuse = k > 0 && l + 1 < H.nlev - 1;
+    // restriction bytes: aggregate pointers and member lists, the fine
+    // residual once, the coarse right-hand side written
+    const double ncv = (double)Lc.M.nbr * bs * sizeof(T);
+    const double rbytes = (double)(Lc.M.nbr + 1) * 4.0 + (double)L.M.nbr * 4.0 + (double)n * sizeof(T) + ncv;
     if (fuse) {
         const Cheb chc = cheb_of(Lc);
-        timed(c, "amg/restrict+first", 0.0, [&] {
+        // + the coarse block-diagonal inverse read, d and x written (+ the copy)
+        const double fbytes = rbytes + (double)Lc.M.nbr * bs * bs * sizeof(T) + 2.0 * ncv + (kc ? ncv : 0.0);
+        timed(c, "amg/restrict+first", fbytes, [&] {
             k_restrict_first<T><<<grid_exact((long long)Lc.M.nbr * 8), 256, 0, c->s>>>(
                 L.mptr, L.mem, Lc.M.nbr, bs, r, bc, dinv_of<T>(Lc), (T)(1.0 / chc.theta), wvec<T>(Lc, 4), wvec<T>(Lc, 2),
                 kc ? wvec<T>(Lc, 5) : (T *)nullptr);
         });
     } else {
-        timed(c, "amg/restrict", 0.0,
+        timed(c, "amg/restrict", rbytes,
               [&] { k_restrict<T><<<grid_exact((long long)Lc.M.nbr * 8), 256, 0, c->s>>>(L.mptr, L.mem, Lc.M.nbr, bs, r, bc); });
     }
     // (a prolongation fused into the coarse level's last kernel, as a scatter
     // over each aggregate's members, was slower: uncoalesced fine updates)
     if (kc) kcycle_level<T>(c, H, l + 1, vsel, bc, xc, fuse);
     else vcycle_level<T>(c, H, l + 1, vsel, bc, xc, fuse);
-    timed(c, "amg/prolong", 0.0, [&] { k_prolong<T><<<grid_exact(n), 256, 0, c->s>>>(L.agg, L.M.nbr, bs, xc, cur); });
+    // prolongation bytes: the aggregate map, the coarse correction, x read and written
+    const double pbytes = (double)L.M.nbr * 4.0 + ncv + 2.0 * n * sizeof(T);
+    timed(c, "amg/prolong", pbytes, [&] { k_prolong<T><<<grid_exact(n), 256, 0, c->s>>>(L.agg, L.M.nbr, bs, xc, cur); });
     T *fin = chebyshev<T>(c, L, vsel, k, b, cur, oth, false);
     if (fin != out) copy<T>(out, fin, n, c->s);
 }
@@ -947,6 +950,7 @@ static void load_lowrank(nbp_ctx *c, const nbp_system *sys) {
         NBP_CUDA(cudaMemcpyAsync(oval.data(), sys->out_val, sizeof(double) * no, cudaMemcpyDeviceToHost, s));
         NBP_CUDA(cudaStreamSynchronize(s));
     }
+    lr.no = no;
     lr.r_host.assign(sys->r, sys->r + lr.n_out);
     for (int k = 0; k < lr.n_out; ++k) {
         require(optr[k + 1] >= optr[k], NBP_ERR_INVALID, "nbp_create: out_ptr not monotone");

@@ -179,17 +179,36 @@ static void launch_sellr(const DMat &M, int vsel, SpmvArgs a, int epi, cudaStrea
     }
 }
 
+// Algorithmic bytes of one product y = epilogue(M x): every stored block's
+// values and column index once, the row pointers (flat kernel) or the slice
+// pointers (sliced layouts; their padding is not counted), x once, and the
+// epilogue's vectors: SET writes y; ADD and SUB read and write y; RES reads
+// b and writes y; CHEB reads b, d and the block-diagonal inverse and writes
+// d and xout (x_i itself is the product's input, counted once).
+static double product_bytes(const DMat &M, int vsel, int xs, int epi, bool sliced) {
+    const double vb = xs == 8 ? 8.0 : (vsel == 2 ? 2.0 : 4.0);
+    double b = (double)M.nnz * (M.bb() * vb + 4.0);
+    b += sliced ? (double)(M.nslice + 1) * 8.0 : (double)(M.nbr + 1) * 4.0;
+    const double nx = (double)M.nbc * M.bc * xs, ny = (double)M.nbr * M.br * xs;
+    b += nx;
+    if (epi == EPI_SET) b += ny;
+    else if (epi == EPI_CHEB) b += 4.0 * ny + (double)M.nbr * M.br * M.br * xs;
+    else b += 2.0 * ny;
+    return b;
+}
+
 template <typename XT>
-void spmv(const DMat &M, int vsel, SpmvArgs a, int epi, bool lr, cudaStream_t s, int G) {
+double spmv(const DMat &M, int vsel, SpmvArgs a, int epi, bool lr, cudaStream_t s, int G) {
     a.nbr = M.nbr;
     a.rp = M.rp;
     a.ci = M.ci;
-    if (a.nbr == 0) return;
+    if (a.nbr == 0) return 0.0;
+    constexpr int xs = (int)sizeof(XT);
     // rectangular coupling blocks: sliced ELL for FP64 / FP32 values (BF16: flat kernel)
     if (M.br != M.bc && M.sl_ci && G <= 0 && epi <= EPI_SUB && vsel != 2 &&
         (sizeof(XT) == 8 ? M.sl_v != nullptr : M.sl_v32 != nullptr)) {
-        if (M.br == 3 && M.bc == 1) { launch_sellr<3, 1, XT>(M, vsel, a, epi, s); return; }
-        if (M.br == 1 && M.bc == 3) { launch_sellr<1, 3, XT>(M, vsel, a, epi, s); return; }
+        if (M.br == 3 && M.bc == 1) { launch_sellr<3, 1, XT>(M, vsel, a, epi, s); return product_bytes(M, vsel, xs, epi, true); }
+        if (M.br == 1 && M.bc == 3) { launch_sellr<1, 3, XT>(M, vsel, a, epi, s); return product_bytes(M, vsel, xs, epi, true); }
     }
     const bool sell_ok = M.sl_ci && M.br == M.bc && (sizeof(XT) == 8 ? M.sl_v != nullptr : true);
     if (G < 0) G = (M.tuned >= 0) ? M.tuned : (sell_ok ? 0 : choose_group(M));
@@ -198,16 +217,17 @@ void spmv(const DMat &M, int vsel, SpmvArgs a, int epi, bool lr, cudaStream_t s,
         const int T = G == 0 ? 1 : G - kSellMT;
         if (M.br == 3) launch_sell<3, XT>(M, vsel, a, epi, lr, s, T);
         else launch_sell<1, XT>(M, vsel, a, epi, lr, s, T);
-        return;
+        return product_bytes(M, vsel, xs, epi, true);
     }
     if (M.br == 3 && M.bc == 3) launch_vt<3, 3, XT>(M, vsel, a, G, epi, lr, s);
     else if (M.br == 3 && M.bc == 1) launch_vt<3, 1, XT>(M, vsel, a, G, epi, lr, s);
     else if (M.br == 1 && M.bc == 3) launch_vt<1, 3, XT>(M, vsel, a, G, epi, lr, s);
     else if (M.br == 1 && M.bc == 1) launch_vt<1, 1, XT>(M, vsel, a, G, epi, lr, s);
     else throw Error{NBP_ERR_INVALID, "spmv: unsupported block shape"};
+    return product_bytes(M, vsel, xs, epi, false);
 }
 
-template void spmv<double>(const DMat &, int, SpmvArgs, int, bool, cudaStream_t, int);
-template void spmv<float>(const DMat &, int, SpmvArgs, int, bool, cudaStream_t, int);
+template double spmv<double>(const DMat &, int, SpmvArgs, int, bool, cudaStream_t, int);
+template double spmv<float>(const DMat &, int, SpmvArgs, int, bool, cudaStream_t, int);
 
 }  // namespace nbp
