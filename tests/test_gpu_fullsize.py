@@ -1,8 +1,14 @@
 """Parity at the benchmark's full size (64x64x256 box, 4,343,300 unknowns,
 Re 2000, 4 outlets) in the launch configuration bench.py times (FP32 inner /
-FP64 outer with BF16 AMG values, default options): properties that hold at any size, checked by
-the oracle's own FP64 arithmetic -- the true residual of the GPU solution,
-sampled rows of the A product, bit-exact aggregates and S_hat."""
+FP64 outer with BF16 AMG values, default options): the solution against the
+oracle's own solution of the same tangent to delta^r = 1e-12 (stored in
+tests/golden/ by make_fullsize_golden.py: 8192 sampled entries, norms and
+random projections), and properties that hold at any size, checked by the
+oracle's FP64 arithmetic -- the true residual of the GPU solution, sampled
+rows of the A product, bit-exact aggregates and S_hat."""
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -26,6 +32,55 @@ def big():
     o = oracle.Oracle(d)
     yield d, s, o
     s.close()
+
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "fullsize_box64x64x256_re2000_q4.json")
+
+
+def _check_against_golden(x, bar):
+    """Solution error bar of the workload (Sec. 3.1 outer tolerance 1e-8):
+    relative error <= bar on the sampled entries; the 2-norm, the velocity and
+    pressure 2-norms and every projection g_k . x within bar of the oracle's,
+    each a consequence of ||x - x_o|| <= bar ||x_o||."""
+    with open(GOLDEN) as f:
+        g = json.load(f)
+    xh = x.cpu().numpy()
+    n = len(xh)
+    assert g["unknowns"] == n and g["rel_res_true"] <= 1e-11
+    idx = np.asarray(g["idx"])
+    xo = np.asarray(g["x"])
+    err = np.linalg.norm(xh[idx] - xo) / np.linalg.norm(xo)
+    assert err <= bar, err
+    nv = 3 * n // 4
+    # the pressure dominates ||x||; the velocity block meets the bar on its own too
+    for part in (idx < nv, idx >= nv):
+        e = np.linalg.norm(xh[idx[part]] - xo[part]) / np.linalg.norm(xo[part])
+        assert e <= bar, e
+    no = g["norm2"]
+    assert abs(np.linalg.norm(xh) - no) <= bar * no
+    assert abs(np.linalg.norm(xh[:nv]) - g["norm2_v"]) <= bar * no
+    assert abs(np.linalg.norm(xh[nv:]) - g["norm2_p"]) <= bar * no
+    for seed, p in zip(g["proj_seeds"], g["proj"]):
+        gk = np.random.default_rng(seed).standard_normal(n)
+        assert abs(gk @ xh - p) <= bar * np.linalg.norm(gk) * no
+    return err
+
+
+def test_fullsize_mixed_solution_vs_oracle(big):
+    """The benchmark's mode (FP32 operators, BF16 AMG values, FP64 outer) at
+    rel. res 1e-8: solution within 1e-5 of the oracle's."""
+    d, s, o = big
+    x, info = s.solve(torch.as_tensor(d["b"], device="cuda:0"))
+    assert info["rel_res_true"] <= 1e-8
+    _check_against_golden(x, 1e-5)
+
+
+def test_fullsize_fp64_solution_vs_oracle(big):
+    """FP64 everywhere at rel. res 1e-8: solution within 1e-6 of the oracle's."""
+    d, s, o = big
+    x, info = s.solve(torch.as_tensor(d["b"], device="cuda:0"), precision=0)
+    assert info["rel_res_true"] <= 1e-8
+    _check_against_golden(x, 1e-6)
 
 
 def test_fullsize_true_residual_by_oracle(big):
