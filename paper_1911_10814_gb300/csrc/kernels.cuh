@@ -117,36 +117,107 @@ __global__ void __launch_bounds__(256) k_bspmv(SpmvArgs a) {
     }
 }
 
+// Streamed loads of matrix values and columns: each is read once per
+// product, so they can bypass L1 allocation (ld.global.nc.L1::no_allocate)
+// and leave L1 to the x gathers, which neighbouring rows share.
+__device__ __forceinline__ float lds(const float *p) {
+    float v;
+    asm volatile("ld.global.nc.L1::no_allocate.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ double lds(const double *p) {
+    double v;
+    asm volatile("ld.global.nc.L1::no_allocate.f64 %0, [%1];" : "=d"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ int lds(const int *p) {
+    int v;
+    asm volatile("ld.global.nc.L1::no_allocate.s32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ int2 lds(const int2 *p) {
+    int2 v;
+    asm volatile("ld.global.nc.L1::no_allocate.v2.s32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ __nv_bfloat16 lds(const __nv_bfloat16 *p) {
+    unsigned short v;
+    asm volatile("ld.global.nc.L1::no_allocate.b16 %0, [%1];" : "=h"(v) : "l"(p));
+    __nv_bfloat16 r;
+    memcpy(&r, &v, 2);
+    return r;
+}
+__device__ __forceinline__ __nv_bfloat162 lds(const __nv_bfloat162 *p) {
+    unsigned v;
+    asm volatile("ld.global.nc.L1::no_allocate.b32 %0, [%1];" : "=r"(v) : "l"(p));
+    __nv_bfloat162 r;
+    memcpy(&r, &v, 4);
+    return r;
+}
+
+// Matrix loads of the sliced layouts: streamed (no L1 allocation) for
+// 32-row slices, whose warps read whole 128-byte segments; 8-row slices read
+// quarter segments, and there the lines that L1 keeps serve the neighbouring
+// components, so those loads stay cached.
+template <bool STREAM, typename P> __device__ __forceinline__ P ldm(const P *p) {
+    if constexpr (STREAM) return lds(p);
+    else return __ldg(p);
+}
+
+// One pair of slots of the paired BF16 layout: columns c, values m, added in
+// slot order (the first slot of the pair, then the second).
+template <int BS>
+__device__ __forceinline__ void pair_fma(const int2 c, const __nv_bfloat162 (&m)[BS * BS], const float *__restrict__ x,
+                                         float &acc0, float &acc1, float &acc2) {
+    if (BS == 1) {
+        const float2 mm = __bfloat1622float2(m[0]);
+        acc0 += mm.x * __ldg(x + c.x);
+        acc0 += mm.y * __ldg(x + c.y);
+    } else {
+        const float xa0 = __ldg(x + 3LL * c.x), xa1 = __ldg(x + 3LL * c.x + 1), xa2 = __ldg(x + 3LL * c.x + 2);
+        const float xb0 = __ldg(x + 3LL * c.y), xb1 = __ldg(x + 3LL * c.y + 1), xb2 = __ldg(x + 3LL * c.y + 2);
+        float2 mm[9];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) mm[q] = __bfloat1622float2(m[q]);
+        acc0 += mm[0].x * xa0 + mm[1].x * xa1 + mm[2].x * xa2;
+        acc1 += mm[3].x * xa0 + mm[4].x * xa1 + mm[5].x * xa2;
+        acc2 += mm[6].x * xa0 + mm[7].x * xa1 + mm[8].x * xa2;
+        acc0 += mm[0].y * xb0 + mm[1].y * xb1 + mm[2].y * xb2;
+        acc1 += mm[3].y * xb0 + mm[4].y * xb1 + mm[5].y * xb2;
+        acc2 += mm[6].y * xb0 + mm[7].y * xb1 + mm[8].y * xb2;
+    }
+}
+
 // Slots p0, p0 + step, ... of the paired BF16 layout (DMat::sl2_ptr) of one
 // row: per pair, one int2 of columns and one bf16x2 per component; the two
-// slots are added in slot order, as the unpaired loop adds them.
+// slots are added in slot order, as the unpaired loop adds them.  Two pairs
+// are loaded before either is used (more loads in flight per thread); the
+// pairs are still added in ascending order.
 template <int BS, int C>
 __device__ __forceinline__ void sell_pairs(const SpmvArgs &a, long long base2, int np, int t, int p0, int step,
                                            const float *__restrict__ x, float &acc0, float &acc1, float &acc2) {
     constexpr int BB = BS * BS;
     const __nv_bfloat162 *__restrict__ val = (const __nv_bfloat162 *)a.val;
     const int2 *__restrict__ ci = (const int2 *)a.sl_ci;
-    for (int p = p0; p < np; p += step) {
-        const long long g = base2 + (long long)C * p;
-        const int2 c = __ldg(ci + g + t);
-        const __nv_bfloat162 *v = val + g * BB + t;
-        if (BS == 1) {
-            const float2 m = __bfloat1622float2(__ldg(v));
-            acc0 += m.x * __ldg(x + c.x);
-            acc0 += m.y * __ldg(x + c.y);
-        } else {
-            const float xa0 = __ldg(x + 3LL * c.x), xa1 = __ldg(x + 3LL * c.x + 1), xa2 = __ldg(x + 3LL * c.x + 2);
-            const float xb0 = __ldg(x + 3LL * c.y), xb1 = __ldg(x + 3LL * c.y + 1), xb2 = __ldg(x + 3LL * c.y + 2);
-            float2 m[9];
+    int p = p0;
+    for (; p + step < np; p += 2 * step) {
+        const long long g0 = base2 + (long long)C * p, g1 = g0 + (long long)C * step;
+        const int2 c0 = ldm<C == 32>(ci + g0 + t), c1 = ldm<C == 32>(ci + g1 + t);
+        __nv_bfloat162 m0[BB], m1[BB];
 #pragma unroll
-            for (int q = 0; q < 9; ++q) m[q] = __bfloat1622float2(__ldg(v + q * C));
-            acc0 += m[0].x * xa0 + m[1].x * xa1 + m[2].x * xa2;
-            acc1 += m[3].x * xa0 + m[4].x * xa1 + m[5].x * xa2;
-            acc2 += m[6].x * xa0 + m[7].x * xa1 + m[8].x * xa2;
-            acc0 += m[0].y * xb0 + m[1].y * xb1 + m[2].y * xb2;
-            acc1 += m[3].y * xb0 + m[4].y * xb1 + m[5].y * xb2;
-            acc2 += m[6].y * xb0 + m[7].y * xb1 + m[8].y * xb2;
-        }
+        for (int q = 0; q < BB; ++q) m0[q] = ldm<C == 32>(val + g0 * BB + t + q * C);
+#pragma unroll
+        for (int q = 0; q < BB; ++q) m1[q] = ldm<C == 32>(val + g1 * BB + t + q * C);
+        pair_fma<BS>(c0, m0, x, acc0, acc1, acc2);
+        pair_fma<BS>(c1, m1, x, acc0, acc1, acc2);
+    }
+    if (p < np) {
+        const long long g0 = base2 + (long long)C * p;
+        const int2 c0 = ldm<C == 32>(ci + g0 + t);
+        __nv_bfloat162 m0[BB];
+#pragma unroll
+        for (int q = 0; q < BB; ++q) m0[q] = ldm<C == 32>(val + g0 * BB + t + q * C);
+        pair_fma<BS>(c0, m0, x, acc0, acc1, acc2);
     }
 }
 
@@ -174,15 +245,15 @@ __global__ void __launch_bounds__(256) k_sell(SpmvArgs a) {
 #pragma unroll 2
         for (int k = 0; k < w; ++k) {
             const long long g = base + (long long)C * k;
-            const int c = __ldg(ci + g + t);
+            const int c = ldm<C == 32>(ci + g + t);
             const VT *v = val + g * BB + t;
             if (BS == 1) {
-                acc0 += cvt<AT>(__ldg(v)) * __ldg(x + c);
+                acc0 += cvt<AT>(ldm<C == 32>(v)) * __ldg(x + c);
             } else {
                 const AT x0 = __ldg(x + 3LL * c), x1 = __ldg(x + 3LL * c + 1), x2 = __ldg(x + 3LL * c + 2);
-                acc0 += cvt<AT>(__ldg(v)) * x0 + cvt<AT>(__ldg(v + C)) * x1 + cvt<AT>(__ldg(v + 2 * C)) * x2;
-                acc1 += cvt<AT>(__ldg(v + 3 * C)) * x0 + cvt<AT>(__ldg(v + 4 * C)) * x1 + cvt<AT>(__ldg(v + 5 * C)) * x2;
-                acc2 += cvt<AT>(__ldg(v + 6 * C)) * x0 + cvt<AT>(__ldg(v + 7 * C)) * x1 + cvt<AT>(__ldg(v + 8 * C)) * x2;
+                acc0 += cvt<AT>(ldm<C == 32>(v)) * x0 + cvt<AT>(ldm<C == 32>(v + C)) * x1 + cvt<AT>(ldm<C == 32>(v + 2 * C)) * x2;
+                acc1 += cvt<AT>(ldm<C == 32>(v + 3 * C)) * x0 + cvt<AT>(ldm<C == 32>(v + 4 * C)) * x1 + cvt<AT>(ldm<C == 32>(v + 5 * C)) * x2;
+                acc2 += cvt<AT>(ldm<C == 32>(v + 6 * C)) * x0 + cvt<AT>(ldm<C == 32>(v + 7 * C)) * x1 + cvt<AT>(ldm<C == 32>(v + 8 * C)) * x2;
             }
         }
     }
@@ -254,7 +325,7 @@ __global__ void __launch_bounds__(256) k_sellr(SpmvArgs a) {
 #pragma unroll 2
     for (int k = 0; k < w; ++k) {
         const long long g = base + (long long)C * k;
-        const int c = __ldg(ci + g + t);
+        const int c = ldm<C == 32>(ci + g + t);
         const VT *v = val + g * BB + t;
         AT xs[BC];
 #pragma unroll
@@ -263,7 +334,7 @@ __global__ void __launch_bounds__(256) k_sellr(SpmvArgs a) {
         for (int r = 0; r < BR; ++r) {
             AT u = 0;
 #pragma unroll
-            for (int cc = 0; cc < BC; ++cc) u += cvt<AT>(__ldg(v + (r * BC + cc) * C)) * xs[cc];
+            for (int cc = 0; cc < BC; ++cc) u += cvt<AT>(ldm<C == 32>(v + (r * BC + cc) * C)) * xs[cc];
             acc[r] += u;
         }
     }
@@ -304,15 +375,15 @@ __global__ void __launch_bounds__(256) k_sellm(SpmvArgs a) {
     } else {
         for (int k = h; k < w; k += T) {
             const long long g = base + (long long)C * k;
-            const int c = __ldg(ci + g + t);
+            const int c = ldm<C == 32>(ci + g + t);
             const VT *v = val + g * BB + t;
             if (BS == 1) {
-                acc0 += cvt<AT>(__ldg(v)) * __ldg(x + c);
+                acc0 += cvt<AT>(ldm<C == 32>(v)) * __ldg(x + c);
             } else {
                 const AT x0 = __ldg(x + 3LL * c), x1 = __ldg(x + 3LL * c + 1), x2 = __ldg(x + 3LL * c + 2);
-                acc0 += cvt<AT>(__ldg(v)) * x0 + cvt<AT>(__ldg(v + C)) * x1 + cvt<AT>(__ldg(v + 2 * C)) * x2;
-                acc1 += cvt<AT>(__ldg(v + 3 * C)) * x0 + cvt<AT>(__ldg(v + 4 * C)) * x1 + cvt<AT>(__ldg(v + 5 * C)) * x2;
-                acc2 += cvt<AT>(__ldg(v + 6 * C)) * x0 + cvt<AT>(__ldg(v + 7 * C)) * x1 + cvt<AT>(__ldg(v + 8 * C)) * x2;
+                acc0 += cvt<AT>(ldm<C == 32>(v)) * x0 + cvt<AT>(ldm<C == 32>(v + C)) * x1 + cvt<AT>(ldm<C == 32>(v + 2 * C)) * x2;
+                acc1 += cvt<AT>(ldm<C == 32>(v + 3 * C)) * x0 + cvt<AT>(ldm<C == 32>(v + 4 * C)) * x1 + cvt<AT>(ldm<C == 32>(v + 5 * C)) * x2;
+                acc2 += cvt<AT>(ldm<C == 32>(v + 6 * C)) * x0 + cvt<AT>(ldm<C == 32>(v + 7 * C)) * x1 + cvt<AT>(ldm<C == 32>(v + 8 * C)) * x2;
             }
         }
     }
