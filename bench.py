@@ -58,6 +58,9 @@ def _args():
     p.add_argument("--amg-coarse-max", type=int, default=300, help="coarsest level size (block rows)")
     p.add_argument("--outlets", type=int, default=0,
                    help="split the outlet face into this many patches (many-outlet stress case, e.g. 772)")
+    p.add_argument("--pc-rebuild-every", type=int, default=0,
+                   help="newton workload: 0 builds the preconditioner from every tangent; K >= 1 builds it at the "
+                        "first corrector of every K-th time step and keeps it (lagged) otherwise")
     p.add_argument("--workload", default="large", choices=["large", "batch", "newton"],
                    help="large: the 4.34M-unknown tangent (default); batch: 48 uneven cubes in one batched call; "
                         "newton: predictor multi-corrector time steps with on-device assembly")
@@ -514,9 +517,11 @@ def run_newton(a):
     yd = torch.zeros(4 * N, dtype=torch.float64, device=dev)
     infos, ts = [], []
     for k in range(a.warmup + a.steps):
+        K = a.pc_rebuild_every
+        mode = 0 if K <= 0 else (1 if k % K == 0 else 2)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        y, yd, Pi, info = vm.newton_step(y, yd, rcr, tol_R=1e-6, tol_A=1e-10, l_max=20, nts=10)
+        y, yd, Pi, info = vm.newton_step(y, yd, rcr, tol_R=1e-6, tol_A=1e-10, l_max=20, nts=10, pc_rebuild=mode)
         torch.cuda.synchronize()
         rcr = dict(rcr, Pi=Pi.clone())
         if k >= a.warmup:
@@ -529,10 +534,14 @@ def run_newton(a):
                       "dtype": "f32", "data": "synthetic",
                       "config": {"workload": spec.name, "unknowns": 4 * N, "tets": len(m["tets"]),
                                  "tol_R": 1e-6, "nested_tolerance": 1e-8, "inner_precision": a.precision,
-                                 "tangent": "fp32 dual numbers", "outlets": "4 x RCR, R = 1e3"},
+                                 "tangent": "fp32 dual numbers", "outlets": "4 x RCR, R = 1e3",
+                                 "preconditioner": ("rebuilt from every tangent" if a.pc_rebuild_every <= 0 else
+                                                    f"built every {a.pc_rebuild_every} time steps, kept (lagged) "
+                                                    "in between")},
                       "correctors_mean": tot("iters"), "outer_iters_mean": tot("outer_iters"),
                       "residual_s": tot("residual_s"), "tangent_s": tot("tangent_s"), "setup_s": tot("setup_s"),
-                      "solve_s": tot("solve_s"), "vms_create_s": t_create,
+                      "solve_s": tot("solve_s"), "vms_create_s": t_create, "setups_mean": tot("setups"),
+                      "correctors": [i["iters"] for i in infos],
                       "res_last": [i["res"] for i in infos]}), flush=True)
     vm.close()
     s.close()

@@ -409,6 +409,15 @@ typedef struct {
     double tol_R, tol_A;      /* stopping rule ||R_(l)|| / ||R_(0)|| <= tol_R or ||R_(l)|| <= tol_A (1e-6 in Sec. 2.5) */
     int32_t l_max;            /* corrector iterations (20 in Sec. 2.5) */
     int32_t nts;              /* RK4 substeps of the outlet model per time step */
+    int32_t pc_rebuild;       /* preconditioner of the nested solves (AMG(A), S_hat, AMG(S_hat)):
+                                 0 built from every tangent; 1 from the first tangent of this
+                                 step only; 2 the one the context holds (from nbp_setup or an
+                                 earlier step) is kept, one is built only if there is none.  A
+                                 kept preconditioner acts on the new tangent's operators (their
+                                 sliced and precision copies are refreshed): a lagged
+                                 preconditioner changes the path of each solve, not its
+                                 solution.  A caller rebuilding every k steps passes 1 on
+                                 those steps and 2 on the others. */
 } nbp_newton_opts;
 
 typedef struct {
@@ -418,6 +427,7 @@ typedef struct {
     double res0, res;         /* ||R_(0)|| (at the predictor) and the last ||R|| */
     int64_t outer_iters, A_iters, S_iters, I_iters;   /* summed over the solves */
     double residual_s, tangent_s, setup_s, solve_s, total_s;   /* wall seconds per phase */
+    int32_t setups;           /* preconditioner builds made in this step */
 } nbp_newton_info;
 
 /* One time step by the predictor multi-corrector of Sec. 2.5: predictor

@@ -117,6 +117,7 @@ def _load():
             ("or_apply_D", [vp, _dp, _dp]), ("or_apply_full", [vp, _dp, _dp]), ("or_apply_S", [vp, _dp, _dp]),
             ("or_apply_pscr", [vp, _dp, _dp]), ("or_vcycle", [vp, ctypes.c_int, _dp, _dp]),
             ("or_set_options", [vp, ctypes.POINTER(Options)]), ("or_get_options", [vp, ctypes.POINTER(Options)]),
+            ("or_set_values", [vp, _dp, _dp, _dp, _dp]),
             ("or_default_options", [ctypes.POINTER(Options)]), ("or_set_resistances", [vp, _dp]),
             ("or_amg_level_get", [vp, ctypes.c_int, ctypes.c_int, _ip, _ip, _dp, _ip]),
             ("or_shat_get", [vp, _ip, _ip, _dp]), ("or_diag_A", [vp, _dp]),
@@ -224,6 +225,12 @@ class Oracle:
     def set_resistances(self, r):
         r = _d(r)
         self.lib.or_set_resistances(self.ctx, _pd(r))
+
+    def set_values(self, A, B, C, D):
+        """New values of the tangent blocks on the same patterns; the built
+        preconditioner is kept (a lagged preconditioner, see newton_step)."""
+        vals = [_d(np.asarray(M).reshape(-1)) for M in (A, B, C, D)]
+        self.lib.or_set_values(self.ctx, *[_pd(v) for v in vals])
 
     def setup(self):
         self.lib.or_setup(self.ctx)
@@ -502,13 +509,20 @@ def vms_assemble(mesh: dict, sysd: dict, phys: VmsPhys, vd, v, p, P=None, vtau=N
 
 
 def newton_step(mesh: dict, sysd: dict, phys: VmsPhys, y_n, yd_n, rcr: dict, tol_R=1e-6, tol_A=1e-6, l_max=20,
-                **solve_opts):
+                pc_rebuild=0, pc=None, **solve_opts):
     """One time step by the predictor multi-corrector of Sec. 2.5 around the
     oracle's nested solve.  y = [v (3N); p (N)], yd its time derivative;
     rcr = dict(Rp, C, Rd, Pd, Pi, nts) per outlet (Pi = Pi^k_n).
     Readings: ||R_(0)|| is the residual at the predictor (the first residual
     evaluated); velocity increments at Dirichlet nodes are set to zero.
-    Returns dict(y, yd, Pi, P, iters (linear solves), res (residual norms))."""
+    Preconditioner of the nested solves (AMG(A), S_hat, AMG(S_hat)):
+    pc_rebuild 0 builds it from every tangent; 1 from the first tangent of
+    this step only; 2 keeps the one held in the caller's dict `pc` (key
+    "oracle", from an earlier step) and builds one only if there is none.  A
+    kept preconditioner is applied to the new tangent's operators (a lagged
+    preconditioner: only the path of the solve changes, not its solution).
+    Returns dict(y, yd, Pi, P, iters (linear solves), res (residual norms),
+    setups (preconditioner builds))."""
     N = sysd["n_nodes"]
     am, af, gm = gen_alpha(phys.rho_inf)
     dt = phys.dt
@@ -522,6 +536,8 @@ def newton_step(mesh: dict, sysd: dict, phys: VmsPhys, y_n, yd_n, rcr: dict, tol
     Q_n = outlet_flows(sysd, y_n[:3 * N]) if n_out else np.zeros(0)
     P_n = Rp * Q_n + Pi_n + Pd
     res, r0, lin = [], None, []
+    setups = 0
+    held = pc if pc is not None else {}
     P1 = Pi1 = np.zeros(n_out)
     for l in range(1, l_max + 1):
         Q1 = outlet_flows(sysd, y1[:3 * N]) if n_out else np.zeros(0)                   # step 1
@@ -538,11 +554,20 @@ def newton_step(mesh: dict, sysd: dict, phys: VmsPhys, y_n, yd_n, rcr: dict, tol
         if r0 is None:
             r0 = nr
         if (r0 > 0 and nr / r0 <= tol_R) or nr <= tol_A:                                 # step 7
-            return dict(y=y1, yd=yd1, Pi=Pi1, P=P1, iters=l - 1, res=res, lin=lin)
+            return dict(y=y1, yd=yd1, Pi=Pi1, P=P1, iters=l - 1, res=res, lin=lin, setups=setups)
         T = vms_assemble(mesh, sysd, phys, ydam[:3 * N], yaf[:3 * N], yaf[3 * N:], Paf, residual=False)  # step 8
-        sl = dict(sysd, A=T["A"], B=T["B"], C=T["C"], D=T["D"], r=af * gm * dt * m)
-        o = Oracle(sl, **solve_opts)
-        o.setup()
+        r_k = af * gm * dt * m
+        rebuild = pc_rebuild == 0 or (pc_rebuild == 1 and l == 1) or "oracle" not in held
+        if rebuild:
+            o = Oracle(dict(sysd, A=T["A"], B=T["B"], C=T["C"], D=T["D"], r=r_k), **solve_opts)
+            o.setup()
+            held["oracle"] = o
+            setups += 1
+        else:                                         # lagged: new operators, the held preconditioner
+            o = held["oracle"]
+            o.set_values(T["A"], T["B"], T["C"], T["D"])
+            if n_out:
+                o.set_resistances(r_k)
         dx, info, rc = o.solve(-R)                                                       # step 9
         if rc != 0:
             raise RuntimeError(f"newton_step: nested solve failed (status {rc})")

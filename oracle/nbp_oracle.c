@@ -1113,6 +1113,17 @@ or_ctx *or_create(int N, const int *arp, const int *aci, const double *av, const
     return c;
 }
 
+/* New operator values on the same patterns (a later Newton tangent, Sec.
+ * 2.5); the preconditioner built by the last or_setup -- AMG(A), S_hat,
+ * AMG(S_hat) -- is kept, which makes it a lagged preconditioner of the new
+ * operator (the outer FGMRES accepts any preconditioner, Sec. 3). */
+void or_set_values(or_ctx *c, const double *av, const double *bv, const double *cv, const double *dv) {
+    memcpy(c->A.v, av, sizeof(double) * (size_t)c->A.rp[c->N] * 9);
+    memcpy(c->B.v, bv, sizeof(double) * (size_t)c->B.rp[c->N] * 3);
+    memcpy(c->C.v, cv, sizeof(double) * (size_t)c->C.rp[c->N] * 3);
+    memcpy(c->D.v, dv, sizeof(double) * (size_t)c->D.rp[c->N]);
+}
+
 void or_set_options(or_ctx *c, const or_options *o) { c->opt = *o; }
 void or_get_options(const or_ctx *c, or_options *o) { *o = c->opt; }
 

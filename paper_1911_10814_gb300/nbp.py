@@ -90,7 +90,7 @@ class nbp_vms_params(ctypes.Structure):
 
 class nbp_newton_opts(ctypes.Structure):
     _fields_ = [("tol_R", ctypes.c_double), ("tol_A", ctypes.c_double), ("l_max", ctypes.c_int32),
-                ("nts", ctypes.c_int32)]
+                ("nts", ctypes.c_int32), ("pc_rebuild", ctypes.c_int32)]
 
 
 class nbp_newton_info(ctypes.Structure):
@@ -98,7 +98,8 @@ class nbp_newton_info(ctypes.Structure):
                 ("res0", ctypes.c_double), ("res", ctypes.c_double),
                 ("outer_iters", ctypes.c_int64), ("A_iters", ctypes.c_int64), ("S_iters", ctypes.c_int64),
                 ("I_iters", ctypes.c_int64), ("residual_s", ctypes.c_double), ("tangent_s", ctypes.c_double),
-                ("setup_s", ctypes.c_double), ("solve_s", ctypes.c_double), ("total_s", ctypes.c_double)]
+                ("setup_s", ctypes.c_double), ("solve_s", ctypes.c_double), ("total_s", ctypes.c_double),
+                ("setups", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -570,16 +571,18 @@ class Vms:
         return out
 
     def newton_step(self, y_n, yd_n, rcr: dict = None, tol_R=1e-6, tol_A=1e-6, l_max=20, nts=10, eps_abs=1e-8,
-                    eps_rel=1e-5, allow_not_converged=False):
+                    eps_rel=1e-5, allow_not_converged=False, pc_rebuild=0):
         """One predictor multi-corrector time step (nbp_newton_step).  rcr:
-        CUDA float64 tensors Rp, C, Rd, Pd, Pi (Pi^k_n).  Returns (y, ydot, Pi_np1, info)."""
+        CUDA float64 tensors Rp, C, Rd, Pd, Pi (Pi^k_n).  pc_rebuild: 0 a
+        preconditioner per tangent, 1 one per step, 2 keep the context's.
+        Returns (y, ydot, Pi_np1, info)."""
         y = self.s.zeros(4 * self.N)
         yd = self.s.zeros(4 * self.N)
         Pi = self.s.zeros(max(self.s.n_out, 1))
         p = None
         if rcr is not None:
             p = rcr_params(rcr["Rp"], rcr["C"], rcr["Rd"], rcr["Pd"], rcr["Pi"], rcr["Pi"], eps_abs, eps_rel)
-        o = nbp_newton_opts(tol_R, tol_A, l_max, nts)
+        o = nbp_newton_opts(tol_R, tol_A, l_max, nts, pc_rebuild)
         info = nbp_newton_info()
         st = self.lib.nbp_newton_step(self.h, ctypes.byref(p) if p is not None else None, _ptr(y_n), _ptr(yd_n),
                                       _ptr(y), _ptr(yd), _ptr(Pi), ctypes.byref(o), ctypes.byref(info))

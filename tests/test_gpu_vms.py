@@ -168,6 +168,45 @@ def test_newton_step_matches_oracle(case, fp32):
     s.close()
 
 
+def test_lagged_preconditioner_matches_oracle(case):
+    """Two time steps with one preconditioner for both (pc_rebuild 2: built
+    from the first tangent, kept for every later one): the same corrector
+    counts and accepted states as the oracle's lagged steps, and the same
+    corrector counts as a build per tangent (pc_rebuild 0)."""
+    d, m, ph = case
+    N = d["n_nodes"]
+    rng = np.random.default_rng(9)
+    y_n = np.concatenate([d["vel"], 10.0 * rng.standard_normal(N)])
+    yd_n = np.concatenate([rng.standard_normal(3 * N) * np.repeat(m["dir"] == 0, 3), rng.standard_normal(N)])
+    rc = _rcr()
+    iters = {}
+    for mode in (0, 2):
+        s, vm = _vms(d, m, False, rtol=1e-10)
+        pc = {}
+        y, yd, Pi_h, rch = _t(y_n), _t(yd_n), rc["Pi"], dict(rc)
+        yo, ydo = y_n, yd_n
+        iters[mode] = []
+        for step in range(2):
+            rct = {k: _t(rch[k]) for k in ("Rp", "C", "Rd", "Pd")}
+            rct["Pi"] = _t(Pi_h)
+            y, yd, Pi, info = vm.newton_step(y, yd, rct, tol_R=1e-8, tol_A=1e-12, nts=rc["nts"], pc_rebuild=mode)
+            assert info["converged"] == 1
+            iters[mode].append(info["iters"])
+            ref = oracle.newton_step(m, d, ph, yo, ydo, dict(rch, Pi=Pi_h), tol_R=1e-8, tol_A=1e-12, rtol=1e-10,
+                                     pc_rebuild=mode, pc=pc)
+            assert info["iters"] == ref["iters"]
+            assert info["setups"] == ref["setups"]
+            if mode == 2:
+                assert info["setups"] == (1 if step == 0 else 0)
+            assert _maxrel(y.cpu().numpy(), ref["y"]) <= 1e-7
+            Pi_h = Pi.cpu().numpy()
+            yo, ydo = ref["y"], ref["yd"]
+            y, yd = _t(yo), _t(ydo)
+        vm.close()
+        s.close()
+    assert iters[0] == iters[2]
+
+
 def test_newton_without_outlets():
     sp = synth.MeshSpec(4, 4, 5, Re=200.0, seed=2, R=(), name="box4_no_outlets")
     d, m = synth.generate(sp), synth.mesh(sp)

@@ -234,3 +234,32 @@ def test_newton_quadratic_from_consistent_start():
         for a, b in zip(rate[:-1], rate[1:]):
             assert b <= 0.1 * a
         y, yd, rc = out["y"], out["yd"], dict(rc, Pi=out["Pi"])
+
+
+def test_lagged_preconditioner_keeps_the_newton_iterates():
+    """A preconditioner built from an earlier tangent changes only the path of
+    each nested solve, not its solution (Sec. 3: the outer FGMRES takes any
+    preconditioner): over three time steps from a consistent start, one build
+    for all steps (pc_rebuild 2) gives the same corrector counts and the same
+    states, to the solve tolerance, as a build per tangent (pc_rebuild 0)."""
+    sp = synth.MeshSpec(4, 4, 12, Lz=3.0, Re=500.0, seed=2, R=(1e3,) * 4, pert=0.0, name="box4x4x12_eq")
+    d, m, ph = synth.generate(sp), synth.mesh(sp), oracle.vms_phys(sp)
+    N = d["n_nodes"]
+    R = np.asarray(sp.R)
+    Q0 = oracle.outlet_flows(d, d["vel"])
+    rc0 = dict(Rp=0.1 * R, Rd=0.9 * R, C=0.1 / R, Pd=np.zeros(4), Pi=0.9 * R * Q0, nts=10)
+    y0 = np.concatenate([d["vel"], np.full(N, float(np.mean(R * Q0)))])
+    runs = {}
+    for mode in (0, 2):
+        y, yd, rc, pc = y0.copy(), np.zeros(4 * N), dict(rc0), {}
+        iters, setups = [], 0
+        for _ in range(3):
+            out = oracle.newton_step(m, d, ph, y, yd, rc, tol_R=1e-9, tol_A=1e-14, rtol=1e-12, pc_rebuild=mode, pc=pc)
+            iters.append(out["iters"])
+            setups += out["setups"]
+            y, yd, rc = out["y"], out["yd"], dict(rc, Pi=out["Pi"])
+        runs[mode] = (iters, setups, y, yd)
+    assert runs[0][0] == runs[2][0]
+    assert runs[2][1] == 1 and runs[0][1] == sum(runs[0][0])
+    for a, b in zip(runs[0][2:], runs[2][2:]):
+        assert np.abs(a - b).max() <= 1e-9 * np.abs(a).max()
