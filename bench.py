@@ -95,11 +95,11 @@ def _peaks():
 
 
 def _source_hash():
-    """Hash of the source text of the dominant kernel (sell_pairs and k_sell in kernels.cuh)."""
+    """Hash of the source text of the dominant kernel: kernels.cuh from the
+    streamed-load helpers through the paired BF16 loop to the end of k_sell."""
     with open(os.path.join(ROOT, "paper_1911_10814_gb300", "csrc", "kernels.cuh")) as f:
         src = f.read()
-    k = src.index("__device__ __forceinline__ void sell_pairs(")   # the paired BF16 loop, then k_sell
-    a = src.rindex("template <", 0, k)
+    a = src.index("// Streamed loads of matrix values and columns")
     k2 = src.index("__global__ void __launch_bounds__(256) k_sell(", a)
     b = src.index("\n}\n", k2) + 3                                   # end of k_sell
     return hashlib.sha256(src[a:b].encode()).hexdigest()[:16]
