@@ -200,18 +200,22 @@ __device__ __forceinline__ void sell_pairs(const SpmvArgs &a, long long base2, i
     const __nv_bfloat162 *__restrict__ val = (const __nv_bfloat162 *)a.val;
     const int2 *__restrict__ ci = (const int2 *)a.sl_ci;
     int p = p0;
-    for (; p + step < np; p += 2 * step) {
-        const long long g0 = base2 + (long long)C * p, g1 = g0 + (long long)C * step;
-        const int2 c0 = ldm<C == 32>(ci + g0 + t), c1 = ldm<C == 32>(ci + g1 + t);
-        __nv_bfloat162 m0[BB], m1[BB];
+    // 32-row slices (the fine level, HBM-bound): two pairs per step; 8-row
+    // slices (coarse levels) measured faster one pair at a time
+    if (C == 32) {
+        for (; p + step < np; p += 2 * step) {
+            const long long g0 = base2 + (long long)C * p, g1 = g0 + (long long)C * step;
+            const int2 c0 = ldm<C == 32>(ci + g0 + t), c1 = ldm<C == 32>(ci + g1 + t);
+            __nv_bfloat162 m0[BB], m1[BB];
 #pragma unroll
-        for (int q = 0; q < BB; ++q) m0[q] = ldm<C == 32>(val + g0 * BB + t + q * C);
+            for (int q = 0; q < BB; ++q) m0[q] = ldm<C == 32>(val + g0 * BB + t + q * C);
 #pragma unroll
-        for (int q = 0; q < BB; ++q) m1[q] = ldm<C == 32>(val + g1 * BB + t + q * C);
-        pair_fma<BS>(c0, m0, x, acc0, acc1, acc2);
-        pair_fma<BS>(c1, m1, x, acc0, acc1, acc2);
+            for (int q = 0; q < BB; ++q) m1[q] = ldm<C == 32>(val + g1 * BB + t + q * C);
+            pair_fma<BS>(c0, m0, x, acc0, acc1, acc2);
+            pair_fma<BS>(c1, m1, x, acc0, acc1, acc2);
+        }
     }
-    if (p < np) {
+    for (; p < np; p += step) {
         const long long g0 = base2 + (long long)C * p;
         const int2 c0 = ldm<C == 32>(ci + g0 + t);
         __nv_bfloat162 m0[BB];
@@ -364,13 +368,32 @@ __global__ void __launch_bounds__(256) k_sellm(SpmvArgs a) {
     const int row = (int)(gid / T), h = (int)(gid % T);
     const int sl = row / C, t = row % C;
     const bool live = sl < a.nslice;
+    // the row's own epilogue operands are loaded before the slot loop, so that
+    // their latency overlaps the gather chain (these small levels are
+    // latency-bound: fewer rows than the GPU has threads in flight)
+    const bool own = h == 0 && live && row < a.nbr;
+    AT eb[3] = {0, 0, 0}, ed[3] = {0, 0, 0}, ex[3] = {0, 0, 0}, edi[BB];
+    if (own && (EPI == EPI_RES || EPI == EPI_CHEB)) {
+#pragma unroll
+        for (int q = 0; q < BS; ++q) eb[q] = ((const XT *)a.b)[(long long)row * BS + q];
+    }
+    if (own && EPI == EPI_CHEB) {
+        const XT *dv = (const XT *)a.dinv + (long long)row * BB;
+#pragma unroll
+        for (int q = 0; q < BS; ++q) {
+            ed[q] = ((const XT *)a.d)[(long long)row * BS + q];
+            ex[q] = ((const XT *)a.x)[(long long)row * BS + q];
+        }
+#pragma unroll
+        for (int q = 0; q < BB; ++q) edi[q] = dv[q];
+    }
     const long long base = live ? a.sl_ptr[sl] : 0;
     const int w = live ? (int)((a.sl_ptr[sl + 1] - base) / C) : 0;
     const VT *__restrict__ val = (const VT *)a.val;
     const int *__restrict__ ci = a.sl_ci;
     const XT *__restrict__ x = (const XT *)a.x;
     AT acc0 = 0, acc1 = 0, acc2 = 0;
-    if constexpr (std::is_same<VT, __nv_bfloat16>::value) {   // paired layout: the two threads take alternate pairs
+    if constexpr (std::is_same<VT, __nv_bfloat16>::value) {   // paired layout: the T threads take alternate pairs
         sell_pairs<BS, C>(a, base / 2, w / 2, t, h, T, x, acc0, acc1, acc2);
     } else {
         for (int k = h; k < w; k += T) {
@@ -395,27 +418,25 @@ __global__ void __launch_bounds__(256) k_sellm(SpmvArgs a) {
             acc2 += __shfl_xor_sync(0xffffffffu, acc2, o);
         }
     }
-    if (h != 0 || row >= a.nbr) return;
+    if (!own) return;
     const AT accs[3] = {acc0, acc1, acc2};
     XT *y = (XT *)a.y;
     if (EPI == EPI_CHEB) {
-        const XT *b = (const XT *)a.b;
-        const XT *dinv = (const XT *)a.dinv + (long long)row * BB;
         XT *d = (XT *)a.d;
         XT *xo = (XT *)a.xout;
         const AT c1 = sizeof(AT) == 4 ? (AT)a.c1f : (AT)a.c1, c2 = sizeof(AT) == 4 ? (AT)a.c2f : (AT)a.c2;
         AT r[3];
 #pragma unroll
-        for (int q = 0; q < BS; ++q) r[q] = b[(long long)row * BS + q] - accs[q];
+        for (int q = 0; q < BS; ++q) r[q] = eb[q] - accs[q];
 #pragma unroll
         for (int q = 0; q < BS; ++q) {
             AT tq = 0;
 #pragma unroll
-            for (int c = 0; c < BS; ++c) tq += dinv[q * BS + c] * r[c];
+            for (int c = 0; c < BS; ++c) tq += edi[q * BS + c] * r[c];
             const long long idx = (long long)row * BS + q;
-            const AT dn = c1 * d[idx] + c2 * tq;
+            const AT dn = c1 * ed[q] + c2 * tq;
             d[idx] = dn;
-            xo[idx] = x[idx] + dn;
+            xo[idx] = ex[q] + dn;
         }
         return;
     }
@@ -425,7 +446,7 @@ __global__ void __launch_bounds__(256) k_sellm(SpmvArgs a) {
         if (EPI == EPI_SET) y[idx] = accs[q];
         else if (EPI == EPI_ADD) y[idx] += accs[q];
         else if (EPI == EPI_SUB) y[idx] -= accs[q];
-        else y[idx] = ((const XT *)a.b)[idx] - accs[q];
+        else y[idx] = eb[q] - accs[q];
     }
 }
 
