@@ -891,16 +891,39 @@ __global__ void k_cheb_first(int nbr, int bs, const T *__restrict__ dinv, const 
     x[t] = dn;
 }
 // x = Cinv b, dense (coarsest level); one warp per row; the inverse is stored
-// in the vector type (FP64 or FP32)
+// in the vector type (FP64 or FP32).  Each lane keeps four independent
+// partial sums and, when rows start on 16-byte boundaries, reads 16 bytes
+// at a time, so a lane has several loads in flight instead of one long
+// chain of dependent adds; the partials are added in a fixed order.
 template <typename T>
 __global__ void k_dense_gemv(const T *__restrict__ Cinv, int n, const T *__restrict__ b, T *__restrict__ x) {
+    constexpr int W = Vec16<T>::W;
     const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int ln = threadIdx.x & 31;
     if (row >= n) return;
-    T s = 0;
-    for (int c = ln; c < n; c += 32) s += Cinv[(long long)row * n + c] * b[c];
-    s = warp_sum(s);
-    if (ln == 0) x[row] = s;
+    const T *r = Cinv + (long long)row * n;
+    T s[4] = {0, 0, 0, 0};
+    if (n % W == 0 && ((uintptr_t)Cinv & 15u) == 0 && ((uintptr_t)b & 15u) == 0) {
+        const int nv = n / W;
+#pragma unroll 4
+        for (int c = ln; c < nv; c += 32) {
+            T a[W], v[W];
+            vld(r + (long long)c * W, a);
+            vld(b + (long long)c * W, v);
+#pragma unroll
+            for (int e = 0; e < W; ++e) s[e % 4] += a[e] * v[e];
+        }
+    } else {
+        int c = ln;
+        for (; c + 96 < n; c += 128) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) s[q] += r[c + 32 * q] * b[c + 32 * q];
+        }
+        for (; c < n; c += 32) s[0] += r[c] * b[c];
+    }
+    T t = (s[0] + s[1]) + (s[2] + s[3]);
+    t = warp_sum(t);
+    if (ln == 0) x[row] = t;
 }
 
 // ============================================================== K-cycle

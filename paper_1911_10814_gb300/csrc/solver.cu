@@ -1668,17 +1668,24 @@ struct nbp_batch {
 };
 
 namespace nbp {
+// Runs f(i) for every instance on a pool of host threads (one per hardware
+// thread, at most one per instance).  Instances are handed out largest
+// first (longest-processing-time order), so that the largest solves start
+// early and the small ones fill in behind them.
 template <typename F> static nbp_status batch_run(nbp_batch *B, F f) {
     const int n = (int)B->ctx.size();
     const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
     const int nt = std::max(1, std::min(n, hw));
+    std::vector<int> order(n);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return B->ctx[a]->N > B->ctx[b]->N; });
     std::atomic<int> next(0);
     std::vector<nbp_status> st(n, NBP_OK);
     std::vector<std::thread> pool;
     for (int t = 0; t < nt; ++t)
         pool.emplace_back([&]() {
             cudaSetDevice(B->dev);
-            for (int i = next++; i < n; i = next++) st[i] = f(i);
+            for (int k = next++; k < n; k = next++) st[order[k]] = f(order[k]);
         });
     for (auto &th : pool) th.join();
     nbp_status worst = NBP_OK;
