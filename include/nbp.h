@@ -75,7 +75,7 @@ typedef struct {
  * delta^a, m, m_A, m_S, n_max).  Defaults from nbp_default_options():
  * rtol 1e-8, rtol_A 1e-3, rtol_S 1e-2, rtol_I 1e-2, atol 1e-50,
  * m = m_A = m_S = nmax = nmax_A = nmax_S = 200, AMG P_A and P_S with a
- * K-cycle on the S_hat hierarchy. */
+ * K-cycle on the S_hat hierarchy, device-driven Krylov loops. */
 typedef struct {
     double rtol, rtol_A, rtol_S, rtol_I, atol;
     int32_t m, m_A, m_S, nmax, nmax_A, nmax_S;
@@ -103,6 +103,17 @@ typedef struct {
                                below */
     int32_t cheb_degree_S;  /* Chebyshev degree of the AMG(S_hat) smoother, default 1
                                (cheb_degree, default 2, is that of AMG(A)) */
+    int32_t device_loop;    /* 1 (default): the whole nested solve is one CUDA graph whose
+                               GMRES loops are graph WHILE nodes driven on the device (one
+                               launch per solve, captured at the first solve and kept;
+                               nbp_batch_solve then runs every instance in one launch);
+                               0: the host drives the Krylov loops, reading one status per
+                               iteration.  Needs m_A >= nmax_A and m_S >= nmax_S (inner
+                               solves in one cycle) and variant 0 or 1; otherwise, or while
+                               profiling, the host-driven loop runs.  Same kernels, same
+                               arithmetic; the fused Gram-Schmidt kernel of the device loop
+                               splits its sums over one fixed grid for every basis length, so
+                               results differ from the host loop at rounding level. */
 } nbp_options;
 
 typedef struct {
@@ -223,7 +234,9 @@ const char *nbp_profile_report(const nbp_ctx *ctx);
 /* ---- batched solves (many independent tangents of uneven size) ----
  * One context and one CUDA stream per instance; nbp_batch_setup and
  * nbp_batch_solve drive the instances from a pool of host threads so that
- * their kernels overlap on the GPU.  systems: HOST array of `count` nbp_system
+ * their kernels overlap on the GPU.  With opt->device_loop = 1 the solve is
+ * one CUDA graph holding every instance's device-driven nested solve as a
+ * parallel branch, captured once and launched once per call.  systems: HOST array of `count` nbp_system
  * (each with its own DEVICE arrays, copied during the call).  b, x: HOST arrays
  * of `count` DEVICE pointers (4 N_i doubles each); infos: HOST array of
  * `count` (may be NULL).  Returns NBP_OK when every instance converged, else

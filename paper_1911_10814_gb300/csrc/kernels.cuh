@@ -535,6 +535,7 @@ struct GmState {
 struct GivensArgs {
     double *H = nullptr;
     int ldh = 0, j = 0;
+    const int *jp = nullptr;   // when set, the column index is read here (device-driven loops)
     const double *h1 = nullptr, *h2 = nullptr;
     double *cs = nullptr, *sn = nullptr, *g = nullptr;
     GmState *st = nullptr;
@@ -547,7 +548,7 @@ struct GivensArgs {
 __device__ __forceinline__ void givens_step(const GivensArgs &q, double nrm2) {
     double *H = q.H;
     const long long ldh = q.ldh;
-    const int j = q.j;
+    const int j = q.jp ? *q.jp : q.j;
     for (int i = 0; i <= j; ++i) H[i * ldh + j] = q.h1[i] + q.h2[i];
     const double beta = (nrm2 >= 0.0) ? sqrt(nrm2) : nrm2;   // NaN passes through
     H[(j + 1) * ldh + j] = beta;
@@ -575,9 +576,9 @@ __device__ __forceinline__ void givens_step(const GivensArgs &q, double nrm2) {
 // (ncols == 1, w the new Arnoldi vector) the last block also applies the
 // Givens update with out[0] = ||w||^2.
 template <typename T, int CB, bool VEC>
-__global__ void __launch_bounds__(256) k_mdot(const T *__restrict__ V, long long ldv, int ncols, const T *__restrict__ w,
-                                              long long n, double *__restrict__ partial, double *__restrict__ out,
-                                              unsigned *ticket, GivensArgs gv) {
+__device__ __forceinline__ void mdot_body(const T *__restrict__ V, long long ldv, int ncols, const T *__restrict__ w,
+                                          long long n, double *__restrict__ partial, double *__restrict__ out,
+                                          unsigned *ticket, const GivensArgs &gv) {
     constexpr int W = VEC ? Vec16<T>::W : 1;
     __shared__ double red[CB][8];
     long long lo, hi;
@@ -639,10 +640,24 @@ __global__ void __launch_bounds__(256) k_mdot(const T *__restrict__ V, long long
     }
 }
 
+template <typename T, int CB, bool VEC>
+__global__ void __launch_bounds__(256) k_mdot(const T *__restrict__ V, long long ldv, int ncols, const T *__restrict__ w,
+                                              long long n, double *__restrict__ partial, double *__restrict__ out,
+                                              unsigned *ticket, GivensArgs gv) {
+    mdot_body<T, CB, VEC>(V, ldv, ncols, w, n, partial, out, ticket, gv);
+}
+// the same with ncols = *jp + off read on the device (device-driven loops)
+template <typename T, int CB, bool VEC>
+__global__ void __launch_bounds__(256) k_mdot_dl(const T *__restrict__ V, long long ldv, const int *jp, int off,
+                                                 const T *__restrict__ w, long long n, double *__restrict__ partial,
+                                                 double *__restrict__ out, unsigned *ticket, GivensArgs gv) {
+    mdot_body<T, CB, VEC>(V, ldv, *jp + off, w, n, partial, out, ticket, gv);
+}
+
 // w[t] += alpha * sum_j coef[j] V[j][t]  (coef on the device, FP64)
 template <typename T, bool VEC>
-__global__ void __launch_bounds__(256) k_maxpy(const T *__restrict__ V, long long ldv, int ncols, const double *__restrict__ coef,
-                                               double alpha, T *__restrict__ w, long long n) {
+__device__ __forceinline__ void maxpy_body(const T *__restrict__ V, long long ldv, int ncols, const double *__restrict__ coef,
+                                           double alpha, T *__restrict__ w, long long n) {
     constexpr int W = VEC ? Vec16<T>::W : 1;
     __shared__ T cs[256];
     const long long nv = n / W;
@@ -675,15 +690,27 @@ __global__ void __launch_bounds__(256) k_maxpy(const T *__restrict__ V, long lon
     }
 }
 
+template <typename T, bool VEC>
+__global__ void __launch_bounds__(256) k_maxpy(const T *__restrict__ V, long long ldv, int ncols, const double *__restrict__ coef,
+                                               double alpha, T *__restrict__ w, long long n) {
+    maxpy_body<T, VEC>(V, ldv, ncols, coef, alpha, w, n);
+}
+template <typename T, bool VEC>
+__global__ void __launch_bounds__(256) k_maxpy_dl(const T *__restrict__ V, long long ldv, const int *jp, int off,
+                                                  const double *__restrict__ coef, double alpha, T *__restrict__ w,
+                                                  long long n) {
+    maxpy_body<T, VEC>(V, ldv, *jp + off, coef, alpha, w, n);
+}
+
 // Fused CGS pass for up to MAXC columns: w_new = w - sum_j coef[j] V[j], then
 // the dots of the same columns with w_new (norm_only = 0) or the squared norm
 // of w_new (norm_only = 1), V read once; partials reduced by the last block
 // into out (and, with gv.H set, the Givens update with out[0] = ||w_new||^2).
 template <typename T, int MAXC, bool VEC>
-__global__ void __launch_bounds__(256) k_maxpy_dot(const T *__restrict__ V, long long ldv, int ncols,
-                                                   const double *__restrict__ coef, T *__restrict__ w, long long n,
-                                                   int norm_only, double *__restrict__ partial, double *__restrict__ out,
-                                                   unsigned *ticket, GivensArgs gv) {
+__device__ __forceinline__ void maxpy_dot_body(const T *__restrict__ V, long long ldv, int ncols,
+                                               const double *__restrict__ coef, T *__restrict__ w, long long n,
+                                               int norm_only, double *__restrict__ partial, double *__restrict__ out,
+                                               unsigned *ticket, const GivensArgs &gv) {
     constexpr int W = VEC ? Vec16<T>::W : 1;
     __shared__ double red[MAXC][8];
     __shared__ T cs[MAXC];
@@ -748,6 +775,66 @@ __global__ void __launch_bounds__(256) k_maxpy_dot(const T *__restrict__ V, long
     }
 }
 
+template <typename T, int MAXC, bool VEC>
+__global__ void __launch_bounds__(256) k_maxpy_dot(const T *__restrict__ V, long long ldv, int ncols,
+                                                   const double *__restrict__ coef, T *__restrict__ w, long long n,
+                                                   int norm_only, double *__restrict__ partial, double *__restrict__ out,
+                                                   unsigned *ticket, GivensArgs gv) {
+    maxpy_dot_body<T, MAXC, VEC>(V, ldv, ncols, coef, w, n, norm_only, partial, out, ticket, gv);
+}
+
+// The device-driven form of the fused pass, ncols = *jp + off read on the
+// device.  A basis longer than MAXC takes two sweeps over the block's own
+// chunk: the subtraction w -= V coef (columns in ascending order, each
+// thread on the elements it owns), then mdot_body's products (or norm and
+// Givens update) on the same elements, so no element crosses threads.
+template <typename T, int MAXC, bool VEC>
+__global__ void __launch_bounds__(256) k_maxpy_dot_dl(const T *__restrict__ V, long long ldv, const int *jp, int off,
+                                                      const double *__restrict__ coef, T *__restrict__ w, long long n,
+                                                      int norm_only, double *__restrict__ partial,
+                                                      double *__restrict__ out, unsigned *ticket, GivensArgs gv) {
+    const int ncols = *jp + off;
+    if (ncols <= MAXC) {
+        maxpy_dot_body<T, MAXC, VEC>(V, ldv, ncols, coef, w, n, norm_only, partial, out, ticket, gv);
+        return;
+    }
+    constexpr int W = VEC ? Vec16<T>::W : 1;
+    __shared__ T cs[256];
+    long long lo, hi;
+    block_chunk(n, Vec16<T>::W, lo, hi);
+    const long long nv = (hi - lo) / W;
+    for (int c0 = 0; c0 < ncols; c0 += 256) {
+        const int cn = min(256, ncols - c0);
+        __syncthreads();
+        if ((int)threadIdx.x < cn) cs[threadIdx.x] = (T)coef[c0 + threadIdx.x];
+        __syncthreads();
+        for (long long i = threadIdx.x; i < nv; i += blockDim.x) {
+            const long long t = lo + i * W;
+            T a[W];
+            if constexpr (VEC) vld(w + t, a);
+            else a[0] = w[t];
+            for (int j = 0; j < cn; ++j) {
+                T v[W];
+                if constexpr (VEC) vld(V + (long long)(c0 + j) * ldv + t, v);
+                else v[0] = V[(long long)(c0 + j) * ldv + t];
+#pragma unroll
+                for (int e = 0; e < W; ++e) a[e] -= cs[j] * v[e];
+            }
+            if constexpr (VEC) vst(w + t, a);
+            else w[t] = a[0];
+        }
+        if (VEC && threadIdx.x < hi - lo - nv * W) {   // ragged end, the thread mdot_body gives it
+            const long long t = lo + nv * W + threadIdx.x;
+            T a = w[t];
+            for (int j = 0; j < cn; ++j) a -= cs[j] * V[(long long)(c0 + j) * ldv + t];
+            w[t] = a;
+        }
+    }
+    __syncthreads();
+    if (norm_only) mdot_body<T, 8, VEC>(w, ldv, 1, w, n, partial, out, ticket, gv);
+    else mdot_body<T, 8, VEC>(V, ldv, ncols, w, n, partial, out, ticket, gv);
+}
+
 // ============================================================== vectors
 template <typename T> __global__ void k_fill(T *x, T v, long long n) {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) x[i] = v;
@@ -767,7 +854,7 @@ template <typename T> __global__ void k_sub(T *z, const T *x, const T *y, long l
         z[i] = x[i] - y[i];
 }
 // v = w / s[0] (skips when s[0] == 0); VEC: v, w 16-byte aligned
-template <typename T, bool VEC> __global__ void k_scale_inv(T *v, const T *w, const double *s, long long n) {
+template <typename T, bool VEC> __device__ __forceinline__ void scale_inv_body(T *v, const T *w, const double *s, long long n) {
     constexpr int W = VEC ? Vec16<T>::W : 1;
     __shared__ T inv_s;
     __shared__ int zero;
@@ -793,6 +880,14 @@ template <typename T, bool VEC> __global__ void k_scale_inv(T *v, const T *w, co
     }
     if (VEC && blockIdx.x == 0 && threadIdx.x < n - nv * W) v[nv * W + threadIdx.x] = w[nv * W + threadIdx.x] * inv;
 }
+template <typename T, bool VEC> __global__ void k_scale_inv(T *v, const T *w, const double *s, long long n) {
+    scale_inv_body<T, VEC>(v, w, s, n);
+}
+// v = column *jp + off of the basis at vbase (stride ld)
+template <typename T, bool VEC>
+__global__ void k_scale_inv_dl(T *vbase, long long ld, const int *jp, int off, const T *w, const double *s, long long n) {
+    scale_inv_body<T, VEC>(vbase + (long long)(*jp + off) * ld, w, s, n);
+}
 
 // ============================================= least squares (GMRES end)
 // y = H(0:k,0:k)^{-1} g(0:k), upper triangular.  One thread.
@@ -801,6 +896,54 @@ __global__ void k_trisolve(const double *H, int ldh, const double *g, double *y,
 __global__ void k_gm_init(double *g, int m1, const double *beta2, double *beta, GmState *st);
 
 __global__ void k_recip(long long n, const double *a, double *b);
+
+// ============================== device-driven Krylov loops (graph WHILE)
+// Loop state of one GMRES level on the device.
+struct GmDev {
+    int j, its, m, nmax;        // column of the current cycle, iterations, restart length, iteration limit
+    int conv, nan, pad0, pad1;  // pad0: restart cycles run (outer level)
+    double tol, bnorm, res, rel_true;
+};
+// Per-solve options of the device-driven solve (written before each launch).
+struct DlParams {
+    double rtol, rtol_A, rtol_S, rtol_I, atol;
+    int m, m_A, m_S, nmax, nmax_A, nmax_S;
+};
+// Iteration counters of one device-driven solve.
+struct DlCounters {
+    long long A, S, I, nA, nS, nI;
+};
+__global__ void k_dl_init(GmDev *st, double *g, int m1, const double *nrm2, double *beta, GmState *gs,
+                          const double *rtol, const double *atol, const int *m, const int *nmax,
+                          cudaGraphConditionalHandle h);
+__global__ void k_dl_step(GmDev *st, const GmState *gs, cudaGraphConditionalHandle h);
+__global__ void k_dl_cycle_start(GmDev *st, cudaGraphConditionalHandle h);
+__global__ void k_dl_end(GmDev *st, const double *H, int ldh, const double *g, double *y, long long *its_total,
+                         long long *solves);
+__global__ void k_dl_restart(GmDev *st, const double *nrm2, double *g, int m1, double *beta, GmState *gs,
+                             cudaGraphConditionalHandle h);
+
+// out = entries [from, from + n) of basis column *jp + off (stride ld), converted
+template <typename D, typename S>
+__global__ void k_col_get(D *out, const S *vbase, long long ld, const int *jp, int off, long long from, long long n) {
+    const S *v = vbase + (long long)(*jp + off) * ld + from;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = (D)v[i];
+}
+// entries [to, to + n) of basis column *jp + off = in, converted
+template <typename D, typename S>
+__global__ void k_col_put(D *vbase, long long ld, const int *jp, int off, long long to, const S *in, long long n) {
+    D *v = vbase + (long long)(*jp + off) * ld + to;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        v[i] = (D)in[i];
+}
+// out = x .* d with x basis column *jp (point Jacobi from a column)
+template <typename T>
+__global__ void k_mul_col(T *out, const T *vbase, long long ld, const int *jp, const T *d, long long n) {
+    const T *x = vbase + (long long)(*jp) * ld;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = x[i] * d[i];
+}
 
 // ================================================================= AMG
 // coarse r_c[I] = sum_{i in I} r[i], bs components: 8 lanes per aggregate
@@ -882,6 +1025,21 @@ __global__ void k_cheb_first(int nbr, int bs, const T *__restrict__ dinv, const 
                              T *__restrict__ x, T *__restrict__ bcopy) {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (long long)nbr * bs) return;
+    if (bcopy) bcopy[t] = b[t];
+    const int i = (int)(t / bs), a = (int)(t - (long long)i * bs);
+    T s = 0;
+    for (int c = 0; c < bs; ++c) s += dinv[(long long)i * bs * bs + a * bs + c] * b[(long long)i * bs + c];
+    const T dn = c2 * s;
+    d[t] = dn;
+    x[t] = dn;
+}
+// k_cheb_first with b = basis column *jp (stride ld)
+template <typename T>
+__global__ void k_cheb_first_col(int nbr, int bs, const T *__restrict__ dinv, const T *__restrict__ vbase, long long ld,
+                                 const int *jp, T c2, T *__restrict__ d, T *__restrict__ x, T *__restrict__ bcopy) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long long)nbr * bs) return;
+    const T *b = vbase + (long long)(*jp) * ld;
     if (bcopy) bcopy[t] = b[t];
     const int i = (int)(t / bs), a = (int)(t - (long long)i * bs);
     T s = 0;

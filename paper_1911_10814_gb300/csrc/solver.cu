@@ -153,6 +153,28 @@ struct nbp_ctx {
     CycleGraph graphs[2][3];
     cudaStream_t cap = nullptr;   // private stream used only while capturing
     bool use_graphs = true;
+    // device-driven solve: the whole nested solve as one CUDA graph whose
+    // Krylov loops are graph WHILE nodes (dl_st: loop states of the outer,
+    // S and A levels; dl_par: per-solve options; dl_cnt: iteration counters;
+    // dl_b, dl_x: its fixed right-hand side and solution; dl_zo: the outer
+    // preconditioned vector; dl_zA, dl_zS: preconditioner outputs when the
+    // preconditioner is not an AMG cycle; dl_cap: capture streams by loop depth)
+    nbp::GmDev *dl_st = nullptr;
+    nbp::DlParams *dl_par = nullptr;
+    nbp::DlCounters *dl_cnt = nullptr;
+    double *dl_b = nullptr, *dl_x = nullptr, *dl_zo = nullptr;
+    void *dl_zA = nullptr, *dl_zS = nullptr;
+    nbp::DlParams dl_hpar{};               // host copy of the per-solve options (source of the upload)
+    nbp::GmDev *dl_host = nullptr;         // pinned copy of the outer loop state
+    nbp::DlCounters *dl_hcnt = nullptr;    // pinned copy of the counters
+    cudaStream_t dl_cap[4] = {};
+    cudaGraphExec_t dl_exec = nullptr;     // the single-solve graph
+    // kernel nodes of the captured solve, to count the kernels one solve runs:
+    // outside every loop, per restart cycle, per outer iteration, per A- or
+    // I-iteration, per S-iteration (nested loops' bodies not included)
+    long long dl_k_top = 0, dl_k_cycle = 0, dl_k_outer = 0, dl_k_A = 0, dl_k_S = 0;
+    unsigned long long graph_gen = 0;      // bumped whenever captured graphs go stale
+    std::vector<const void *> dl_key;      // buffers and options the graph was captured with
 };
 
 namespace nbp {
@@ -269,12 +291,27 @@ template <typename F> static unsigned one_wave(F kernel) {
 
 // out = V(:, 0..ncols-1)^T w, reduced on the device by the grid's last block
 // (which also applies the Givens update gv when gv.H is set)
+constexpr int kFusedCols = 16;   // longest basis of the fused subtract + products kernel
+
+// grids of the fixed-grid Arnoldi kernels, taken once per kernel (and before
+// any graph capture: see dl_prepare)
+template <typename T> struct ArnoldiGrids {
+    unsigned mdot_v, mdot_s, mdot_dl_v, mdot_dl_s, mpd_dl_v, mpd_dl_s;
+};
+template <typename T> static const ArnoldiGrids<T> &arnoldi_grids() {
+    static const ArnoldiGrids<T> g = {one_wave(k_mdot<T, 8, true>), one_wave(k_mdot<T, 8, false>),
+                                      one_wave(k_mdot_dl<T, 8, true>), one_wave(k_mdot_dl<T, 8, false>),
+                                      one_wave(k_maxpy_dot_dl<T, kFusedCols, true>),
+                                      one_wave(k_maxpy_dot_dl<T, kFusedCols, false>)};
+    return g;
+}
+
 template <typename T> static void mdot(nbp_ctx *c, Krylov<T> &K, const T *V, long long ldv, int ncols, const T *w, double *out,
                                        GivensArgs gv = GivensArgs()) {
     cudaEvent_t e0;
     prof_begin(c, e0);
     const bool vec = al16(V) && al16(w) && (ncols <= 1 || (ldv * (long long)sizeof(T)) % 16 == 0);
-    static const unsigned g1 = one_wave(k_mdot<T, 8, true>), g0 = one_wave(k_mdot<T, 8, false>);
+    const unsigned g1 = arnoldi_grids<T>().mdot_v, g0 = arnoldi_grids<T>().mdot_s;
     if (vec) k_mdot<T, 8, true><<<g1, 256, 0, c->s>>>(V, ldv, ncols, w, K.n, K.partial, out, K.ticket, gv);
     else k_mdot<T, 8, false><<<g0, 256, 0, c->s>>>(V, ldv, ncols, w, K.n, K.partial, out, K.ticket, gv);
     NBP_LAUNCHED();
@@ -291,8 +328,6 @@ template <typename T> static void maxpy(nbp_ctx *c, long long n, const T *V, lon
     NBP_LAUNCHED();
     prof_end(c, CAT_ARNOLDI, (double)(ncols + 2) * n * sizeof(T), "arnoldi/maxpy");
 }
-
-constexpr int kFusedCols = 16;
 
 template <typename T, int MAXC, bool VEC>
 static void launch_maxpy_dot_v(nbp_ctx *c, Krylov<T> &K, const T *V, long long ldv, int ncols, const double *coef, T *w,
@@ -673,6 +708,10 @@ static void drop_graphs(nbp_ctx *c) {
             if (g.exec) cudaGraphExecDestroy(g.exec);
             g = nbp_ctx::CycleGraph();
         }
+    if (c->dl_exec) cudaGraphExecDestroy(c->dl_exec);
+    c->dl_exec = nullptr;
+    c->dl_key.clear();
+    c->graph_gen++;
 }
 
 // One AMG cycle x = M^{-1} b.  Outside profiling the whole cycle (every level,
@@ -896,6 +935,409 @@ static nbp_status nested_solve(nbp_ctx *c, const double *b, double *x) {
     c->info.rel_res_true = R.rel_true;
     c->info.status = R.conv ? NBP_OK : NBP_NOT_CONVERGED;
     return R.conv ? NBP_OK : NBP_NOT_CONVERGED;
+}
+
+// ------------------------------------------------- device-driven solve
+// The whole nested solve captured once as a CUDA graph in which every GMRES
+// level's loop is a graph WHILE node (nested: restart cycles of the outer
+// FGMRES > its iterations > the A- and S-solves of Algorithm 3 > the inner
+// A-solve of Algorithm 2).  The loop state lives on the device (GmDev) and
+// each iteration ends with a one-thread kernel that applies the host loop's
+// stopping rule and sets the node's condition, so a solve needs no host
+// round trip per iteration and many solves can run as one launch.  The
+// kernels are those of the host-driven loop; the ones that depend on the
+// iteration index read it from the device state.  The inner levels run one
+// cycle (m >= n_max), the outer one restarts on the device.
+
+constexpr int kDlDepth = 4;   // nesting depth of WHILE bodies
+
+static cudaGraph_t capture_graph_of(cudaStream_t s) {
+    cudaStreamCaptureStatus st;
+    cudaGraph_t g = nullptr;
+    NBP_CUDA(cudaStreamGetCaptureInfo(s, &st, nullptr, &g, nullptr, nullptr, nullptr));
+    require(st == cudaStreamCaptureStatusActive && g, NBP_ERR_STATE, "device loop: stream is not capturing");
+    return g;
+}
+static cudaGraphConditionalHandle new_handle(nbp_ctx *c) {
+    cudaGraphConditionalHandle h;
+    NBP_CUDA(cudaGraphConditionalHandleCreate(&h, capture_graph_of(c->s), 0, 0));
+    return h;
+}
+// kernel nodes directly in graph g (not inside its conditional nodes' bodies)
+static long long kernel_nodes(cudaGraph_t g) {
+    size_t n = 0;
+    NBP_CUDA(cudaGraphGetNodes(g, nullptr, &n));
+    std::vector<cudaGraphNode_t> nodes(n);
+    if (n) NBP_CUDA(cudaGraphGetNodes(g, nodes.data(), &n));
+    long long k = 0;
+    for (size_t i = 0; i < n; ++i) {
+        cudaGraphNodeType t;
+        NBP_CUDA(cudaGraphNodeGetType(nodes[i], &t));
+        if (t == cudaGraphNodeTypeKernel) ++k;
+    }
+    return k;
+}
+
+// A WHILE node on handle h at the current capture position; body() is
+// captured into its body graph on the capture stream of nesting depth
+// `depth`.  Returns the kernel nodes of the body (nested bodies excluded).
+template <class F> static long long emit_while(nbp_ctx *c, cudaGraphConditionalHandle h, int depth, F body) {
+    require(depth < kDlDepth, NBP_ERR_STATE, "device loop: nesting too deep");
+    cudaStreamCaptureStatus st;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t nd = 0;
+    NBP_CUDA(cudaStreamGetCaptureInfo(c->s, &st, nullptr, &g, &deps, nullptr, &nd));
+    cudaGraphNodeParams p = {};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = h;
+    p.conditional.type = cudaGraphCondTypeWhile;
+    p.conditional.size = 1;
+    cudaGraphNode_t node;
+    NBP_CUDA(cudaGraphAddNode(&node, g, deps, nullptr, nd, &p));
+    NBP_CUDA(cudaStreamUpdateCaptureDependencies(c->s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    cudaGraph_t bg = p.conditional.phGraph_out[0];
+    if (!c->dl_cap[depth]) NBP_CUDA(cudaStreamCreateWithFlags(&c->dl_cap[depth], cudaStreamNonBlocking));
+    cudaStream_t saved = c->s;
+    NBP_CUDA(cudaStreamBeginCaptureToGraph(c->dl_cap[depth], bg, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    c->s = c->dl_cap[depth];
+    try {
+        body();
+    } catch (...) {
+        cudaGraph_t x = nullptr;
+        cudaStreamEndCapture(c->dl_cap[depth], &x);
+        c->s = saved;
+        throw;
+    }
+    cudaGraph_t out = nullptr;
+    NBP_CUDA(cudaStreamEndCapture(c->dl_cap[depth], &out));
+    c->s = saved;
+    return kernel_nodes(bg);
+}
+
+// The Arnoldi step of iteration st->j (the host loop's kernels, index read
+// on the device): h1 = V^T w; w -= V h1, h2 = V^T w; w -= V h2, ||w|| and the
+// Givens update of column j; V(:, j+1) = w / ||w||.
+template <typename T> static void arnoldi_dl(nbp_ctx *c, Krylov<T> &K, GmDev *st) {
+    const bool vec = al16(K.V) && al16(K.w) && (K.ld * (long long)sizeof(T)) % 16 == 0;
+    const int *jp = &st->j;
+    GivensArgs gv = K.givens(0);
+    gv.jp = jp;
+    if (vec) {
+        const unsigned g1 = arnoldi_grids<T>().mdot_dl_v, g2 = arnoldi_grids<T>().mpd_dl_v;
+        k_mdot_dl<T, 8, true><<<g1, 256, 0, c->s>>>(K.V, K.ld, jp, 1, K.w, K.n, K.partial, K.h1, K.ticket, GivensArgs());
+        k_maxpy_dot_dl<T, kFusedCols, true><<<g2, 256, 0, c->s>>>(K.V, K.ld, jp, 1, K.h1, K.w, K.n, 0, K.partial, K.h2,
+                                                                  K.ticket, GivensArgs());
+        k_maxpy_dot_dl<T, kFusedCols, true><<<g2, 256, 0, c->s>>>(K.V, K.ld, jp, 1, K.h2, K.w, K.n, 1, K.partial, K.nrm,
+                                                                  K.ticket, gv);
+        k_scale_inv_dl<T, true><<<grid_for(K.n / Vec16<T>::W + 1), 256, 0, c->s>>>(K.V, K.ld, jp, 1, K.w, &K.st->beta, K.n);
+    } else {
+        const unsigned g1 = arnoldi_grids<T>().mdot_dl_s, g2 = arnoldi_grids<T>().mpd_dl_s;
+        k_mdot_dl<T, 8, false><<<g1, 256, 0, c->s>>>(K.V, K.ld, jp, 1, K.w, K.n, K.partial, K.h1, K.ticket, GivensArgs());
+        k_maxpy_dot_dl<T, kFusedCols, false><<<g2, 256, 0, c->s>>>(K.V, K.ld, jp, 1, K.h1, K.w, K.n, 0, K.partial, K.h2,
+                                                                   K.ticket, GivensArgs());
+        k_maxpy_dot_dl<T, kFusedCols, false><<<g2, 256, 0, c->s>>>(K.V, K.ld, jp, 1, K.h2, K.w, K.n, 1, K.partial, K.nrm,
+                                                                   K.ticket, gv);
+        k_scale_inv_dl<T, false><<<grid_for(K.n + 1), 256, 0, c->s>>>(K.V, K.ld, jp, 1, K.w, &K.st->beta, K.n);
+    }
+    NBP_LAUNCHED();
+}
+
+// x += Z(:, 0..j-1) y after the cycle (j read on the device)
+template <typename T> static void update_dl(nbp_ctx *c, Krylov<T> &K, GmDev *st, T *x) {
+    const bool vec = al16(K.Z) && al16(x) && (K.ld * (long long)sizeof(T)) % 16 == 0;
+    const unsigned grid = grid_for(K.n / (vec ? Vec16<T>::W : 1) + 1, 256, 8LL * kSMs * 4);
+    if (vec) k_maxpy_dl<T, true><<<grid, 256, 0, c->s>>>(K.Z, K.ld, &st->j, 0, K.y, 1.0, x, K.n);
+    else k_maxpy_dl<T, false><<<grid, 256, 0, c->s>>>(K.Z, K.ld, &st->j, 0, K.y, 1.0, x, K.n);
+    NBP_LAUNCHED();
+}
+
+// One single-cycle GMRES level (inner A- and S-solves): pc(vbase, ld, jp)
+// preconditions basis column j into a fixed buffer it returns; op(z, w).
+template <typename T, typename Op, typename Pc>
+static long long gmres_dl(nbp_ctx *c, Krylov<T> &K, long long n, GmDev *st, const double *rtol, const int *m,
+                          const int *nmax, long long *its_total, long long *solves, const T *b, T *x, Pc pc, Op op,
+                          int depth) {
+    fill<T>(x, T(0), n, c->s);
+    mdot<T>(c, K, b, n, 1, b, K.nrm);
+    const cudaGraphConditionalHandle h = new_handle(c);
+    k_dl_init<<<1, 256, 0, c->s>>>(st, K.g, K.m + 1, K.nrm, K.beta, K.st, rtol, &c->dl_par->atol, m, nmax, h);
+    NBP_LAUNCHED();
+    scale_inv<T>(c, K.V, b, K.beta, n);
+    NBP_LAUNCHED();
+    const long long kb = emit_while(c, h, depth, [&] {
+        T *z = pc(K.V, K.ld, &st->j);
+        op(z, K.w);
+        k_col_put<T, T><<<grid_for(n), 256, 0, c->s>>>(K.Z, K.ld, &st->j, 0, 0, z, n);
+        NBP_LAUNCHED();
+        arnoldi_dl<T>(c, K, st);
+        k_dl_step<<<1, 1, 0, c->s>>>(st, K.st, h);
+        NBP_LAUNCHED();
+    });
+    k_dl_end<<<1, 1, 0, c->s>>>(st, K.H, K.m, K.g, K.y, its_total, solves);
+    NBP_LAUNCHED();
+    update_dl<T>(c, K, st, x);
+    return kb;
+}
+
+// An AMG cycle on hierarchy H from basis column *jp into the hierarchy's
+// level-0 output buffer (the copy-in fused with the first smoothing step, as
+// the replayed cycle does); returns that buffer.
+template <typename T> static T *cycle_from_col(nbp_ctx *c, Hier &H, const T *vbase, long long ld, const int *jp) {
+    const int avsel = amg_vsel_of(c->opt.precision);
+    Level &L0 = H.L[0];
+    const long long n = (long long)L0.M.nbr * H.bs;
+    T *gb = wvec<T>(L0, 0), *gx = wvec<T>(L0, 1);
+    const bool first_in = H.cheb > 0 && H.nlev > 1;
+    if (first_in) {
+        const Cheb ch = cheb_of(L0);
+        k_cheb_first_col<T><<<grid_exact(n), 256, 0, c->s>>>(L0.M.nbr, H.bs, dinv_of<T>(L0), vbase, ld, jp,
+                                                             (T)(1.0 / ch.theta), wvec<T>(L0, 4), wvec<T>(L0, 2), gb);
+    } else {
+        k_col_get<T, T><<<grid_for(n), 256, 0, c->s>>>(gb, vbase, ld, jp, 0, 0, n);
+    }
+    NBP_LAUNCHED();
+    vcycle_level<T>(c, H, 0, avsel, gb, gx, first_in);
+    return gx;
+}
+
+// A-solve (GMRES(m_A) + P_A) of s into y inside the graph
+template <typename T>
+static void solve_A_dl(nbp_ctx *c, int vsel, const T *s, T *y, const double *rtol, long long *its, long long *solves,
+                       int depth) {
+    const long long n = 3LL * c->N;
+    auto op = [&](const T *x, T *out) { apply_A<T>(c, vsel, x, out); };
+    auto pc = [&](T *vbase, long long ld, const int *jp) -> T * {
+        if (c->opt.pc_A == 1) {
+            T *z = (T *)c->dl_zA;
+            k_mul_col<T><<<grid_for(n), 256, 0, c->s>>>(z, vbase, ld, jp, BUF<T>(c).dinvA, n);
+            NBP_LAUNCHED();
+            return z;
+        }
+        return cycle_from_col<T>(c, c->HA, vbase, ld, jp);
+    };
+    c->dl_k_A = gmres_dl<T>(c, KA<T>(c), n, &c->dl_st[2], rtol, &c->dl_par->m_A, &c->dl_par->nmax_A, its, solves, s, y, pc,
+                            op, depth);
+}
+
+// Algorithm 3 on outer basis column *jp (FP64) into c->dl_zo (FP64)
+template <typename T> static double *pscr_dl(nbp_ctx *c, const double *vbase, long long ld, const int *jp, int depth) {
+    const int vsel = vsel_of(c->opt.precision);
+    const long long N = c->N, nv = 3 * N;
+    Bufs<T> &Bf = BUF<T>(c);
+    DlCounters *cnt = c->dl_cnt;
+    DlParams *par = c->dl_par;
+    k_col_get<T, double><<<grid_for(nv), 256, 0, c->s>>>(Bf.sv, vbase, ld, jp, 0, 0, nv);
+    k_col_get<T, double><<<grid_for(N), 256, 0, c->s>>>(Bf.sp, vbase, ld, jp, 0, nv, N);
+    NBP_LAUNCHED();
+    if (c->opt.variant == 0) {
+        solve_A_dl<T>(c, vsel, Bf.sv, Bf.yvh, &par->rtol_A, &cnt->A, &cnt->nA, depth);            // step 1
+        do_spmv<T>(c, c->C, vsel, sargs(Bf.yvh, Bf.sp), EPI_SUB, false);                          // step 2
+    }
+    auto opS = [&](const T *x, T *out) {                                                          // Algorithm 2
+        do_spmv<T>(c, c->D, vsel, sargs(x, out), EPI_SET, false);
+        do_spmv<T>(c, c->B, vsel, sargs(x, Bf.xbar), EPI_SET, false);
+        solve_A_dl<T>(c, vsel, Bf.xbar, Bf.xtil, &par->rtol_I, &cnt->I, &cnt->nI, depth + 1);
+        do_spmv<T>(c, c->C, vsel, sargs(Bf.xtil, out), EPI_SUB, false);
+    };
+    auto pcS = [&](T *vb, long long l, const int *j) -> T * {
+        if (c->opt.pc_S == 1) {
+            T *z = (T *)c->dl_zS;
+            k_col_get<T, T><<<grid_for(N), 256, 0, c->s>>>(z, vb, l, j, 0, 0, N);
+            NBP_LAUNCHED();
+            return z;
+        }
+        return cycle_from_col<T>(c, c->HS, vb, l, j);
+    };
+    c->dl_k_S = gmres_dl<T>(c, KS<T>(c), N, &c->dl_st[1], &par->rtol_S, &par->m_S, &par->nmax_S, &cnt->S, &cnt->nS,
+                            Bf.sp, Bf.yp, pcS, opS, depth);                                         // step 3
+    do_spmv<T>(c, c->B, vsel, sargs(Bf.yp, Bf.sv), EPI_SUB, false);                               // step 4
+    solve_A_dl<T>(c, vsel, Bf.sv, Bf.yv, &par->rtol_A, &cnt->A, &cnt->nA, depth);                // step 5
+    convert<double, T>(c->dl_zo, Bf.yv, nv, c->s);
+    convert<double, T>(c->dl_zo + nv, Bf.yp, N, c->s);
+    return c->dl_zo;
+}
+
+// The outer FGMRES(m) with P_SCR and the true-residual check, on dl_b into dl_x
+static void outer_dl(nbp_ctx *c) {
+    Krylov<double> &K = c->Kout;
+    const long long n = 4LL * c->N;
+    GmDev *st = &c->dl_st[0];
+    DlParams *par = c->dl_par;
+    const double *b = c->dl_b;
+    double *x = c->dl_x;
+    fill<double>(x, 0.0, n, c->s);
+    copy<double>(K.r, b, n, c->s);
+    mdot<double>(c, K, b, n, 1, b, K.nrm);
+    const cudaGraphConditionalHandle hr = new_handle(c);
+    k_dl_init<<<1, 256, 0, c->s>>>(st, K.g, K.m + 1, K.nrm, K.beta, K.st, &par->rtol, &par->atol, &par->m, &par->nmax, hr);
+    NBP_LAUNCHED();
+    c->dl_k_cycle = emit_while(c, hr, 0, [&] {       // restart cycles
+        const cudaGraphConditionalHandle hi = new_handle(c);
+        k_dl_cycle_start<<<1, 1, 0, c->s>>>(st, hi);
+        NBP_LAUNCHED();
+        scale_inv<double>(c, K.V, K.r, K.beta, n);
+        NBP_LAUNCHED();
+        c->dl_k_outer = emit_while(c, hi, 1, [&] {   // iterations
+            double *z = c->opt.precision == 0 ? pscr_dl<double>(c, K.V, K.ld, &st->j, 2)
+                                              : pscr_dl<float>(c, K.V, K.ld, &st->j, 2);
+            apply_full(c, z, K.w);
+            k_col_put<double, double><<<grid_for(n), 256, 0, c->s>>>(K.Z, K.ld, &st->j, 0, 0, z, n);
+            NBP_LAUNCHED();
+            arnoldi_dl<double>(c, K, st);
+            k_dl_step<<<1, 1, 0, c->s>>>(st, K.st, hi);
+            NBP_LAUNCHED();
+        });
+        k_dl_end<<<1, 1, 0, c->s>>>(st, K.H, K.m, K.g, K.y, nullptr, nullptr);
+        NBP_LAUNCHED();
+        update_dl<double>(c, K, st, x);
+        apply_full(c, x, K.w);                       // true residual: the next restart vector or the check
+        k_sub<double><<<grid_for(n), 256, 0, c->s>>>(K.r, b, K.w, n);
+        NBP_LAUNCHED();
+        mdot<double>(c, K, K.r, n, 1, K.r, K.nrm);
+        k_dl_restart<<<1, 256, 0, c->s>>>(st, K.nrm, K.g, K.m + 1, K.beta, K.st, hr);
+        NBP_LAUNCHED();
+    });
+}
+
+// Whether the device-driven solve can run with the current options: one
+// cycle per inner solve (m >= n_max), not SIMPLE, not profiling.
+static bool dl_supported(const nbp_ctx *c) {
+    const nbp_options &o = c->opt;
+    return o.m_A >= o.nmax_A && o.m_S >= o.nmax_S && o.variant != 2 && !c->prof.on;
+}
+
+// Buffers of the device-driven solve and every Krylov space at the sizes the
+// options need, before any capture (a capture must not allocate).
+static void dl_prepare(nbp_ctx *c) {
+    prepare_inner(c);
+    cudaStream_t s = c->s;
+    const long long N = c->N, n = 4 * N;
+    if (!c->full_w) c->full_w = dmalloc<double>(n, s);
+    if (!c->dl_st) {
+        c->dl_st = dmalloc<GmDev>(3, s);
+        c->dl_par = dmalloc<DlParams>(1, s);
+        c->dl_cnt = dmalloc<DlCounters>(1, s);
+        c->dl_b = dmalloc<double>(n, s);
+        c->dl_x = dmalloc<double>(n, s);
+        c->dl_zo = dmalloc<double>(n, s);
+        c->dl_zA = dmalloc<double>(3 * N, s);   // room for either inner type
+        c->dl_zS = dmalloc<double>(N, s);
+        NBP_CUDA(cudaMallocHost((void **)&c->dl_host, sizeof(GmDev)));
+        NBP_CUDA(cudaMallocHost((void **)&c->dl_hcnt, sizeof(DlCounters)));
+    }
+    const nbp_options &o = c->opt;
+    auto cl = [](int m, int nmax) { return std::max(1, std::min(m, std::max(nmax, 1))); };
+    c->Kout.ensure(n, cl(o.m, o.nmax), s);
+    if (o.precision == 0) {
+        c->KA64.ensure(3 * N, cl(o.m_A, o.nmax_A), s);
+        c->KS64.ensure(N, cl(o.m_S, o.nmax_S), s);
+    } else {
+        c->KA32.ensure(3 * N, cl(o.m_A, o.nmax_A), s);
+        c->KS32.ensure(N, cl(o.m_S, o.nmax_S), s);
+    }
+    // the graph bakes in these buffers and option switches (the operators'
+    // value copies too: a refresh of the values reallocates them)
+    std::vector<const void *> key = {c->Kout.V, c->KA64.V, c->KS64.V, c->KA32.V, c->KS32.V, c->B32.sv, c->B64.sv,
+                                     c->full_w, c->diagA, c->lr.lr_rp, c->lr.f,
+                                     (const void *)(intptr_t)o.precision, (const void *)(intptr_t)o.variant,
+                                     (const void *)(intptr_t)o.pc_A, (const void *)(intptr_t)o.pc_S,
+                                     (const void *)(intptr_t)c->Kout.m, (const void *)(intptr_t)c->KA32.m,
+                                     (const void *)(intptr_t)c->KS32.m, (const void *)(intptr_t)c->KA64.m,
+                                     (const void *)(intptr_t)c->KS64.m};
+    for (const DMat *M : {&c->A, &c->B, &c->C, &c->D})
+        for (const void *q : {(const void *)M->v, (const void *)M->v32, (const void *)M->v16, (const void *)M->sl_ptr,
+                              (const void *)M->sl_ci, (const void *)M->sl_v, (const void *)M->sl_v32,
+                              (const void *)M->sl2_ptr, (const void *)M->sl2_ci, (const void *)M->sl_v16})
+            key.push_back(q);
+    if (key != c->dl_key && c->dl_exec) {
+        cudaGraphExecDestroy(c->dl_exec);
+        c->dl_exec = nullptr;
+    }
+    c->dl_key = key;
+    DlParams p;
+    p.rtol = o.rtol; p.rtol_A = o.rtol_A; p.rtol_S = o.rtol_S; p.rtol_I = o.rtol_I; p.atol = o.atol;
+    p.m = o.m; p.m_A = o.m_A; p.m_S = o.m_S; p.nmax = o.nmax; p.nmax_A = o.nmax_A; p.nmax_S = o.nmax_S;
+    c->dl_hpar = p;
+    NBP_CUDA(cudaMemcpyAsync(c->dl_par, &c->dl_hpar, sizeof(DlParams), cudaMemcpyHostToDevice, s));
+    NBP_CUDA(cudaMemsetAsync(c->dl_cnt, 0, sizeof(DlCounters), s));
+    // the Arnoldi kernels' grids are fixed at their first use: take them now
+    (void)arnoldi_grids<float>();
+    (void)arnoldi_grids<double>();
+}
+
+// Capture the device-driven solve of context c on its (capturing) stream.
+static void capture_solve(nbp_ctx *c) {
+    const bool prof = c->prof.on;
+    c->prof.on = false;
+    try {
+        const long long k0 = kernel_nodes(capture_graph_of(c->s));
+        outer_dl(c);
+        c->dl_k_top = kernel_nodes(capture_graph_of(c->s)) - k0;
+    } catch (...) {
+        c->prof.on = prof;
+        throw;
+    }
+    c->prof.on = prof;
+}
+
+static void dl_build(nbp_ctx *c) {
+    if (c->dl_exec) return;
+    if (!c->cap) NBP_CUDA(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
+    NBP_CUDA(cudaStreamSynchronize(c->s));
+    cudaStream_t saved = c->s;
+    c->s = c->cap;
+    cudaGraph_t g = nullptr;
+    NBP_CUDA(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
+    try {
+        capture_solve(c);
+    } catch (...) {
+        cudaStreamEndCapture(c->cap, &g);
+        if (g) cudaGraphDestroy(g);
+        c->s = saved;
+        throw;
+    }
+    NBP_CUDA(cudaStreamEndCapture(c->cap, &g));
+    c->s = saved;
+    const cudaError_t e = cudaGraphInstantiate(&c->dl_exec, g, 0);
+    cudaGraphDestroy(g);
+    NBP_CUDA(e);
+}
+
+// Results of a finished device-driven solve (host copies taken on the stream)
+static nbp_status dl_collect(nbp_ctx *c) {
+    const GmDev &o = *c->dl_host;
+    const DlCounters &k = *c->dl_hcnt;
+    // kernels the solve ran: the captured kernel nodes times their executions
+    c->prof.launches += c->dl_k_top + (long long)o.pad0 * c->dl_k_cycle + (long long)o.its * c->dl_k_outer +
+                        (k.A + k.I) * c->dl_k_A + k.S * c->dl_k_S;
+    require(!o.nan, NBP_ERR_NAN, "device loop: NaN/Inf in the nested solve");
+    c->info.outer_iters = o.its;
+    c->info.A_iters += k.A;
+    c->info.S_iters += k.S;
+    c->info.I_iters += k.I;
+    c->info.rel_res_est = o.bnorm > 0 ? o.res / o.bnorm : 0.0;
+    c->info.rel_res_true = o.rel_true;
+    c->info.status = o.conv ? NBP_OK : NBP_NOT_CONVERGED;
+    return o.conv ? NBP_OK : NBP_NOT_CONVERGED;
+}
+
+static void dl_fetch(nbp_ctx *c) {
+    NBP_CUDA(cudaMemcpyAsync(c->dl_host, c->dl_st, sizeof(GmDev), cudaMemcpyDeviceToHost, c->s));
+    NBP_CUDA(cudaMemcpyAsync(c->dl_hcnt, c->dl_cnt, sizeof(DlCounters), cudaMemcpyDeviceToHost, c->s));
+}
+
+// The nested solve as one graph launch: b in, x out (device pointers)
+static nbp_status nested_solve_dl(nbp_ctx *c, const double *b, double *x) {
+    dl_prepare(c);
+    dl_build(c);
+    const long long n = 4LL * c->N;
+    copy<double>(c->dl_b, b, n, c->s);
+    NBP_CUDA(cudaGraphLaunch(c->dl_exec, c->s));
+    copy<double>(x, c->dl_x, n, c->s);
+    dl_fetch(c);
+    NBP_CUDA(cudaStreamSynchronize(c->s));
+    return dl_collect(c);
 }
 
 // ---------------------------------------------------------- create / setup
@@ -1150,6 +1592,12 @@ static void destroy_ctx(nbp_ctx *c) {
     if (c->tctx) destroy_ctx(c->tctx);
     drop_graphs(c);
     if (c->cap) cudaStreamDestroy(c->cap);
+    for (cudaStream_t q : c->dl_cap)
+        if (q) cudaStreamDestroy(q);
+    dfree(c->dl_st, s); dfree(c->dl_par, s); dfree(c->dl_cnt, s); dfree(c->dl_b, s); dfree(c->dl_x, s);
+    dfree(c->dl_zo, s); dfree(c->dl_zA, s); dfree(c->dl_zS, s);
+    if (c->dl_host) cudaFreeHost(c->dl_host);
+    if (c->dl_hcnt) cudaFreeHost(c->dl_hcnt);
     dmat_free(c->A, s); dmat_free(c->B, s); dmat_free(c->C, s); dmat_free(c->D, s); dmat_free(c->Shat, s);
     free_lowrank(c->lr, s);
     hier_free(c->HA, s); hier_free(c->HS, s);
@@ -1308,6 +1756,7 @@ void nbp_default_options(nbp_options *o) {
     o->amg_cycle = 1;
     o->amg_kdepth = 99;
     o->cheb_degree_S = 1;
+    o->device_loop = 1;
 }
 
 static nbp_status check_options(const nbp_options *o, std::string &msg) {
@@ -1315,6 +1764,7 @@ static nbp_status check_options(const nbp_options *o, std::string &msg) {
     if (o->m < 1 || o->m_A < 1 || o->m_S < 1 || o->nmax < 1 || o->nmax_A < 1 || o->nmax_S < 1) { msg = "restart/n_max < 1"; return NBP_ERR_INVALID; }
     if (o->precision < 0 || o->precision > 3 || o->pc_A < 0 || o->pc_A > 1 || o->pc_S < 0 || o->pc_S > 1 || o->variant < 0 || o->variant > 2) { msg = "bad mode switch"; return NBP_ERR_INVALID; }
     if (o->cheb_degree < 0 || o->cheb_degree > 8 || o->cheb_degree_S < 0 || o->cheb_degree_S > 8 || o->amg_max_levels < 1 || o->amg_cycle < 0 || o->amg_cycle > 2 || o->amg_kdepth < 1) { msg = "bad AMG option"; return NBP_ERR_INVALID; }
+    if (o->device_loop < 0 || o->device_loop > 1) { msg = "device_loop must be 0 or 1"; return NBP_ERR_INVALID; }
     return NBP_OK;
 }
 
@@ -1436,7 +1886,7 @@ static nbp_status solve_common(nbp_ctx *c, const double *b, double *x, const nbp
     auto t0 = std::chrono::steady_clock::now();
     nbp_status st;
     try {
-        st = nested_solve(c, b, x);
+        st = (c->opt.device_loop && dl_supported(c)) ? nested_solve_dl(c, b, x) : nested_solve(c, b, x);
     } catch (...) {
         c->opt = saved;
         throw;
@@ -1665,6 +2115,13 @@ struct nbp_batch {
     std::vector<cudaStream_t> streams;
     int dev = 0;
     std::string err;
+    // one graph with every instance's device-driven solve as a parallel
+    // branch (device_loop = 1), and what it was captured from
+    cudaStream_t s0 = nullptr;
+    cudaGraphExec_t dl_exec = nullptr;
+    std::vector<unsigned long long> dl_gen;
+    std::vector<std::vector<const void *>> dl_key;
+    std::vector<cudaEvent_t> ev;
 };
 
 namespace nbp {
@@ -1723,8 +2180,128 @@ nbp_status nbp_batch_setup(nbp_batch *B) {
     return nbp::batch_run(B, [&](int i) { return nbp_setup(B->ctx[i]); });
 }
 
+namespace nbp {
+// Every instance's device-driven nested solve in one graph launch on B->s0:
+// the right-hand sides are copied in, the graph (one parallel branch per
+// instance, captured once and kept while no instance's buffers or options
+// change) runs, the solutions are copied out and the counters read.
+static nbp_status batch_solve_dl(nbp_batch *B, const double *const *b, double *const *x, const nbp_options *opt,
+                                 nbp_info *infos) {
+    const int n = (int)B->ctx.size();
+    std::vector<nbp_options> saved(n);
+    for (int i = 0; i < n; ++i) {
+        nbp_ctx *c = B->ctx[i];
+        saved[i] = c->opt;
+        c->opt = *opt;
+        memset(&c->info, 0, sizeof(c->info));
+    }
+    auto restore = [&] {
+        for (int i = 0; i < n; ++i) B->ctx[i]->opt = saved[i];
+    };
+    try {
+        if (!B->s0) NBP_CUDA(cudaStreamCreateWithFlags(&B->s0, cudaStreamNonBlocking));
+        if ((int)B->ev.size() < n + 1) {
+            for (int i = (int)B->ev.size(); i < n + 1; ++i) {
+                cudaEvent_t e;
+                NBP_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+                B->ev.push_back(e);
+            }
+        }
+        bool stale = B->dl_exec == nullptr || (int)B->dl_gen.size() != n;
+        for (int i = 0; i < n; ++i) {
+            nbp_ctx *c = B->ctx[i];
+            require(dl_supported(c), NBP_ERR_INVALID, "nbp_batch_solve: device_loop needs m_A >= nmax_A, m_S >= nmax_S and "
+                                                      "variant 0 or 1");
+            dl_prepare(c);                      // buffers, options upload, counters reset (instance stream)
+            if (!stale && (B->dl_gen[i] != c->graph_gen || B->dl_key[i] != c->dl_key)) stale = true;
+            NBP_CUDA(cudaEventRecord(B->ev[i], c->s));
+            NBP_CUDA(cudaStreamWaitEvent(B->s0, B->ev[i], 0));
+        }
+        if (stale) {
+            if (B->dl_exec) cudaGraphExecDestroy(B->dl_exec);
+            B->dl_exec = nullptr;
+            NBP_CUDA(cudaStreamSynchronize(B->s0));
+            for (int i = 0; i < n; ++i) NBP_CUDA(cudaStreamSynchronize(B->ctx[i]->s));
+            cudaGraph_t g = nullptr;
+            NBP_CUDA(cudaStreamBeginCapture(B->s0, cudaStreamCaptureModeThreadLocal));
+            try {
+                NBP_CUDA(cudaEventRecord(B->ev[n], B->s0));
+                for (int i = 0; i < n; ++i) NBP_CUDA(cudaStreamWaitEvent(B->ctx[i]->s, B->ev[n], 0));   // fork
+                for (int i = 0; i < n; ++i) capture_solve(B->ctx[i]);
+                for (int i = 0; i < n; ++i) {                                                         // join
+                    NBP_CUDA(cudaEventRecord(B->ev[i], B->ctx[i]->s));
+                    NBP_CUDA(cudaStreamWaitEvent(B->s0, B->ev[i], 0));
+                }
+            } catch (...) {
+                cudaStreamEndCapture(B->s0, &g);
+                if (g) cudaGraphDestroy(g);
+                throw;
+            }
+            NBP_CUDA(cudaStreamEndCapture(B->s0, &g));
+            const cudaError_t e = cudaGraphInstantiate(&B->dl_exec, g, 0);
+            cudaGraphDestroy(g);
+            NBP_CUDA(e);
+            B->dl_gen.assign(n, 0);
+            B->dl_key.assign(n, {});
+            for (int i = 0; i < n; ++i) {
+                B->dl_gen[i] = B->ctx[i]->graph_gen;
+                B->dl_key[i] = B->ctx[i]->dl_key;
+            }
+        }
+        for (int i = 0; i < n; ++i) {
+            nbp_ctx *c = B->ctx[i];
+            NBP_CUDA(cudaMemcpyAsync(c->dl_b, b[i], sizeof(double) * 4 * c->N, cudaMemcpyDeviceToDevice, B->s0));
+        }
+        NBP_CUDA(cudaGraphLaunch(B->dl_exec, B->s0));
+        for (int i = 0; i < n; ++i) {
+            nbp_ctx *c = B->ctx[i];
+            NBP_CUDA(cudaMemcpyAsync(x[i], c->dl_x, sizeof(double) * 4 * c->N, cudaMemcpyDeviceToDevice, B->s0));
+            NBP_CUDA(cudaMemcpyAsync(c->dl_host, c->dl_st, sizeof(GmDev), cudaMemcpyDeviceToHost, B->s0));
+            NBP_CUDA(cudaMemcpyAsync(c->dl_hcnt, c->dl_cnt, sizeof(DlCounters), cudaMemcpyDeviceToHost, B->s0));
+        }
+        NBP_CUDA(cudaStreamSynchronize(B->s0));
+    } catch (const Error &e) {
+        restore();
+        B->err = e.msg;
+        return e.st;
+    } catch (const std::exception &e) {
+        restore();
+        B->err = e.what();
+        return NBP_ERR_CUDA;
+    }
+    nbp_status worst = NBP_OK;
+    for (int i = 0; i < n; ++i) {
+        nbp_ctx *c = B->ctx[i];
+        nbp_status st;
+        try {
+            st = dl_collect(c);
+        } catch (const Error &e) {
+            st = e.st;
+            c->err = e.msg;
+        }
+        c->info.setup_s = c->setup_s;
+        if (infos) infos[i] = c->info;
+        if (st != NBP_OK && (worst == NBP_OK || worst == NBP_NOT_CONVERGED)) {
+            worst = st;
+            if (st != NBP_NOT_CONVERGED) B->err = "instance " + std::to_string(i) + ": " + c->err;
+        }
+    }
+    restore();
+    return worst;
+}
+}  // namespace nbp
+
 nbp_status nbp_batch_solve(nbp_batch *B, const double *const *b, double *const *x, const nbp_options *opt, nbp_info *infos) {
     if (!B || !b || !x) return NBP_ERR_INVALID;
+    if (opt && opt->device_loop) {
+        std::string m;
+        const nbp_status st = check_options(opt, m);
+        if (st != NBP_OK) { B->err = "nbp_batch_solve: " + m; return st; }
+        for (int i = 0; i < (int)B->ctx.size(); ++i)
+            if (!B->ctx[i]->setup_done) { B->err = "nbp_batch_solve: instance " + std::to_string(i) + " not set up"; return NBP_ERR_STATE; }
+        cudaSetDevice(B->dev);
+        return nbp::batch_solve_dl(B, b, x, opt, infos);
+    }
     return nbp::batch_run(B, [&](int i) { return nbp_solve(B->ctx[i], b[i], x[i], opt, infos ? &infos[i] : nullptr); });
 }
 
@@ -1732,6 +2309,12 @@ int32_t nbp_batch_size(const nbp_batch *B) { return B ? (int32_t)B->ctx.size() :
 
 nbp_status nbp_batch_destroy(nbp_batch *B) {
     if (!B) return NBP_ERR_INVALID;
+    if (B->dl_exec) cudaGraphExecDestroy(B->dl_exec);
+    for (auto e : B->ev) cudaEventDestroy(e);
+    if (B->s0) {
+        cudaStreamSynchronize(B->s0);
+        cudaStreamDestroy(B->s0);
+    }
     for (auto *c : B->ctx) nbp_destroy(c);
     for (auto s : B->streams) cudaStreamDestroy(s);
     delete B;
@@ -1842,6 +2425,11 @@ static void values_changed(nbp_ctx *c) {
 // diag(A) and the replayed cycle graphs stay as they are.
 static void refresh_operators(nbp_ctx *c) {
     const int prec = build_level(c->setup_precision);
+    // the captured device-driven solve holds the old copies' addresses
+    if (c->dl_exec) cudaGraphExecDestroy(c->dl_exec);
+    c->dl_exec = nullptr;
+    c->dl_key.clear();
+    c->graph_gen++;
     for (DMat *M : {&c->A, &c->B, &c->C, &c->D}) {
         drop_value_copies(*M, c->s);
         make_sell(*M, prec, c->s);

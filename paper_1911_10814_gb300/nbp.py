@@ -37,7 +37,7 @@ class nbp_options(ctypes.Structure):
         ("precision", ctypes.c_int32), ("pc_A", ctypes.c_int32), ("pc_S", ctypes.c_int32),
         ("variant", ctypes.c_int32), ("amg_max_levels", ctypes.c_int32), ("amg_coarse_max", ctypes.c_int32),
         ("cheb_degree", ctypes.c_int32), ("theta", ctypes.c_double), ("amg_cycle", ctypes.c_int32),
-        ("amg_kdepth", ctypes.c_int32), ("cheb_degree_S", ctypes.c_int32),
+        ("amg_kdepth", ctypes.c_int32), ("cheb_degree_S", ctypes.c_int32), ("device_loop", ctypes.c_int32),
     ]
 
 

@@ -55,3 +55,34 @@ def test_batch_of_48_uneven_tangents():
         assert np.linalg.norm(r) / np.linalg.norm(d["b"]) <= 1e-8
         assert info["status"] == 0
     B.close()
+
+
+@pytest.mark.parametrize("prec", [1, 3])
+def test_batch_in_one_launch_matches_single_solves(prec):
+    """The batch as one CUDA graph (every instance's device-driven nested
+    solve a parallel branch, device_loop = 1) against each instance's
+    host-driven single solve: the same outer iterations (within one),
+    solutions equal to far below the solve tolerance, true residuals
+    <= 1e-8 by the oracle's product; a second launch of the kept graph gives
+    the same solutions bitwise."""
+    specs = synth.batch(count=6, seed=7, smin=5, smax=11)
+    systems = [synth.generate(sp) for sp in specs]
+    B = BatchSolver(systems, precision=prec)
+    B.setup()
+    bs = [_t(d["b"]) for d in systems]
+    xs, infos = B.solve(bs, device_loop=1)
+    xs2, infos2 = B.solve(bs, device_loop=1)
+    torch.cuda.synchronize()
+    for d, x, x2, info in zip(systems, xs, xs2, infos):
+        assert torch.equal(x, x2)
+        s = Solver(d, precision=prec)
+        s.setup()
+        x1, info1 = s.solve(_t(d["b"]), device_loop=0)
+        assert abs(info["outer_iters"] - info1["outer_iters"]) <= 1
+        xh, x1h = x.cpu().numpy(), x1.cpu().numpy()
+        assert np.linalg.norm(xh - x1h) / np.linalg.norm(x1h) <= 1e-6
+        o = oracle.Oracle(d)
+        assert np.linalg.norm(d["b"] - o.apply_full(xh)) / np.linalg.norm(d["b"]) <= 1e-8
+        assert info["status"] == 0
+        s.close()
+    B.close()

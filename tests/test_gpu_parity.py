@@ -175,6 +175,46 @@ def test_nested_solve_mixed(prec):
     s.close()
 
 
+@pytest.mark.parametrize("prec,pc_A,variant", [(0, 0, 0), (1, 0, 0), (3, 0, 0), (3, 1, 0), (3, 0, 1)])
+def test_device_loop_matches_host_loop(prec, pc_A, variant):
+    """The nested solve as one graph with device-driven WHILE loops against
+    the host-driven loop: the same iteration counts (within one), solutions
+    equal to far below the solve tolerance, the oracle's true residual
+    <= 1e-8, and two device-loop solves in a row (one captured graph, two
+    launches) bitwise equal."""
+    d = synth.generate(CASES["box9x11x23_q4"])
+    s = Solver(d, precision=prec, pc_A=pc_A, variant=variant)
+    s.setup()
+    b = _t(d["b"])
+    x0, i0 = s.solve(b, device_loop=0)
+    x1, i1 = s.solve(b, device_loop=1)
+    x2, i2 = s.solve(b, device_loop=1)
+    assert torch.equal(x1, x2)
+    for k in ("outer_iters", "A_iters", "S_iters", "I_iters"):
+        assert i1[k] == i2[k]
+    assert abs(i1["outer_iters"] - i0["outer_iters"]) <= 1
+    assert abs(i1["S_iters"] - i0["S_iters"]) <= max(2, 0.05 * i0["S_iters"])
+    x0h, x1h = x0.cpu().numpy(), x1.cpu().numpy()
+    assert _rel(x1h, x0h) <= 1e-6
+    o = oracle.Oracle(d)
+    assert np.linalg.norm(d["b"] - o.apply_full(x1h)) / np.linalg.norm(d["b"]) <= 1e-8
+    assert i1["rel_res_true"] <= 1e-8
+    s.close()
+
+
+def test_device_loop_falls_back_when_inner_solves_restart():
+    """With m_A < n_max_A an inner solve may restart, which the device loop
+    does not do: the host-driven loop runs instead, with the same result."""
+    d = synth.generate(synth.tiny())
+    s = Solver(d, precision=1)
+    s.setup()
+    b = _t(d["b"])
+    x0, i0 = s.solve(b, m_A=4, device_loop=0)
+    x1, i1 = s.solve(b, m_A=4, device_loop=1)
+    assert torch.equal(x0, x1)
+    s.close()
+
+
 def test_block_triangular_two_iterations():
     d = synth.generate(synth.tiny())
     s = Solver(d, variant=1, rtol_A=1e-13, rtol_S=1e-13, rtol_I=1e-13)
