@@ -67,9 +67,12 @@ template <typename T> struct Krylov {
     double *h1 = nullptr, *h2 = nullptr, *nrm = nullptr, *beta = nullptr, *partial = nullptr;
     unsigned *ticket = nullptr;   // last-block ticket of the Arnoldi reductions
     GmState *st = nullptr;
+    unsigned grid = 0;            // blocks of the Gram-Schmidt reductions (autotuned per n; 0: one wave)
     void ensure(long long n_, int m_, cudaStream_t s) {
         if (n_ == n && m_ <= m) return;
+        const unsigned keep_grid = (n_ == n) ? grid : 0u;
         release(s);
+        grid = keep_grid;
         n = n_; m = m_;
         ld = (n + 31) / 32 * 32;
         V = dmalloc<T>((size_t)ld * (m + 1), s);
@@ -311,7 +314,7 @@ template <typename T> static void mdot(nbp_ctx *c, Krylov<T> &K, const T *V, lon
     cudaEvent_t e0;
     prof_begin(c, e0);
     const bool vec = al16(V) && al16(w) && (ncols <= 1 || (ldv * (long long)sizeof(T)) % 16 == 0);
-    const unsigned g1 = arnoldi_grids<T>().mdot_v, g0 = arnoldi_grids<T>().mdot_s;
+    const unsigned g1 = K.grid ? K.grid : arnoldi_grids<T>().mdot_v, g0 = K.grid ? K.grid : arnoldi_grids<T>().mdot_s;
     if (vec) k_mdot<T, 8, true><<<g1, 256, 0, c->s>>>(V, ldv, ncols, w, K.n, K.partial, out, K.ticket, gv);
     else k_mdot<T, 8, false><<<g0, 256, 0, c->s>>>(V, ldv, ncols, w, K.n, K.partial, out, K.ticket, gv);
     NBP_LAUNCHED();
@@ -332,7 +335,8 @@ template <typename T> static void maxpy(nbp_ctx *c, long long n, const T *V, lon
 template <typename T, int MAXC, bool VEC>
 static void launch_maxpy_dot_v(nbp_ctx *c, Krylov<T> &K, const T *V, long long ldv, int ncols, const double *coef, T *w,
                                int norm_only, double *out, GivensArgs gv) {
-    static const unsigned grid = one_wave(k_maxpy_dot<T, MAXC, VEC>);
+    static const unsigned wave = one_wave(k_maxpy_dot<T, MAXC, VEC>);
+    const unsigned grid = K.grid ? K.grid : wave;
     k_maxpy_dot<T, MAXC, VEC><<<grid, 256, 0, c->s>>>(V, ldv, ncols, coef, w, K.n, norm_only, K.partial, out, K.ticket, gv);
 }
 template <typename T, int MAXC>
@@ -364,6 +368,77 @@ template <typename T> static void scale_inv(nbp_ctx *c, T *v, const T *w, const 
     else k_scale_inv<T, false><<<grid, 256, 0, c->s>>>(v, w, sc, n);
 }
 
+// Autotuner of the Gram-Schmidt kernels' grid for one vector length: the
+// candidates (one wave, a half and a quarter of it, a quarter block per SM,
+// and just enough blocks for eight 16-byte pieces per thread) are timed on a
+// four-column step -- multi-dot, subtract + products, subtract + norm -- in
+// the space's own buffers, three batches of five, the fastest batch kept.
+// A short vector leaves most of a one-wave grid idle in its reductions;
+// this is what a batch of small instances meets.  The choice is cached per
+// (vector length, type) for the life of the process, so every space of that
+// length sums in the same order.
+static std::mutex g_arnoldi_tune_mutex;
+static std::map<std::pair<long long, int>, unsigned> g_arnoldi_tune;
+
+template <typename T> static void tune_arnoldi(nbp_ctx *c, Krylov<T> &K) {
+    if (K.grid || K.m < 4 || c->prof.on) return;
+    const auto key = std::make_pair(K.n, (int)sizeof(T));
+    {
+        std::lock_guard<std::mutex> lock(g_arnoldi_tune_mutex);
+        auto it = g_arnoldi_tune.find(key);
+        if (it != g_arnoldi_tune.end()) { K.grid = it->second; return; }
+    }
+    const bool vec = al16(K.V) && al16(K.w) && (K.ld * (long long)sizeof(T)) % 16 == 0;
+    const ArnoldiGrids<T> &ag = arnoldi_grids<T>();
+    static const unsigned w4v = one_wave(k_maxpy_dot<T, 4, true>), w4s = one_wave(k_maxpy_dot<T, 4, false>);
+    unsigned gmax = vec ? std::min({ag.mdot_v, ag.mdot_dl_v, ag.mpd_dl_v, w4v})
+                        : std::min({ag.mdot_s, ag.mdot_dl_s, ag.mpd_dl_s, w4s});
+    gmax = std::max(1u, std::min(gmax, (unsigned)kReduceBlocks));
+    const long long pieces = (K.n + Vec16<T>::W - 1) / Vec16<T>::W;
+    std::vector<unsigned> cands = {gmax, gmax / 2, gmax / 4, (unsigned)kSMs / 4,
+                                   (unsigned)std::min<long long>(gmax, (pieces + 8 * 256 - 1) / (8 * 256))};
+    std::sort(cands.begin(), cands.end());
+    cands.erase(std::unique(cands.begin(), cands.end()), cands.end());
+    fill<T>(K.V, T(1), (long long)K.ld * 4, c->s);
+    fill<T>(K.w, T(1), K.n, c->s);
+    NBP_CUDA(cudaMemsetAsync(K.h1, 0, sizeof(double) * 4, c->s));
+    cudaEvent_t e0, e1;
+    NBP_CUDA(cudaEventCreate(&e0));
+    NBP_CUDA(cudaEventCreate(&e1));
+    float best = 1e30f;
+    unsigned arg = gmax;
+    const long long launches = c->prof.launches;
+    for (unsigned g : cands) {
+        if (g == 0) continue;
+        K.grid = g;
+        auto step = [&] {
+            mdot<T>(c, K, K.V, K.ld, 4, K.w, K.h2);
+            maxpy_dot<T>(c, K, K.V, K.ld, 4, K.h1, K.w, 0, K.h2);
+            maxpy_dot<T>(c, K, K.V, K.ld, 4, K.h1, K.w, 1, K.nrm);
+        };
+        step();
+        float tb = 1e30f;
+        for (int r = 0; r < 3; ++r) {
+            NBP_CUDA(cudaEventRecord(e0, c->s));
+            for (int q = 0; q < 5; ++q) step();
+            NBP_CUDA(cudaEventRecord(e1, c->s));
+            NBP_CUDA(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            NBP_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+            tb = std::min(tb, ms);
+        }
+        if (tb < best) { best = tb; arg = g; }
+    }
+    c->prof.launches = launches;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    std::lock_guard<std::mutex> lock(g_arnoldi_tune_mutex);
+    auto it = g_arnoldi_tune.find(key);
+    if (it != g_arnoldi_tune.end()) arg = it->second;
+    else g_arnoldi_tune[key] = arg;
+    K.grid = arg;
+}
+
 // ----------------------------------------------------------------- GMRES
 struct GmResult { int its = 0; double rel = 0.0, rel_true = -1.0; int conv = 0; };
 
@@ -385,6 +460,7 @@ static GmResult gmres(nbp_ctx *c, Krylov<T> &K, long long n, Op op, Pc pc, const
     GmResult R;
     m = std::max(1, std::min(m, std::max(nmax, 1)));
     K.ensure(n, m, s);
+    tune_arnoldi<T>(c, K);
     fill<T>(x, T(0), n, s);
     mdot<T>(c, K, b, n, 1, b, K.nrm);
     c->prof.launches++;
@@ -1024,7 +1100,8 @@ template <typename T> static void arnoldi_dl(nbp_ctx *c, Krylov<T> &K, GmDev *st
     GivensArgs gv = K.givens(0);
     gv.jp = jp;
     if (vec) {
-        const unsigned g1 = arnoldi_grids<T>().mdot_dl_v, g2 = arnoldi_grids<T>().mpd_dl_v;
+        const unsigned g1 = K.grid ? K.grid : arnoldi_grids<T>().mdot_dl_v;
+        const unsigned g2 = K.grid ? K.grid : arnoldi_grids<T>().mpd_dl_v;
         k_mdot_dl<T, 8, true><<<g1, 256, 0, c->s>>>(K.V, K.ld, jp, 1, K.w, K.n, K.partial, K.h1, K.ticket, GivensArgs());
         k_maxpy_dot_dl<T, kFusedCols, true><<<g2, 256, 0, c->s>>>(K.V, K.ld, jp, 1, K.h1, K.w, K.n, 0, K.partial, K.h2,
                                                                   K.ticket, GivensArgs());
@@ -1032,7 +1109,8 @@ template <typename T> static void arnoldi_dl(nbp_ctx *c, Krylov<T> &K, GmDev *st
                                                                   K.ticket, gv);
         k_scale_inv_dl<T, true><<<grid_for(K.n / Vec16<T>::W + 1), 256, 0, c->s>>>(K.V, K.ld, jp, 1, K.w, &K.st->beta, K.n);
     } else {
-        const unsigned g1 = arnoldi_grids<T>().mdot_dl_s, g2 = arnoldi_grids<T>().mpd_dl_s;
+        const unsigned g1 = K.grid ? K.grid : arnoldi_grids<T>().mdot_dl_s;
+        const unsigned g2 = K.grid ? K.grid : arnoldi_grids<T>().mpd_dl_s;
         k_mdot_dl<T, 8, false><<<g1, 256, 0, c->s>>>(K.V, K.ld, jp, 1, K.w, K.n, K.partial, K.h1, K.ticket, GivensArgs());
         k_maxpy_dot_dl<T, kFusedCols, false><<<g2, 256, 0, c->s>>>(K.V, K.ld, jp, 1, K.h1, K.w, K.n, 0, K.partial, K.h2,
                                                                    K.ticket, GivensArgs());
@@ -1229,12 +1307,17 @@ static void dl_prepare(nbp_ctx *c) {
     const nbp_options &o = c->opt;
     auto cl = [](int m, int nmax) { return std::max(1, std::min(m, std::max(nmax, 1))); };
     c->Kout.ensure(n, cl(o.m, o.nmax), s);
+    tune_arnoldi<double>(c, c->Kout);
     if (o.precision == 0) {
         c->KA64.ensure(3 * N, cl(o.m_A, o.nmax_A), s);
         c->KS64.ensure(N, cl(o.m_S, o.nmax_S), s);
+        tune_arnoldi<double>(c, c->KA64);
+        tune_arnoldi<double>(c, c->KS64);
     } else {
         c->KA32.ensure(3 * N, cl(o.m_A, o.nmax_A), s);
         c->KS32.ensure(N, cl(o.m_S, o.nmax_S), s);
+        tune_arnoldi<float>(c, c->KA32);
+        tune_arnoldi<float>(c, c->KS32);
     }
     // the graph bakes in these buffers and option switches (the operators'
     // value copies too: a refresh of the values reallocates them)
@@ -1244,7 +1327,9 @@ static void dl_prepare(nbp_ctx *c) {
                                      (const void *)(intptr_t)o.pc_A, (const void *)(intptr_t)o.pc_S,
                                      (const void *)(intptr_t)c->Kout.m, (const void *)(intptr_t)c->KA32.m,
                                      (const void *)(intptr_t)c->KS32.m, (const void *)(intptr_t)c->KA64.m,
-                                     (const void *)(intptr_t)c->KS64.m};
+                                     (const void *)(intptr_t)c->KS64.m, (const void *)(intptr_t)c->Kout.grid,
+                                     (const void *)(intptr_t)c->KA32.grid, (const void *)(intptr_t)c->KS32.grid,
+                                     (const void *)(intptr_t)c->KA64.grid, (const void *)(intptr_t)c->KS64.grid};
     for (const DMat *M : {&c->A, &c->B, &c->C, &c->D})
         for (const void *q : {(const void *)M->v, (const void *)M->v32, (const void *)M->v16, (const void *)M->sl_ptr,
                               (const void *)M->sl_ci, (const void *)M->sl_v, (const void *)M->sl_v32,
