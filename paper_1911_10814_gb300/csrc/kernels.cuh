@@ -225,6 +225,27 @@ __device__ __forceinline__ void sell_pairs(const SpmvArgs &a, long long base2, i
     }
 }
 
+// The unpaired last slot of an odd-width slice of the paired layout: its
+// columns at sl_ci[g + t] and value q at val[g bb + C q + t] (int and bf16
+// units), g = the slice's slot offset + C (width - 1).
+template <int BS, int C>
+__device__ __forceinline__ void sell_single(const SpmvArgs &a, long long g, int t, const float *__restrict__ x,
+                                            float &acc0, float &acc1, float &acc2) {
+    const __nv_bfloat16 *__restrict__ val = (const __nv_bfloat16 *)a.val + g * (BS * BS) + t;
+    const int c = ldm<C == 32>(a.sl_ci + g + t);
+    if (BS == 1) {
+        acc0 += __bfloat162float(ldm<C == 32>(val)) * __ldg(x + c);
+    } else {
+        const float x0 = __ldg(x + 3LL * c), x1 = __ldg(x + 3LL * c + 1), x2 = __ldg(x + 3LL * c + 2);
+        float m[9];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) m[q] = __bfloat162float(ldm<C == 32>(val + q * C));
+        acc0 += m[0] * x0 + m[1] * x1 + m[2] * x2;
+        acc1 += m[3] * x0 + m[4] * x1 + m[5] * x2;
+        acc2 += m[6] * x0 + m[7] * x1 + m[8] * x2;
+    }
+}
+
 // Sliced-ELL product for square BS x BS blocks: one thread per block row, C
 // rows per slice (C = 32: a warp per slice; C = 8 for matrices whose row
 // lengths vary, to cut padding).  Every load of values and columns by the C
@@ -243,8 +264,9 @@ __global__ void __launch_bounds__(256) k_sell(SpmvArgs a) {
     const int *__restrict__ ci = a.sl_ci;
     const XT *__restrict__ x = (const XT *)a.x;
     AT acc0 = 0, acc1 = 0, acc2 = 0;
-    if constexpr (std::is_same<VT, __nv_bfloat16>::value) {   // paired layout: w counts slots, even
+    if constexpr (std::is_same<VT, __nv_bfloat16>::value) {   // paired layout: w / 2 pairs, then one slot if w is odd
         sell_pairs<BS, C>(a, base / 2, w / 2, t, 0, 1, x, acc0, acc1, acc2);
+        if (w & 1) sell_single<BS, C>(a, base + (long long)C * (w - 1), t, x, acc0, acc1, acc2);
     } else {
 #pragma unroll 2
         for (int k = 0; k < w; ++k) {
@@ -395,6 +417,8 @@ __global__ void __launch_bounds__(256) k_sellm(SpmvArgs a) {
     AT acc0 = 0, acc1 = 0, acc2 = 0;
     if constexpr (std::is_same<VT, __nv_bfloat16>::value) {   // paired layout: the T threads take alternate pairs
         sell_pairs<BS, C>(a, base / 2, w / 2, t, h, T, x, acc0, acc1, acc2);
+        // an odd width's last slot goes to the thread whose turn comes next
+        if ((w & 1) && h == (w / 2) % T) sell_single<BS, C>(a, base + (long long)C * (w - 1), t, x, acc0, acc1, acc2);
     } else {
         for (int k = h; k < w; k += T) {
             const long long g = base + (long long)C * k;

@@ -86,11 +86,14 @@ struct DMat {
     int *sl_ci = nullptr;
     double *sl_v = nullptr;
     float *sl_v32 = nullptr;
-    // BF16 values use a paired variant of the same slices: widths rounded up
-    // to even, and slots 2p, 2p+1 of a row stored side by side, so that one
-    // thread loads both with one 4-byte load (bf16x2) per component and one
-    // 8-byte load (int2) of columns: pair slot g = sl2_ptr[s] / 2 + C p, its
-    // columns at sl2_ci[2 (g + t) + h], value q at sl_v16[2 ((g bb) + C q + t) + h].
+    // BF16 values use a paired variant of the same slices (same widths):
+    // slots 2p, 2p+1 of a row stored side by side, so that one thread loads
+    // both with one 4-byte load (bf16x2) per component and one 8-byte load
+    // (int2) of columns: pair slot g = sl2_ptr[s] / 2 + C p, its columns at
+    // sl2_ci[2 (g + t) + h], value q at sl_v16[2 ((g bb) + C q + t) + h].  An
+    // odd width w's last slot is stored unpaired after the pairs: with
+    // g = sl2_ptr[s] + C (w - 1), its columns at sl2_ci[g + t], value q at
+    // sl_v16[g bb + C q + t].
     long long *sl2_ptr = nullptr;
     int *sl2_ci = nullptr;
     __nv_bfloat16 *sl_v16 = nullptr;
