@@ -371,10 +371,6 @@ def oracle_model(t, counts, outer_solves=1):
     return sum(parts.values()), parts
 
 
-def _threads():
-    return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-
-
 def cpu_oracle_sample(d, counts, validate_scale=32):
     """The oracle (all host cores, OpenMP with fixed-order sums) on a bounded
     sample of the workload: its building blocks timed on the full tangent,
@@ -391,6 +387,8 @@ def cpu_oracle_sample(d, counts, validate_scale=32):
     t = oracle_phase_times(o, d)
     t_sample = time.perf_counter() - t0
     v, parts = oracle_model(t, counts)
+    cores = oracle.threads()
+    single = _single_thread(o, d, counts)
     del o
     check = None
     if validate_scale:
@@ -407,12 +405,26 @@ def cpu_oracle_sample(d, counts, validate_scale=32):
                  "measured_solve_s": measured, "model_s": model_v, "model_over_measured": model_v / measured,
                  "iters": cv}
         del ov
-    return {"value": v, "unit": "s", "cores": _threads(), "kind": "oracle",
+    return {"value": v, "unit": "s", "cores": cores, "kind": "oracle",
             "sample": f"oracle building blocks timed on the full 4.34M-unknown tangent ({t_sample:.1f} s: AMG(A) and "
                       f"AMG(S_hat) cycles, A/B/C/D/full products, a Gram-Schmidt column), combined by the measured "
                       f"solve's iteration counts {counts}; oracle setup {t_setup:.1f} s untimed",
             "parts_s": {k: round(x, 3) for k, x in parts.items()}, "phase_s": {k: round(x, 5) for k, x in t.items()},
-            "model_check": check}
+            "single_thread": single, "model_check": check}
+
+
+def _single_thread(o, d, counts):
+    """The same building blocks and model at one oracle thread (the results
+    are the same at any thread count; only the time changes)."""
+    import oracle
+    before = oracle.threads()
+    try:
+        oracle.threads(1)
+        t1 = oracle_phase_times(o, d)
+    finally:
+        oracle.threads(before)
+    v1, _ = oracle_model(t1, counts)
+    return {"value": v1, "unit": "s", "cores": 1, "phase_s": {k: round(x, 5) for k, x in t1.items()}}
 
 
 def run_reference(a):
@@ -437,12 +449,14 @@ def run_reference(a):
     for _ in range(a.steps):
         ts.append(oracle_model(oracle_phase_times(o, d), counts)[0])
     v = float(np.mean(ts))
+    cores = oracle.threads()
+    single = _single_thread(o, d, counts)
     line = {"metric": METRIC, "value": v, "unit": "s", "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
             "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": {"workload": synth.large_mixed(a.scale).name, "unknowns": 4 * d["n_nodes"],
                        "tolerance": 1e-8, "l2": "inputs larger than L2"},
-            "cpu_baseline": {"value": v, "unit": "s", "cores": _threads(), "kind": "oracle",
+            "cpu_baseline": {"value": v, "unit": "s", "cores": cores, "kind": "oracle", "single_thread": single,
                              "sample": "per step the oracle's building blocks (AMG cycles, A/B/C/D/full products, a "
                                        "Gram-Schmidt column) timed on the full tangent, combined by the iteration "
                                        f"counts {counts} of the oracle's own full-size solve "

@@ -141,6 +141,7 @@ def _load():
             ("or_amg_level_nnz", [vp, ctypes.c_int, ctypes.c_int], ctypes.c_int),
             ("or_amg_level_rho", [vp, ctypes.c_int, ctypes.c_int], ctypes.c_double),
             ("or_shat_nnz", [vp], ctypes.c_int),
+            ("or_threads", [ctypes.c_int], ctypes.c_int),
             ("or_strength_and_aggregate", [ctypes.c_int, ctypes.c_int, _ip, _ip, _dp, ctypes.c_double, _ip],
              ctypes.c_int),
             ("or_vms_assemble", [ctypes.c_int, _dp, ctypes.c_int, _ip, ctypes.c_int, _ip, ctypes.c_void_p,
@@ -152,6 +153,12 @@ def _load():
             f.restype = rt
         _lib = lib
     return _lib
+
+
+def threads(n: int = 0) -> int:
+    """Set the oracle's thread count when n > 0 (timing only: every result is
+    the same at any count); returns the count in use."""
+    return int(_load().or_threads(int(n)))
 
 
 def _d(a):

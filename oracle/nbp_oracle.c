@@ -71,6 +71,9 @@
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define OR_MAXLEV 12
 /* Loops whose iterations are independent (the rows of a sparse product,
@@ -1122,6 +1125,18 @@ void or_set_values(or_ctx *c, const double *av, const double *bv, const double *
     memcpy(c->B.v, bv, sizeof(double) * (size_t)c->B.rp[c->N] * 3);
     memcpy(c->C.v, cv, sizeof(double) * (size_t)c->C.rp[c->N] * 3);
     memcpy(c->D.v, dv, sizeof(double) * (size_t)c->D.rp[c->N]);
+}
+
+/* Threads of the parallel loops (timing only: results are the same at any
+ * count); n <= 0 leaves the count unchanged.  Returns the count in use. */
+int or_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
 }
 
 void or_set_options(or_ctx *c, const or_options *o) { c->opt = *o; }
