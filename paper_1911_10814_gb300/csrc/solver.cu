@@ -67,12 +67,17 @@ template <typename T> struct Krylov {
     double *h1 = nullptr, *h2 = nullptr, *nrm = nullptr, *beta = nullptr, *partial = nullptr;
     unsigned *ticket = nullptr;   // last-block ticket of the Arnoldi reductions
     GmState *st = nullptr;
-    unsigned grid = 0;            // blocks of the Gram-Schmidt reductions (autotuned per n; 0: one wave)
+    // blocks of the Gram-Schmidt reductions, autotuned per n (0: one wave):
+    // grid_md for the first multi-dot of a step, which meets the basis cold
+    // (the preconditioner's sweeps have evicted it from L2), grid for the
+    // fused subtract + products passes that follow it on the same columns
+    unsigned grid = 0, grid_md = 0;
     void ensure(long long n_, int m_, cudaStream_t s) {
         if (n_ == n && m_ <= m) return;
-        const unsigned keep_grid = (n_ == n) ? grid : 0u;
+        const unsigned keep_grid = (n_ == n) ? grid : 0u, keep_md = (n_ == n) ? grid_md : 0u;
         release(s);
         grid = keep_grid;
+        grid_md = keep_md;
         n = n_; m = m_;
         ld = (n + 31) / 32 * 32;
         V = dmalloc<T>((size_t)ld * (m + 1), s);
@@ -314,7 +319,7 @@ template <typename T> static void mdot(nbp_ctx *c, Krylov<T> &K, const T *V, lon
     cudaEvent_t e0;
     prof_begin(c, e0);
     const bool vec = al16(V) && al16(w) && (ncols <= 1 || (ldv * (long long)sizeof(T)) % 16 == 0);
-    const unsigned g1 = K.grid ? K.grid : arnoldi_grids<T>().mdot_v, g0 = K.grid ? K.grid : arnoldi_grids<T>().mdot_s;
+    const unsigned g1 = K.grid_md ? K.grid_md : arnoldi_grids<T>().mdot_v, g0 = K.grid_md ? K.grid_md : arnoldi_grids<T>().mdot_s;
     if (vec) k_mdot<T, 8, true><<<g1, 256, 0, c->s>>>(V, ldv, ncols, w, K.n, K.partial, out, K.ticket, gv);
     else k_mdot<T, 8, false><<<g0, 256, 0, c->s>>>(V, ldv, ncols, w, K.n, K.partial, out, K.ticket, gv);
     NBP_LAUNCHED();
@@ -368,17 +373,20 @@ template <typename T> static void scale_inv(nbp_ctx *c, T *v, const T *w, const 
     else k_scale_inv<T, false><<<grid, 256, 0, c->s>>>(v, w, sc, n);
 }
 
-// Autotuner of the Gram-Schmidt kernels' grid for one vector length: the
+// Autotuner of the Gram-Schmidt kernels' grids for one vector length: the
 // candidates (one wave, a half and a quarter of it, a quarter block per SM,
 // and just enough blocks for eight 16-byte pieces per thread) are timed on a
-// four-column step -- multi-dot, subtract + products, subtract + norm -- in
-// the space's own buffers, three batches of five, the fastest batch kept.
-// A short vector leaves most of a one-wave grid idle in its reductions;
-// this is what a batch of small instances meets.  The choice is cached per
-// (vector length, type) for the life of the process, so every space of that
-// length sums in the same order.
+// four-column step in the space's own buffers, as the solve meets it: the
+// multi-dot after a write of a buffer larger than L2 (between two steps the
+// preconditioner's sweeps evict the basis), then the subtract + products and
+// subtract + norm passes on the columns it left in L2.  Three batches of
+// five steps; each kernel keeps its own fastest grid.  A short vector leaves
+// most of a one-wave grid idle in its reductions (what a batch of small
+// instances meets), while a cold pass over a long one needs every block's
+// loads in flight.  The choice is cached per (vector length, type) for the
+// life of the process, so every space of that length sums in the same order.
 static std::mutex g_arnoldi_tune_mutex;
-static std::map<std::pair<long long, int>, unsigned> g_arnoldi_tune;
+static std::map<std::pair<long long, int>, std::pair<unsigned, unsigned>> g_arnoldi_tune;
 
 template <typename T> static void tune_arnoldi(nbp_ctx *c, Krylov<T> &K) {
     if (K.grid || K.m < 4 || c->prof.on) return;
@@ -386,7 +394,7 @@ template <typename T> static void tune_arnoldi(nbp_ctx *c, Krylov<T> &K) {
     {
         std::lock_guard<std::mutex> lock(g_arnoldi_tune_mutex);
         auto it = g_arnoldi_tune.find(key);
-        if (it != g_arnoldi_tune.end()) { K.grid = it->second; return; }
+        if (it != g_arnoldi_tune.end()) { K.grid = it->second.first; K.grid_md = it->second.second; return; }
     }
     const bool vec = al16(K.V) && al16(K.w) && (K.ld * (long long)sizeof(T)) % 16 == 0;
     const ArnoldiGrids<T> &ag = arnoldi_grids<T>();
@@ -399,44 +407,52 @@ template <typename T> static void tune_arnoldi(nbp_ctx *c, Krylov<T> &K) {
                                    (unsigned)std::min<long long>(gmax, (pieces + 8 * 256 - 1) / (8 * 256))};
     std::sort(cands.begin(), cands.end());
     cands.erase(std::unique(cands.begin(), cands.end()), cands.end());
+    constexpr size_t kFlush = 256ull << 20;   // twice the L2
+    char *flush = dmalloc<char>(kFlush, c->s);
     fill<T>(K.V, T(1), (long long)K.ld * 4, c->s);
     fill<T>(K.w, T(1), K.n, c->s);
     NBP_CUDA(cudaMemsetAsync(K.h1, 0, sizeof(double) * 4, c->s));
-    cudaEvent_t e0, e1;
-    NBP_CUDA(cudaEventCreate(&e0));
-    NBP_CUDA(cudaEventCreate(&e1));
-    float best = 1e30f;
-    unsigned arg = gmax;
+    cudaEvent_t ev[3];
+    for (cudaEvent_t &e : ev) NBP_CUDA(cudaEventCreate(&e));
+    float best = 1e30f, best_md = 1e30f;
+    unsigned arg = gmax, arg_md = gmax;
     const long long launches = c->prof.launches;
     for (unsigned g : cands) {
         if (g == 0) continue;
-        K.grid = g;
-        auto step = [&] {
-            mdot<T>(c, K, K.V, K.ld, 4, K.w, K.h2);
-            maxpy_dot<T>(c, K, K.V, K.ld, 4, K.h1, K.w, 0, K.h2);
-            maxpy_dot<T>(c, K, K.V, K.ld, 4, K.h1, K.w, 1, K.nrm);
-        };
-        step();
-        float tb = 1e30f;
+        K.grid = K.grid_md = g;
+        float tb = 1e30f, tb_md = 1e30f;
         for (int r = 0; r < 3; ++r) {
-            NBP_CUDA(cudaEventRecord(e0, c->s));
-            for (int q = 0; q < 5; ++q) step();
-            NBP_CUDA(cudaEventRecord(e1, c->s));
-            NBP_CUDA(cudaEventSynchronize(e1));
-            float ms = 0.f;
-            NBP_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-            tb = std::min(tb, ms);
+            float t = 0.f, t_md = 0.f;
+            for (int q = 0; q < 5; ++q) {
+                NBP_CUDA(cudaMemsetAsync(flush, (r * 5 + q) & 0xff, kFlush, c->s));
+                NBP_CUDA(cudaEventRecord(ev[0], c->s));
+                mdot<T>(c, K, K.V, K.ld, 4, K.w, K.h2);
+                NBP_CUDA(cudaEventRecord(ev[1], c->s));
+                maxpy_dot<T>(c, K, K.V, K.ld, 4, K.h1, K.w, 0, K.h2);
+                maxpy_dot<T>(c, K, K.V, K.ld, 4, K.h1, K.w, 1, K.nrm);
+                NBP_CUDA(cudaEventRecord(ev[2], c->s));
+                NBP_CUDA(cudaEventSynchronize(ev[2]));
+                float a = 0.f, b = 0.f;
+                NBP_CUDA(cudaEventElapsedTime(&a, ev[0], ev[1]));
+                NBP_CUDA(cudaEventElapsedTime(&b, ev[1], ev[2]));
+                t_md += a;
+                t += b;
+            }
+            tb = std::min(tb, t);
+            tb_md = std::min(tb_md, t_md);
         }
         if (tb < best) { best = tb; arg = g; }
+        if (tb_md < best_md) { best_md = tb_md; arg_md = g; }
     }
     c->prof.launches = launches;
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+    for (cudaEvent_t &e : ev) cudaEventDestroy(e);
+    dfree(flush, c->s);
     std::lock_guard<std::mutex> lock(g_arnoldi_tune_mutex);
     auto it = g_arnoldi_tune.find(key);
-    if (it != g_arnoldi_tune.end()) arg = it->second;
-    else g_arnoldi_tune[key] = arg;
+    if (it != g_arnoldi_tune.end()) { arg = it->second.first; arg_md = it->second.second; }
+    else g_arnoldi_tune[key] = std::make_pair(arg, arg_md);
     K.grid = arg;
+    K.grid_md = arg_md;
 }
 
 // ----------------------------------------------------------------- GMRES
@@ -1100,7 +1116,7 @@ template <typename T> static void arnoldi_dl(nbp_ctx *c, Krylov<T> &K, GmDev *st
     GivensArgs gv = K.givens(0);
     gv.jp = jp;
     if (vec) {
-        const unsigned g1 = K.grid ? K.grid : arnoldi_grids<T>().mdot_dl_v;
+        const unsigned g1 = K.grid_md ? K.grid_md : arnoldi_grids<T>().mdot_dl_v;
         const unsigned g2 = K.grid ? K.grid : arnoldi_grids<T>().mpd_dl_v;
         k_mdot_dl<T, 8, true><<<g1, 256, 0, c->s>>>(K.V, K.ld, jp, 1, K.w, K.n, K.partial, K.h1, K.ticket, GivensArgs());
         k_maxpy_dot_dl<T, kFusedCols, true><<<g2, 256, 0, c->s>>>(K.V, K.ld, jp, 1, K.h1, K.w, K.n, 0, K.partial, K.h2,
@@ -1109,7 +1125,7 @@ template <typename T> static void arnoldi_dl(nbp_ctx *c, Krylov<T> &K, GmDev *st
                                                                   K.ticket, gv);
         k_scale_inv_dl<T, true><<<grid_for(K.n / Vec16<T>::W + 1), 256, 0, c->s>>>(K.V, K.ld, jp, 1, K.w, &K.st->beta, K.n);
     } else {
-        const unsigned g1 = K.grid ? K.grid : arnoldi_grids<T>().mdot_dl_s;
+        const unsigned g1 = K.grid_md ? K.grid_md : arnoldi_grids<T>().mdot_dl_s;
         const unsigned g2 = K.grid ? K.grid : arnoldi_grids<T>().mpd_dl_s;
         k_mdot_dl<T, 8, false><<<g1, 256, 0, c->s>>>(K.V, K.ld, jp, 1, K.w, K.n, K.partial, K.h1, K.ticket, GivensArgs());
         k_maxpy_dot_dl<T, kFusedCols, false><<<g2, 256, 0, c->s>>>(K.V, K.ld, jp, 1, K.h1, K.w, K.n, 0, K.partial, K.h2,
@@ -1329,7 +1345,10 @@ static void dl_prepare(nbp_ctx *c) {
                                      (const void *)(intptr_t)c->KS32.m, (const void *)(intptr_t)c->KA64.m,
                                      (const void *)(intptr_t)c->KS64.m, (const void *)(intptr_t)c->Kout.grid,
                                      (const void *)(intptr_t)c->KA32.grid, (const void *)(intptr_t)c->KS32.grid,
-                                     (const void *)(intptr_t)c->KA64.grid, (const void *)(intptr_t)c->KS64.grid};
+                                     (const void *)(intptr_t)c->KA64.grid, (const void *)(intptr_t)c->KS64.grid,
+                                     (const void *)(intptr_t)c->Kout.grid_md, (const void *)(intptr_t)c->KA32.grid_md,
+                                     (const void *)(intptr_t)c->KS32.grid_md, (const void *)(intptr_t)c->KA64.grid_md,
+                                     (const void *)(intptr_t)c->KS64.grid_md};
     for (const DMat *M : {&c->A, &c->B, &c->C, &c->D})
         for (const void *q : {(const void *)M->v, (const void *)M->v32, (const void *)M->v16, (const void *)M->sl_ptr,
                               (const void *)M->sl_ci, (const void *)M->sl_v, (const void *)M->sl_v32,
