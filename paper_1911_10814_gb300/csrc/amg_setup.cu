@@ -41,7 +41,7 @@ void hier_free(Hier &H, cudaStream_t s) {
         dmat_free(L.M, s);
         dfree(L.agg, s); dfree(L.mptr, s); dfree(L.mem, s); dfree(L.dinv, s); dfree(L.dinv32, s);
         for (int q = 0; q < Level::kWork; ++q) { dfree(L.w64[q], s); dfree(L.w32[q], s); }
-        dfree(L.kdots, s);
+        dfree(L.kdots, s); dfree(L.kpart, s);
         L = Level();
     }
     dfree(H.cinv, s);
@@ -805,6 +805,10 @@ void amg_build(Hier &H, const DMat &fine, const nbp_options &o, int precision, c
             }
             make_lowcopies(L.M, precision, s);
             make_sell(L.M, precision, s);
+            if (L.M.sl_ci) {   // grids of the sliced kernels, up to 8 threads per row
+                L.kpart_blocks = ((long long)L.M.nslice * L.M.sl_c * 8 + 255) / 256;
+                L.kpart = dmalloc<double>(2 * L.kpart_blocks, s);
+            }
         }
     }
     dfree(rb, s);

@@ -546,6 +546,72 @@ __device__ __forceinline__ void block_reduce_partials(const double *partial, int
     }
 }
 
+// Scalar-block (Ŝ level) sliced-ELL product y = M x fused with the inner
+// products the K-cycle takes of it: kd[o0] = y . da and, when db is set,
+// kd[o1] = y . db (da may be y itself).  T threads per row as in k_sellm
+// (T = 1: one thread per row); each row's sum is the same as the unfused
+// kernels'.  The row products are summed per warp in FP64, per block in a
+// fixed order into part[b] and part[nb + b], and the last block to finish
+// (ticket kd[7]) adds the block partials in a fixed order -- one launch
+// instead of a product and a reduction, the same result whatever the order
+// the blocks run in.
+struct DotArgs {
+    const void *da, *db;   // vectors the product is dotted with (same type as y); db may be null
+    double *part;          // 2 x gridDim.x block partials
+    double *kd;            // results kd[o0], kd[o1]; kd[7] is the ticket
+    int o0, o1;
+};
+template <typename VT, typename XT, int C, int T>
+__global__ void __launch_bounds__(256) k_sell_dot(SpmvArgs a, DotArgs q) {
+    using AT = XT;
+    const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int row = (int)(gid / T), h = (int)(gid % T);
+    const int sl = row / C, t = row % C;
+    const bool live = sl < a.nslice;
+    const long long base = live ? a.sl_ptr[sl] : 0;
+    const int w = live ? (int)((a.sl_ptr[sl + 1] - base) / C) : 0;
+    const VT *__restrict__ val = (const VT *)a.val;
+    const XT *__restrict__ x = (const XT *)a.x;
+    AT acc0 = 0, acc1 = 0, acc2 = 0;
+    if constexpr (std::is_same<VT, __nv_bfloat16>::value) {
+        sell_pairs<1, C>(a, base / 2, w / 2, t, h, T, x, acc0, acc1, acc2);
+        if ((w & 1) && h == (w / 2) % T) sell_single<1, C>(a, base + (long long)C * (w - 1), t, x, acc0, acc1, acc2);
+    } else {
+        for (int k = h; k < w; k += T) {
+            const long long g = base + (long long)C * k;
+            acc0 += cvt<AT>(ldm<C == 32>(val + g + t)) * __ldg(x + ldm<C == 32>(a.sl_ci + g + t));
+        }
+    }
+#pragma unroll
+    for (int o = T / 2; o > 0; o >>= 1) acc0 += __shfl_xor_sync(0xffffffffu, acc0, o);
+    AT p0 = 0, p1 = 0;
+    if (h == 0 && live && row < a.nbr) {
+        ((XT *)a.y)[row] = acc0;
+        p0 = acc0 * (q.da == a.y ? acc0 : ((const XT *)q.da)[row]);
+        if (q.db) p1 = acc0 * ((const XT *)q.db)[row];
+    }
+    __shared__ double red[2][8];
+    const int warp = threadIdx.x >> 5, ln = threadIdx.x & 31;
+    const double s0 = warp_sum((double)p0), s1 = warp_sum((double)p1);
+    if (ln == 0) { red[0][warp] = s0; red[1][warp] = s1; }
+    __syncthreads();
+    if (threadIdx.x < 2) {
+        double u = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) u += red[threadIdx.x][k];
+        q.part[(long long)threadIdx.x * gridDim.x + blockIdx.x] = u;
+    }
+    unsigned *ticket = (unsigned *)(q.kd + 7);
+    if (!grid_last_block(ticket)) return;
+    __shared__ double out[2];
+    block_reduce_partials(q.part, gridDim.x, q.db ? 2 : 1, out);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        q.kd[q.o0] = out[0];
+        if (q.db) q.kd[q.o1] = out[1];
+        *ticket = 0;
+    }
+}
+
 // ================================================ Givens / least squares
 struct GmState {
     double res;      // |g_{j+1}|
@@ -1178,6 +1244,58 @@ template <typename T> __global__ void k_kupd2(T *w2, T *z2, const T *w1, const T
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         w2[i] = w2[i] - beta * w1[i];
         z2[i] = z2[i] - beta * z1[i];
+    }
+}
+// k_kupd2 followed by kd[4] = w2.w2, kd[5] = w2.r on the updated w2, in one
+// launch: the chunks, per-thread sums and fixed-order block and grid
+// reductions of k_kdots (grid kKdotBlocks, ticket kd[7])
+template <typename T>
+__global__ void __launch_bounds__(256) k_kupd2_dots(T *__restrict__ w2, T *__restrict__ z2, const T *__restrict__ w1,
+                                                    const T *__restrict__ z1, const T *__restrict__ r, double *kd,
+                                                    long long n) {
+    __shared__ double s0[8], s1[8];
+    __shared__ bool last;
+    __shared__ T bs_;
+    if (threadIdx.x == 0) bs_ = (T)(kd[0] > 0.0 ? kd[3] / kd[0] : 0.0);
+    __syncthreads();
+    const T beta = bs_;
+    const long long chunk = (n + gridDim.x - 1) / gridDim.x;
+    const long long lo = (long long)blockIdx.x * chunk, hi = min(n, lo + chunk);
+    T p0 = 0, p1 = 0;
+    for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        const T wn = w2[i] - beta * w1[i];
+        w2[i] = wn;
+        z2[i] = z2[i] - beta * z1[i];
+        p0 += wn * wn;
+        p1 += wn * r[i];
+    }
+    double t0 = warp_sum((double)p0);
+    double t1 = warp_sum((double)p1);
+    if ((threadIdx.x & 31) == 0) { s0[threadIdx.x >> 5] = t0; s1[threadIdx.x >> 5] = t1; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double u0 = 0.0, u1 = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { u0 += s0[w]; u1 += s1[w]; }
+        kd[8 + 2 * blockIdx.x] = u0;
+        kd[9 + 2 * blockIdx.x] = u1;
+        __threadfence();
+        last = (atomicAdd((unsigned int *)(kd + 7), 1u) == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (last && threadIdx.x < 32) {
+        __threadfence();
+        double u0 = 0.0, u1 = 0.0;
+        for (unsigned qb = threadIdx.x; qb < gridDim.x; qb += 32) {
+            u0 += __ldcg(kd + 8 + 2 * qb);
+            u1 += __ldcg(kd + 9 + 2 * qb);
+        }
+        u0 = warp_sum(u0);
+        u1 = warp_sum(u1);
+        if (threadIdx.x == 0) {
+            kd[4] = u0;
+            kd[5] = u1;
+            *(unsigned int *)(kd + 7) = 0u;
+        }
     }
 }
 // x = a1 z1 + a2 z2 with a2 = (w2.r)/(w2.w2) = kd[5]/kd[4]

@@ -130,6 +130,8 @@ struct Level {
     double *w64[kWork] = {};
     float *w32[kWork] = {};
     double *kdots = nullptr;                 // K-cycle inner products (device)
+    double *kpart = nullptr;                 // block partials of the K-cycle's product + inner products kernel
+    long long kpart_blocks = 0;              // ... for grids up to this many blocks
 };
 
 struct Hier {

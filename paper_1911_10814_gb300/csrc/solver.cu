@@ -620,6 +620,34 @@ static void vcycle_level(nbp_ctx *c, Hier &H, int l, int vsel, const T *b, T *ou
 // coefficient stays on the device, so the whole cycle can be replayed from a
 // CUDA graph.  x = a1 z1 + a2 z2 with a1 = (w1.b)/(w1.w1), r = b - a1 w1,
 // beta = (w2.w1)/(w1.w1), w2 -= beta w1, z2 -= beta z1, a2 = (w2.r)/(w2.w2).
+// w = L.M z with kd[o0] = w . da and (db set) kd[o1] = w . db: one fused
+// launch (k_sell_dot) where the level's tuned kernel is a scalar sliced one,
+// else the product and k_kdots
+template <typename T>
+static void kc_product_dots(nbp_ctx *c, Level &L, int vsel, const T *z, T *w, const T *da, const T *db, int o0, int o1) {
+    const long long n = (long long)L.M.nbr * L.M.br;
+    if (L.kpart && spmv_dot_ok(L.M, vsel, (int)sizeof(T), L.kpart_blocks)) {
+        cudaEvent_t e0;
+        prof_begin(c, e0);
+        DotArgs q{da, db, L.kpart, L.kdots, o0, o1};
+        const double bytes = spmv_dot<T>(L.M, vsel, sargs(z, w), q, c->s);
+        std::string tag;
+        if (c->prof.on) {
+            tag = mat_tag(c, L.M, EPI_SET);
+            tag.replace(tag.find("/set/"), 5, "/setdot/");
+        }
+        prof_end(c, CAT_SPMV, bytes, tag);
+        return;
+    }
+    do_spmv<T>(c, L.M, vsel, sargs(z, w), EPI_SET, false);
+    // algorithmic bytes: each distinct vector the dots read, once
+    const double vn = (double)n * sizeof(T);
+    const double nvec = 1.0 + (da != w ? 1.0 : 0.0) + (db && db != w && db != da ? 1.0 : 0.0);
+    timed(c, "kcycle/dots", nvec * vn, [&] {
+        k_kdots<T><<<kKdotBlocks, 256, 0, c->s>>>(w, da, db ? w : (const T *)nullptr, db, n, L.kdots, o0, o1);
+    });
+}
+
 template <typename T>
 static void kcycle_level(nbp_ctx *c, Hier &H, int cl, int vsel, const T *b, T *x, bool first_done = false) {
     Level &L = H.L[cl];
@@ -629,17 +657,14 @@ static void kcycle_level(nbp_ctx *c, Hier &H, int cl, int vsel, const T *b, T *x
     const double vn = (double)n * sizeof(T);   // bytes of one level vector
     if (!first_done) copy<T>(r, b, n, c->s);   // else the restriction wrote r
     vcycle_level<T>(c, H, cl, vsel, b, z1, first_done);
-    do_spmv<T>(c, L.M, vsel, sargs(z1, w1), EPI_SET, false);
-    // algorithmic bytes: each distinct vector an update or a pair of dots reads or writes, once
-    timed(c, "kcycle/dots", 2.0 * vn, [&] { k_kdots<T><<<kKdotBlocks, 256, 0, c->s>>>(w1, w1, w1, r, n, L.kdots, 0, 1); });
+    kc_product_dots<T>(c, L, vsel, z1, w1, w1, r, 0, 1);   // kd[0] = w1.w1, kd[1] = w1.r
+    // algorithmic bytes: each distinct vector an update reads or writes, once
     timed(c, "kcycle/update", 3.0 * vn, [&] { k_kupd1<T><<<g, 256, 0, c->s>>>(r, w1, L.kdots, n); });
     vcycle_level<T>(c, H, cl, vsel, r, z2);
-    do_spmv<T>(c, L.M, vsel, sargs(z2, w2), EPI_SET, false);
-    timed(c, "kcycle/dots", 2.0 * vn, [&] {
-        k_kdots<T><<<kKdotBlocks, 256, 0, c->s>>>(w2, w1, (const T *)nullptr, (const T *)nullptr, n, L.kdots, 3, 3);
-    });
-    timed(c, "kcycle/update", 6.0 * vn, [&] { k_kupd2<T><<<g, 256, 0, c->s>>>(w2, z2, w1, z1, L.kdots, n); });
-    timed(c, "kcycle/dots", 2.0 * vn, [&] { k_kdots<T><<<kKdotBlocks, 256, 0, c->s>>>(w2, w2, w2, r, n, L.kdots, 4, 5); });
+    kc_product_dots<T>(c, L, vsel, z2, w2, w1, (const T *)nullptr, 3, 3);   // kd[3] = w2.w1
+    // w2 -= beta w1, z2 -= beta z1, then kd[4] = w2.w2, kd[5] = w2.r
+    timed(c, "kcycle/update+dots", 7.0 * vn,
+          [&] { k_kupd2_dots<T><<<kKdotBlocks, 256, 0, c->s>>>(w2, z2, w1, z1, r, L.kdots, n); });
     timed(c, "kcycle/update", 3.0 * vn, [&] { k_kupd3<T><<<g, 256, 0, c->s>>>(x, z1, z2, L.kdots, n); });
 }
 

@@ -197,6 +197,58 @@ static double product_bytes(const DMat &M, int vsel, int xs, int epi, bool slice
     return b;
 }
 
+static int sell_threads(const DMat &M) {
+    const int G = M.tuned >= 0 ? M.tuned : 0;
+    return G == 0 ? 1 : (is_sellm(G) ? G - kSellMT : 0);
+}
+
+bool spmv_dot_ok(const DMat &M, int vsel, int xbytes, long long max_blocks) {
+    if (M.br != 1 || M.bc != 1 || !M.sl_ci || M.nbr == 0) return false;
+    const int T = sell_threads(M);
+    if (T == 0) return false;
+    if (((long long)M.nslice * M.sl_c * T + 255) / 256 > max_blocks) return false;
+    if (xbytes == 8) return M.sl_v != nullptr;
+    return vsel == 2 ? M.sl_v16 != nullptr : M.sl_v32 != nullptr;
+}
+
+template <typename VT, typename XT, int C>
+static void launch_sell_dot(const SpmvArgs &a, const DotArgs &q, int T, cudaStream_t s) {
+    const unsigned grid = grid_exact((long long)a.nslice * C * T);
+    if (T == 8) k_sell_dot<VT, XT, C, 8><<<grid, 256, 0, s>>>(a, q);
+    else if (T == 4) k_sell_dot<VT, XT, C, 4><<<grid, 256, 0, s>>>(a, q);
+    else if (T == 2) k_sell_dot<VT, XT, C, 2><<<grid, 256, 0, s>>>(a, q);
+    else k_sell_dot<VT, XT, C, 1><<<grid, 256, 0, s>>>(a, q);
+    NBP_LAUNCHED();
+}
+template <typename VT, typename XT>
+static void launch_sell_dot_c(const DMat &M, const SpmvArgs &a, const DotArgs &q, int T, cudaStream_t s) {
+    if (M.sl_c == 8) launch_sell_dot<VT, XT, 8>(a, q, T, s);
+    else launch_sell_dot<VT, XT, 32>(a, q, T, s);
+}
+
+template <typename XT>
+double spmv_dot(const DMat &M, int vsel, SpmvArgs a, const DotArgs &q, cudaStream_t s) {
+    const int T = sell_threads(M);
+    a.nbr = M.nbr;
+    a.nslice = M.nslice;
+    a.sl_ptr = M.sl_ptr;
+    a.sl_ci = M.sl_ci;
+    if constexpr (sizeof(XT) == 8) {
+        a.val = M.sl_v;
+        launch_sell_dot_c<double, double>(M, a, q, T, s);
+    } else if (vsel == 2) {
+        a.sl_ptr = M.sl2_ptr;   // paired layout
+        a.sl_ci = M.sl2_ci;
+        a.val = M.sl_v16;
+        launch_sell_dot_c<__nv_bfloat16, float>(M, a, q, T, s);
+    } else {
+        a.val = M.sl_v32;
+        launch_sell_dot_c<float, float>(M, a, q, T, s);
+    }
+    const double ny = (double)M.nbr * sizeof(XT);
+    return product_bytes(M, vsel, (int)sizeof(XT), EPI_SET, true) + (q.da != a.y ? ny : 0.0) + (q.db ? ny : 0.0);
+}
+
 template <typename XT>
 double spmv(const DMat &M, int vsel, SpmvArgs a, int epi, bool lr, cudaStream_t s, int G) {
     a.nbr = M.nbr;
@@ -229,5 +281,7 @@ double spmv(const DMat &M, int vsel, SpmvArgs a, int epi, bool lr, cudaStream_t 
 
 template double spmv<double>(const DMat &, int, SpmvArgs, int, bool, cudaStream_t, int);
 template double spmv<float>(const DMat &, int, SpmvArgs, int, bool, cudaStream_t, int);
+template double spmv_dot<double>(const DMat &, int, SpmvArgs, const DotArgs &, cudaStream_t);
+template double spmv_dot<float>(const DMat &, int, SpmvArgs, const DotArgs &, cudaStream_t);
 
 }  // namespace nbp

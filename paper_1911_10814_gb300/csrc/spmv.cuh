@@ -16,5 +16,15 @@ double spmv(const DMat &M, int vsel, SpmvArgs a, int epi, bool lr, cudaStream_t 
 
 int choose_group(const DMat &M);
 
+// Whether y = M x with the K-cycle's inner products fused (k_sell_dot) runs
+// for this matrix: scalar blocks, the sliced kernel (1-8 threads per row) as
+// the tuned choice, the value copy of vsel built, and a grid of at most
+// max_blocks blocks (the partials buffer).
+bool spmv_dot_ok(const DMat &M, int vsel, int xbytes, long long max_blocks);
+// Launch it (spmv_dot_ok must hold); returns the algorithmic bytes: the
+// product's, plus da and db when they are not y.
+template <typename XT>
+double spmv_dot(const DMat &M, int vsel, SpmvArgs a, const DotArgs &q, cudaStream_t s);
+
 
 }  // namespace nbp
