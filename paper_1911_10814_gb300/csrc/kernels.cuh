@@ -973,11 +973,6 @@ template <typename T, bool VEC> __device__ __forceinline__ void scale_inv_body(T
 template <typename T, bool VEC> __global__ void k_scale_inv(T *v, const T *w, const double *s, long long n) {
     scale_inv_body<T, VEC>(v, w, s, n);
 }
-// v = column *jp + off of the basis at vbase (stride ld)
-template <typename T, bool VEC>
-__global__ void k_scale_inv_dl(T *vbase, long long ld, const int *jp, int off, const T *w, const double *s, long long n) {
-    scale_inv_body<T, VEC>(vbase + (long long)(*jp + off) * ld, w, s, n);
-}
 
 // ============================================= least squares (GMRES end)
 // y = H(0:k,0:k)^{-1} g(0:k), upper triangular.  One thread.
@@ -1006,7 +1001,56 @@ struct DlCounters {
 __global__ void k_dl_init(GmDev *st, double *g, int m1, const double *nrm2, double *beta, GmState *gs,
                           const double *rtol, const double *atol, const int *m, const int *nmax,
                           cudaGraphConditionalHandle h);
-__global__ void k_dl_step(GmDev *st, const GmState *gs, cudaGraphConditionalHandle h);
+// The end of one iteration of a device-driven GMRES loop (one thread):
+// counters, then the stopping rule of the host-driven loop -- continue while
+// |g_{j+1}| > max(rtol ||b||, atol), h_{j+1,j} != 0, no NaN, j < m and
+// its < n_max -- as the WHILE node's condition.
+__device__ __forceinline__ void dl_step(GmDev *st, const GmState *gs, cudaGraphConditionalHandle h) {
+    st->its += 1;
+    st->j += 1;
+    st->res = gs->res;
+    if (gs->nan) st->nan = 1;
+    const bool go = !st->nan && st->res > st->tol && gs->beta != 0.0 && st->j < st->m && st->its < st->nmax;
+    cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+// The last kernel of an iteration: basis column j + 1 = w / h_{j+1,j}
+// (gs->beta, the reciprocal taken once per block as in k_scale_inv), then,
+// in the grid's last block -- every block has read j by then -- dl_step.
+template <typename T, bool VEC>
+__global__ void k_scale_step_dl(T *vbase, long long ld, GmDev *st, const T *w, const GmState *gs, long long n,
+                                unsigned *ticket, cudaGraphConditionalHandle h) {
+    constexpr int W = VEC ? Vec16<T>::W : 1;
+    __shared__ T inv_s;
+    __shared__ int zero;
+    if (threadIdx.x == 0) {
+        const double d = gs->beta;
+        zero = (d == 0.0);
+        inv_s = zero ? T(0) : (T)(1.0 / d);
+    }
+    __syncthreads();
+    T *v = vbase + (long long)(st->j + 1) * ld;
+    if (!zero) {
+        const T inv = inv_s;
+        const long long nv = n / W;
+        for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += (long long)gridDim.x * blockDim.x) {
+            if constexpr (VEC) {
+                T u[W];
+                vld(w + i * W, u);
+#pragma unroll
+                for (int e = 0; e < W; ++e) u[e] *= inv;
+                vst(v + i * W, u);
+            } else {
+                v[i] = w[i] * inv;
+            }
+        }
+        if (VEC && blockIdx.x == 0 && threadIdx.x < n - nv * W) v[nv * W + threadIdx.x] = w[nv * W + threadIdx.x] * inv;
+    }
+    if (!grid_last_block(ticket)) return;
+    if (threadIdx.x == 0) {
+        dl_step(st, gs, h);
+        *ticket = 0;
+    }
+}
 __global__ void k_dl_cycle_start(GmDev *st, cudaGraphConditionalHandle h);
 __global__ void k_dl_end(GmDev *st, const double *H, int ldh, const double *g, double *y, long long *its_total,
                          long long *solves);

@@ -37,9 +37,8 @@ __global__ void k_gm_init(double *g, int m1, const double *beta2, double *beta, 
 // ------------------------------------------------ device-driven Krylov loops
 // The loop of one GMRES level runs as a graph WHILE node; these one-thread
 // (or one-block) kernels keep its state in GmDev and set the node's
-// condition, with the same stopping rule as the host-driven loop:
-// continue while |g_{j+1}| > max(rtol ||b||, atol), h_{j+1,j} != 0, no
-// NaN, j < m and its < n_max.
+// condition at the start and end of a cycle; each iteration ends in
+// k_scale_step_dl, whose last block applies the stopping rule (dl_step).
 
 __global__ void k_dl_init(GmDev *st, double *g, int m1, const double *nrm2, double *beta, GmState *gs,
                           const double *rtol, const double *atol, const int *m, const int *nmax,
@@ -66,15 +65,6 @@ __global__ void k_dl_init(GmDev *st, double *g, int m1, const double *nrm2, doub
     st->conv = (b <= st->tol) ? 1 : 0;
     st->rel_true = b > 0.0 ? 1.0 : 0.0;
     cudaGraphSetConditional(h, (!st->conv && !st->nan && st->nmax > 0) ? 1u : 0u);
-}
-
-__global__ void k_dl_step(GmDev *st, const GmState *gs, cudaGraphConditionalHandle h) {
-    st->its += 1;
-    st->j += 1;
-    st->res = gs->res;
-    if (gs->nan) st->nan = 1;
-    const bool go = !st->nan && st->res > st->tol && gs->beta != 0.0 && st->j < st->m && st->its < st->nmax;
-    cudaGraphSetConditional(h, go ? 1u : 0u);
 }
 
 __global__ void k_dl_cycle_start(GmDev *st, cudaGraphConditionalHandle h) {

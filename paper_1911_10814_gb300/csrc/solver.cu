@@ -1135,7 +1135,9 @@ template <class F> static long long emit_while(nbp_ctx *c, cudaGraphConditionalH
 // The Arnoldi step of iteration st->j (the host loop's kernels, index read
 // on the device): h1 = V^T w; w -= V h1, h2 = V^T w; w -= V h2, ||w|| and the
 // Givens update of column j; V(:, j+1) = w / ||w||.
-template <typename T> static void arnoldi_dl(nbp_ctx *c, Krylov<T> &K, GmDev *st) {
+// One Arnoldi step of a device-driven loop, ending the iteration (its last
+// kernel advances the loop state and sets the WHILE condition h)
+template <typename T> static void arnoldi_dl(nbp_ctx *c, Krylov<T> &K, GmDev *st, cudaGraphConditionalHandle h) {
     const bool vec = al16(K.V) && al16(K.w) && (K.ld * (long long)sizeof(T)) % 16 == 0;
     const int *jp = &st->j;
     GivensArgs gv = K.givens(0);
@@ -1148,7 +1150,8 @@ template <typename T> static void arnoldi_dl(nbp_ctx *c, Krylov<T> &K, GmDev *st
                                                                   K.ticket, GivensArgs());
         k_maxpy_dot_dl<T, kFusedCols, true><<<g2, 256, 0, c->s>>>(K.V, K.ld, jp, 1, K.h2, K.w, K.n, 1, K.partial, K.nrm,
                                                                   K.ticket, gv);
-        k_scale_inv_dl<T, true><<<grid_for(K.n / Vec16<T>::W + 1), 256, 0, c->s>>>(K.V, K.ld, jp, 1, K.w, &K.st->beta, K.n);
+        k_scale_step_dl<T, true><<<grid_for(K.n / Vec16<T>::W + 1), 256, 0, c->s>>>(K.V, K.ld, st, K.w, K.st, K.n,
+                                                                                   K.ticket, h);
     } else {
         const unsigned g1 = K.grid_md ? K.grid_md : arnoldi_grids<T>().mdot_dl_s;
         const unsigned g2 = K.grid ? K.grid : arnoldi_grids<T>().mpd_dl_s;
@@ -1157,7 +1160,7 @@ template <typename T> static void arnoldi_dl(nbp_ctx *c, Krylov<T> &K, GmDev *st
                                                                    K.ticket, GivensArgs());
         k_maxpy_dot_dl<T, kFusedCols, false><<<g2, 256, 0, c->s>>>(K.V, K.ld, jp, 1, K.h2, K.w, K.n, 1, K.partial, K.nrm,
                                                                    K.ticket, gv);
-        k_scale_inv_dl<T, false><<<grid_for(K.n + 1), 256, 0, c->s>>>(K.V, K.ld, jp, 1, K.w, &K.st->beta, K.n);
+        k_scale_step_dl<T, false><<<grid_for(K.n + 1), 256, 0, c->s>>>(K.V, K.ld, st, K.w, K.st, K.n, K.ticket, h);
     }
     NBP_LAUNCHED();
 }
@@ -1189,9 +1192,7 @@ static long long gmres_dl(nbp_ctx *c, Krylov<T> &K, long long n, GmDev *st, cons
         op(z, K.w);
         k_col_put<T, T><<<grid_for(n), 256, 0, c->s>>>(K.Z, K.ld, &st->j, 0, 0, z, n);
         NBP_LAUNCHED();
-        arnoldi_dl<T>(c, K, st);
-        k_dl_step<<<1, 1, 0, c->s>>>(st, K.st, h);
-        NBP_LAUNCHED();
+        arnoldi_dl<T>(c, K, st, h);
     });
     k_dl_end<<<1, 1, 0, c->s>>>(st, K.H, K.m, K.g, K.y, its_total, solves);
     NBP_LAUNCHED();
@@ -1303,9 +1304,7 @@ static void outer_dl(nbp_ctx *c) {
             apply_full(c, z, K.w);
             k_col_put<double, double><<<grid_for(n), 256, 0, c->s>>>(K.Z, K.ld, &st->j, 0, 0, z, n);
             NBP_LAUNCHED();
-            arnoldi_dl<double>(c, K, st);
-            k_dl_step<<<1, 1, 0, c->s>>>(st, K.st, hi);
-            NBP_LAUNCHED();
+            arnoldi_dl<double>(c, K, st, hi);
         });
         k_dl_end<<<1, 1, 0, c->s>>>(st, K.H, K.m, K.g, K.y, nullptr, nullptr);
         NBP_LAUNCHED();
