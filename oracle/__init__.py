@@ -132,6 +132,7 @@ def _load():
             f.restype = None
         for name, args, rt in [
             ("or_setup", [vp], ctypes.c_int),
+            ("or_setup_numeric", [vp], ctypes.c_int),
             ("or_solve", [vp, _dp, _dp, ctypes.POINTER(Info)], ctypes.c_int),
             ("or_solve_A", [vp, _dp, _dp, ctypes.c_double, _ip], ctypes.c_int),
             ("or_gmres_A", [vp, _dp, _dp, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int, _ip, _dp],
@@ -242,6 +243,12 @@ class Oracle:
     def setup(self):
         self.lib.or_setup(self.ctx)
         self._ready = True
+
+    def setup_numeric(self):
+        """Rebuild the preconditioner from the current values on the
+        aggregates of the last setup() (numeric re-setup)."""
+        if not self._ready or self.lib.or_setup_numeric(self.ctx) != 0:
+            raise RuntimeError("setup_numeric needs an earlier setup()")
 
     def _ensure_setup(self):
         # the solves and cycles use the AMG hierarchies; building them on
@@ -525,11 +532,14 @@ def newton_step(mesh: dict, sysd: dict, phys: VmsPhys, y_n, yd_n, rcr: dict, tol
     Preconditioner of the nested solves (AMG(A), S_hat, AMG(S_hat)):
     pc_rebuild 0 builds it from every tangent; 1 from the first tangent of
     this step only; 2 keeps the one held in the caller's dict `pc` (key
-    "oracle", from an earlier step) and builds one only if there is none.  A
-    kept preconditioner is applied to the new tangent's operators (a lagged
+    "oracle", from an earlier step) and builds one only if there is none; 3
+    rebuilds it numerically (setup_numeric: new values on the held
+    aggregates) from every tangent; 4 numerically from the first tangent of
+    this step only.  Modes 2-4 build one in full when none is held.  A kept
+    preconditioner is applied to the new tangent's operators (a lagged
     preconditioner: only the path of the solve changes, not its solution).
     Returns dict(y, yd, Pi, P, iters (linear solves), res (residual norms),
-    setups (preconditioner builds))."""
+    setups (full preconditioner builds), numeric (numeric re-setups))."""
     N = sysd["n_nodes"]
     am, af, gm = gen_alpha(phys.rho_inf)
     dt = phys.dt
@@ -543,7 +553,7 @@ def newton_step(mesh: dict, sysd: dict, phys: VmsPhys, y_n, yd_n, rcr: dict, tol
     Q_n = outlet_flows(sysd, y_n[:3 * N]) if n_out else np.zeros(0)
     P_n = Rp * Q_n + Pi_n + Pd
     res, r0, lin = [], None, []
-    setups = 0
+    setups = numeric = 0
     held = pc if pc is not None else {}
     P1 = Pi1 = np.zeros(n_out)
     for l in range(1, l_max + 1):
@@ -561,20 +571,25 @@ def newton_step(mesh: dict, sysd: dict, phys: VmsPhys, y_n, yd_n, rcr: dict, tol
         if r0 is None:
             r0 = nr
         if (r0 > 0 and nr / r0 <= tol_R) or nr <= tol_A:                                 # step 7
-            return dict(y=y1, yd=yd1, Pi=Pi1, P=P1, iters=l - 1, res=res, lin=lin, setups=setups)
+            return dict(y=y1, yd=yd1, Pi=Pi1, P=P1, iters=l - 1, res=res, lin=lin, setups=setups, numeric=numeric)
         T = vms_assemble(mesh, sysd, phys, ydam[:3 * N], yaf[:3 * N], yaf[3 * N:], Paf, residual=False)  # step 8
         r_k = af * gm * dt * m
+        if pc_rebuild not in (0, 1, 2, 3, 4):
+            raise ValueError("pc_rebuild must be 0-4")
         rebuild = pc_rebuild == 0 or (pc_rebuild == 1 and l == 1) or "oracle" not in held
         if rebuild:
             o = Oracle(dict(sysd, A=T["A"], B=T["B"], C=T["C"], D=T["D"], r=r_k), **solve_opts)
             o.setup()
             held["oracle"] = o
             setups += 1
-        else:                                         # lagged: new operators, the held preconditioner
+        else:                                         # new operators on the held context
             o = held["oracle"]
             o.set_values(T["A"], T["B"], T["C"], T["D"])
             if n_out:
                 o.set_resistances(r_k)
+            if pc_rebuild == 3 or (pc_rebuild == 4 and l == 1):
+                o.setup_numeric()                     # new values on the held aggregates
+                numeric += 1
         dx, info, rc = o.solve(-R)                                                       # step 9
         if rc != 0:
             raise RuntimeError(f"newton_step: nested solve failed (status {rc})")

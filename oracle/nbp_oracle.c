@@ -716,9 +716,12 @@ static double arnoldi_rho(const bmat *M, const double *dinv) {
 }
 
 /* tight_rho: Chebyshev bound from the Arnoldi estimate (AMG(A)); else the
- * Gershgorin bound (AMG(S_hat)) */
+ * Gershgorin bound (AMG(S_hat)).  keep: the aggregate maps of an earlier
+ * hierarchy of the same pattern to build on instead of aggregating again
+ * (the numeric re-setup; everything else is computed from the new values);
+ * its maps are moved into H. */
 static void amg_build(amg *H, const bmat *fine, const or_options *o, int kcycle, int degree, int tight_rho,
-                      double lodiv) {
+                      double lodiv, amg *keep) {
     memset(H, 0, sizeof(*H));
     H->cheb_lo = lodiv;
     H->bs = fine->br;
@@ -727,11 +730,17 @@ static void amg_build(amg *H, const bmat *fine, const or_options *o, int kcycle,
     H->kdepth = o->amg_kdepth;
     bmat_copy(&H->L[0], fine->nbr, fine->nbc, fine->br, fine->bc, fine->rp, fine->ci, fine->v);
     int l = 0;
-    while (H->L[l].nbr > o->amg_coarse_max && l + 1 < o->amg_max_levels && l + 1 < OR_MAXLEV) {
-        int n = H->L[l].nbr;
-        H->agg[l] = (int *)xmalloc(sizeof(int) * n);
-        int nc = aggregate(&H->L[l], o->theta, H->agg[l]);
-        if (nc >= n || nc == 0) { free(H->agg[l]); H->agg[l] = NULL; break; }
+    while (keep ? (l + 1 < keep->nlev) : (H->L[l].nbr > o->amg_coarse_max && l + 1 < o->amg_max_levels && l + 1 < OR_MAXLEV)) {
+        int n = H->L[l].nbr, nc;
+        if (keep) {   /* the kept map and its coarse size */
+            H->agg[l] = keep->agg[l];
+            keep->agg[l] = NULL;
+            nc = keep->L[l + 1].nbr;
+        } else {
+            H->agg[l] = (int *)xmalloc(sizeof(int) * n);
+            nc = aggregate(&H->L[l], o->theta, H->agg[l]);
+            if (nc >= n || nc == 0) { free(H->agg[l]); H->agg[l] = NULL; break; }
+        }
         galerkin(&H->L[l], H->agg[l], nc, &H->L[l + 1]);
         H->mptr[l] = (int *)calloc((size_t)nc + 1, sizeof(int));   /* members of each aggregate, ascending */
         H->mem[l] = (int *)xmalloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
@@ -1151,11 +1160,27 @@ void or_set_resistances(or_ctx *c, const double *r) {
 int or_setup(or_ctx *c) {
     if (c->have_amgA) amg_free(&c->amgA);
     if (c->have_amgS) amg_free(&c->amgS);
-    amg_build(&c->amgA, &c->A, &c->opt, c->opt.amg_cycle == 2, c->opt.cheb_degree, 1, 10.0);
+    amg_build(&c->amgA, &c->A, &c->opt, c->opt.amg_cycle == 2, c->opt.cheb_degree, 1, 10.0, NULL);
     c->have_amgA = 1;
     build_shat(c);
-    amg_build(&c->amgS, &c->Shat, &c->opt, c->opt.amg_cycle >= 1, c->opt.cheb_degree_S, 0, 3.0);
+    amg_build(&c->amgS, &c->Shat, &c->opt, c->opt.amg_cycle >= 1, c->opt.cheb_degree_S, 0, 3.0, NULL);
     c->have_amgS = 1;
+    return 0;
+}
+
+/* Numeric re-setup after new values on the same patterns (a later Newton
+ * tangent, Sec. 2.5): AMG(A), S_hat and AMG(S_hat) rebuilt from the current
+ * values on the aggregates of the last or_setup -- Galerkin operators,
+ * block-diagonal inverses, Chebyshev bounds and coarsest factorisations all
+ * new, only the aggregation is kept.  Returns 1 without a previous setup. */
+int or_setup_numeric(or_ctx *c) {
+    if (!c->have_amgA || !c->have_amgS) return 1;
+    amg oldA = c->amgA, oldS = c->amgS;
+    amg_build(&c->amgA, &c->A, &c->opt, c->opt.amg_cycle == 2, c->opt.cheb_degree, 1, 10.0, &oldA);
+    amg_free(&oldA);
+    build_shat(c);
+    amg_build(&c->amgS, &c->Shat, &c->opt, c->opt.amg_cycle >= 1, c->opt.cheb_degree_S, 0, 3.0, &oldS);
+    amg_free(&oldS);
     return 0;
 }
 

@@ -263,3 +263,35 @@ def test_lagged_preconditioner_keeps_the_newton_iterates():
     assert runs[2][1] == 1 and runs[0][1] == sum(runs[0][0])
     for a, b in zip(runs[0][2:], runs[2][2:]):
         assert np.abs(a - b).max() <= 1e-9 * np.abs(a).max()
+
+
+def test_numeric_resetup_keeps_the_newton_iterates():
+    """A preconditioner rebuilt from each new tangent on the aggregates of the
+    first build (pc_rebuild 3, every tangent; 4, the first tangent of each
+    step) gives the same corrector counts and states, to the solve
+    tolerance, as a full build per tangent (pc_rebuild 0); one full build in
+    all, the rest numeric."""
+    sp = synth.MeshSpec(4, 4, 12, Lz=3.0, Re=500.0, seed=2, R=(1e3,) * 4, pert=0.0, name="box4x4x12_eq")
+    d, m, ph = synth.generate(sp), synth.mesh(sp), oracle.vms_phys(sp)
+    N = d["n_nodes"]
+    R = np.asarray(sp.R)
+    Q0 = oracle.outlet_flows(d, d["vel"])
+    rc0 = dict(Rp=0.1 * R, Rd=0.9 * R, C=0.1 / R, Pd=np.zeros(4), Pi=0.9 * R * Q0, nts=10)
+    y0 = np.concatenate([d["vel"], np.full(N, float(np.mean(R * Q0)))])
+    runs = {}
+    for mode in (0, 3, 4):
+        y, yd, rc, pc = y0.copy(), np.zeros(4 * N), dict(rc0), {}
+        iters, setups, numeric = [], 0, 0
+        for _ in range(3):
+            out = oracle.newton_step(m, d, ph, y, yd, rc, tol_R=1e-9, tol_A=1e-14, rtol=1e-12, pc_rebuild=mode, pc=pc)
+            iters.append(out["iters"])
+            setups += out["setups"]
+            numeric += out["numeric"]
+            y, yd, rc = out["y"], out["yd"], dict(rc, Pi=out["Pi"])
+        runs[mode] = (iters, setups, numeric, y, yd)
+    assert runs[0][0] == runs[3][0] == runs[4][0]
+    assert runs[3][1] == 1 and runs[3][2] == sum(runs[3][0]) - 1
+    assert runs[4][1] == 1 and runs[4][2] == len(runs[4][0]) - 1
+    for mode in (3, 4):
+        for a, b in zip(runs[0][3:], runs[mode][3:]):
+            assert np.abs(a - b).max() <= 1e-9 * np.abs(a).max()
