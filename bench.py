@@ -61,6 +61,9 @@ def _args():
     p.add_argument("--pc-rebuild-every", type=int, default=0,
                    help="newton workload: 0 builds the preconditioner from every tangent; K >= 1 builds it at the "
                         "first corrector of every K-th time step and keeps it (lagged) otherwise")
+    p.add_argument("--pc-numeric", action="store_true",
+                   help="newton workload: every build after the first is a numeric re-setup on the first build's "
+                        "aggregates (nbp_setup_numeric)")
     p.add_argument("--workload", default="large", choices=["large", "batch", "newton"],
                    help="large: the 4.34M-unknown tangent (default); batch: 48 uneven cubes in one batched call; "
                         "newton: predictor multi-corrector time steps with on-device assembly")
@@ -532,7 +535,10 @@ def run_newton(a):
     infos, ts = [], []
     for k in range(a.warmup + a.steps):
         K = a.pc_rebuild_every
-        mode = 0 if K <= 0 else (1 if k % K == 0 else 2)
+        if a.pc_numeric:
+            mode = 3 if K <= 0 else (4 if k % K == 0 else 2)
+        else:
+            mode = 0 if K <= 0 else (1 if k % K == 0 else 2)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         y, yd, Pi, info = vm.newton_step(y, yd, rcr, tol_R=1e-6, tol_A=1e-10, l_max=20, nts=10, pc_rebuild=mode)
@@ -551,10 +557,12 @@ def run_newton(a):
                                  "tangent": "fp32 dual numbers", "outlets": "4 x RCR, R = 1e3",
                                  "preconditioner": ("rebuilt from every tangent" if a.pc_rebuild_every <= 0 else
                                                     f"built every {a.pc_rebuild_every} time steps, kept (lagged) "
-                                                    "in between")},
+                                                    "in between") + ("; rebuilds after the first numeric, on its "
+                                                                      "aggregates" if a.pc_numeric else "")},
                       "correctors_mean": tot("iters"), "outer_iters_mean": tot("outer_iters"),
                       "residual_s": tot("residual_s"), "tangent_s": tot("tangent_s"), "setup_s": tot("setup_s"),
                       "solve_s": tot("solve_s"), "vms_create_s": t_create, "setups_mean": tot("setups"),
+                      "numeric_setups_mean": tot("numeric_setups"),
                       "correctors": [i["iters"] for i in infos],
                       "res_last": [i["res"] for i in infos]}), flush=True)
     vm.close()

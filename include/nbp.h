@@ -140,6 +140,17 @@ nbp_status nbp_create(nbp_ctx **ctx, const nbp_system *sys, const nbp_options *o
  * needs.  Time is reported in info.setup_s of the next solve. */
 nbp_status nbp_setup(nbp_ctx *ctx);
 
+/* Numeric re-setup after new values on the same patterns (nbp_set_values,
+ * nbp_set_resistances; the Newton tangents of a time step, Sec. 2.5): both
+ * AMG hierarchies, S_hat and the value copies are rebuilt from the current
+ * values on the aggregate maps of the last nbp_setup -- Galerkin operators,
+ * block-diagonal inverses, Chebyshev bounds and coarsest inverses all new,
+ * only the aggregation (the most expensive part of the setup) is kept, and
+ * with it the number of levels.  The options' theta and level limits are
+ * those of that nbp_setup.  Errors: NBP_ERR_STATE (no earlier nbp_setup),
+ * NBP_ERR_INVALID (a singular diagonal block), NBP_ERR_CUDA, NBP_ERR_OOM. */
+nbp_status nbp_setup_numeric(nbp_ctx *ctx);
+
 /* Replaces the n_out weights r_k (HOST array).  S_hat depends on them through
  * diag(A); call nbp_setup again before solving if P_S should track them. */
 nbp_status nbp_set_resistances(nbp_ctx *ctx, const double *r);
@@ -425,11 +436,14 @@ typedef struct {
     int32_t pc_rebuild;       /* preconditioner of the nested solves (AMG(A), S_hat, AMG(S_hat)):
                                  0 built from every tangent; 1 from the first tangent of this
                                  step only; 2 the one the context holds (from nbp_setup or an
-                                 earlier step) is kept, one is built only if there is none.  A
-                                 kept preconditioner acts on the new tangent's operators (their
-                                 sliced and precision copies are refreshed): a lagged
-                                 preconditioner changes the path of each solve, not its
-                                 solution.  A caller rebuilding every k steps passes 1 on
+                                 earlier step) is kept, one is built only if there is none;
+                                 3 rebuilt from every tangent by nbp_setup_numeric (new values
+                                 on the held aggregates); 4 the same from the first tangent of
+                                 this step only.  Modes 2-4 build one in full when the context
+                                 holds none.  A kept preconditioner acts on the new tangent's
+                                 operators (their sliced and precision copies are refreshed): a
+                                 lagged preconditioner changes the path of each solve, not its
+                                 solution.  A caller rebuilding every k steps passes 1 (or 4) on
                                  those steps and 2 on the others. */
 } nbp_newton_opts;
 
@@ -440,7 +454,8 @@ typedef struct {
     double res0, res;         /* ||R_(0)|| (at the predictor) and the last ||R|| */
     int64_t outer_iters, A_iters, S_iters, I_iters;   /* summed over the solves */
     double residual_s, tangent_s, setup_s, solve_s, total_s;   /* wall seconds per phase */
-    int32_t setups;           /* preconditioner builds made in this step */
+    int32_t setups;           /* full preconditioner builds made in this step */
+    int32_t numeric_setups;   /* numeric re-setups (pc_rebuild 3, 4) made in this step */
 } nbp_newton_info;
 
 /* One time step by the predictor multi-corrector of Sec. 2.5: predictor

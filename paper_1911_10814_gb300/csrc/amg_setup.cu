@@ -752,29 +752,58 @@ static void dense_inverse(const DMat &M, double *&cinv, int &nc, cudaStream_t s)
     require(!f, NBP_ERR_INVALID, "setup: coarsest AMG matrix is singular");
 }
 
-void amg_build(Hier &H, const DMat &fine, const nbp_options &o, int precision, cudaStream_t s) {
-    hier_free(H, s);
-    H.bs = fine.br;
-    // level 0 is a private copy of the fine matrix pattern and values
-    DMat &F = H.L[0].M;
-    F.nbr = fine.nbr; F.nbc = fine.nbc; F.br = fine.br; F.bc = fine.bc; F.nnz = fine.nnz;
-    F.rp = dmalloc<int>(F.nbr + 1, s);
-    F.ci = dmalloc<int>(F.nnz, s);
-    F.v = dmalloc<double>(F.nnz * F.bb(), s);
-    NBP_CUDA(cudaMemcpyAsync(F.rp, fine.rp, sizeof(int) * (F.nbr + 1), cudaMemcpyDeviceToDevice, s));
-    NBP_CUDA(cudaMemcpyAsync(F.ci, fine.ci, sizeof(int) * F.nnz, cudaMemcpyDeviceToDevice, s));
-    NBP_CUDA(cudaMemcpyAsync(F.v, fine.v, sizeof(double) * F.nnz * F.bb(), cudaMemcpyDeviceToDevice, s));
+void amg_build(Hier &H, const DMat &fine, const nbp_options &o, int precision, cudaStream_t s, bool keep_aggregates) {
+    // numeric re-setup: the aggregate maps and member lists of the hierarchy
+    // H holds are taken over (same pattern); every operator is rebuilt
+    int knlev = 0, knc[kMaxLevels] = {};
+    int *kagg[kMaxLevels] = {}, *kmptr[kMaxLevels] = {}, *kmem[kMaxLevels] = {};
+    if (keep_aggregates) {
+        require(H.built && H.nlev >= 1 && H.L[0].M.nbr == fine.nbr && H.L[0].M.nnz == fine.nnz && H.bs == fine.br,
+                NBP_ERR_STATE, "setup: no earlier hierarchy of this pattern to build on");
+        knlev = H.nlev;
+        for (int l = 0; l + 1 < knlev; ++l) {
+            kagg[l] = H.L[l].agg; kmptr[l] = H.L[l].mptr; kmem[l] = H.L[l].mem;
+            knc[l] = H.L[l + 1].M.nbr;
+            H.L[l].agg = nullptr; H.L[l].mptr = nullptr; H.L[l].mem = nullptr;
+        }
+    }
+    auto drop_kept = [&](int from) {
+        for (int l = from; l + 1 < knlev; ++l) { dfree(kagg[l], s); dfree(kmptr[l], s); dfree(kmem[l], s); }
+    };
     int l = 0;
-    const int maxlev = std::max(1, std::min((int)o.amg_max_levels, kMaxLevels));
-    while (H.L[l].M.nbr > o.amg_coarse_max && l + 1 < maxlev) {
-        Level &L = H.L[l];
-        const int n = L.M.nbr;
-        L.agg = dmalloc<int>(n, s);
-        const int nc = aggregate(L.M, o.theta, L.agg, s);
-        if (nc >= n || nc == 0) { dfree(L.agg, s); L.agg = nullptr; break; }
-        member_lists(L, n, nc, s);
-        galerkin(L.M, L.agg, nc, H.L[l + 1].M, s);
-        ++l;
+    try {
+        hier_free(H, s);
+        H.bs = fine.br;
+        // level 0 is a private copy of the fine matrix pattern and values
+        DMat &F = H.L[0].M;
+        F.nbr = fine.nbr; F.nbc = fine.nbc; F.br = fine.br; F.bc = fine.bc; F.nnz = fine.nnz;
+        F.rp = dmalloc<int>(F.nbr + 1, s);
+        F.ci = dmalloc<int>(F.nnz, s);
+        F.v = dmalloc<double>(F.nnz * F.bb(), s);
+        NBP_CUDA(cudaMemcpyAsync(F.rp, fine.rp, sizeof(int) * (F.nbr + 1), cudaMemcpyDeviceToDevice, s));
+        NBP_CUDA(cudaMemcpyAsync(F.ci, fine.ci, sizeof(int) * F.nnz, cudaMemcpyDeviceToDevice, s));
+        NBP_CUDA(cudaMemcpyAsync(F.v, fine.v, sizeof(double) * F.nnz * F.bb(), cudaMemcpyDeviceToDevice, s));
+        const int maxlev = std::max(1, std::min((int)o.amg_max_levels, kMaxLevels));
+        while (keep_aggregates ? l + 1 < knlev : (H.L[l].M.nbr > o.amg_coarse_max && l + 1 < maxlev)) {
+            Level &L = H.L[l];
+            const int n = L.M.nbr;
+            int nc;
+            if (keep_aggregates) {   // the kept map, now owned by this level
+                L.agg = kagg[l]; L.mptr = kmptr[l]; L.mem = kmem[l];
+                kagg[l] = kmptr[l] = kmem[l] = nullptr;
+                nc = knc[l];
+            } else {
+                L.agg = dmalloc<int>(n, s);
+                nc = aggregate(L.M, o.theta, L.agg, s);
+                if (nc >= n || nc == 0) { dfree(L.agg, s); L.agg = nullptr; break; }
+                member_lists(L, n, nc, s);
+            }
+            galerkin(L.M, L.agg, nc, H.L[l + 1].M, s);
+            ++l;
+        }
+    } catch (...) {
+        drop_kept(0);
+        throw;
     }
     H.nlev = l + 1;
     int *singular = dmalloc<int>(1, s);

@@ -180,7 +180,11 @@ void dmat_free(DMat &m, cudaStream_t s);
 void hier_free(Hier &H, cudaStream_t s);
 
 // Setup entry points (amg_setup.cu)
-void amg_build(Hier &H, const DMat &fine, const nbp_options &o, int precision, cudaStream_t s);
+// Aggregation AMG hierarchy of `fine`; keep_aggregates: rebuild every
+// operator of the hierarchy H already holds (same pattern) from the new
+// values on its aggregate maps instead of aggregating again.
+void amg_build(Hier &H, const DMat &fine, const nbp_options &o, int precision, cudaStream_t s,
+               bool keep_aggregates = false);
 void build_shat(const DMat &A, const DMat &B, const DMat &C, const DMat &D, const LowRank &lr, int N, DMat &Shat,
                 double *diagA_out, cudaStream_t s);
 void make_lowcopies(DMat &m, int precision, cudaStream_t s);

@@ -1670,16 +1670,18 @@ static void refine_rhos(nbp_ctx *c, Hier &H) {
         if (l < H.nlev - 1 || !H.cinv) refine_rho(c, H, l);
 }
 
-static void do_setup(nbp_ctx *c) {
+// numeric: rebuild both hierarchies on the aggregates of the last full
+// setup (new values, same patterns) instead of aggregating again
+static void do_setup(nbp_ctx *c, bool numeric = false) {
     auto t0 = std::chrono::steady_clock::now();
     cudaStream_t s = c->s;
     drop_graphs(c);
     const int prec = build_level(c->opt.precision);
     if (!c->diagA) c->diagA = dmalloc<double>(3LL * c->N, s);
-    amg_build(c->HA, c->A, c->opt, prec, s);
+    amg_build(c->HA, c->A, c->opt, prec, s, numeric);
     refine_rhos(c, c->HA);
     build_shat(c->A, c->B, c->C, c->D, c->lr, c->N, c->Shat, c->diagA, s);
-    amg_build(c->HS, c->Shat, c->opt, prec, s);   // AMG(S_hat) keeps the Gershgorin bound (see refine_rho)
+    amg_build(c->HS, c->Shat, c->opt, prec, s, numeric);   // AMG(S_hat) keeps the Gershgorin bound (see refine_rho)
     // Chebyshev intervals [rho/10, rho] on AMG(A) and [rho/3, rho] on AMG(S_hat):
     // for the degree-1 smoothing of S_hat the lower end only sets the Jacobi
     // weight (1.5 / rho); rho/3 there cut S-iterations 97 -> 91 on the 4.34M
@@ -1933,6 +1935,15 @@ nbp_status nbp_setup(nbp_ctx *c) {
     NBP_API_BEGIN(c)
     begin_call(c);
     do_setup(c);
+    return NBP_OK;
+    NBP_API_END(c)
+}
+
+nbp_status nbp_setup_numeric(nbp_ctx *c) {
+    NBP_API_BEGIN(c)
+    begin_call(c);
+    require(c->HA.built && c->HS.built, NBP_ERR_STATE, "nbp_setup_numeric: call nbp_setup first");
+    do_setup(c, true);
     return NBP_OK;
     NBP_API_END(c)
 }
@@ -2874,7 +2885,7 @@ nbp_status nbp_newton_step(nbp_vms *v, const nbp_rcr *rcr, const double *y_n, co
     const auto t_all = clk::now();
     require(y_n && yd_n && y && yd && o, NBP_ERR_INVALID, "nbp_newton_step: null argument");
     require(o->l_max >= 1 && o->nts >= 1 && o->tol_R >= 0 && o->tol_A >= 0 && o->pc_rebuild >= 0 &&
-                o->pc_rebuild <= 2,
+                o->pc_rebuild <= 4,
             NBP_ERR_INVALID, "nbp_newton_step: bad options");
     const int n_out = c->lr.n_out;
     nbp_rcr chk{};
@@ -2922,10 +2933,13 @@ nbp_status nbp_newton_step(nbp_vms *v, const nbp_rcr *rcr, const double *y_n, co
         inf.res = nr;
         if ((r0 > 0 && nr / r0 <= o->tol_R) || nr <= o->tol_A) { inf.converged = 1; break; }   // step 7
         t0 = clk::now();
-        // preconditioner from this tangent, or the one held (lagged)
-        const bool rebuild = o->pc_rebuild == 0 || (o->pc_rebuild == 1 && l == 1) || !c->setup_done;
+        // preconditioner from this tangent (in full, or numerically on the
+        // held aggregates), or the one held (lagged)
+        const bool held = c->setup_done && c->HA.built && c->HS.built;
+        const bool rebuild = o->pc_rebuild == 0 || (o->pc_rebuild == 1 && l == 1) || !held;
+        const bool numeric = !rebuild && (o->pc_rebuild == 3 || (o->pc_rebuild == 4 && l == 1));
         vms_tangent(v->m, k, v->ydam, v->yaf, v->yaf + 3LL * N, nullptr, c->A.v, c->B.v, c->C.v, c->D.v, s);   // step 8
-        if (rebuild) values_changed(c);
+        if (rebuild || numeric) values_changed(c);
         else refresh_operators(c);
         if (n_out) {
             int bad = readback(v->bad, s);
@@ -2942,6 +2956,9 @@ nbp_status nbp_newton_step(nbp_vms *v, const nbp_rcr *rcr, const double *y_n, co
         if (rebuild) {
             do_setup(c);
             inf.setups++;
+        } else if (numeric) {
+            do_setup(c, true);
+            inf.numeric_setups++;
         }
         inf.setup_s += std::chrono::duration<double>(clk::now() - t0).count();
         t0 = clk::now();

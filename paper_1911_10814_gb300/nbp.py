@@ -99,7 +99,7 @@ class nbp_newton_info(ctypes.Structure):
                 ("outer_iters", ctypes.c_int64), ("A_iters", ctypes.c_int64), ("S_iters", ctypes.c_int64),
                 ("I_iters", ctypes.c_int64), ("residual_s", ctypes.c_double), ("tangent_s", ctypes.c_double),
                 ("setup_s", ctypes.c_double), ("solve_s", ctypes.c_double), ("total_s", ctypes.c_double),
-                ("setups", ctypes.c_int32)]
+                ("setups", ctypes.c_int32), ("numeric_setups", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -114,6 +114,7 @@ SIGNATURES = {
     "nbp_default_options": (None, [ctypes.POINTER(nbp_options)]),
     "nbp_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.POINTER(nbp_system), ctypes.POINTER(nbp_options), _vp]),
     "nbp_setup": (ctypes.c_int, [_vp]),
+    "nbp_setup_numeric": (ctypes.c_int, [_vp]),
     "nbp_set_resistances": (ctypes.c_int, [_vp, ctypes.POINTER(_d)]),
     "nbp_solve": (ctypes.c_int, [_vp, _vp, _vp, ctypes.POINTER(nbp_options), ctypes.POINTER(nbp_info)]),
     "nbp_solve_host": (ctypes.c_int, [_vp, _vp, _vp, ctypes.POINTER(nbp_options), ctypes.POINTER(nbp_info)]),
@@ -377,8 +378,11 @@ class Solver:
         except Exception:
             pass
 
-    def setup(self):
-        self._check(self.lib.nbp_setup(self.ctx))
+    def setup(self, numeric=False):
+        """Build the preconditioner (nbp_setup); numeric=True rebuilds it from
+        the current values on the aggregates of the last full setup
+        (nbp_setup_numeric)."""
+        self._check((self.lib.nbp_setup_numeric if numeric else self.lib.nbp_setup)(self.ctx))
 
     def set_resistances(self, r):
         r = np.ascontiguousarray(r, dtype=np.float64)
@@ -574,7 +578,8 @@ class Vms:
                     eps_rel=1e-5, allow_not_converged=False, pc_rebuild=0):
         """One predictor multi-corrector time step (nbp_newton_step).  rcr:
         CUDA float64 tensors Rp, C, Rd, Pd, Pi (Pi^k_n).  pc_rebuild: 0 a
-        preconditioner per tangent, 1 one per step, 2 keep the context's.
+        preconditioner per tangent, 1 one per step, 2 keep the context's, 3 a
+        numeric re-setup on the held aggregates per tangent, 4 one per step.
         Returns (y, ydot, Pi_np1, info)."""
         y = self.s.zeros(4 * self.N)
         yd = self.s.zeros(4 * self.N)

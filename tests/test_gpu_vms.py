@@ -168,11 +168,14 @@ def test_newton_step_matches_oracle(case, fp32):
     s.close()
 
 
-def test_lagged_preconditioner_matches_oracle(case):
-    """Two time steps with one preconditioner for both (pc_rebuild 2: built
-    from the first tangent, kept for every later one): the same corrector
-    counts and accepted states as the oracle's lagged steps, and the same
-    corrector counts as a build per tangent (pc_rebuild 0)."""
+@pytest.mark.parametrize("lag", [2, 3, 4])
+def test_lagged_preconditioner_matches_oracle(case, lag):
+    """Two time steps with a preconditioner other than a build per tangent
+    (pc_rebuild 2: built from the first tangent, kept for every later one;
+    3: rebuilt numerically on the first build's aggregates from every
+    tangent; 4: the same once per step, kept within it): the same corrector
+    counts, builds and accepted states as the oracle's steps in that mode,
+    and the same corrector counts as a build per tangent (pc_rebuild 0)."""
     d, m, ph = case
     N = d["n_nodes"]
     rng = np.random.default_rng(9)
@@ -180,7 +183,7 @@ def test_lagged_preconditioner_matches_oracle(case):
     yd_n = np.concatenate([rng.standard_normal(3 * N) * np.repeat(m["dir"] == 0, 3), rng.standard_normal(N)])
     rc = _rcr()
     iters = {}
-    for mode in (0, 2):
+    for mode in (0, lag):
         s, vm = _vms(d, m, False, rtol=1e-10)
         pc = {}
         y, yd, Pi_h, rch = _t(y_n), _t(yd_n), rc["Pi"], dict(rc)
@@ -196,7 +199,8 @@ def test_lagged_preconditioner_matches_oracle(case):
                                      pc_rebuild=mode, pc=pc)
             assert info["iters"] == ref["iters"]
             assert info["setups"] == ref["setups"]
-            if mode == 2:
+            assert info["numeric_setups"] == ref["numeric"]
+            if mode in (2, 3, 4):
                 assert info["setups"] == (1 if step == 0 else 0)
             assert _maxrel(y.cpu().numpy(), ref["y"]) <= 1e-7
             Pi_h = Pi.cpu().numpy()
@@ -204,7 +208,7 @@ def test_lagged_preconditioner_matches_oracle(case):
             y, yd = _t(yo), _t(ydo)
         vm.close()
         s.close()
-    assert iters[0] == iters[2]
+    assert iters[0] == iters[lag]
 
 
 def test_newton_without_outlets():
