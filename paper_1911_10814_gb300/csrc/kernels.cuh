@@ -1279,18 +1279,8 @@ template <typename T> __global__ void k_kupd1(T *r, const T *w1, double *kd, lon
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         r[i] = r[i] - a1 * w1[i];
 }
-// beta = (w2.w1)/(w1.w1) = kd[3]/kd[0]; w2 -= beta w1; z2 -= beta z1
-template <typename T> __global__ void k_kupd2(T *w2, T *z2, const T *w1, const T *z1, const double *kd, long long n) {
-    __shared__ T bs_;
-    if (threadIdx.x == 0) bs_ = (T)(kd[0] > 0.0 ? kd[3] / kd[0] : 0.0);
-    __syncthreads();
-    const T beta = bs_;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        w2[i] = w2[i] - beta * w1[i];
-        z2[i] = z2[i] - beta * z1[i];
-    }
-}
-// k_kupd2 followed by kd[4] = w2.w2, kd[5] = w2.r on the updated w2, in one
+// w2 -= beta w1 and z2 -= beta z1 with beta = (w2.w1)/(w1.w1) = kd[3]/kd[0],
+// followed by kd[4] = w2.w2, kd[5] = w2.r on the updated w2, in one
 // launch: the chunks, per-thread sums and fixed-order block and grid
 // reductions of k_kdots (grid kKdotBlocks, ticket kd[7])
 template <typename T>
