@@ -83,10 +83,13 @@ typedef struct {
                                2 BF16 inner matrix values with FP32 vectors/accumulation;
                                3 FP32 inner operators (A, B, C, D) and Krylov bases with
                                BF16 values in the two AMG hierarchies only (smoothers,
-                               residuals and coarse levels of the preconditioners).
+                               residuals and coarse levels of the preconditioners);
+                               4 as 3, with A applied with BF16 values inside the inner
+                               A-solves of Algorithm 2 (the S-apply's A^{-1}, tolerance
+                               rtol_I; the rank-one term stays FP64 there too).
                                The outer FGMRES, Givens update, true residual and the
-                               rank-one term stay FP64 in every mode.  Modes 2 and 3 need
-                               nbp_setup run with mode 2 or 3 (both build every copy). */
+                               rank-one term stay FP64 in every mode.  Modes 2-4 need
+                               nbp_setup run with one of modes 2-4 (all build every copy). */
     int32_t pc_A;           /* 0 AMG V-cycle, 1 point Jacobi diag(A)^{-1} */
     int32_t pc_S;           /* 0 AMG on S_hat, 1 none */
     int32_t variant;        /* 0 P_SCR (Algorithm 3); 1 upper block-triangular [[A,B],[0,S]];

@@ -190,10 +190,13 @@ namespace nbp {
 // ------------------------------------------------------------ small helpers
 // value copy of the inner operators (0 FP64, 1 FP32, 2 BF16) per precision mode
 static inline int vsel_of(int precision) { return precision == 2 ? 2 : (precision >= 1 ? 1 : 0); }
-// value copy of the AMG hierarchies: BF16 in modes 2 and 3
+// value copy of the AMG hierarchies: BF16 in modes 2-4
 static inline int amg_vsel_of(int precision) { return precision >= 2 ? 2 : (precision == 1 ? 1 : 0); }
-// copies a precision mode needs built at setup (modes 2 and 3 need the same)
+// copies a precision mode needs built at setup (modes 2-4 need the same)
 static inline int build_level(int precision) { return precision >= 2 ? 2 : precision; }
+// value copy of A in the inner A-solves of Algorithm 2 (the S-apply's
+// A^{-1}, tolerance rtol_I): mode 4 applies A there with BF16 values
+static inline int vsel_I_of(int precision) { return precision == 4 ? 2 : vsel_of(precision); }
 
 template <typename T> static void fill(T *x, T v, long long n, cudaStream_t s) {
     k_fill<T><<<grid_for(n), 256, 0, s>>>(x, v, n);
@@ -935,7 +938,7 @@ template <typename T> static void apply_S(nbp_ctx *c, int vsel, const T *xp, T *
     Bufs<T> &Bf = BUF<T>(c);
     do_spmv<T>(c, c->D, vsel, sargs(xp, y), EPI_SET, false);          // line 1: x_hat = D x_p (into y)
     do_spmv<T>(c, c->B, vsel, sargs(xp, Bf.xbar), EPI_SET, false);    // line 2: x_bar = B x_p
-    GmResult R = solve_A<T>(c, vsel, Bf.xbar, Bf.xtil, c->opt.rtol_I);  // line 3
+    GmResult R = solve_A<T>(c, vsel_I_of(c->opt.precision), Bf.xbar, Bf.xtil, c->opt.rtol_I);  // line 3
     c->info.I_iters += R.its;
     c->info.n_I_solves++;
     do_spmv<T>(c, c->C, vsel, sargs(Bf.xtil, y), EPI_SUB, false);     // lines 4-5: y = x_hat - C x_tilde
@@ -1257,7 +1260,7 @@ template <typename T> static double *pscr_dl(nbp_ctx *c, const double *vbase, lo
     auto opS = [&](const T *x, T *out) {                                                          // Algorithm 2
         do_spmv<T>(c, c->D, vsel, sargs(x, out), EPI_SET, false);
         do_spmv<T>(c, c->B, vsel, sargs(x, Bf.xbar), EPI_SET, false);
-        solve_A_dl<T>(c, vsel, Bf.xbar, Bf.xtil, &par->rtol_I, &cnt->I, &cnt->nI, depth + 1);
+        solve_A_dl<T>(c, vsel_I_of(c->opt.precision), Bf.xbar, Bf.xtil, &par->rtol_I, &cnt->I, &cnt->nI, depth + 1);
         do_spmv<T>(c, c->C, vsel, sargs(Bf.xtil, out), EPI_SUB, false);
     };
     auto pcS = [&](T *vb, long long l, const int *j) -> T * {
@@ -1892,7 +1895,7 @@ void nbp_default_options(nbp_options *o) {
 static nbp_status check_options(const nbp_options *o, std::string &msg) {
     if (!(o->rtol >= 0 && o->rtol_A >= 0 && o->rtol_S >= 0 && o->rtol_I >= 0 && o->atol >= 0)) { msg = "negative tolerance"; return NBP_ERR_INVALID; }
     if (o->m < 1 || o->m_A < 1 || o->m_S < 1 || o->nmax < 1 || o->nmax_A < 1 || o->nmax_S < 1) { msg = "restart/n_max < 1"; return NBP_ERR_INVALID; }
-    if (o->precision < 0 || o->precision > 3 || o->pc_A < 0 || o->pc_A > 1 || o->pc_S < 0 || o->pc_S > 1 || o->variant < 0 || o->variant > 2) { msg = "bad mode switch"; return NBP_ERR_INVALID; }
+    if (o->precision < 0 || o->precision > 4 || o->pc_A < 0 || o->pc_A > 1 || o->pc_S < 0 || o->pc_S > 1 || o->variant < 0 || o->variant > 2) { msg = "bad mode switch"; return NBP_ERR_INVALID; }
     if (o->cheb_degree < 0 || o->cheb_degree > 8 || o->cheb_degree_S < 0 || o->cheb_degree_S > 8 || o->amg_max_levels < 1 || o->amg_cycle < 0 || o->amg_cycle > 2 || o->amg_kdepth < 1) { msg = "bad AMG option"; return NBP_ERR_INVALID; }
     if (o->device_loop < 0 || o->device_loop > 1) { msg = "device_loop must be 0 or 1"; return NBP_ERR_INVALID; }
     return NBP_OK;

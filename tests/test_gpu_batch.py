@@ -57,7 +57,7 @@ def test_batch_of_48_uneven_tangents():
     B.close()
 
 
-@pytest.mark.parametrize("prec", [1, 3])
+@pytest.mark.parametrize("prec", [1, 3, 4])
 def test_batch_in_one_launch_matches_single_solves(prec):
     """The batch as one CUDA graph (every instance's device-driven nested
     solve a parallel branch, device_loop = 1) against each instance's

@@ -160,7 +160,7 @@ def test_nested_solve_iteration_counts_match_oracle(case):
     assert abs(info["S_iters"] - oinfo.S_iters) <= max(2, 0.1 * oinfo.S_iters)
 
 
-@pytest.mark.parametrize("prec", [1, 2, 3])
+@pytest.mark.parametrize("prec", [1, 2, 3, 4])
 def test_nested_solve_mixed(prec):
     d = synth.generate(CASES["box9x11x23_q4"])
     s = Solver(d, precision=prec)
@@ -175,7 +175,7 @@ def test_nested_solve_mixed(prec):
     s.close()
 
 
-@pytest.mark.parametrize("prec,pc_A,variant", [(0, 0, 0), (1, 0, 0), (3, 0, 0), (3, 1, 0), (3, 0, 1)])
+@pytest.mark.parametrize("prec,pc_A,variant", [(0, 0, 0), (1, 0, 0), (3, 0, 0), (4, 0, 0), (3, 1, 0), (3, 0, 1)])
 def test_device_loop_matches_host_loop(prec, pc_A, variant):
     """The nested solve as one graph with device-driven WHILE loops against
     the host-driven loop: the same iteration counts (within one), solutions
@@ -333,7 +333,7 @@ def test_zero_rhs_gives_zero_solution():
     s = Solver(d, precision=3)
     s.setup()
     b = torch.zeros(4 * d["n_nodes"], dtype=torch.float64, device=DEV)
-    for prec in (0, 1, 3):
+    for prec in (0, 1, 3, 4):
         x, info = s.solve(b, precision=prec)
         assert float(torch.abs(x).max()) == 0.0 and info["outer_iters"] == 0
     s.close()
