@@ -24,6 +24,7 @@
 #include <cmath>
 #include <cstring>
 #include <algorithm>
+#include <numeric>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -2367,9 +2368,14 @@ static nbp_status batch_solve_dl(nbp_batch *B, const double *const *b, double *c
             cudaGraph_t g = nullptr;
             NBP_CUDA(cudaStreamBeginCapture(B->s0, cudaStreamCaptureModeThreadLocal));
             try {
+                // branches made largest instance first (the order the graph's
+                // root nodes are issued in)
+                std::vector<int> order(n);
+                std::iota(order.begin(), order.end(), 0);
+                std::stable_sort(order.begin(), order.end(), [&](int p, int q) { return B->ctx[p]->N > B->ctx[q]->N; });
                 NBP_CUDA(cudaEventRecord(B->ev[n], B->s0));
-                for (int i = 0; i < n; ++i) NBP_CUDA(cudaStreamWaitEvent(B->ctx[i]->s, B->ev[n], 0));   // fork
-                for (int i = 0; i < n; ++i) capture_solve(B->ctx[i]);
+                for (int i : order) NBP_CUDA(cudaStreamWaitEvent(B->ctx[i]->s, B->ev[n], 0));   // fork
+                for (int i : order) capture_solve(B->ctx[i]);
                 for (int i = 0; i < n; ++i) {                                                         // join
                     NBP_CUDA(cudaEventRecord(B->ev[i], B->ctx[i]->s));
                     NBP_CUDA(cudaStreamWaitEvent(B->s0, B->ev[i], 0));
