@@ -54,6 +54,8 @@ def _args():
     p.add_argument("--amg-kdepth", type=int, default=99, help="K-cycle on coarse levels 1..k")
     p.add_argument("--cheb-degree", type=int, default=2, help="Chebyshev smoothing degree of AMG(A)")
     p.add_argument("--cheb-degree-S", type=int, default=1, help="Chebyshev smoothing degree of AMG(S_hat)")
+    p.add_argument("--cheb-degree-I", type=int, default=1,
+                   help="Chebyshev degree of the AMG(A) cycle in the inner A-solves of Algorithm 2")
     p.add_argument("--theta", type=float, default=0.0064, help="aggregation strength threshold")
     p.add_argument("--amg-max-levels", type=int, default=5)
     p.add_argument("--amg-coarse-max", type=int, default=300, help="coarsest level size (block rows)")
@@ -599,7 +601,7 @@ def main():
     t_gen = time.perf_counter() - t0
     s = Solver(d, device=dev, precision=a.precision, pc_A=a.pc_A, variant=a.variant, amg_cycle=a.amg_cycle,
                amg_kdepth=a.amg_kdepth,
-               cheb_degree=a.cheb_degree, cheb_degree_S=a.cheb_degree_S, theta=a.theta,
+               cheb_degree=a.cheb_degree, cheb_degree_S=a.cheb_degree_S, cheb_degree_I=a.cheb_degree_I, theta=a.theta,
                amg_max_levels=a.amg_max_levels, amg_coarse_max=a.amg_coarse_max)
     s.setup()
     b = torch.as_tensor(d["b"], device=f"cuda:{dev}")
@@ -722,7 +724,8 @@ def main():
                                   a.precision, str(a.precision)),
                    "P_A": "AMG" if a.pc_A == 0 else "Jacobi", "variant": ["P_SCR", "block-triangular", "SIMPLE"][a.variant],
                    "amg_cycle": a.amg_cycle, "amg_kdepth": a.amg_kdepth,
-                   "cheb_degree": a.cheb_degree, "cheb_degree_S": a.cheb_degree_S, "theta": a.theta,
+                   "cheb_degree": a.cheb_degree, "cheb_degree_S": a.cheb_degree_S, "cheb_degree_I": a.cheb_degree_I,
+                   "theta": a.theta,
                    "amg_max_levels": a.amg_max_levels, "amg_coarse_max": a.amg_coarse_max,
                    "parallelism": f"replicas{ws}", "l2": "inputs larger than L2 (no flush)"},
         "fp64": ({"solve_s": info64["solve_s"], "rel_res_true": info64["rel_res_true"], **counts64} if info64 else None),

@@ -117,6 +117,10 @@ typedef struct {
                                arithmetic; the fused Gram-Schmidt kernel of the device loop
                                splits its sums over one fixed grid for every basis length, so
                                results differ from the host loop at rounding level. */
+    int32_t cheb_degree_I;  /* Chebyshev degree of the AMG(A) cycle that preconditions the
+                               inner A-solves of Algorithm 2 (the S-apply's A^{-1}, solved only
+                               to rtol_I), default 1; cheb_degree (default 2) in the A-solves of
+                               Algorithm 3 */
 } nbp_options;
 
 typedef struct {

@@ -58,7 +58,7 @@ class Options(ctypes.Structure):
         ("pc_A", ctypes.c_int), ("pc_S", ctypes.c_int), ("variant", ctypes.c_int),
         ("amg_max_levels", ctypes.c_int), ("amg_coarse_max", ctypes.c_int), ("cheb_degree", ctypes.c_int),
         ("theta", ctypes.c_double), ("amg_cycle", ctypes.c_int), ("amg_kdepth", ctypes.c_int),
-        ("cheb_degree_S", ctypes.c_int),
+        ("cheb_degree_S", ctypes.c_int), ("cheb_degree_I", ctypes.c_int),
     ]
 
 

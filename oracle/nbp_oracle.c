@@ -105,6 +105,8 @@ typedef struct {
                            AMG(S_hat); 2 K-cycle on both hierarchies */
     int amg_kdepth;     /* K-cycle on coarse levels 1..amg_kdepth, V-cycles below */
     int cheb_degree_S;  /* Chebyshev degree of the AMG(S_hat) smoother (cheb_degree: AMG(A)) */
+    int cheb_degree_I;  /* Chebyshev degree of the AMG(A) cycle inside the inner A-solves of
+                           Algorithm 2 (tolerance rtol_I); cheb_degree in every other A-solve */
 } or_options;
 
 typedef struct {
@@ -1010,7 +1012,10 @@ void or_apply_S(or_ctx *c, const double *xp, double *y) {
     double *xhat = dvec(N), *xbar = dvec(3 * (size_t)N), *xtil = dvec(3 * (size_t)N), *cx = dvec(N);
     spmv(&c->D, xp, xhat);                                 /* line 1 */
     spmv(&c->B, xp, xbar);                                 /* line 2 */
-    or_solve_A(c, xbar, xtil, c->opt.rtol_I, &its);        /* line 3 */
+    const int deg = c->amgA.cheb_degree;                   /* line 3, with its own cycle degree */
+    c->amgA.cheb_degree = c->opt.cheb_degree_I;
+    or_solve_A(c, xbar, xtil, c->opt.rtol_I, &its);
+    c->amgA.cheb_degree = deg;
     c->info.I_iters += its; c->info.n_I_solves++;
     spmv(&c->C, xtil, cx);                                 /* line 4 */
 #pragma omp parallel for schedule(static) if ((N) > OR_PAR_MIN)
@@ -1095,6 +1100,7 @@ void or_default_options(or_options *o) {
     o->amg_cycle = 1;
     o->amg_kdepth = 99;
     o->cheb_degree_S = 1;
+    o->cheb_degree_I = 1;
 }
 
 or_ctx *or_create(int N, const int *arp, const int *aci, const double *av, const int *brp, const int *bci,

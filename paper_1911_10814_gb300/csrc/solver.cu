@@ -157,9 +157,10 @@ struct nbp_ctx {
     std::string report;
     nbp_ctx *tctx = nullptr;      // transposed system (adjoint), built lazily
     bool is_transposed = false;
-    // CUDA graphs of the AMG cycles, keyed by (hierarchy, value precision)
+    // CUDA graphs of the AMG cycles, keyed by (hierarchy, value precision, Chebyshev degree)
     struct CycleGraph { cudaGraphExec_t exec = nullptr; int cheb = -1; long long kernels = 0; };
-    CycleGraph graphs[2][3];
+    static constexpr int kMaxChebDegree = 8;
+    CycleGraph graphs[2][3][kMaxChebDegree + 1];
     cudaStream_t cap = nullptr;   // private stream used only while capturing
     bool use_graphs = true;
     // device-driven solve: the whole nested solve as one CUDA graph whose
@@ -270,6 +271,20 @@ static SpmvArgs sargs(const void *x, void *y) {
     a.x = x;
     a.y = y;
     return a;
+}
+
+// Run f with the AMG(A) cycle of the inner A-solves of Algorithm 2 (degree
+// cheb_degree_I; the hierarchy's own degree, cheb_degree, everywhere else)
+template <class F> static void with_inner_degree(nbp_ctx *c, F f) {
+    const int keep = c->HA.cheb;
+    c->HA.cheb = c->opt.cheb_degree_I;
+    try {
+        f();
+    } catch (...) {
+        c->HA.cheb = keep;
+        throw;
+    }
+    c->HA.cheb = keep;
 }
 
 // y = A x (+ sum_k r_k a^k (a^k . x)); the rank-one factors f_k are FP64
@@ -824,11 +839,12 @@ template <typename T> static void autotune_cycles(nbp_ctx *c) {
 }
 
 static void drop_graphs(nbp_ctx *c) {
-    for (auto &row : c->graphs)
-        for (auto &g : row) {
-            if (g.exec) cudaGraphExecDestroy(g.exec);
-            g = nbp_ctx::CycleGraph();
-        }
+    for (auto &plane : c->graphs)
+        for (auto &row : plane)
+            for (auto &g : row) {
+                if (g.exec) cudaGraphExecDestroy(g.exec);
+                g = nbp_ctx::CycleGraph();
+            }
     if (c->dl_exec) cudaGraphExecDestroy(c->dl_exec);
     c->dl_exec = nullptr;
     c->dl_key.clear();
@@ -852,7 +868,7 @@ template <typename T> static void vcycle(nbp_ctx *c, Hier &H, int vsel, const T 
         // with a smoothed level 0, the copy of b into the replay buffer and
         // the first smoothing step from zero are one kernel outside the graph
         const bool first_in = H.cheb > 0 && H.nlev > 1;
-        nbp_ctx::CycleGraph &G = c->graphs[&H == &c->HS ? 1 : 0][vsel];
+        nbp_ctx::CycleGraph &G = c->graphs[&H == &c->HS ? 1 : 0][vsel][H.cheb];
         if (G.exec && G.cheb != H.cheb) {
             cudaGraphExecDestroy(G.exec);
             G.exec = nullptr;
@@ -939,7 +955,8 @@ template <typename T> static void apply_S(nbp_ctx *c, int vsel, const T *xp, T *
     Bufs<T> &Bf = BUF<T>(c);
     do_spmv<T>(c, c->D, vsel, sargs(xp, y), EPI_SET, false);          // line 1: x_hat = D x_p (into y)
     do_spmv<T>(c, c->B, vsel, sargs(xp, Bf.xbar), EPI_SET, false);    // line 2: x_bar = B x_p
-    GmResult R = solve_A<T>(c, vsel_I_of(c->opt.precision), Bf.xbar, Bf.xtil, c->opt.rtol_I);  // line 3
+    GmResult R;
+    with_inner_degree(c, [&] { R = solve_A<T>(c, vsel_I_of(c->opt.precision), Bf.xbar, Bf.xtil, c->opt.rtol_I); });   // line 3
     c->info.I_iters += R.its;
     c->info.n_I_solves++;
     do_spmv<T>(c, c->C, vsel, sargs(Bf.xtil, y), EPI_SUB, false);     // lines 4-5: y = x_hat - C x_tilde
@@ -1261,7 +1278,9 @@ template <typename T> static double *pscr_dl(nbp_ctx *c, const double *vbase, lo
     auto opS = [&](const T *x, T *out) {                                                          // Algorithm 2
         do_spmv<T>(c, c->D, vsel, sargs(x, out), EPI_SET, false);
         do_spmv<T>(c, c->B, vsel, sargs(x, Bf.xbar), EPI_SET, false);
-        solve_A_dl<T>(c, vsel_I_of(c->opt.precision), Bf.xbar, Bf.xtil, &par->rtol_I, &cnt->I, &cnt->nI, depth + 1);
+        with_inner_degree(c, [&] {
+            solve_A_dl<T>(c, vsel_I_of(c->opt.precision), Bf.xbar, Bf.xtil, &par->rtol_I, &cnt->I, &cnt->nI, depth + 1);
+        });
         do_spmv<T>(c, c->C, vsel, sargs(Bf.xtil, out), EPI_SUB, false);
     };
     auto pcS = [&](T *vb, long long l, const int *j) -> T * {
@@ -1369,6 +1388,7 @@ static void dl_prepare(nbp_ctx *c) {
                                      c->full_w, c->diagA, c->lr.lr_rp, c->lr.f,
                                      (const void *)(intptr_t)o.precision, (const void *)(intptr_t)o.variant,
                                      (const void *)(intptr_t)o.pc_A, (const void *)(intptr_t)o.pc_S,
+                                     (const void *)(intptr_t)o.cheb_degree_I,
                                      (const void *)(intptr_t)c->Kout.m, (const void *)(intptr_t)c->KA32.m,
                                      (const void *)(intptr_t)c->KS32.m, (const void *)(intptr_t)c->KA64.m,
                                      (const void *)(intptr_t)c->KS64.m, (const void *)(intptr_t)c->Kout.grid,
@@ -1890,6 +1910,7 @@ void nbp_default_options(nbp_options *o) {
     o->amg_cycle = 1;
     o->amg_kdepth = 99;
     o->cheb_degree_S = 1;
+    o->cheb_degree_I = 1;
     o->device_loop = 1;
 }
 
@@ -1897,7 +1918,8 @@ static nbp_status check_options(const nbp_options *o, std::string &msg) {
     if (!(o->rtol >= 0 && o->rtol_A >= 0 && o->rtol_S >= 0 && o->rtol_I >= 0 && o->atol >= 0)) { msg = "negative tolerance"; return NBP_ERR_INVALID; }
     if (o->m < 1 || o->m_A < 1 || o->m_S < 1 || o->nmax < 1 || o->nmax_A < 1 || o->nmax_S < 1) { msg = "restart/n_max < 1"; return NBP_ERR_INVALID; }
     if (o->precision < 0 || o->precision > 4 || o->pc_A < 0 || o->pc_A > 1 || o->pc_S < 0 || o->pc_S > 1 || o->variant < 0 || o->variant > 2) { msg = "bad mode switch"; return NBP_ERR_INVALID; }
-    if (o->cheb_degree < 0 || o->cheb_degree > 8 || o->cheb_degree_S < 0 || o->cheb_degree_S > 8 || o->amg_max_levels < 1 || o->amg_cycle < 0 || o->amg_cycle > 2 || o->amg_kdepth < 1) { msg = "bad AMG option"; return NBP_ERR_INVALID; }
+    if (o->cheb_degree < 0 || o->cheb_degree > 8 || o->cheb_degree_S < 0 || o->cheb_degree_S > 8 ||
+        o->cheb_degree_I < 0 || o->cheb_degree_I > 8 || o->amg_max_levels < 1 || o->amg_cycle < 0 || o->amg_cycle > 2 || o->amg_kdepth < 1) { msg = "bad AMG option"; return NBP_ERR_INVALID; }
     if (o->device_loop < 0 || o->device_loop > 1) { msg = "device_loop must be 0 or 1"; return NBP_ERR_INVALID; }
     return NBP_OK;
 }

@@ -359,3 +359,22 @@ def test_no_outlets(prec):
     xo, _, _ = o.solve(d["b"])
     assert _rel(xh, xo) <= (1e-6 if prec == 0 else 1e-5)
     s.close()
+
+
+@pytest.mark.parametrize("deg", [1, 2])
+def test_inner_cycle_degree_matches_oracle(deg):
+    """Algorithm 2's inner A-solves preconditioned by the AMG(A) cycle of
+    degree cheb_degree_I (1 by default, 2 the degree of the other A-solves):
+    FP64 solve, the oracle's iteration counts and solution."""
+    d = synth.generate(CASES["box9x11x23_q4"])
+    s = Solver(d, cheb_degree_I=deg)
+    s.setup()
+    o = oracle.Oracle(d, cheb_degree_I=deg)
+    o.setup()
+    x, info = s.solve(_t(d["b"]))
+    xo, oi, rc = o.solve(d["b"])
+    assert rc == 0 and info["rel_res_true"] <= 1e-8
+    assert info["outer_iters"] == oi.outer_iters
+    assert abs(info["I_iters"] - oi.I_iters) <= max(2, 0.05 * oi.I_iters)
+    assert _rel(x.cpu().numpy(), xo) <= 1e-6
+    s.close()

@@ -311,10 +311,12 @@ def test_two_level_cycle_is_coarse_projection(tiny):
     assert _rel(o.vcycle(0, b), ref) <= 1e-12
 
 
-def test_vcycle_error_propagation(tiny):
-    """Two-level V(1,1): E = (I - S A)(I - P A_c^{-1} P^T A)(I - S A), M^{-1} = (I - E) A^{-1}."""
+@pytest.mark.parametrize("deg", [1, 2])
+def test_vcycle_error_propagation(tiny, deg):
+    """Two-level V(1,1): E = (I - S A)(I - P A_c^{-1} P^T A)(I - S A), M^{-1} = (I - E) A^{-1},
+    S the Chebyshev smoother of degree deg (1: the cycle of the inner A-solves of Algorithm 2)."""
     d, _ = tiny
-    o = oracle.Oracle(d, amg_max_levels=2, amg_coarse_max=10)
+    o = oracle.Oracle(d, amg_max_levels=2, amg_coarse_max=10, cheb_degree=deg)
     o.setup()
     L = o.amg_levels(0)
     n0, n1 = len(L[0]["rowptr"]) - 1, len(L[1]["rowptr"]) - 1
@@ -325,7 +327,7 @@ def test_vcycle_error_propagation(tiny):
     Dinv = np.linalg.inv(Db)
     n = 3 * n0
     # smoother as a matrix: x = S b from x0 = 0
-    Sm = _cheb_closed_form(A0, Dinv, L[0]["rho"], 2, None)
+    Sm = _cheb_closed_form(A0, Dinv, L[0]["rho"], deg, None)
     P = np.zeros((n, 3 * n1))
     for i, I in enumerate(L[0]["agg"]):
         if I >= 0:
@@ -600,3 +602,23 @@ def test_solve_without_explicit_setup_builds_the_hierarchies(tiny):
     o = oracle.Oracle(d)
     x, info, rc = o.solve(d["b"])
     assert rc == 0 and np.linalg.norm(d["b"] - F @ x) <= 1e-8 * np.linalg.norm(d["b"])
+
+
+def test_schur_apply_inner_solve_uses_its_own_cycle_degree(tiny):
+    """Algorithm 2's inner A-solve (line 3, tolerance rtol_I) is preconditioned
+    by the AMG(A) cycle of degree cheb_degree_I, every other A-solve by that of
+    cheb_degree: the S-apply equals D x_p - C y with y from an A-solve whose
+    context has cheb_degree = cheb_degree_I, bit for bit, and differs from the
+    one with the other degree."""
+    d, _ = tiny
+    xp = np.random.default_rng(23).standard_normal(d["n_nodes"])
+    o1 = oracle.Oracle(d, cheb_degree=2, cheb_degree_I=1)
+    o1.setup()
+    y1 = o1.apply_S(xp)
+    o2 = oracle.Oracle(d, cheb_degree=1)
+    o2.setup()
+    xt = o2.solve_A(o2.apply_B(xp), o2.options().rtol_I)[0]
+    assert np.array_equal(y1, o2.apply_D(xp) - o2.apply_C(xt))
+    o3 = oracle.Oracle(d, cheb_degree=2, cheb_degree_I=2)
+    o3.setup()
+    assert not np.array_equal(y1, o3.apply_S(xp))
