@@ -51,7 +51,7 @@ def _args():
     p.add_argument("--pc-A", type=int, default=0, help="P_A: 0 AMG V-cycle (default), 1 Jacobi")
     p.add_argument("--variant", type=int, default=0, help="0 P_SCR (Algorithm 3), 1 block-triangular, 2 SIMPLE")
     p.add_argument("--amg-cycle", type=int, default=1, help="0 V-cycles, 1 K-cycle on AMG(S_hat), 2 K-cycle on both")
-    p.add_argument("--amg-kdepth", type=int, default=99, help="K-cycle on coarse levels 1..k")
+    p.add_argument("--amg-kdepth", type=int, default=2, help="K-cycle on coarse levels 1..k")
     p.add_argument("--cheb-degree", type=int, default=2, help="Chebyshev smoothing degree of AMG(A)")
     p.add_argument("--cheb-degree-S", type=int, default=1, help="Chebyshev smoothing degree of AMG(S_hat)")
     p.add_argument("--cheb-degree-I", type=int, default=None,

@@ -102,7 +102,7 @@ typedef struct {
     int32_t amg_cycle;      /* 0 V-cycle on both hierarchies; 1 (default) K-cycle on the
                                coarse levels of AMG(S_hat); 2 K-cycle on both.  Takes
                                effect at nbp_setup. */
-    int32_t amg_kdepth;     /* K-cycle on coarse levels 1..amg_kdepth (default 99: all), V-cycles
+    int32_t amg_kdepth;     /* K-cycle on coarse levels 1..amg_kdepth (default 2), V-cycles
                                below */
     int32_t cheb_degree_S;  /* Chebyshev degree of the AMG(S_hat) smoother, default 1
                                (cheb_degree, default 2, is that of AMG(A)) */

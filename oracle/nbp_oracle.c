@@ -1098,7 +1098,7 @@ void or_default_options(or_options *o) {
     o->pc_A = 0; o->pc_S = 0; o->variant = 0;
     o->amg_max_levels = 5; o->amg_coarse_max = 300; o->cheb_degree = 2; o->theta = 0.0064;
     o->amg_cycle = 1;
-    o->amg_kdepth = 99;
+    o->amg_kdepth = 2;
     o->cheb_degree_S = 1;
     o->cheb_degree_I = 1;
 }

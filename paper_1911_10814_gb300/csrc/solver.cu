@@ -1908,7 +1908,7 @@ void nbp_default_options(nbp_options *o) {
     o->precision = 0; o->pc_A = 0; o->pc_S = 0; o->variant = 0;
     o->amg_max_levels = 5; o->amg_coarse_max = 300; o->cheb_degree = 2; o->theta = 0.0064;
     o->amg_cycle = 1;
-    o->amg_kdepth = 99;
+    o->amg_kdepth = 2;
     o->cheb_degree_S = 1;
     o->cheb_degree_I = 1;
     o->device_loop = 1;
