@@ -51,7 +51,8 @@ def _args():
     p.add_argument("--pc-A", type=int, default=0, help="P_A: 0 AMG V-cycle (default), 1 Jacobi")
     p.add_argument("--variant", type=int, default=0, help="0 P_SCR (Algorithm 3), 1 block-triangular, 2 SIMPLE")
     p.add_argument("--amg-cycle", type=int, default=1, help="0 V-cycles, 1 K-cycle on AMG(S_hat), 2 K-cycle on both")
-    p.add_argument("--amg-kdepth", type=int, default=2, help="K-cycle on coarse levels 1..k")
+    p.add_argument("--amg-kdepth", type=int, default=None,
+                   help="K-cycle on coarse levels 1..k; default 2, and 99 (every coarse level) for the newton workload")
     p.add_argument("--cheb-degree", type=int, default=2, help="Chebyshev smoothing degree of AMG(A)")
     p.add_argument("--cheb-degree-S", type=int, default=1, help="Chebyshev smoothing degree of AMG(S_hat)")
     p.add_argument("--cheb-degree-I", type=int, default=None,
@@ -74,12 +75,15 @@ def _args():
     a = p.parse_args()
     # per-workload defaults, each the fastest measured for its workload: the
     # Newton tangents from a consistent start take more outer iterations with
-    # the cheaper inner A-solves (10.0 against 8.7 per 4.34M step)
+    # the cheaper inner A-solves (10.0 against 8.7 per 4.34M step) and with
+    # the K-cycle on two coarse levels only (9.3 against 8.7)
     newton = a.workload == "newton"
     if a.precision is None:
         a.precision = 3 if newton else 4
     if a.cheb_degree_I is None:
         a.cheb_degree_I = 2 if newton else 1
+    if a.amg_kdepth is None:
+        a.amg_kdepth = 99 if newton else 2
     return a
 
 
@@ -533,7 +537,7 @@ def run_newton(a):
     d = synth.generate(spec)
     m = synth.mesh(spec)
     N = d["n_nodes"]
-    s = Solver(d, precision=a.precision, cheb_degree_I=a.cheb_degree_I)
+    s = Solver(d, precision=a.precision, cheb_degree_I=a.cheb_degree_I, amg_kdepth=a.amg_kdepth)
     t0 = time.perf_counter()
     vm = Vms(s, m, spec.rho, spec.mu, spec.dt, spec.rho_inf, tangent_fp32=True)
     t_create = time.perf_counter() - t0
@@ -569,7 +573,7 @@ def run_newton(a):
                       "dtype": "f32", "data": "synthetic",
                       "config": {"workload": spec.name, "unknowns": 4 * N, "tets": len(m["tets"]),
                                  "tol_R": 1e-6, "nested_tolerance": 1e-8, "inner_precision": a.precision,
-                                 "cheb_degree_I": a.cheb_degree_I,
+                                 "cheb_degree_I": a.cheb_degree_I, "amg_kdepth": a.amg_kdepth,
                                  "tangent": "fp32 dual numbers", "outlets": "4 x RCR, R = 1e3",
                                  "preconditioner": ("rebuilt from every tangent" if a.pc_rebuild_every <= 0 else
                                                     f"built every {a.pc_rebuild_every} time steps, kept (lagged) "
