@@ -355,7 +355,9 @@ def oracle_phase_times(o, d):
     N = d["n_nodes"]
     rng = np.random.default_rng(0)
     bv, bp, b = rng.standard_normal(3 * N), rng.standard_normal(N), rng.standard_normal(4 * N)
-    t = {"pcA": _wall(lambda: o.vcycle(0, bv)), "pcS": _wall(lambda: o.vcycle(1, bp)),
+    deg_I = o.options().cheb_degree_I
+    t = {"pcA": _wall(lambda: o.vcycle(0, bv)), "pcA_I": _wall(lambda: o.vcycle(0, bv, degree=deg_I)),
+         "pcS": _wall(lambda: o.vcycle(1, bp)),
          "A": _wall(lambda: o.apply_A(bv)), "B": _wall(lambda: o.apply_B(bp)), "C": _wall(lambda: o.apply_C(bv)),
          "D": _wall(lambda: o.apply_D(bp)), "full": _wall(lambda: o.apply_full(b))}
     t12 = _wall(lambda: o.gmres_A(bv, 1e-30, 12, 12, 0))
@@ -366,7 +368,8 @@ def oracle_phase_times(o, d):
 def oracle_model(t, counts, outer_solves=1):
     """Seconds of one oracle nested solve from its building blocks and the
     iteration counts of the solve (Algorithms 2-3 inside FGMRES):
-      A- and I-iterations: one AMG(A) cycle + one A product each;
+      A- and I-iterations: one AMG(A) cycle + one A product each (the
+        I-iterations' cycle of degree cheb_degree_I);
       S-iterations: the B, D, C products of Algorithm 2 and one AMG(S_hat)
         cycle (the inner A-solve is counted in the I-iterations);
       outer iterations: one full tangent product, the C and B products of
@@ -385,7 +388,7 @@ def oracle_model(t, counts, outer_solves=1):
         return solves * (J * (J + 1) / 2 + 1.5 * J) * t["col3N"] * scale
 
     parts = {
-        "A_I_iterations": (a_ + i_) * (t["pcA"] + t["A"]),
+        "A_I_iterations": a_ * (t["pcA"] + t["A"]) + i_ * (t.get("pcA_I", t["pcA"]) + t["A"]),
         "S_iterations": s_ * (t["pcS"] + t["B"] + t["C"] + t["D"]),
         "outer_iterations": o_ * (t["full"] + t["B"] + t["C"]) + outer_solves * t["full"],
         "gram_schmidt": gs(a_, 2 * o_, 1.0) + gs(i_, s_, 1.0) + gs(s_, o_, 1.0 / 3.0) + gs(o_, outer_solves, 4.0 / 3.0),

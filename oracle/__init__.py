@@ -116,6 +116,7 @@ def _load():
             ("or_apply_A", [vp, _dp, _dp]), ("or_apply_B", [vp, _dp, _dp]), ("or_apply_C", [vp, _dp, _dp]),
             ("or_apply_D", [vp, _dp, _dp]), ("or_apply_full", [vp, _dp, _dp]), ("or_apply_S", [vp, _dp, _dp]),
             ("or_apply_pscr", [vp, _dp, _dp]), ("or_vcycle", [vp, ctypes.c_int, _dp, _dp]),
+            ("or_vcycle_degree", [vp, ctypes.c_int, ctypes.c_int, _dp, _dp]),
             ("or_set_options", [vp, ctypes.POINTER(Options)]), ("or_get_options", [vp, ctypes.POINTER(Options)]),
             ("or_set_values", [vp, _dp, _dp, _dp, _dp]),
             ("or_default_options", [ctypes.POINTER(Options)]), ("or_set_resistances", [vp, _dp]),
@@ -288,11 +289,16 @@ class Oracle:
         self._ensure_setup()
         return self._apply(self.lib.or_apply_pscr, s, 4 * self.N)
 
-    def vcycle(self, which, b):
+    def vcycle(self, which, b, degree=None):
+        """One AMG cycle (0: AMG(A), 1: AMG(S_hat)); degree: its Chebyshev
+        degree instead of the hierarchy's own."""
         self._ensure_setup()
         b = _d(b)
         x = np.zeros_like(b)
-        self.lib.or_vcycle(self.ctx, which, _pd(b), _pd(x))
+        if degree is None:
+            self.lib.or_vcycle(self.ctx, which, _pd(b), _pd(x))
+        else:
+            self.lib.or_vcycle_degree(self.ctx, which, int(degree), _pd(b), _pd(x))
         return x
 
     def solve_A(self, b, rtol):

@@ -1192,6 +1192,16 @@ int or_setup_numeric(or_ctx *c) {
 
 void or_vcycle(or_ctx *c, int which, const double *b, double *x) { amg_apply(which ? &c->amgS : &c->amgA, b, x); }
 
+/* The same cycle with Chebyshev degree `degree` (the inner A-solves' cycle of
+ * Algorithm 2 when degree = cheb_degree_I) */
+void or_vcycle_degree(or_ctx *c, int which, int degree, const double *b, double *x) {
+    amg *H = which ? &c->amgS : &c->amgA;
+    const int keep = H->cheb_degree;
+    H->cheb_degree = degree;
+    amg_apply(H, b, x);
+    H->cheb_degree = keep;
+}
+
 int or_amg_nlev(or_ctx *c, int which) { return (which ? &c->amgS : &c->amgA)->nlev; }
 int or_amg_level_rows(or_ctx *c, int which, int l) { return (which ? &c->amgS : &c->amgA)->L[l].nbr; }
 int or_amg_level_nnz(or_ctx *c, int which, int l) { amg *H = which ? &c->amgS : &c->amgA; return H->L[l].rp[H->L[l].nbr]; }

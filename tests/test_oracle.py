@@ -622,3 +622,16 @@ def test_schur_apply_inner_solve_uses_its_own_cycle_degree(tiny):
     o3 = oracle.Oracle(d, cheb_degree=2, cheb_degree_I=2)
     o3.setup()
     assert not np.array_equal(y1, o3.apply_S(xp))
+
+
+def test_cycle_with_a_chosen_degree(tiny):
+    """or_vcycle_degree: the AMG(A) cycle of degree k on a context built with
+    another degree equals the cycle of a context built with degree k."""
+    d, _ = tiny
+    b = np.random.default_rng(29).standard_normal(3 * d["n_nodes"])
+    o = oracle.Oracle(d)
+    o.setup()
+    o1 = oracle.Oracle(d, cheb_degree=1)
+    o1.setup()
+    assert np.array_equal(o.vcycle(0, b, degree=1), o1.vcycle(0, b))
+    assert np.array_equal(o.vcycle(0, b, degree=2), o.vcycle(0, b))
