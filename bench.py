@@ -55,6 +55,9 @@ def _args():
                    help="K-cycle on coarse levels 1..k; default 2, and 99 (every coarse level) for the newton workload")
     p.add_argument("--cheb-degree", type=int, default=2, help="Chebyshev smoothing degree of AMG(A)")
     p.add_argument("--cheb-degree-S", type=int, default=1, help="Chebyshev smoothing degree of AMG(S_hat)")
+    p.add_argument("--gs-passes-I", type=int, default=None,
+                   help="Gram-Schmidt passes per Arnoldi step in the inner A-solves of Algorithm 2; default 1, and 2 "
+                        "for the newton workload")
     p.add_argument("--cheb-degree-I", type=int, default=None,
                    help="Chebyshev degree of the AMG(A) cycle in the inner A-solves of Algorithm 2; default 1, and 2 "
                         "for the newton workload")
@@ -84,6 +87,8 @@ def _args():
         a.cheb_degree_I = 2 if newton else 1
     if a.amg_kdepth is None:
         a.amg_kdepth = 99 if newton else 2
+    if a.gs_passes_I is None:
+        a.gs_passes_I = 2 if newton else 1
     return a
 
 
@@ -540,7 +545,8 @@ def run_newton(a):
     d = synth.generate(spec)
     m = synth.mesh(spec)
     N = d["n_nodes"]
-    s = Solver(d, precision=a.precision, cheb_degree_I=a.cheb_degree_I, amg_kdepth=a.amg_kdepth)
+    s = Solver(d, precision=a.precision, cheb_degree_I=a.cheb_degree_I, amg_kdepth=a.amg_kdepth,
+               gs_passes_I=a.gs_passes_I)
     t0 = time.perf_counter()
     vm = Vms(s, m, spec.rho, spec.mu, spec.dt, spec.rho_inf, tangent_fp32=True)
     t_create = time.perf_counter() - t0
@@ -577,6 +583,7 @@ def run_newton(a):
                       "config": {"workload": spec.name, "unknowns": 4 * N, "tets": len(m["tets"]),
                                  "tol_R": 1e-6, "nested_tolerance": 1e-8, "inner_precision": a.precision,
                                  "cheb_degree_I": a.cheb_degree_I, "amg_kdepth": a.amg_kdepth,
+                                 "gs_passes_I": a.gs_passes_I,
                                  "tangent": "fp32 dual numbers", "outlets": "4 x RCR, R = 1e3",
                                  "preconditioner": ("rebuilt from every tangent" if a.pc_rebuild_every <= 0 else
                                                     f"built every {a.pc_rebuild_every} time steps, kept (lagged) "
@@ -619,7 +626,8 @@ def main():
     t_gen = time.perf_counter() - t0
     s = Solver(d, device=dev, precision=a.precision, pc_A=a.pc_A, variant=a.variant, amg_cycle=a.amg_cycle,
                amg_kdepth=a.amg_kdepth,
-               cheb_degree=a.cheb_degree, cheb_degree_S=a.cheb_degree_S, cheb_degree_I=a.cheb_degree_I, theta=a.theta,
+               cheb_degree=a.cheb_degree, cheb_degree_S=a.cheb_degree_S, cheb_degree_I=a.cheb_degree_I,
+               gs_passes_I=a.gs_passes_I, theta=a.theta,
                amg_max_levels=a.amg_max_levels, amg_coarse_max=a.amg_coarse_max)
     s.setup()
     b = torch.as_tensor(d["b"], device=f"cuda:{dev}")
@@ -743,6 +751,7 @@ def main():
                    "P_A": "AMG" if a.pc_A == 0 else "Jacobi", "variant": ["P_SCR", "block-triangular", "SIMPLE"][a.variant],
                    "amg_cycle": a.amg_cycle, "amg_kdepth": a.amg_kdepth,
                    "cheb_degree": a.cheb_degree, "cheb_degree_S": a.cheb_degree_S, "cheb_degree_I": a.cheb_degree_I,
+                   "gs_passes_I": a.gs_passes_I,
                    "theta": a.theta,
                    "amg_max_levels": a.amg_max_levels, "amg_coarse_max": a.amg_coarse_max,
                    "parallelism": f"replicas{ws}", "l2": "inputs larger than L2 (no flush)"},

@@ -121,6 +121,9 @@ typedef struct {
                                inner A-solves of Algorithm 2 (the S-apply's A^{-1}, solved only
                                to rtol_I), default 1; cheb_degree (default 2) in the A-solves of
                                Algorithm 3 */
+    int32_t gs_passes_I;    /* Gram-Schmidt passes per Arnoldi step in those inner A-solves:
+                               1 (default, classical Gram-Schmidt) or 2 (CGS2, as in every
+                               other solve) */
 } nbp_options;
 
 typedef struct {

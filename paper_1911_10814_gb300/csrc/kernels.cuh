@@ -631,7 +631,8 @@ struct GivensArgs {
     GmState *st = nullptr;
 };
 
-// Column j of the Hessenberg matrix: H(i,j) = h1_i + h2_i (i <= j),
+// Column j of the Hessenberg matrix: H(i,j) = h1_i + h2_i (i <= j; h1_i
+// alone when h2 is null, a single Gram-Schmidt pass),
 // H(j+1,j) = ||w|| (from ||w||^2 = nrm2); the previous rotations applied, a
 // new rotation chosen to zero H(j+1,j), and the right-hand side g rotated
 // (Saad 1993, FGMRES with Givens rotations).  One thread.
@@ -639,7 +640,7 @@ __device__ __forceinline__ void givens_step(const GivensArgs &q, double nrm2) {
     double *H = q.H;
     const long long ldh = q.ldh;
     const int j = q.jp ? *q.jp : q.j;
-    for (int i = 0; i <= j; ++i) H[i * ldh + j] = q.h1[i] + q.h2[i];
+    for (int i = 0; i <= j; ++i) H[i * ldh + j] = q.h2 ? q.h1[i] + q.h2[i] : q.h1[i];
     const double beta = (nrm2 >= 0.0) ? sqrt(nrm2) : nrm2;   // NaN passes through
     H[(j + 1) * ldh + j] = beta;
     for (int i = 0; i < j; ++i) {

@@ -160,6 +160,9 @@ struct nbp_ctx {
     // CUDA graphs of the AMG cycles, keyed by (hierarchy, value precision, Chebyshev degree)
     struct CycleGraph { cudaGraphExec_t exec = nullptr; int cheb = -1; long long kernels = 0; };
     static constexpr int kMaxChebDegree = 8;
+    // inside an inner A-solve of Algorithm 2 with gs_passes_I = 1: one
+    // classical Gram-Schmidt pass per Arnoldi step instead of two
+    bool gs_one_pass = false;
     CycleGraph graphs[2][3][kMaxChebDegree + 1];
     cudaStream_t cap = nullptr;   // private stream used only while capturing
     bool use_graphs = true;
@@ -273,18 +276,23 @@ static SpmvArgs sargs(const void *x, void *y) {
     return a;
 }
 
-// Run f with the AMG(A) cycle of the inner A-solves of Algorithm 2 (degree
-// cheb_degree_I; the hierarchy's own degree, cheb_degree, everywhere else)
+// Run f as an inner A-solve of Algorithm 2: the AMG(A) cycle of degree
+// cheb_degree_I (the hierarchy's own degree, cheb_degree, everywhere else)
+// and gs_passes_I Gram-Schmidt passes per Arnoldi step (two elsewhere)
 template <class F> static void with_inner_degree(nbp_ctx *c, F f) {
     const int keep = c->HA.cheb;
+    const bool keep1 = c->gs_one_pass;
     c->HA.cheb = c->opt.cheb_degree_I;
+    c->gs_one_pass = c->opt.gs_passes_I == 1;
     try {
         f();
     } catch (...) {
         c->HA.cheb = keep;
+        c->gs_one_pass = keep1;
         throw;
     }
     c->HA.cheb = keep;
+    c->gs_one_pass = keep1;
 }
 
 // y = A x (+ sum_k r_k a^k (a^k . x)); the rank-one factors f_k are FP64
@@ -524,7 +532,16 @@ static GmResult gmres(nbp_ctx *c, Krylov<T> &K, long long n, Op op, Pc pc, const
             mdot<T>(c, K, K.V, K.ld, j + 1, K.w, K.h1);
             // second pass; the last kernel also forms ||w|| and applies the
             // Givens update of column j on the device
-            if (j + 1 <= kFusedCols) {
+            if (c->gs_one_pass) {   // one pass: subtract, norm and Givens update
+                GivensArgs gv = K.givens(j);
+                gv.h2 = nullptr;
+                if (j + 1 <= kFusedCols) {
+                    maxpy_dot<T>(c, K, K.V, K.ld, j + 1, K.h1, K.w, 1, K.nrm, gv);
+                } else {
+                    maxpy<T>(c, n, K.V, K.ld, j + 1, K.h1, -1.0, K.w);
+                    mdot<T>(c, K, K.w, K.ld, 1, K.w, K.nrm, gv);
+                }
+            } else if (j + 1 <= kFusedCols) {
                 maxpy_dot<T>(c, K, K.V, K.ld, j + 1, K.h1, K.w, 0, K.h2);
                 maxpy_dot<T>(c, K, K.V, K.ld, j + 1, K.h2, K.w, 1, K.nrm, K.givens(j));
             } else {
@@ -1163,13 +1180,17 @@ template <typename T> static void arnoldi_dl(nbp_ctx *c, Krylov<T> &K, GmDev *st
     const int *jp = &st->j;
     GivensArgs gv = K.givens(0);
     gv.jp = jp;
+    if (c->gs_one_pass) gv.h2 = nullptr;
+    // one pass: the multi-dot, then subtract + norm + Givens update
+    const double *coef = c->gs_one_pass ? K.h1 : K.h2;
     if (vec) {
         const unsigned g1 = K.grid_md ? K.grid_md : arnoldi_grids<T>().mdot_dl_v;
         const unsigned g2 = K.grid ? K.grid : arnoldi_grids<T>().mpd_dl_v;
         k_mdot_dl<T, 8, true><<<g1, 256, 0, c->s>>>(K.V, K.ld, jp, 1, K.w, K.n, K.partial, K.h1, K.ticket, GivensArgs());
-        k_maxpy_dot_dl<T, kFusedCols, true><<<g2, 256, 0, c->s>>>(K.V, K.ld, jp, 1, K.h1, K.w, K.n, 0, K.partial, K.h2,
-                                                                  K.ticket, GivensArgs());
-        k_maxpy_dot_dl<T, kFusedCols, true><<<g2, 256, 0, c->s>>>(K.V, K.ld, jp, 1, K.h2, K.w, K.n, 1, K.partial, K.nrm,
+        if (!c->gs_one_pass)
+            k_maxpy_dot_dl<T, kFusedCols, true><<<g2, 256, 0, c->s>>>(K.V, K.ld, jp, 1, K.h1, K.w, K.n, 0, K.partial,
+                                                                      K.h2, K.ticket, GivensArgs());
+        k_maxpy_dot_dl<T, kFusedCols, true><<<g2, 256, 0, c->s>>>(K.V, K.ld, jp, 1, coef, K.w, K.n, 1, K.partial, K.nrm,
                                                                   K.ticket, gv);
         k_scale_step_dl<T, true><<<grid_for(K.n / Vec16<T>::W + 1), 256, 0, c->s>>>(K.V, K.ld, st, K.w, K.st, K.n,
                                                                                    K.ticket, h);
@@ -1177,10 +1198,11 @@ template <typename T> static void arnoldi_dl(nbp_ctx *c, Krylov<T> &K, GmDev *st
         const unsigned g1 = K.grid_md ? K.grid_md : arnoldi_grids<T>().mdot_dl_s;
         const unsigned g2 = K.grid ? K.grid : arnoldi_grids<T>().mpd_dl_s;
         k_mdot_dl<T, 8, false><<<g1, 256, 0, c->s>>>(K.V, K.ld, jp, 1, K.w, K.n, K.partial, K.h1, K.ticket, GivensArgs());
-        k_maxpy_dot_dl<T, kFusedCols, false><<<g2, 256, 0, c->s>>>(K.V, K.ld, jp, 1, K.h1, K.w, K.n, 0, K.partial, K.h2,
-                                                                   K.ticket, GivensArgs());
-        k_maxpy_dot_dl<T, kFusedCols, false><<<g2, 256, 0, c->s>>>(K.V, K.ld, jp, 1, K.h2, K.w, K.n, 1, K.partial, K.nrm,
-                                                                   K.ticket, gv);
+        if (!c->gs_one_pass)
+            k_maxpy_dot_dl<T, kFusedCols, false><<<g2, 256, 0, c->s>>>(K.V, K.ld, jp, 1, K.h1, K.w, K.n, 0, K.partial,
+                                                                       K.h2, K.ticket, GivensArgs());
+        k_maxpy_dot_dl<T, kFusedCols, false><<<g2, 256, 0, c->s>>>(K.V, K.ld, jp, 1, coef, K.w, K.n, 1, K.partial,
+                                                                   K.nrm, K.ticket, gv);
         k_scale_step_dl<T, false><<<grid_for(K.n + 1), 256, 0, c->s>>>(K.V, K.ld, st, K.w, K.st, K.n, K.ticket, h);
     }
     NBP_LAUNCHED();
@@ -1388,7 +1410,7 @@ static void dl_prepare(nbp_ctx *c) {
                                      c->full_w, c->diagA, c->lr.lr_rp, c->lr.f,
                                      (const void *)(intptr_t)o.precision, (const void *)(intptr_t)o.variant,
                                      (const void *)(intptr_t)o.pc_A, (const void *)(intptr_t)o.pc_S,
-                                     (const void *)(intptr_t)o.cheb_degree_I,
+                                     (const void *)(intptr_t)o.cheb_degree_I, (const void *)(intptr_t)o.gs_passes_I,
                                      (const void *)(intptr_t)c->Kout.m, (const void *)(intptr_t)c->KA32.m,
                                      (const void *)(intptr_t)c->KS32.m, (const void *)(intptr_t)c->KA64.m,
                                      (const void *)(intptr_t)c->KS64.m, (const void *)(intptr_t)c->Kout.grid,
@@ -1911,6 +1933,7 @@ void nbp_default_options(nbp_options *o) {
     o->amg_kdepth = 2;
     o->cheb_degree_S = 1;
     o->cheb_degree_I = 1;
+    o->gs_passes_I = 1;
     o->device_loop = 1;
 }
 
@@ -1919,7 +1942,7 @@ static nbp_status check_options(const nbp_options *o, std::string &msg) {
     if (o->m < 1 || o->m_A < 1 || o->m_S < 1 || o->nmax < 1 || o->nmax_A < 1 || o->nmax_S < 1) { msg = "restart/n_max < 1"; return NBP_ERR_INVALID; }
     if (o->precision < 0 || o->precision > 4 || o->pc_A < 0 || o->pc_A > 1 || o->pc_S < 0 || o->pc_S > 1 || o->variant < 0 || o->variant > 2) { msg = "bad mode switch"; return NBP_ERR_INVALID; }
     if (o->cheb_degree < 0 || o->cheb_degree > 8 || o->cheb_degree_S < 0 || o->cheb_degree_S > 8 ||
-        o->cheb_degree_I < 0 || o->cheb_degree_I > 8 || o->amg_max_levels < 1 || o->amg_cycle < 0 || o->amg_cycle > 2 || o->amg_kdepth < 1) { msg = "bad AMG option"; return NBP_ERR_INVALID; }
+        o->cheb_degree_I < 0 || o->cheb_degree_I > 8 || o->gs_passes_I < 1 || o->gs_passes_I > 2 || o->amg_max_levels < 1 || o->amg_cycle < 0 || o->amg_cycle > 2 || o->amg_kdepth < 1) { msg = "bad AMG option"; return NBP_ERR_INVALID; }
     if (o->device_loop < 0 || o->device_loop > 1) { msg = "device_loop must be 0 or 1"; return NBP_ERR_INVALID; }
     return NBP_OK;
 }

@@ -38,7 +38,7 @@ class nbp_options(ctypes.Structure):
         ("variant", ctypes.c_int32), ("amg_max_levels", ctypes.c_int32), ("amg_coarse_max", ctypes.c_int32),
         ("cheb_degree", ctypes.c_int32), ("theta", ctypes.c_double), ("amg_cycle", ctypes.c_int32),
         ("amg_kdepth", ctypes.c_int32), ("cheb_degree_S", ctypes.c_int32), ("device_loop", ctypes.c_int32),
-        ("cheb_degree_I", ctypes.c_int32),
+        ("cheb_degree_I", ctypes.c_int32), ("gs_passes_I", ctypes.c_int32),
     ]
 
 
