@@ -56,8 +56,7 @@ def _args():
     p.add_argument("--cheb-degree", type=int, default=2, help="Chebyshev smoothing degree of AMG(A)")
     p.add_argument("--cheb-degree-S", type=int, default=1, help="Chebyshev smoothing degree of AMG(S_hat)")
     p.add_argument("--gs-passes-I", type=int, default=None,
-                   help="Gram-Schmidt passes per Arnoldi step in the inner A-solves of Algorithm 2; default 1, and 2 "
-                        "for the newton workload")
+                   help="Gram-Schmidt passes per Arnoldi step in the inner A-solves of Algorithm 2 (default 1)")
     p.add_argument("--cheb-degree-I", type=int, default=None,
                    help="Chebyshev degree of the AMG(A) cycle in the inner A-solves of Algorithm 2; default 1, and 2 "
                         "for the newton workload")
@@ -88,7 +87,7 @@ def _args():
     if a.amg_kdepth is None:
         a.amg_kdepth = 99 if newton else 2
     if a.gs_passes_I is None:
-        a.gs_passes_I = 2 if newton else 1
+        a.gs_passes_I = 1
     return a
 
 
