@@ -279,7 +279,7 @@ static SpmvArgs sargs(const void *x, void *y) {
 // Run f as an inner A-solve of Algorithm 2: the AMG(A) cycle of degree
 // cheb_degree_I (the hierarchy's own degree, cheb_degree, everywhere else)
 // and gs_passes_I Gram-Schmidt passes per Arnoldi step (two elsewhere)
-template <class F> static void with_inner_degree(nbp_ctx *c, F f) {
+template <class F> static void as_inner_solve(nbp_ctx *c, F f) {
     const int keep = c->HA.cheb;
     const bool keep1 = c->gs_one_pass;
     c->HA.cheb = c->opt.cheb_degree_I;
@@ -973,7 +973,7 @@ template <typename T> static void apply_S(nbp_ctx *c, int vsel, const T *xp, T *
     do_spmv<T>(c, c->D, vsel, sargs(xp, y), EPI_SET, false);          // line 1: x_hat = D x_p (into y)
     do_spmv<T>(c, c->B, vsel, sargs(xp, Bf.xbar), EPI_SET, false);    // line 2: x_bar = B x_p
     GmResult R;
-    with_inner_degree(c, [&] { R = solve_A<T>(c, vsel_I_of(c->opt.precision), Bf.xbar, Bf.xtil, c->opt.rtol_I); });   // line 3
+    as_inner_solve(c, [&] { R = solve_A<T>(c, vsel_I_of(c->opt.precision), Bf.xbar, Bf.xtil, c->opt.rtol_I); });   // line 3
     c->info.I_iters += R.its;
     c->info.n_I_solves++;
     do_spmv<T>(c, c->C, vsel, sargs(Bf.xtil, y), EPI_SUB, false);     // lines 4-5: y = x_hat - C x_tilde
@@ -1300,7 +1300,7 @@ template <typename T> static double *pscr_dl(nbp_ctx *c, const double *vbase, lo
     auto opS = [&](const T *x, T *out) {                                                          // Algorithm 2
         do_spmv<T>(c, c->D, vsel, sargs(x, out), EPI_SET, false);
         do_spmv<T>(c, c->B, vsel, sargs(x, Bf.xbar), EPI_SET, false);
-        with_inner_degree(c, [&] {
+        as_inner_solve(c, [&] {
             solve_A_dl<T>(c, vsel_I_of(c->opt.precision), Bf.xbar, Bf.xtil, &par->rtol_I, &cnt->I, &cnt->nI, depth + 1);
         });
         do_spmv<T>(c, c->C, vsel, sargs(Bf.xtil, out), EPI_SUB, false);
