@@ -361,13 +361,15 @@ def test_no_outlets(prec):
     s.close()
 
 
-@pytest.mark.parametrize("deg", [1, 2])
-def test_inner_cycle_degree_matches_oracle(deg):
+@pytest.mark.parametrize("deg,gs", [(1, 1), (2, 1), (1, 2)])
+def test_inner_cycle_degree_matches_oracle(deg, gs):
     """Algorithm 2's inner A-solves preconditioned by the AMG(A) cycle of
-    degree cheb_degree_I (1 by default, 2 the degree of the other A-solves):
-    FP64 solve, the oracle's iteration counts and solution."""
+    degree cheb_degree_I (1 by default, 2 the degree of the other A-solves),
+    with gs Gram-Schmidt passes per Arnoldi step (the oracle's modified
+    Gram-Schmidt is the same process in exact arithmetic): FP64 solve, the
+    oracle's iteration counts and solution."""
     d = synth.generate(CASES["box9x11x23_q4"])
-    s = Solver(d, cheb_degree_I=deg)
+    s = Solver(d, cheb_degree_I=deg, gs_passes_I=gs)
     s.setup()
     o = oracle.Oracle(d, cheb_degree_I=deg)
     o.setup()
