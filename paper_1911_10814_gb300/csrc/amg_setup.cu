@@ -931,6 +931,142 @@ __global__ void k_shat_reduce(int nseg, long long ntup, const unsigned long long
     atomicAdd(rowcnt + i, 1);
 }
 
+// ---- S_hat one row per warp: the row's tuples (the same as k_shat_fill
+// makes, in the same order q) sorted in shared memory by (column, q), so that
+// every entry is D_ij minus its terms in order q, as k_shat_reduce sums them;
+// for rows of at most kShatRowTuples tuples.
+constexpr int kShatRowTuples = 256;
+constexpr int kShatWarps = 8;   // warps per block
+
+// Tuples of row i into sk (key = column * 256 + q, padded with ~0u) and, when
+// t is set, their terms into t[q].  Returns the tuple count.
+__device__ __forceinline__ int shat_row_tuples(int i, int lane, const int *drp, const int *dci, const int *crp,
+                                               const int *cci, const double *cv, const int *brp, const int *bci,
+                                               const double *bv, const double *dinv, unsigned *sk, double *t) {
+    const int d0 = drp[i], dlen = drp[i + 1] - d0;
+    const int c0 = crp[i], clen = crp[i + 1] - c0;
+    for (int q = lane; q < kShatRowTuples; q += 32) sk[q] = ~0u;
+    __syncwarp();
+    for (int q = lane; q < dlen; q += 32) {   // the D pattern first, placeholder terms 0
+        sk[q] = ((unsigned)dci[d0 + q] << 8) | (unsigned)q;
+        if (t) t[q] = 0.0;
+    }
+    // then C_ik B_kj for k ascending (C's row order), j in B's row order; the
+    // start of entry e's tuples is dlen + the B row lengths before it
+    int off = dlen;
+    for (int e0 = 0; e0 < clen; e0 += 32) {
+        const int e = e0 + lane;
+        const int k = e < clen ? cci[c0 + e] : 0;
+        const int len = e < clen ? brp[k + 1] - brp[k] : 0;
+        int incl = len;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        const int start = off + incl - len;
+        if (e < clen) {
+            const long long ce = c0 + e;
+            double w0 = 0.0, w1 = 0.0, w2 = 0.0;
+            if (t) {
+                w0 = __dmul_rn(cv[3LL * ce], dinv[3LL * k]);
+                w1 = __dmul_rn(cv[3LL * ce + 1], dinv[3LL * k + 1]);
+                w2 = __dmul_rn(cv[3LL * ce + 2], dinv[3LL * k + 2]);
+            }
+            for (int f = 0; f < len; ++f) {
+                const int fe = brp[k] + f, q = start + f;
+                sk[q] = ((unsigned)bci[fe] << 8) | (unsigned)q;
+                if (t) {
+                    double tt = __dmul_rn(w0, bv[3LL * fe]);
+                    tt = __dadd_rn(tt, __dmul_rn(w1, bv[3LL * fe + 1]));
+                    tt = __dadd_rn(tt, __dmul_rn(w2, bv[3LL * fe + 2]));
+                    t[q] = tt;
+                }
+            }
+        }
+        off += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    __syncwarp();
+    // bitonic sort of the 256 keys (unique: q differs), ascending
+    for (int k = 2; k <= kShatRowTuples; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int p = lane; p < kShatRowTuples; p += 32) {
+                const int x = p ^ j;
+                if (x > p) {
+                    const unsigned a = sk[p], b = sk[x];
+                    if ((a > b) == ((p & k) == 0)) { sk[p] = b; sk[x] = a; }
+                }
+            }
+            __syncwarp();
+        }
+    }
+    return off;
+}
+
+// entries per row (distinct columns)
+__global__ void __launch_bounds__(32 * kShatWarps) k_shat_row_count(int N, const int *drp, const int *dci, const int *crp,
+                                                                   const int *cci, const int *brp, const int *bci, int *cnt) {
+    __shared__ unsigned keys[kShatWarps][kShatRowTuples];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int i = blockIdx.x * kShatWarps + w;
+    if (i >= N) return;
+    unsigned *sk = keys[w];
+    const int n = shat_row_tuples(i, lane, drp, dci, crp, cci, nullptr, brp, bci, nullptr, nullptr, sk, nullptr);
+    int c = 0;
+    for (int p = lane; p < n; p += 32) c += (p == 0 || (sk[p] >> 8) != (sk[p - 1] >> 8)) ? 1 : 0;
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if (lane == 0) cnt[i] = c;
+}
+
+// the row's entries at rp_out[i]..: columns ascending, each D_ij (or 0)
+// minus its terms in order q (as k_shat_reduce)
+__global__ void __launch_bounds__(32 * kShatWarps) k_shat_row_fill(int N, const int *drp, const int *dci, const double *dv,
+                                                                  const int *crp, const int *cci, const double *cv,
+                                                                  const int *brp, const int *bci, const double *bv,
+                                                                  const double *dinv, const int *rp_out, int *ci_out,
+                                                                  double *v_out) {
+    __shared__ unsigned keys[kShatWarps][kShatRowTuples];
+    __shared__ double terms[kShatWarps][kShatRowTuples];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int i = blockIdx.x * kShatWarps + w;
+    if (i >= N) return;
+    unsigned *sk = keys[w];
+    double *tv = terms[w];
+    const int n = shat_row_tuples(i, lane, drp, dci, crp, cci, cv, brp, bci, bv, dinv, sk, tv);
+    constexpr int P = kShatRowTuples / 32;   // positions per lane, contiguous
+    const int p0 = lane * P;
+    bool head[P];
+    int mine = 0;
+#pragma unroll
+    for (int u = 0; u < P; ++u) {
+        const int p = p0 + u;
+        head[u] = p < n && (p == 0 || (sk[p] >> 8) != (sk[p - 1] >> 8));
+        mine += head[u] ? 1 : 0;
+    }
+    int incl = mine;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    int slot = rp_out[i] + incl - mine;
+#pragma unroll
+    for (int u = 0; u < P; ++u) {
+        if (!head[u]) continue;
+        const int p = p0 + u;
+        const unsigned j = sk[p] >> 8;
+        const int e = find_entry(drp, dci, i, (int)j);
+        double sum = (e >= 0) ? dv[e] : 0.0;
+        for (int r = p; r < n && (sk[r] >> 8) == j; ++r) sum = __dsub_rn(sum, tv[sk[r] & 255u]);
+        ci_out[slot] = (int)j;
+        v_out[slot] = sum;
+        ++slot;
+    }
+}
+
+__global__ void k_max_ll(long long n, const long long *a, unsigned long long *out) {
+    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < n) atomicMax(out, (unsigned long long)a[q]);
+}
+
 void build_shat(const DMat &A, const DMat &B, const DMat &C, const DMat &D, const LowRank &lr, int N, DMat &S,
                 double *diagA_out, cudaStream_t s) {
     double *diag = diagA_out;
@@ -950,6 +1086,35 @@ void build_shat(const DMat &A, const DMat &B, const DMat &C, const DMat &D, cons
     long long *cnt = dmalloc<long long>(N + 1, s), *off = dmalloc<long long>(N + 1, s);
     k_shat_count<<<grid_exact(N), 256, 0, s>>>(N, D.rp, C.rp, C.ci, B.rp, cnt);
     NBP_LAUNCHED();
+    {   // every row within one warp's sort: the per-row build, no global sort
+        unsigned long long *mx = dmalloc<unsigned long long>(1, s);
+        NBP_CUDA(cudaMemsetAsync(mx, 0, sizeof(unsigned long long), s));
+        k_max_ll<<<grid_exact(N), 256, 0, s>>>(N, cnt, mx);
+        NBP_LAUNCHED();
+        const unsigned long long maxtup = readback(mx, s);
+        dfree(mx, s);
+        if (maxtup <= (unsigned long long)kShatRowTuples && N < (1 << 24)) {
+            dfree(cnt, s); dfree(off, s);
+            int *rowcnt = dmalloc<int>(N + 1, s);
+            const unsigned blocks = (unsigned)((N + kShatWarps - 1) / kShatWarps);
+            k_shat_row_count<<<blocks, 32 * kShatWarps, 0, s>>>(N, D.rp, D.ci, C.rp, C.ci, B.rp, B.ci, rowcnt);
+            NBP_LAUNCHED();
+            NBP_CUDA(cudaMemsetAsync(rowcnt + N, 0, sizeof(int), s));
+            dmat_free(S, s);
+            S.nbr = N; S.nbc = N; S.br = 1; S.bc = 1;
+            S.rp = dmalloc<int>(N + 1, s);
+            exclusive_scan(rowcnt, S.rp, N + 1, s);
+            dfree(rowcnt, s);
+            S.nnz = readback(S.rp + N, s);
+            S.ci = dmalloc<int>(S.nnz, s);
+            S.v = dmalloc<double>(S.nnz, s);
+            k_shat_row_fill<<<blocks, 32 * kShatWarps, 0, s>>>(N, D.rp, D.ci, D.v, C.rp, C.ci, C.v, B.rp, B.ci, B.v, dinv,
+                                                               S.rp, S.ci, S.v);
+            NBP_LAUNCHED();
+            dfree(dinv, s);
+            return;
+        }
+    }
     NBP_CUDA(cudaMemsetAsync(cnt + N, 0, sizeof(long long), s));
     exclusive_scan(cnt, off, N + 1, s);
     const long long ntup = readback(off + N, s);
