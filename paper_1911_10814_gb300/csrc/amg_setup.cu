@@ -623,9 +623,189 @@ static int match_pass(const Graph &G, double theta, int *map, cudaStream_t s) {
     return nc;
 }
 
+// ---- coarse rows one per warp: coarse row I gathers its members' entries
+// (members ascending, each row's entries in order: ascending fine entry
+// index q), maps their columns (dropping map < 0 and, for the graph, I
+// itself), sorts them in shared memory by (coarse column, q), and reduces
+// each coarse column's entries in order q -- the order of the global sort's
+// segments, so the results are the same bit for bit.  For coarse rows of at
+// most kGroupCap entries.
+constexpr int kGroupCap = 1024;
+constexpr int kGroupWarps = 4;   // warps per block (shared: 8 bytes per entry)
+
+// Entries of coarse row I into sk (key = J * kGroupCap + q, padded with ~0u
+// to the sort length L, the power of two >= 32 at or above the entry count)
+// and their fine entry index into se[q]; returns L, and the number of
+// entries kept (dropped ones sort last) in *kept.
+__device__ __forceinline__ int group_row_entries(int I, int lane, const int *mptr, const int *mem, const int *rp,
+                                                 const int *ci, const int *map, int drop_diag, unsigned *sk, int *se,
+                                                 int *kept) {
+    const int m0 = mptr[I], nm = mptr[I + 1] - m0;
+    int off = 0;
+    for (int a0 = 0; a0 < nm; a0 += 32) {   // members, a lane each; their entries at off + prefix
+        const int a = a0 + lane;
+        const int i = a < nm ? mem[m0 + a] : 0;
+        const int len = a < nm ? rp[i + 1] - rp[i] : 0;
+        int incl = len;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        const int start = off + incl - len;
+        for (int f = 0; f < len; ++f) {
+            const int e = rp[i] + f, q = start + f;
+            const int J = map[ci[e]];
+            const bool keep = J >= 0 && !(drop_diag && J == I);
+            sk[q] = keep ? (((unsigned)J * (unsigned)kGroupCap) | (unsigned)q) : ~0u;
+            se[q] = e;
+        }
+        off += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    int L = 32;
+    while (L < off) L <<= 1;
+    for (int q = off + lane; q < L; q += 32) sk[q] = ~0u;
+    __syncwarp();
+    for (int k = 2; k <= L; k <<= 1) {   // bitonic sort, ascending
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int p = lane; p < L; p += 32) {
+                const int x = p ^ j;
+                if (x > p) {
+                    const unsigned u = sk[p], w = sk[x];
+                    if ((u > w) == ((p & k) == 0)) { sk[p] = w; sk[x] = u; }
+                }
+            }
+            __syncwarp();
+        }
+    }
+    int c = 0;
+    for (int p = lane; p < off; p += 32) c += sk[p] != ~0u ? 1 : 0;
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    *kept = c;
+    return L;
+}
+
+__global__ void __launch_bounds__(32 * kGroupWarps) k_group_count(int nc, const int *mptr, const int *mem, const int *rp,
+                                                                 const int *ci, const int *map, int drop_diag, int *cnt) {
+    __shared__ unsigned keys[kGroupWarps][kGroupCap];
+    __shared__ int ents[kGroupWarps][kGroupCap];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int I = blockIdx.x * kGroupWarps + w;
+    if (I >= nc) return;
+    unsigned *sk = keys[w];
+    int n;
+    group_row_entries(I, lane, mptr, mem, rp, ci, map, drop_diag, sk, ents[w], &n);
+    int c = 0;
+    for (int p = lane; p < n; p += 32) c += (p == 0 || sk[p] / kGroupCap != sk[p - 1] / kGroupCap) ? 1 : 0;
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if (lane == 0) cnt[I] = c;
+}
+
+// MAX: the graph's edge weight, fmax over the coarse column's entries (one
+// value per entry); otherwise the Galerkin block, the sum of nb values per
+// entry in order q
+template <bool MAX>
+__global__ void __launch_bounds__(32 * kGroupWarps) k_group_fill(int nc, const int *mptr, const int *mem, const int *rp,
+                                                                const int *ci, const int *map, int drop_diag, int nb,
+                                                                const double *v, const int *rp_out, int *ci_out,
+                                                                double *v_out) {
+    __shared__ unsigned keys[kGroupWarps][kGroupCap];
+    __shared__ int ents[kGroupWarps][kGroupCap];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int I = blockIdx.x * kGroupWarps + w;
+    if (I >= nc) return;
+    unsigned *sk = keys[w];
+    const int *se = ents[w];
+    int n;
+    const int P = group_row_entries(I, lane, mptr, mem, rp, ci, map, drop_diag, sk, ents[w], &n) / 32;
+    const int p0 = lane * P;   // P contiguous positions per lane
+    int mine = 0;
+    for (int u = 0; u < P; ++u) {
+        const int p = p0 + u;
+        mine += (p < n && (p == 0 || sk[p] / kGroupCap != sk[p - 1] / kGroupCap)) ? 1 : 0;
+    }
+    int incl = mine;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int x = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += x;
+    }
+    long long slot = (long long)rp_out[I] + incl - mine;
+    for (int u = 0; u < P; ++u) {
+        const int p = p0 + u;
+        if (!(p < n && (p == 0 || sk[p] / kGroupCap != sk[p - 1] / kGroupCap))) continue;
+        const unsigned J = sk[p] / kGroupCap;
+        ci_out[slot] = (int)J;
+        if (MAX) {
+            double m = v[se[sk[p] % kGroupCap]];
+            for (int r = p + 1; r < n && sk[r] / kGroupCap == J; ++r) m = fmax(m, v[se[sk[r] % kGroupCap]]);
+            v_out[slot] = m;
+        } else {
+            double acc[9];
+            const double *src = v + (long long)se[sk[p] % kGroupCap] * nb;
+            for (int q = 0; q < nb; ++q) acc[q] = src[q];
+            for (int r = p + 1; r < n && sk[r] / kGroupCap == J; ++r) {
+                src = v + (long long)se[sk[r] % kGroupCap] * nb;
+                for (int q = 0; q < nb; ++q) acc[q] = __dadd_rn(acc[q], src[q]);
+            }
+            for (int q = 0; q < nb; ++q) v_out[slot * nb + q] = acc[q];
+        }
+        ++slot;
+    }
+}
+
+// entries of each coarse row before any drop (members' row lengths summed)
+__global__ void k_group_size(int nc, const int *mptr, const int *mem, const int *rp, unsigned long long *mx) {
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    if (I >= nc) return;
+    long long t = 0;
+    for (int a = mptr[I]; a < mptr[I + 1]; ++a) t += rp[mem[a] + 1] - rp[mem[a]];
+    atomicMax(mx, (unsigned long long)t);
+}
+
+// Coarse CSR (rp, ci, values) from the per-row grouping; false, with nothing
+// made, when a coarse row holds more than kGroupCap entries or the columns
+// would not fit the keys
+template <bool MAX>
+static bool group_rows_local(int nc, const int *mptr, const int *mem, const int *rp, const int *ci, const int *map,
+                             int drop_diag, int nb, const double *v, int *&rp_out, int *&ci_out, double *&v_out,
+                             long long &nnz_out, cudaStream_t s) {
+    if (nc <= 0 || (unsigned long long)nc * kGroupCap >= (1ULL << 32)) return false;
+    unsigned long long *mx = dmalloc<unsigned long long>(1, s);
+    NBP_CUDA(cudaMemsetAsync(mx, 0, sizeof(unsigned long long), s));
+    k_group_size<<<grid_exact(nc), 256, 0, s>>>(nc, mptr, mem, rp, mx);
+    NBP_LAUNCHED();
+    const unsigned long long most = readback(mx, s);
+    dfree(mx, s);
+    if (most > (unsigned long long)kGroupCap) return false;
+    const unsigned blocks = (unsigned)((nc + kGroupWarps - 1) / kGroupWarps);
+    int *cnt = dmalloc<int>(nc + 1, s);
+    k_group_count<<<blocks, 32 * kGroupWarps, 0, s>>>(nc, mptr, mem, rp, ci, map, drop_diag, cnt);
+    NBP_LAUNCHED();
+    NBP_CUDA(cudaMemsetAsync(cnt + nc, 0, sizeof(int), s));
+    rp_out = dmalloc<int>(nc + 1, s);
+    exclusive_scan(cnt, rp_out, nc + 1, s);
+    dfree(cnt, s);
+    nnz_out = readback(rp_out + nc, s);
+    ci_out = dmalloc<int>(nnz_out > 0 ? nnz_out : 1, s);
+    v_out = dmalloc<double>((nnz_out > 0 ? nnz_out : 1) * nb, s);
+    k_group_fill<MAX><<<blocks, 32 * kGroupWarps, 0, s>>>(nc, mptr, mem, rp, ci, map, drop_diag, nb, v, rp_out, ci_out,
+                                                          v_out);
+    NBP_LAUNCHED();
+    return true;
+}
+
+static void members_of(const int *map, int n, int nc, int *&mptr, int *&mem, cudaStream_t s);
+
 static Graph coarse_graph(const Graph &G, const int *map, int nc, cudaStream_t s) {
     Graph Gc;
     Gc.n = nc;
+    {
+        int *mptr = nullptr, *mem = nullptr;
+        members_of(map, G.n, nc, mptr, mem, s);
+        const bool local = group_rows_local<true>(nc, mptr, mem, G.rp, G.ci, map, 1, 1, G.w, Gc.rp, Gc.ci, Gc.w,
+                                                  Gc.nnz, s);
+        dfree(mptr, s); dfree(mem, s);
+        if (local) return Gc;
+    }
     Segments sg = group_by_coarse(G.n, G.nnz, G.rp, G.ci, map, nc, 1, s);
     Gc.nnz = sg.nseg;
     Gc.rp = rowptr_from_segments(sg, nc, s);
@@ -685,10 +865,16 @@ static int aggregate(const DMat &M, double theta, int *agg, cudaStream_t s) {
     return m;
 }
 
-static void galerkin(const DMat &M, const int *agg, int nc, DMat &Mc, cudaStream_t s) {
-    Segments sg = group_by_coarse(M.nbr, M.nnz, M.rp, M.ci, agg, nc, 0, s);
+// mptr/mem: the aggregates' member lists (ascending fine index)
+static void galerkin(const DMat &M, const int *agg, const int *mptr, const int *mem, int nc, DMat &Mc, cudaStream_t s) {
     Mc = DMat();
     Mc.nbr = nc; Mc.nbc = nc; Mc.br = M.br; Mc.bc = M.bc;
+    long long nnz = 0;
+    if (group_rows_local<false>(nc, mptr, mem, M.rp, M.ci, agg, 0, M.bb(), M.v, Mc.rp, Mc.ci, Mc.v, nnz, s)) {
+        Mc.nnz = nnz;
+        return;
+    }
+    Segments sg = group_by_coarse(M.nbr, M.nnz, M.rp, M.ci, agg, nc, 0, s);
     Mc.nnz = sg.nseg;
     Mc.rp = rowptr_from_segments(sg, nc, s);
     Mc.ci = dmalloc<int>(sg.nseg, s);
@@ -714,21 +900,25 @@ __global__ void k_member_count(int n, const int *agg, int *cnt) {
     if (agg[i] >= 0) atomicAdd(cnt + agg[i], 1);
 }
 
-static void member_lists(Level &L, int n, int nc, cudaStream_t s) {
+// members of coarse node I (map[i] == I) at mem[mptr[I] .. mptr[I+1]-1],
+// ascending; nodes with map < 0 trail
+static void members_of(const int *map, int n, int nc, int *&mptr, int *&mem, cudaStream_t s) {
     unsigned int *key = dmalloc<unsigned int>(n, s);
     int *val = dmalloc<int>(n, s);
-    k_member_keys<<<grid_exact(n), 256, 0, s>>>(n, L.agg, nc, key, val);
+    k_member_keys<<<grid_exact(n), 256, 0, s>>>(n, map, nc, key, val);
     NBP_LAUNCHED();
     sort_pairs(key, val, n, bits_for((unsigned long long)nc), s);
     int *cnt = dmalloc<int>(nc + 1, s);
     NBP_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * (nc + 1), s));
-    k_member_count<<<grid_exact(n), 256, 0, s>>>(n, L.agg, cnt);
+    k_member_count<<<grid_exact(n), 256, 0, s>>>(n, map, cnt);
     NBP_LAUNCHED();
-    L.mptr = dmalloc<int>(nc + 1, s);
-    exclusive_scan(cnt, L.mptr, nc + 1, s);
-    L.mem = val;   // members of aggregate I at mem[mptr[I] .. mptr[I+1]-1]; left-out nodes trail
+    mptr = dmalloc<int>(nc + 1, s);
+    exclusive_scan(cnt, mptr, nc + 1, s);
+    mem = val;
     dfree(cnt, s); dfree(key, s);
 }
+
+static void member_lists(Level &L, int n, int nc, cudaStream_t s) { members_of(L.agg, n, nc, L.mptr, L.mem, s); }
 
 static void dense_inverse(const DMat &M, double *&cinv, int &nc, cudaStream_t s) {
     const int n = M.nbr * M.br;
@@ -798,7 +988,7 @@ void amg_build(Hier &H, const DMat &fine, const nbp_options &o, int precision, c
                 if (nc >= n || nc == 0) { dfree(L.agg, s); L.agg = nullptr; break; }
                 member_lists(L, n, nc, s);
             }
-            galerkin(L.M, L.agg, nc, H.L[l + 1].M, s);
+            galerkin(L.M, L.agg, L.mptr, L.mem, nc, H.L[l + 1].M, s);
             ++l;
         }
     } catch (...) {
