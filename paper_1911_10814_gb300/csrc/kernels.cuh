@@ -518,6 +518,8 @@ __device__ __forceinline__ bool grid_last_block(unsigned *ticket) {
 // thread t adds partials b = t, t + blockDim, ... of up to 8 columns at a time
 // (all loads independent), then a warp tree and a fixed sum over the warps --
 // one order whatever the scheduling.
+// The FP32 kernels' partials are float-float pairs (float2 in the double
+// slots); those go through block_reduce_partials_ff.
 __device__ __forceinline__ void block_reduce_partials(const double *partial, int nb, int ncols, double *out) {
     __shared__ double red[8][32];
     const int warp = threadIdx.x >> 5, ln = threadIdx.x & 31, nw = blockDim.x >> 5;
@@ -543,6 +545,68 @@ __device__ __forceinline__ void block_reduce_partials(const double *partial, int
             out[c0 + threadIdx.x] = u;
         }
         __syncthreads();
+    }
+}
+
+// out[col] = sum_b of the float-float partials of column col: warp w takes
+// columns w, w + 8, ...; lane l adds partials b = l, l + 32, ... in ascending
+// order, then a fixed warp tree (one order whatever the scheduling).
+__device__ __forceinline__ void block_reduce_partials_ff(const double *partial, int nb, int ncols, double *out) {
+    const int warp = threadIdx.x >> 5, ln = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int col = warp; col < ncols; col += nw) {
+        const float2 *p = reinterpret_cast<const float2 *>(partial + (long long)col * nb);
+        FF a{0.f, 0.f};
+#pragma unroll 4
+        for (int b = ln; b < nb; b += 32) {
+            const float2 v = __ldcg(p + b);
+            a = ff_add(a, FF{v.x, v.y});
+        }
+        a = ff_warp_sum(a);
+        if (ln == 0) out[col] = ff_to_double(a);
+    }
+}
+// the last block's reduction of a T kernel's partials
+template <typename T> __device__ __forceinline__ void reduce_partials(const double *partial, int nb, int ncols, double *out) {
+    if constexpr (std::is_same<T, float>::value) block_reduce_partials_ff(partial, nb, ncols, out);
+    else block_reduce_partials(partial, nb, ncols, out);
+}
+
+// Block stage of the grid reductions: for q < nq, the sum of acc[q] over the
+// block's threads into partial[(col0 + q) * gridDim.x + blockIdx.x].  FP64
+// kernels: FP64 warp trees, then the warps' sums in order; FP32 kernels: the
+// same in float-float (the partial stored as a float2).  256 threads.
+template <typename T, int NQ>
+__device__ __forceinline__ void block_partials(const T (&acc)[NQ], int nq, double *partial, int col0) {
+    const int warp = threadIdx.x >> 5, ln = threadIdx.x & 31, nw = blockDim.x >> 5;
+    if constexpr (std::is_same<T, float>::value) {
+        __shared__ FF redf[NQ][8];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q)
+            if (q < nq) {   // uniform over the block
+                const FF v = ff_warp_sum(FF{acc[q], 0.f});
+                if (ln == 0) redf[q][warp] = v;
+            }
+        __syncthreads();
+        if ((int)threadIdx.x < nq) {
+            FF u = redf[threadIdx.x][0];
+            for (int k = 1; k < nw; ++k) u = ff_add(u, redf[threadIdx.x][k]);
+            *reinterpret_cast<float2 *>(partial + (long long)(col0 + threadIdx.x) * gridDim.x + blockIdx.x) =
+                make_float2(u.hi, u.lo);
+        }
+    } else {
+        __shared__ double redd[NQ][8];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q)
+            if (q < nq) {
+                const double v = warp_sum((double)acc[q]);
+                if (ln == 0) redd[q][warp] = v;
+            }
+        __syncthreads();
+        if ((int)threadIdx.x < nq) {
+            double u = 0.0;
+            for (int k = 0; k < nw; ++k) u += redd[threadIdx.x][k];
+            partial[(long long)(col0 + threadIdx.x) * gridDim.x + blockIdx.x] = u;
+        }
     }
 }
 
@@ -590,20 +654,12 @@ __global__ void __launch_bounds__(256) k_sell_dot(SpmvArgs a, DotArgs q) {
         p0 = acc0 * (q.da == a.y ? acc0 : ((const XT *)q.da)[row]);
         if (q.db) p1 = acc0 * ((const XT *)q.db)[row];
     }
-    __shared__ double red[2][8];
-    const int warp = threadIdx.x >> 5, ln = threadIdx.x & 31;
-    const double s0 = warp_sum((double)p0), s1 = warp_sum((double)p1);
-    if (ln == 0) { red[0][warp] = s0; red[1][warp] = s1; }
-    __syncthreads();
-    if (threadIdx.x < 2) {
-        double u = 0.0;
-        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) u += red[threadIdx.x][k];
-        q.part[(long long)threadIdx.x * gridDim.x + blockIdx.x] = u;
-    }
+    const AT pp[2] = {p0, p1};
+    block_partials<AT, 2>(pp, 2, q.part, 0);
     unsigned *ticket = (unsigned *)(q.kd + 7);
     if (!grid_last_block(ticket)) return;
     __shared__ double out[2];
-    block_reduce_partials(q.part, gridDim.x, q.db ? 2 : 1, out);
+    reduce_partials<AT>(q.part, gridDim.x, q.db ? 2 : 1, out);
     __syncthreads();
     if (threadIdx.x == 0) {
         q.kd[q.o0] = out[0];
@@ -671,11 +727,9 @@ __device__ __forceinline__ void mdot_body(const T *__restrict__ V, long long ldv
                                           long long n, double *__restrict__ partial, double *__restrict__ out,
                                           unsigned *ticket, const GivensArgs &gv) {
     constexpr int W = VEC ? Vec16<T>::W : 1;
-    __shared__ double red[CB][8];
     long long lo, hi;
     block_chunk(n, Vec16<T>::W, lo, hi);
     const long long nv = (hi - lo) / W;
-    const int warp = threadIdx.x >> 5, ln = threadIdx.x & 31;
     for (int c0 = 0; c0 < ncols; c0 += CB) {
         T acc[CB];
 #pragma unroll
@@ -707,23 +761,11 @@ __device__ __forceinline__ void mdot_body(const T *__restrict__ V, long long ldv
             for (int q = 0; q < CB; ++q)
                 if (c0 + q < ncols) acc[q] += V[(long long)(c0 + q) * ldv + t] * wt;
         }
-#pragma unroll
-        for (int q = 0; q < CB; ++q) {
-            if (c0 + q < ncols) {   // uniform over the block
-                const double v = warp_sum((double)acc[q]);
-                if (ln == 0) red[q][warp] = v;
-            }
-        }
-        __syncthreads();
-        if (threadIdx.x < CB && c0 + (int)threadIdx.x < ncols) {
-            double s = 0.0;
-            for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += red[threadIdx.x][k];
-            partial[(long long)(c0 + threadIdx.x) * gridDim.x + blockIdx.x] = s;
-        }
+        block_partials<T, CB>(acc, min(CB, ncols - c0), partial, c0);
         __syncthreads();
     }
     if (!grid_last_block(ticket)) return;
-    block_reduce_partials(partial, gridDim.x, ncols, out);
+    reduce_partials<T>(partial, gridDim.x, ncols, out);
     __syncthreads();
     if (threadIdx.x == 0) {
         if (gv.H) givens_step(gv, out[0]);
@@ -803,14 +845,12 @@ __device__ __forceinline__ void maxpy_dot_body(const T *__restrict__ V, long lon
                                                int norm_only, double *__restrict__ partial, double *__restrict__ out,
                                                unsigned *ticket, const GivensArgs &gv) {
     constexpr int W = VEC ? Vec16<T>::W : 1;
-    __shared__ double red[MAXC][8];
     __shared__ T cs[MAXC];
     if ((int)threadIdx.x < ncols) cs[threadIdx.x] = (T)coef[threadIdx.x];
     __syncthreads();
     long long lo, hi;
     block_chunk(n, Vec16<T>::W, lo, hi);
     const long long nv = (hi - lo) / W;
-    const int warp = threadIdx.x >> 5, ln = threadIdx.x & 31;
     T acc[MAXC];
 #pragma unroll
     for (int q = 0; q < MAXC; ++q) acc[q] = 0;
@@ -844,21 +884,9 @@ __device__ __forceinline__ void maxpy_dot_body(const T *__restrict__ V, long lon
     for (long long i = threadIdx.x; i < nv; i += blockDim.x) body(lo + i * W, std::integral_constant<int, W>());
     if (VEC && threadIdx.x < hi - lo - nv * W) body(lo + nv * W + threadIdx.x, std::integral_constant<int, 1>());
     const int nout = norm_only ? 1 : ncols;
-#pragma unroll
-    for (int q = 0; q < MAXC; ++q) {
-        if (q < nout) {
-            const double r = warp_sum((double)acc[q]);
-            if (ln == 0) red[q][warp] = r;
-        }
-    }
-    __syncthreads();
-    if ((int)threadIdx.x < nout) {
-        double u = 0.0;
-        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) u += red[threadIdx.x][k];
-        partial[(long long)threadIdx.x * gridDim.x + blockIdx.x] = u;
-    }
+    block_partials<T, MAXC>(acc, nout, partial, 0);
     if (!grid_last_block(ticket)) return;
-    block_reduce_partials(partial, gridDim.x, nout, out);
+    reduce_partials<T>(partial, gridDim.x, nout, out);
     __syncthreads();
     if (threadIdx.x == 0) {
         if (gv.H) givens_step(gv, out[0]);
@@ -1225,47 +1253,88 @@ __global__ void k_dense_gemv(const T *__restrict__ Cinv, int n, const T *__restr
 // (ticket in kd[7]) sums the block partials in a fixed order (one warp,
 // lanes over blocks): one launch, same result whatever order the blocks run in.
 constexpr int kKdotBlocks = 96;
+
+// The two sums p0, p1 of every thread reduced over the grid: per block into
+// kd[8 + 2 blk], kd[9 + 2 blk], then by warp 0 of the last block to finish
+// (ticket kd[7]; lanes over the blocks in steps of 32, a warp tree) into
+// kd[o0] and, when two, kd[o1].  FP64 for FP64 vectors; float-float (float2
+// in the slots) for FP32 ones.
+template <typename T>
+__device__ __forceinline__ void kdot_reduce(T p0, T p1, double *kd, int o0, int o1, bool two) {
+    __shared__ bool last;
+    if constexpr (std::is_same<T, float>::value) {
+        __shared__ FF s0[8], s1[8];
+        const FF t0 = ff_warp_sum(FF{p0, 0.f}), t1 = ff_warp_sum(FF{p1, 0.f});
+        if ((threadIdx.x & 31) == 0) { s0[threadIdx.x >> 5] = t0; s1[threadIdx.x >> 5] = t1; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            FF u0 = s0[0], u1 = s1[0];
+            for (int w = 1; w < (int)(blockDim.x >> 5); ++w) { u0 = ff_add(u0, s0[w]); u1 = ff_add(u1, s1[w]); }
+            *reinterpret_cast<float2 *>(kd + 8 + 2 * blockIdx.x) = make_float2(u0.hi, u0.lo);
+            *reinterpret_cast<float2 *>(kd + 9 + 2 * blockIdx.x) = make_float2(u1.hi, u1.lo);
+            __threadfence();
+            last = (atomicAdd((unsigned int *)(kd + 7), 1u) == gridDim.x - 1);
+        }
+        __syncthreads();
+        if (last && threadIdx.x < 32) {
+            __threadfence();
+            FF u0{0.f, 0.f}, u1{0.f, 0.f};
+            for (unsigned qb = threadIdx.x; qb < gridDim.x; qb += 32) {
+                const float2 a0 = __ldcg(reinterpret_cast<const float2 *>(kd + 8 + 2 * qb));
+                const float2 a1 = __ldcg(reinterpret_cast<const float2 *>(kd + 9 + 2 * qb));
+                u0 = ff_add(u0, FF{a0.x, a0.y});
+                u1 = ff_add(u1, FF{a1.x, a1.y});
+            }
+            u0 = ff_warp_sum(u0);
+            u1 = ff_warp_sum(u1);
+            if (threadIdx.x == 0) {
+                kd[o0] = ff_to_double(u0);
+                if (two) kd[o1] = ff_to_double(u1);
+                *(unsigned int *)(kd + 7) = 0u;   // ready for the next call
+            }
+        }
+    } else {
+        __shared__ double s0[8], s1[8];
+        const double t0 = warp_sum((double)p0), t1 = warp_sum((double)p1);
+        if ((threadIdx.x & 31) == 0) { s0[threadIdx.x >> 5] = t0; s1[threadIdx.x >> 5] = t1; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double u0 = 0.0, u1 = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { u0 += s0[w]; u1 += s1[w]; }
+            kd[8 + 2 * blockIdx.x] = u0;
+            kd[9 + 2 * blockIdx.x] = u1;
+            __threadfence();
+            last = (atomicAdd((unsigned int *)(kd + 7), 1u) == gridDim.x - 1);
+        }
+        __syncthreads();
+        if (last && threadIdx.x < 32) {
+            __threadfence();
+            double u0 = 0.0, u1 = 0.0;
+            for (unsigned qb = threadIdx.x; qb < gridDim.x; qb += 32) {
+                u0 += __ldcg(kd + 8 + 2 * qb);
+                u1 += __ldcg(kd + 9 + 2 * qb);
+            }
+            u0 = warp_sum(u0);
+            u1 = warp_sum(u1);
+            if (threadIdx.x == 0) {
+                kd[o0] = u0;
+                if (two) kd[o1] = u1;
+                *(unsigned int *)(kd + 7) = 0u;
+            }
+        }
+    }
+}
 template <typename T>
 __global__ void __launch_bounds__(256) k_kdots(const T *__restrict__ a, const T *__restrict__ b, const T *__restrict__ c,
                                                const T *__restrict__ d, long long n, double *kd, int o0, int o1) {
-    __shared__ double s0[8], s1[8];
-    __shared__ bool last;
     const long long chunk = (n + gridDim.x - 1) / gridDim.x;
     const long long lo = (long long)blockIdx.x * chunk, hi = min(n, lo + chunk);
-    T p0 = 0, p1 = 0;   // per-thread sums in the vector type; FP64 from the warp level up
+    T p0 = 0, p1 = 0;   // per-thread sums in the vector type
     for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
         p0 += a[i] * b[i];
         if (c) p1 += c[i] * d[i];
     }
-    double t0 = warp_sum((double)p0);
-    double t1 = warp_sum((double)p1);
-    if ((threadIdx.x & 31) == 0) { s0[threadIdx.x >> 5] = t0; s1[threadIdx.x >> 5] = t1; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double u0 = 0.0, u1 = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { u0 += s0[w]; u1 += s1[w]; }
-        kd[8 + 2 * blockIdx.x] = u0;
-        kd[9 + 2 * blockIdx.x] = u1;
-        __threadfence();
-        unsigned int *ticket = (unsigned int *)(kd + 7);
-        last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
-    }
-    __syncthreads();
-    if (last && threadIdx.x < 32) {   // warp 0: lanes over blocks (stride 32), then a warp tree
-        __threadfence();
-        double u0 = 0.0, u1 = 0.0;
-        for (unsigned q = threadIdx.x; q < gridDim.x; q += 32) {
-            u0 += __ldcg(kd + 8 + 2 * q);
-            u1 += __ldcg(kd + 9 + 2 * q);
-        }
-        u0 = warp_sum(u0);
-        u1 = warp_sum(u1);
-        if (threadIdx.x == 0) {
-            kd[o0] = u0;
-            if (c) kd[o1] = u1;
-            *(unsigned int *)(kd + 7) = 0u;   // ready for the next call
-        }
-    }
+    kdot_reduce<T>(p0, p1, kd, o0, o1, c != nullptr);
 }
 // r -= a1 w1 with a1 = (w1.r)/(w1.w1) = kd[1]/kd[0]; a1 saved in kd[2]
 template <typename T> __global__ void k_kupd1(T *r, const T *w1, double *kd, long long n) {
@@ -1288,8 +1357,6 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_kupd2_dots(T *__restrict__ w2, T *__restrict__ z2, const T *__restrict__ w1,
                                                     const T *__restrict__ z1, const T *__restrict__ r, double *kd,
                                                     long long n) {
-    __shared__ double s0[8], s1[8];
-    __shared__ bool last;
     __shared__ T bs_;
     if (threadIdx.x == 0) bs_ = (T)(kd[0] > 0.0 ? kd[3] / kd[0] : 0.0);
     __syncthreads();
@@ -1304,34 +1371,7 @@ __global__ void __launch_bounds__(256) k_kupd2_dots(T *__restrict__ w2, T *__res
         p0 += wn * wn;
         p1 += wn * r[i];
     }
-    double t0 = warp_sum((double)p0);
-    double t1 = warp_sum((double)p1);
-    if ((threadIdx.x & 31) == 0) { s0[threadIdx.x >> 5] = t0; s1[threadIdx.x >> 5] = t1; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double u0 = 0.0, u1 = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { u0 += s0[w]; u1 += s1[w]; }
-        kd[8 + 2 * blockIdx.x] = u0;
-        kd[9 + 2 * blockIdx.x] = u1;
-        __threadfence();
-        last = (atomicAdd((unsigned int *)(kd + 7), 1u) == gridDim.x - 1);
-    }
-    __syncthreads();
-    if (last && threadIdx.x < 32) {
-        __threadfence();
-        double u0 = 0.0, u1 = 0.0;
-        for (unsigned qb = threadIdx.x; qb < gridDim.x; qb += 32) {
-            u0 += __ldcg(kd + 8 + 2 * qb);
-            u1 += __ldcg(kd + 9 + 2 * qb);
-        }
-        u0 = warp_sum(u0);
-        u1 = warp_sum(u1);
-        if (threadIdx.x == 0) {
-            kd[4] = u0;
-            kd[5] = u1;
-            *(unsigned int *)(kd + 7) = 0u;
-        }
-    }
+    kdot_reduce<T>(p0, p1, kd, 4, 5, true);
 }
 // x = a1 z1 + a2 z2 with a2 = (w2.r)/(w2.w2) = kd[5]/kd[4]
 template <typename T> __global__ void k_kupd3(T *x, const T *z1, const T *z2, const double *kd, long long n) {

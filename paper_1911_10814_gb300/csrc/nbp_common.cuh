@@ -69,6 +69,37 @@ template <typename T> __device__ __forceinline__ T warp_sum(T v, unsigned mask =
     return v;
 }
 
+// Float-float sums (the unevaluated sum hi + lo of two floats, about 44
+// significant bits) for the reductions of the FP32 kernels.  The FP64 pipe of
+// this GPU retires only a few operations per clock and SM, so a tree of FP64
+// adds in every block's tail costs microseconds per block; these run on the
+// FP32 pipe.  ff_add is Knuth's error-free two-sum of the leading parts, the
+// trailing parts added to its error, then Dekker's fast two-sum to
+// renormalise; all adds are explicitly rounded (no reassociation).
+struct FF {
+    float hi, lo;
+};
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+    const float s = __fadd_rn(a.hi, b.hi);
+    const float v = __fsub_rn(s, a.hi);
+    float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, v)), __fsub_rn(b.hi, v));
+    e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+    const float h = __fadd_rn(s, e);
+    return FF{h, __fsub_rn(e, __fsub_rn(h, s))};
+}
+// the warp's sum in a fixed xor tree; lane 0's value is the one used
+__device__ __forceinline__ FF ff_warp_sum(FF a) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        FF b;
+        b.hi = __shfl_xor_sync(0xffffffffu, a.hi, o);
+        b.lo = __shfl_xor_sync(0xffffffffu, a.lo, o);
+        a = ff_add(a, b);
+    }
+    return a;
+}
+__device__ __forceinline__ double ff_to_double(FF a) { return (double)a.hi + (double)a.lo; }
+
 // ------------------------------------------------------- device structures
 // Block CSR matrix with br x bc row-major blocks (nbr block rows).
 struct DMat {
