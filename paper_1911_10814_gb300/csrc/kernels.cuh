@@ -1181,6 +1181,39 @@ __global__ void k_prolong(const int *__restrict__ agg, int n, int bs, const T *_
     const int I = agg[i];
     if (I >= 0) x[t] += ec[(long long)I * bs + a];
 }
+// The same for blocks of BS components with W = Vec16<T>::W consecutive
+// nodes per thread: their map entries and BS 16-byte pieces of x loaded at
+// once (the one-component form keeps a single load chain per thread), the
+// same per-element adds; the last n % W nodes one per thread.  x and agg
+// 16-byte aligned.
+template <typename T, int BS>
+__global__ void k_prolong_v(const int *__restrict__ agg, int n, const T *__restrict__ ec, T *__restrict__ x) {
+    constexpr int W = Vec16<T>::W;
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long ng = n / W;
+    if (g < ng) {
+        int I[W];
+#pragma unroll
+        for (int e = 0; e < W; ++e) I[e] = agg[g * W + e];
+        T v[BS][W];
+#pragma unroll
+        for (int c = 0; c < BS; ++c) vld(x + (g * BS + c) * W, v[c]);
+#pragma unroll
+        for (int k = 0; k < BS * W; ++k) {   // element k: node k / BS, component k % BS
+            const int Ik = I[k / BS];
+            if (Ik >= 0) v[k / W][k % W] += ec[(long long)Ik * BS + k % BS];
+        }
+#pragma unroll
+        for (int c = 0; c < BS; ++c) vst(x + (g * BS + c) * W, v[c]);
+    } else if (g < ng + n % W) {
+        const long long i = ng * W + (g - ng);
+        const int Ii = agg[i];
+        if (Ii >= 0) {
+#pragma unroll
+            for (int a = 0; a < BS; ++a) x[i * BS + a] += ec[(long long)Ii * BS + a];
+        }
+    }
+}
 // Chebyshev first step from x = 0: d = c2 Dinv b; x = d
 // (bcopy != nullptr: b is also copied there, for a cycle replayed on fixed buffers)
 template <typename T>

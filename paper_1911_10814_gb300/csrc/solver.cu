@@ -764,7 +764,16 @@ static void vcycle_level(nbp_ctx *c, Hier &H, int l, int vsel, const T *b, T *ou
     else vcycle_level<T>(c, H, l + 1, vsel, bc, xc, fuse);
     // prolongation bytes: the aggregate map, the coarse correction, x read and written
     const double pbytes = (double)L.M.nbr * 4.0 + ncv + 2.0 * n * sizeof(T);
-    timed(c, "amg/prolong", pbytes, [&] { k_prolong<T><<<grid_exact(n), 256, 0, c->s>>>(L.agg, L.M.nbr, bs, xc, cur); });
+    timed(c, "amg/prolong", pbytes, [&] {
+        constexpr int W = Vec16<T>::W;
+        const long long threads = L.M.nbr / W + L.M.nbr % W;
+        if ((bs == 3 || bs == 1) && al16(cur) && al16(L.agg)) {
+            if (bs == 3) k_prolong_v<T, 3><<<grid_exact(threads), 256, 0, c->s>>>(L.agg, L.M.nbr, xc, cur);
+            else k_prolong_v<T, 1><<<grid_exact(threads), 256, 0, c->s>>>(L.agg, L.M.nbr, xc, cur);
+        } else {
+            k_prolong<T><<<grid_exact(n), 256, 0, c->s>>>(L.agg, L.M.nbr, bs, xc, cur);
+        }
+    });
     T *fin = chebyshev<T>(c, L, vsel, k, b, cur, oth, false);
     if (fin != out) copy<T>(out, fin, n, c->s);
 }
