@@ -1280,6 +1280,41 @@ __global__ void k_dense_gemv(const T *__restrict__ Cinv, int n, const T *__restr
     if (ln == 0) x[row] = t;
 }
 
+// The FP32 form with a block of kGemvThreads threads (four warps) per row:
+// each thread keeps four partial sums over the 16-byte pieces t, t + 128, ...
+// of the row, then a fixed warp tree per warp and the four warps' sums in
+// order.  A row of the 1344-wide coarsest inverse is 336 pieces, about three
+// per thread, so a row's loads are in flight together instead of ten deep in
+// one warp.  Rows on 16-byte boundaries (n % 4 == 0, Cinv and b aligned).
+constexpr int kGemvThreads = 128;
+template <typename T>   // float
+__global__ void __launch_bounds__(kGemvThreads) k_dense_gemv_rows(const T *__restrict__ Cinv, int n,
+                                                                  const T *__restrict__ b, T *__restrict__ x) {
+    static_assert(std::is_same<T, float>::value, "FP32 form");
+    __shared__ float ws[kGemvThreads / 32];
+    const int row = blockIdx.x;
+    const float *r = Cinv + (long long)row * n;
+    const int nv = n / 4;
+    float s[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int c = threadIdx.x; c < nv; c += kGemvThreads) {
+        float a[4], v[4];
+        vld(r + (long long)c * 4, a);
+        vld(b + (long long)c * 4, v);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) s[e] += a[e] * v[e];
+    }
+    float t = (s[0] + s[1]) + (s[2] + s[3]);
+    t = warp_sum(t);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float u = ws[0];
+#pragma unroll
+        for (int w = 1; w < kGemvThreads / 32; ++w) u += ws[w];
+        x[row] = u;
+    }
+}
+
 // ============================================================== K-cycle
 // kd[o0] = a.b and, when c != nullptr, kd[o1] = c.d.  Each block reduces a
 // fixed contiguous chunk into kd[8 + 2 blk], and the last block to finish
