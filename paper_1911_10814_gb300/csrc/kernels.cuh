@@ -1283,9 +1283,9 @@ __global__ void k_dense_gemv(const T *__restrict__ Cinv, int n, const T *__restr
 // The FP32 form with a block of kGemvThreads threads (four warps) per row:
 // each thread keeps four partial sums over the 16-byte pieces t, t + 128, ...
 // of the row, then a fixed warp tree per warp and the four warps' sums in
-// order.  A row of the 1344-wide coarsest inverse is 336 pieces, about three
-// per thread, so a row's loads are in flight together instead of ten deep in
-// one warp.  Rows on 16-byte boundaries (n % 4 == 0, Cinv and b aligned).
+// order.  A row of a coarsest inverse about 1300 wide is about 330 pieces,
+// three per thread, so a row's loads are in flight together instead of ten
+// deep in one warp.  Rows on 16-byte boundaries (n % 4 == 0, Cinv and b aligned).
 constexpr int kGemvThreads = 128;
 template <typename T>   // float
 __global__ void __launch_bounds__(kGemvThreads) k_dense_gemv_rows(const T *__restrict__ Cinv, int n,

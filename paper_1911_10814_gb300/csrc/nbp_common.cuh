@@ -70,10 +70,10 @@ template <typename T> __device__ __forceinline__ T warp_sum(T v, unsigned mask =
 }
 
 // Float-float sums (the unevaluated sum hi + lo of two floats, about 44
-// significant bits) for the reductions of the FP32 kernels.  The FP64 pipe of
-// this GPU retires only a few operations per clock and SM, so a tree of FP64
-// adds in every block's tail costs microseconds per block; these run on the
-// FP32 pipe.  ff_add is Knuth's error-free two-sum of the leading parts, the
+// significant bits) for the reductions of the FP32 kernels.  GB300's FP64
+// pipe retires about two operations per clock and SM (1.25 TFLOP/s for the
+// GPU), so a tree of FP64 adds in every block's tail costs microseconds per
+// block; these run on the FP32 pipe.  ff_add is Knuth's error-free two-sum of the leading parts, the
 // trailing parts added to its error, then Dekker's fast two-sum to
 // renormalise; all adds are explicitly rounded (no reassociation).
 struct FF {
