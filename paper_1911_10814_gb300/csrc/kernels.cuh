@@ -84,11 +84,14 @@ __global__ void __launch_bounds__(256) k_bspmv(SpmvArgs a) {
     const long long idx = (long long)row * BR + lane;
     XT *y = (XT *)a.y;
     if (EPI == EPI_SET) {
-        if (LR) {
-            double t = 0.0;
-            for (int q = a.lr_rp[row]; q < a.lr_rp[row + 1]; ++q)
-                if (a.lr_c[q] == lane) t += a.lr_f[a.lr_k[q]] * a.lr_val[q];
-            s = (AT)((double)s + t);
+        if (LR) {   // FP64 only on the rows that carry rank-one entries
+            const int e0 = a.lr_rp[row], e1 = a.lr_rp[row + 1];
+            if (e1 > e0) {
+                double t = 0.0;
+                for (int q = e0; q < e1; ++q)
+                    if (a.lr_c[q] == lane) t += a.lr_f[a.lr_k[q]] * a.lr_val[q];
+                s = (AT)((double)s + t);
+            }
         }
         y[idx] = s;
     } else if (EPI == EPI_ADD) {
@@ -286,6 +289,8 @@ __global__ void __launch_bounds__(256) k_sell(SpmvArgs a) {
     if (row >= a.nbr) return;
     AT accs[3] = {acc0, acc1, acc2};
     XT *y = (XT *)a.y;
+    const bool lr = LR && EPI == EPI_SET;
+    const int lr0 = lr ? a.lr_rp[row] : 0, lr1 = lr ? a.lr_rp[row + 1] : 0;
     if (EPI == EPI_CHEB) {
         const XT *b = (const XT *)a.b;
         const XT *dinv = (const XT *)a.dinv + (long long)row * BB;
@@ -312,9 +317,12 @@ __global__ void __launch_bounds__(256) k_sell(SpmvArgs a) {
         const long long idx = (long long)row * BS + q;
         AT s = accs[q];
         if (EPI == EPI_SET) {
-            if (LR) {
+            // the rank-one term in FP64, only on the rows that carry its
+            // entries (outlet rows): GB300's FP64 pipe would otherwise hold
+            // every warp for the conversions of every row
+            if (lr && lr1 > lr0) {
                 double tt = 0.0;
-                for (int e = a.lr_rp[row]; e < a.lr_rp[row + 1]; ++e)
+                for (int e = lr0; e < lr1; ++e)
                     if (a.lr_c[e] == q) tt += a.lr_f[a.lr_k[e]] * a.lr_val[e];
                 s = (AT)((double)s + tt);
             }
