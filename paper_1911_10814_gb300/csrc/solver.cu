@@ -402,7 +402,8 @@ template <typename T> static void scale_inv(nbp_ctx *c, T *v, const T *w, const 
 
 // Autotuner of the Gram-Schmidt kernels' grids for one vector length: the
 // candidates (one wave, a half and a quarter of it, a quarter block per SM,
-// and just enough blocks for eight 16-byte pieces per thread) are timed on a
+// just enough blocks for eight 16-byte pieces per thread, and kReduceBlocks
+// and half of it, capped at a block per 256 pieces) are timed on a
 // four-column step in the space's own buffers, as the solve meets it: the
 // multi-dot after a write of a buffer larger than L2 (between two steps the
 // preconditioner's sweeps evict the basis), then the subtract + products and
@@ -430,8 +431,14 @@ template <typename T> static void tune_arnoldi(nbp_ctx *c, Krylov<T> &K) {
                         : std::min({ag.mdot_s, ag.mdot_dl_s, ag.mpd_dl_s, w4s});
     gmax = std::max(1u, std::min(gmax, (unsigned)kReduceBlocks));
     const long long pieces = (K.n + Vec16<T>::W - 1) / Vec16<T>::W;
+    // also grids of several waves of the lowest-occupancy kernel, up to the
+    // partial buffers' kReduceBlocks: any grid sums correctly (fixed chunks,
+    // last-block reduction), and a long vector streams faster with more
+    // blocks than one wave of the widest kernel holds
+    const unsigned gbig = (unsigned)std::min<long long>(kReduceBlocks, std::max<long long>(1, pieces / 256));
     std::vector<unsigned> cands = {gmax, gmax / 2, gmax / 4, (unsigned)kSMs / 4,
-                                   (unsigned)std::min<long long>(gmax, (pieces + 8 * 256 - 1) / (8 * 256))};
+                                   (unsigned)std::min<long long>(gmax, (pieces + 8 * 256 - 1) / (8 * 256)),
+                                   gbig, gbig / 2};
     std::sort(cands.begin(), cands.end());
     cands.erase(std::unique(cands.begin(), cands.end()), cands.end());
     constexpr size_t kFlush = 256ull << 20;   // twice the L2
