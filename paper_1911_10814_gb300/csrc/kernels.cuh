@@ -1293,23 +1293,34 @@ __global__ void k_dense_gemv(const T *__restrict__ Cinv, int n, const T *__restr
 // of the row, then a fixed warp tree per warp and the four warps' sums in
 // order.  A row of a coarsest inverse about 1300 wide is about 330 pieces,
 // three per thread, so a row's loads are in flight together instead of ten
-// deep in one warp.  Rows on 16-byte boundaries (n % 4 == 0, Cinv and b aligned).
+// deep in one warp.  VEC: rows on 16-byte boundaries (n % 4 == 0, Cinv and b
+// aligned); otherwise single floats c = t, t + 128, ... into the four sums in
+// turn.
 constexpr int kGemvThreads = 128;
-template <typename T>   // float
+template <typename T, bool VEC>   // float
 __global__ void __launch_bounds__(kGemvThreads) k_dense_gemv_rows(const T *__restrict__ Cinv, int n,
                                                                   const T *__restrict__ b, T *__restrict__ x) {
     static_assert(std::is_same<T, float>::value, "FP32 form");
     __shared__ float ws[kGemvThreads / 32];
     const int row = blockIdx.x;
     const float *r = Cinv + (long long)row * n;
-    const int nv = n / 4;
     float s[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int c = threadIdx.x; c < nv; c += kGemvThreads) {
-        float a[4], v[4];
-        vld(r + (long long)c * 4, a);
-        vld(b + (long long)c * 4, v);
+    if constexpr (VEC) {
+        const int nv = n / 4;
+        for (int c = threadIdx.x; c < nv; c += kGemvThreads) {
+            float a[4], v[4];
+            vld(r + (long long)c * 4, a);
+            vld(b + (long long)c * 4, v);
 #pragma unroll
-        for (int e = 0; e < 4; ++e) s[e] += a[e] * v[e];
+            for (int e = 0; e < 4; ++e) s[e] += a[e] * v[e];
+        }
+    } else {
+        int c = threadIdx.x;
+        for (; c + 3 * kGemvThreads < n; c += 4 * kGemvThreads) {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) s[e] += r[c + e * kGemvThreads] * b[c + e * kGemvThreads];
+        }
+        for (int e = 0; c < n; c += kGemvThreads, ++e) s[e] += r[c] * b[c];
     }
     float t = (s[0] + s[1]) + (s[2] + s[3]);
     t = warp_sum(t);

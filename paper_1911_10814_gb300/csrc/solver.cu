@@ -726,12 +726,13 @@ static void vcycle_level(nbp_ctx *c, Hier &H, int l, int vsel, const T *b, T *ou
                   [&] {
                       const T *ci = cinv_of<T>(H);
                       if constexpr (std::is_same<T, float>::value) {
-                          if (H.nc % 4 == 0 && al16(ci) && al16(b)) {
-                              k_dense_gemv_rows<float><<<(unsigned)H.nc, kGemvThreads, 0, c->s>>>(ci, H.nc, b, out);
-                              return;
-                          }
+                          if (H.nc % 4 == 0 && al16(ci) && al16(b))
+                              k_dense_gemv_rows<float, true><<<(unsigned)H.nc, kGemvThreads, 0, c->s>>>(ci, H.nc, b, out);
+                          else
+                              k_dense_gemv_rows<float, false><<<(unsigned)H.nc, kGemvThreads, 0, c->s>>>(ci, H.nc, b, out);
+                      } else {
+                          k_dense_gemv<T><<<grid_exact((long long)H.nc * 32), 256, 0, c->s>>>(ci, H.nc, b, out);
                       }
-                      k_dense_gemv<T><<<grid_exact((long long)H.nc * 32), 256, 0, c->s>>>(ci, H.nc, b, out);
                   });
         } else {
             T *res = chebyshev<T>(c, L, vsel, std::max(k, 1), b, out, wvec<T>(L, 2), true);  // coarsest: smoothing only
